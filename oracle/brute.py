@@ -1,0 +1,120 @@
+"""Dense-matrix NumPy formulation of the operators and RHS, for tiny grids.
+
+Test infrastructure only.  This is a second, independent writing of the same
+definitions as ``ac_oracle.c``: every derivative operator is an explicit
+N x N matrix (N = nx ny nz) built from periodic shift matrices with Kronecker
+products (x fastest, so the x factor is the last one), and the RHS of
+Eqs. B.1-B.4 is assembled from whole-grid vectors.  It shares no code with the
+C oracle; the two are compared on grids of 8^3 cells or fewer.
+"""
+import numpy as np
+
+NF = 8
+
+
+def _shift(n, m):
+    """n x n periodic shift: (T f)_i = f_{(i + m) mod n}."""
+    T = np.zeros((n, n))
+    for i in range(n):
+        T[i, (i + m) % n] = 1.0
+    return T
+
+
+def _axis_op(n3, a, M1):
+    """Embed a 1-D operator M1 acting along axis a (0 = x) into the 3-D grid."""
+    nx, ny, nz = n3
+    Ix, Iy, Iz = np.eye(nx), np.eye(ny), np.eye(nz)
+    fac = [Ix, Iy, Iz]
+    fac[a] = M1
+    # vector index = (k * ny + j) * nx + i  ->  kron(Z, kron(Y, X))
+    return np.kron(fac[2], np.kron(fac[1], fac[0]))
+
+
+class Operators:
+    """Sixth-order derivative matrices on an (nx, ny, nz) periodic grid."""
+
+    def __init__(self, n3, dx3):
+        self.n3 = tuple(n3)
+        self.dx = tuple(dx3)
+        T = {}
+        for a in range(3):
+            for m in range(-3, 4):
+                T[a, m] = _axis_op(self.n3, a, _shift(self.n3[a], m))
+        self.T = T
+        c1 = {1: 45.0, 2: -9.0, 3: 1.0}
+        self.D1 = []
+        for a in range(3):
+            M = sum(c1[m] * (T[a, m] - T[a, -m]) for m in (1, 2, 3))
+            self.D1.append(M / (60.0 * self.dx[a]))
+        c2 = {1: 1.5, 2: -0.15, 3: 1.0 / 90.0}
+        N = T[0, 0].shape[0]
+        self.D2 = {}
+        for a in range(3):
+            M = -49.0 / 18.0 * np.eye(N) + sum(c2[m] * (T[a, m] + T[a, -m]) for m in (1, 2, 3))
+            self.D2[a, a] = M / self.dx[a] ** 2
+        cx = {1: 270.0, 2: -27.0, 3: 2.0}
+        for a in range(3):
+            for b in range(3):
+                if a == b:
+                    continue
+                M = np.zeros((N, N))
+                for m in (1, 2, 3):
+                    S = (T[a, m] @ T[b, m] + T[a, -m] @ T[b, -m]
+                         - T[a, m] @ T[b, -m] - T[a, -m] @ T[b, m])
+                    M += cx[m] * S
+                self.D2[a, b] = M / (720.0 * self.dx[a] * self.dx[b])
+
+
+def rhs(f, p, ops=None):
+    """RHS of Eqs. B.1-B.4 with whole-grid vectors; f: (8, nz, ny, nx)."""
+    if ops is None:
+        ops = Operators(p.n, p.dx)
+    shape = f.shape[1:]
+    v = [f[q].ravel() for q in range(NF)]
+    lnrho, s = v[0], v[4]
+    u = v[1:4]
+    A = v[5:8]
+    g = [[ops.D1[a] @ v[q] for a in range(3)] for q in range(NF)]
+    Hu = [[[ops.D2[a, b] @ u[m] for b in range(3)] for a in range(3)] for m in range(3)]
+    Ha = [[[ops.D2[a, b] @ A[m] for b in range(3)] for a in range(3)] for m in range(3)]
+    rho = np.exp(lnrho)
+    cs2 = p.cs0 ** 2 * np.exp(p.gamma * s / p.cp + (p.gamma - 1.0) * (lnrho - p.lnrho0))
+    T = cs2 / (p.cp * (p.gamma - 1.0))
+    divu = g[1][0] + g[2][1] + g[3][2]
+    lapu = [Hu[m][0][0] + Hu[m][1][1] + Hu[m][2][2] for m in range(3)]
+    lapa = [Ha[m][0][0] + Ha[m][1][1] + Ha[m][2][2] for m in range(3)]
+    gdu = [Hu[0][m][0] + Hu[1][m][1] + Hu[2][m][2] for m in range(3)]
+    gda = [Ha[0][m][0] + Ha[1][m][1] + Ha[2][m][2] for m in range(3)]
+    gA = g[5:8]
+    B = np.array([gA[2][1] - gA[1][2], gA[0][2] - gA[2][0], gA[1][0] - gA[0][1]])
+    J = np.array([gda[m] - lapa[m] for m in range(3)])
+    U = np.array(u)
+    gu = [g[1 + m] for m in range(3)]
+    S = [[0.5 * (gu[m][n] + gu[n][m]) - (divu / 3.0 if m == n else 0.0) for n in range(3)]
+         for m in range(3)]
+    SS2 = sum(S[m][n] ** 2 for m in range(3) for n in range(3))
+    JxB = np.cross(J, B, axis=0)
+    UxB = np.cross(U, B, axis=0)
+    J2 = (J ** 2).sum(axis=0)
+
+    def adv(q):
+        return U[0] * g[q][0] + U[1] * g[q][1] + U[2] * g[q][2]
+
+    out = np.empty((NF, v[0].size))
+    out[0] = -adv(0) - divu
+    force = np.zeros((3, v[0].size))
+    if p.forcing is not None:
+        nx, ny, nz = p.n
+        kk, jj, ii = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+        ph = p.forcing.phi + 2 * np.pi * (p.forcing.k[0] * ii / nx + p.forcing.k[1] * jj / ny
+                                          + p.forcing.k[2] * kk / nz)
+        for a in range(3):
+            force[a] = (p.forcing.amp * p.forcing.e[a] * np.cos(ph)).ravel()
+    for m in range(3):
+        sgl = S[m][0] * g[0][0] + S[m][1] * g[0][1] + S[m][2] * g[0][2]
+        out[1 + m] = (-adv(1 + m) - cs2 * (g[4][m] / p.cp + g[0][m]) + JxB[m] / rho
+                      + p.nu * (lapu[m] + gdu[m] / 3.0 + 2.0 * sgl) + force[m])
+    out[4] = -adv(4) + (p.eta * J2 + 2.0 * rho * p.nu * SS2) / (rho * T)
+    for m in range(3):
+        out[5 + m] = UxB[m] + p.eta * lapa[m]
+    return out.reshape((NF,) + shape)
