@@ -1,0 +1,389 @@
+#!/usr/bin/env python
+"""Throughput of the fused RK3 MHD substep on GB300, in Gcell-updates/s per substep.
+
+A step is one pass of the whole hot path over the synthetic state: the
+forcing draw and its phase tables, the three fused RHS + Runge-Kutta substeps
+(sixth-order stencils with the periodic map applied on load) and the binary64
+CFL-speed reduction.  Default workload: 256^3 periodic, FP64, forced at
+|k| = 2-3 with a seeded phase each step, noise of amplitude 1e-5 on u and A,
+nu = eta = 5e-3, c_s = 1, gamma = 5/3, dt = 1e-3.
+
+Prints one JSON line.  ``--impl reference`` times the FP64 CPU oracle on the
+host cores instead (a bounded sample of the same workload per step).
+Multi-GPU (torchrun): every rank integrates its own replica (weak scaling, no
+data-path collective); the elapsed time is the max over ranks.
+"""
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "Gcell-updates/s per RK3 substep"
+UNIT = "Gcell-updates/s"
+
+# FP64 flops per cell-substep of the fused formulation (FMA = 2 flops; exp and
+# the one division are not counted): 564 in the 54 derivative stencils, 155 in
+# the physics of Eqs. B.1-B.4 with forcing, 40 in the Runge-Kutta update
+# (24 at substep 0, where w is not read).
+FLOPS_PER_CELL = {0: 743, 1: 759, 2: 759}
+# Algorithmic bytes per cell-substep: read f and w, write f and w (w not read at s = 0).
+def bytes_per_cell(elem_f, elem_w, s):
+    return 8 * (2 * elem_f + (2 if s else 1) * elem_w)
+
+# Nominal dense FP64 rate of one GB300 (no measured FP64 peak is provided).
+FP64_NOMINAL_TFLOPS = 1.25
+
+WORKLOADS = {
+    "forced256_fp64": dict(n=(256, 256, 256), precision="fp64", force_amp=0.05, seed=2,
+                           dt=1e-3, init="noise",
+                           desc="256^3 periodic FP64 non-ideal MHD, 6th-order stencils, RK3, "
+                                "forced |k|=2-3, noise 1e-5 on u and A"),
+    "paper256_fp64": dict(n=(256, 256, 256), precision="fp64", force_amp=0.0, seed=0,
+                          dt=1.19209e-7, init="uniform", vs=1.36,
+                          desc="256^3 periodic FP64, all fields U[0,1], dt=1.19209e-7 "
+                               "(the paper's own benchmark setup, Sec. 5)"),
+    "forced512_fp32": dict(n=(512, 512, 512), precision="fp32", force_amp=0.05, seed=3,
+                           dt=1e-3, init="noise",
+                           desc="512^3 periodic FP32 forced non-ideal MHD (FP64 reductions)"),
+}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="forced256_fp64", choices=sorted(WORKLOADS))
+    ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,pci.bus_id,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    NAMES = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+
+    def __init__(self, bus_id):
+        self.bus_id = (bus_id or "").lower()
+        self.lines = []
+        self.proc = None
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.th = threading.Thread(target=self._read, daemon=True)
+            self.th.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.th.join(timeout=2)
+        rows = []
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 10:
+                continue
+            bus = parts[1].lower()
+            if self.bus_id and not (bus.endswith(self.bus_id[-12:]) or self.bus_id.endswith(bus[-12:])):
+                continue
+            try:
+                rows.append((float(parts[2]), float(parts[3]), parts[6:10]))
+            except ValueError:
+                continue
+        if not rows:
+            return None
+        reasons = sorted({self.NAMES[i] for _, _, r in rows for i in range(4)
+                          if r[i].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(r[0] for r in rows),
+                "sm_max_mhz": max(r[1] for r in rows), "reasons": reasons,
+                "samples": len(rows)}
+
+
+# ---------------------------------------------------------------------------
+# inputs
+# ---------------------------------------------------------------------------
+def make_state(wl):
+    from paper_2103_01597_gb300 import synthetic
+    if wl["init"] == "uniform":
+        return synthetic.uniform_state(wl["n"], wl["seed"])
+    return synthetic.noise_state(wl["n"], wl["seed"])
+
+
+def dist_setup(args):
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+# ---------------------------------------------------------------------------
+# the oracle arm / CPU baseline: a bounded sample of the same workload
+# ---------------------------------------------------------------------------
+def oracle_sample(wl, f, planes):
+    """One RK3 step (3 substeps) of the oracle at the cells of `planes` z-planes
+    of the full-size state (the substeps read the full arrays)."""
+    from oracle import core
+    nx, ny, nz = wl["n"]
+    k, j, i = np.meshgrid(np.arange(planes), np.arange(ny), np.arange(nx), indexing="ij")
+    cells = np.stack([i.ravel(), j.ravel(), k.ravel()], axis=1).astype(np.int64)
+    frc = None
+    if wl["force_amp"]:
+        fr = core.forcing_draw(wl["seed"], 0, wl["force_amp"])
+        frc = fr
+    p = core.Params(n=wl["n"], forcing=frc)
+    w = np.zeros_like(f)
+    t0 = time.perf_counter()
+    for s in range(3):
+        core.substep_cells(f, w, p, wl["dt"], s, cells, nthreads=os.cpu_count())
+    return time.perf_counter() - t0, 3 * cells.shape[0]
+
+
+def cpu_baseline(wl, f, seconds):
+    import oracle
+    oracle.build_oracle()
+    planes = 1
+    dt, cu = oracle_sample(wl, f, planes)
+    planes = max(1, min(wl["n"][2], int(planes * seconds / max(dt, 1e-3))))
+    dt, cu = oracle_sample(wl, f, planes)
+    return {"value": cu / dt / 1e9, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+            "sample": "one RK3 step (3 substeps) at the %d cells of %d z-planes of the %s "
+                      "state, FP64 C oracle, OpenMP over %d threads"
+                      % (cu // 3, planes, "x".join(map(str, wl["n"])), os.cpu_count()),
+            "seconds": dt}
+
+
+def run_reference(args, wl):
+    ws, rank, _ = dist_setup(args)
+    if rank != 0:
+        return 0
+    import oracle
+    oracle.build_oracle()
+    f = make_state(wl)
+    nx, ny, _ = wl["n"]
+    planes = max(1, int(2e5 // (nx * ny)) + 1)
+    for _ in range(args.warmup):
+        oracle_sample(wl, f, planes)
+    tot, cu = 0.0, 0
+    for _ in range(args.steps):
+        dt, c = oracle_sample(wl, f, planes)
+        tot += dt
+        cu += c
+    value = cu / tot / 1e9
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * tot / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": wl["desc"], "grid": list(wl["n"]),
+                       "sample_per_step": "%d z-planes (%d cells) x 3 substeps"
+                                          % (planes, planes * nx * ny)},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": os.cpu_count(),
+                             "kind": "oracle",
+                             "sample": "per step: one RK3 step at the cells of %d z-planes"
+                                       % planes},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+def fp64_dgemm_tflops(torch):
+    n = 4096
+    a = torch.randn(n, n, dtype=torch.float64, device="cuda")
+    b = torch.randn(n, n, dtype=torch.float64, device="cuda")
+    for _ in range(2):
+        torch.matmul(a, b)
+    torch.cuda.synchronize()
+    best = 1e30
+    for _ in range(3):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        torch.matmul(a, b)
+        e1.record()
+        torch.cuda.synchronize()
+        best = min(best, e0.elapsed_time(e1) / 1e3)
+    del a, b
+    return 2 * n ** 3 / best / 1e12
+
+
+def run_ours(args, wl):
+    import torch
+    ws, rank, local = dist_setup(args)
+    torch.cuda.set_device(local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_2103_01597_gb300 import ac, build
+    if rank == 0:
+        build.build()
+    if dist:
+        dist.barrier()
+    prec = {"fp64": ac.AC_FP64, "fp32": ac.AC_FP32, "fp32_w64": ac.AC_FP32_W64}[wl["precision"]]
+    elem_f = 8 if prec == ac.AC_FP64 else 4
+    elem_w = 4 if prec == ac.AC_FP32 else 8
+    n = wl["n"]
+    ncell = n[0] * n[1] * n[2]
+    stream = torch.cuda.current_stream()
+    sim = ac.Simulation(n, precision=prec, force_amp=wl["force_amp"], seed=wl["seed"],
+                        device="cuda:%d" % local, stream=stream.cuda_stream)
+    f0 = make_state(wl)
+    host_in = torch.from_numpy(f0.reshape(-1)).pin_memory()
+    host_out = torch.empty_like(host_in).pin_memory()
+    ac.ac_load(sim.h, ac.AC_ALL, host_in)
+    dt = wl["dt"]
+
+    def step(ev=None):
+        for s in range(3):
+            if ev is not None:
+                ev[s][0].record(stream)
+            ac.ac_integrate_substep(sim.h, dt, s)
+            if ev is not None:
+                ev[s][1].record(stream)
+        return ac.ac_reduce(sim.h, ac.AC_MAX, ac.AC_Q_CFL)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    bus = None
+    try:
+        bus = torch.cuda.get_device_properties(local).pci_bus_id
+    except Exception:
+        bus = None
+    sampler = ClockSampler(bus) if rank == 0 else None
+    time.sleep(0.3 if sampler else 0)
+    evs = [[[torch.cuda.Event(enable_timing=True) for _ in range(2)] for _ in range(3)]
+           for _ in range(args.steps)]
+    launches0 = ac.ac_launch_count(sim.h)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    cfl = 0.0
+    for it in range(args.steps):
+        cfl = step(evs[it])
+    t1.record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    elapsed = t0.elapsed_time(t1) / 1e3
+    launches = ac.ac_launch_count(sim.h) - launches0
+    clocks = sampler.stop() if sampler else None
+    if dist:
+        tt = torch.tensor([elapsed], device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        elapsed = float(tt.item())
+    per_sub = [[evs[it][s][0].elapsed_time(evs[it][s][1]) / 1e3 for it in range(args.steps)]
+               for s in range(3)]
+    value = ws * ncell * 3 * args.steps / elapsed / 1e9
+
+    # dominant kernel: the fused substep; its average launch duration per substep index
+    avg = {s: statistics.mean(per_sub[s]) for s in range(3)}
+    avg_all = statistics.mean(avg.values())
+    if wl["precision"] == "fp64":
+        flops = {s: FLOPS_PER_CELL[s] * ncell for s in range(3)}
+        achieved = statistics.mean(flops[s] / avg[s] for s in range(3)) / 1e12
+        dg = fp64_dgemm_tflops(torch) if rank == 0 else None
+        roof = {"bound": "alu", "achieved": achieved, "peak": FP64_NOMINAL_TFLOPS,
+                "unit": "TFLOP/s", "frac": achieved / FP64_NOMINAL_TFLOPS, "traffic": None,
+                "kernel": "substep_kernel<double,double,IdxPeriodic>",
+                "peak_source": "nominal GB300 dense FP64 (no measured FP64 peak in "
+                               "MEASURED_PEAKS.json)",
+                "fp64_dgemm_measured_tflops": dg,
+                "avg_launch_ms": 1e3 * avg_all,
+                "alg_flops_per_cell_substep": FLOPS_PER_CELL}
+    else:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+        bytes_s = {s: bytes_per_cell(elem_f, elem_w, s) * ncell / 8 for s in range(3)}
+        achieved = statistics.mean(bytes_s[s] / avg[s] for s in range(3)) / 1e9
+        roof = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": achieved / peaks["hbm_gbs"], "traffic": None,
+                "kernel": "substep_kernel<float,float,IdxPeriodic>",
+                "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)",
+                "avg_launch_ms": 1e3 * avg_all}
+
+    # end to end through the C ABI with host buffers: load state, step, reduce, store
+    e2e = None
+    if args.e2e_steps > 0:
+        torch.cuda.synchronize()
+        h2d = 8 * ncell * 8
+        d2h = 8 * ncell * 8 + 16
+        tt0 = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            ac.ac_load(sim.h, ac.AC_ALL, host_in)
+            step()
+            ac.ac_store(sim.h, ac.AC_ALL, host_out)
+        tt = time.perf_counter() - tt0
+        e2e = {"value": ncell * 3 * args.e2e_steps * ws / tt / 1e9, "unit": UNIT,
+               "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+               "steps": args.e2e_steps}
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(wl, f0, args.cpu_seconds)
+    sim.close()
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
+                "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": 1e3 * elapsed / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": (value / ws / wl["vs"]) if "vs" in wl else None,
+                "dtype": "f64" if wl["precision"] == "fp64" else "f32", "data": "synthetic",
+                "config": {"workload": wl["desc"], "grid": list(n), "dt": dt,
+                           "precision": wl["precision"], "layout": "periodic (wrap on load)",
+                           "parallelism": "replicas" if ws > 1 else "single GPU",
+                           "l2": "inputs larger than L2 (%.1f GB of state resident)"
+                                 % (ncell * (16 * elem_f + 8 * elem_w) / 1e9),
+                           "step": "forcing draw + 3 fused substeps + FP64 CFL max reduction"},
+                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
+                "gpu_launches": launches, "clocks": clocks,
+                "last_cfl_speed": cfl,
+                "substep_ms": {str(s): 1e3 * avg[s] for s in range(3)}}
+        print(json.dumps(line))
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    wl = WORKLOADS[args.workload]
+    if args.impl == "reference":
+        return run_reference(args, wl)
+    return run_ours(args, wl)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,223 @@
+/*
+ * ac.h -- C ABI of libac.so: one third-order 2N-storage Runge-Kutta substep of
+ * compressible non-ideal MHD with sixth-order central differences on a
+ * periodic 3-D grid, fused into one CUDA kernel for GB300 (sm_103a).
+ *
+ * Paper: Pekkila, Vaisala, Kapyla, Rheinhardt, Lappi, "Scalable communication
+ * for high-order stencil computations using CUDA-aware MPI" (arXiv:2103.01597).
+ *   - problem statement (computational domain N, halo of radius r, grid
+ *     M = N + 2r): Sec. 2, Eqs. 2-3;
+ *   - stencil point set (axes and face diagonals, radius 3): Sec. 4, Eq. 13;
+ *   - equations and fields: Appendix B, Eqs. B.1-B.4, Tables B.1-B.2;
+ *   - time integration (Williamson third-order Runge-Kutta): Sec. 4;
+ *   - periodic halo map s' = ((s - r) mod n) + r: Sec. 3.3;
+ *   - single and double precision: Sec. 3.3.
+ *
+ * Conventions for every call:
+ *   - Return value: AC_OK (0) or a negative AC_ERR_* code; no call throws, and
+ *     ac_strerror() names a code.  After AC_ERR_CUDA, ac_last_cuda_error()
+ *     gives the CUDA runtime's message.
+ *   - Host buffers are owned by the caller and only read or written during the
+ *     call.  Device buffers are owned by the library unless the caller binds
+ *     its own with ac_bind_buffers(); bound buffers must outlive the handle.
+ *   - Work is issued on the handle's CUDA stream (the one given to ac_init,
+ *     or the legacy default stream for NULL).  ac_store() and ac_reduce()
+ *     synchronise that stream before they return; every other call is
+ *     stream-ordered and returns once its work is enqueued.
+ *   - A handle is used by one host thread at a time.
+ *   - Fields are stored as one array per field (structure of arrays), x
+ *     fastest, in the order of Table B.1: ln rho, u_x, u_y, u_z, s, A_x, A_y,
+ *     A_z.  Host arrays are always unpadded nx*ny*nz float64.
+ */
+#ifndef AC_H
+#define AC_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- return codes ------------------------------------------------------ */
+#define AC_OK 0
+#define AC_ERR_ARG (-1)       /* invalid argument (NULL, range, size)          */
+#define AC_ERR_CUDA (-2)      /* a CUDA runtime call or kernel launch failed    */
+#define AC_ERR_OOM (-3)       /* device or host allocation failed               */
+#define AC_ERR_NONFINITE (-4) /* a reduction met a NaN or infinity              */
+#define AC_ERR_TIMEOUT (-5)   /* a bounded device wait ran out                  */
+#define AC_ERR_STATE (-6)     /* call out of order (e.g. substep s skipped)     */
+
+/* ---- fields (Table B.1) ------------------------------------------------- */
+#define AC_LNRHO 0
+#define AC_UX 1
+#define AC_UY 2
+#define AC_UZ 3
+#define AC_SS 4
+#define AC_AX 5
+#define AC_AY 6
+#define AC_AZ 7
+#define AC_NFIELDS 8
+#define AC_ALL (-1)
+
+/* ---- precision of device storage and arithmetic (Sec. 3.3 supports both) */
+#define AC_FP64 0     /* fields, accumulator and arithmetic in binary64          */
+#define AC_FP32 1     /* fields, accumulator and stencil arithmetic in binary32  */
+#define AC_FP32_W64 2 /* binary32 fields and arithmetic, binary64 accumulator w */
+
+/* ---- device layout ------------------------------------------------------ */
+#define AC_LAYOUT_PERIODIC 0 /* nx*ny*nz per field; the periodic map of Sec. 3.3
+                                is applied to every stencil load (no halo)    */
+#define AC_LAYOUT_PADDED 1   /* (nx+6)(ny+6)(nz+6) per field with a radius-3
+                                halo (grid M of Sec. 2) that ac_periodic_halo()
+                                fills                                          */
+
+/* ---- reductions ---------------------------------------------------------- */
+#define AC_MAX 0
+#define AC_MIN 1
+#define AC_SUM 2 /* plain sum over cells (multiply by dx dy dz for integrals) */
+#define AC_RMS 3 /* sqrt(sum q^2 / N)                                          */
+/* quantities: 0..7 select a field; the rest are derived per cell (mu0 = 1): */
+#define AC_Q_UMAG 8  /* |u|                                                    */
+#define AC_Q_EKIN 9  /* rho |u|^2 / 2                                          */
+#define AC_Q_EMAG 10 /* |B|^2 / 2, B = curl A with the sixth-order first derivative */
+#define AC_Q_CFL 11  /* |u| + sqrt(c_s^2 + |B|^2 / rho): fastest signal speed  */
+
+typedef struct {
+    int nx, ny, nz;      /* computational domain N (Sec. 2); each >= 1           */
+    double lx, ly, lz;   /* box lengths; grid spacing dx = lx / nx etc.          */
+    int layout;          /* AC_LAYOUT_PERIODIC or AC_LAYOUT_PADDED               */
+} ac_grid;
+
+typedef struct {
+    double nu;           /* kinematic viscosity (Eq. B.2)                        */
+    double eta;          /* magnetic diffusivity (Eqs. B.3, B.4)                 */
+    double cs0;          /* sound speed at s = 0, ln rho = lnrho0                */
+    double gamma;        /* adiabatic index (> 1)                                */
+    double cp;           /* specific heat at constant pressure (> 0)             */
+    double lnrho0;       /* reference log density                                */
+    double force_amp;    /* forcing amplitude f0 (0: no forcing)                 */
+    unsigned long long seed; /* seed of the per-step forcing draw                */
+    int precision;       /* AC_FP64, AC_FP32 or AC_FP32_W64                      */
+} ac_params;
+
+typedef struct ac_handle ac_handle; /* opaque; owned by the library */
+
+/*
+ * Create a handle for one grid on the current CUDA device.  Validates the
+ * grid and parameters (AC_ERR_ARG), allocates small device work areas, and
+ * leaves the state buffers unallocated: they are bound with
+ * ac_bind_buffers() or allocated by the library on first use.  `stream` is a
+ * cudaStream_t (NULL: legacy default stream).  The state starts at substep 0
+ * of step 0 with all fields zero once buffers exist.
+ */
+int ac_init(ac_handle **h, const ac_grid *grid, const ac_params *params, void *stream);
+
+/* Release the handle and every device buffer the library owns.  NULL is a no-op. */
+int ac_quit(ac_handle *h);
+
+/* Replace the handle's stream (cudaStream_t; NULL: legacy default stream). */
+int ac_set_stream(ac_handle *h, void *stream);
+
+/*
+ * Bind caller-owned device memory for the state: dev_ptrs[0..7] and
+ * [8..15] are the two state buffers that alternate between input and output
+ * of a substep, dev_ptrs[16..23] the Runge-Kutta accumulator w (Williamson
+ * 2N storage), one array per field.  Element type: double for AC_FP64, float
+ * for AC_FP32 and AC_FP32_W64 (whose w arrays are double).  Each array holds
+ * ac_field_elems() elements and must be 16-byte aligned.  Buffers the library
+ * owned are freed.  The state is not cleared; dev_ptrs[0..7] become the
+ * current state.
+ */
+int ac_bind_buffers(ac_handle *h, void *const dev_ptrs[24]);
+
+/* Elements per device field array for this handle (padded size for
+ * AC_LAYOUT_PADDED). */
+int ac_field_elems(const ac_handle *h, size_t *elems);
+
+/*
+ * Copy the current state's field `field` (0..7, or AC_ALL for all eight
+ * arrays back to back) from unpadded float64 host memory, converting to the
+ * device precision (round to nearest).  Page-locked host memory makes the copy
+ * asynchronous; pageable memory is copied synchronously.  Resets the substep
+ * counter to 0 (a new step begins).
+ */
+int ac_load(ac_handle *h, int field, const double *host_src);
+
+/* Copy the current state's field (or AC_ALL) to unpadded float64 host memory;
+ * synchronises the stream. */
+int ac_store(ac_handle *h, int field, double *host_dst);
+
+/* Same as ac_load/ac_store for the accumulator w (checkpoint and resume). */
+int ac_load_w(ac_handle *h, int field, const double *host_src);
+int ac_store_w(ac_handle *h, int field, double *host_dst);
+
+/*
+ * One Runge-Kutta substep s of the step in progress (Sec. 4; Williamson's
+ * third-order 2N-storage scheme):  w <- alpha_s w + dt RHS(f);  f <- f + beta_s w,
+ * alpha = (0, -5/9, -153/128), beta = (1/3, 15/16, 8/15), with RHS the right-hand
+ * side of Eqs. B.1-B.4 evaluated with sixth-order central differences on the
+ * points of Eq. 13, the periodic map of Sec. 3.3 at the domain boundary, and the
+ * step's forcing term added to du/dt when force_amp != 0.  One fused kernel
+ * reads f and w and writes the new f (into the other state buffer, which then
+ * becomes current) and w.  At s = 0, w is not read.  s must follow the previous
+ * substep ((previous + 1) mod 3, starting at 0): otherwise AC_ERR_STATE.
+ * dt must be finite.  With AC_LAYOUT_PADDED the halo is refreshed first.
+ * At s = 0 with forcing on, the step's forcing is drawn (ac_forcing_draw with
+ * the handle's seed and step counter) unless ac_set_forcing() fixed it.  After
+ * s = 2 the step counter advances.
+ */
+int ac_integrate_substep(ac_handle *h, double dt, int s);
+
+/* Substeps 0, 1, 2 with the same dt (one full Runge-Kutta step). */
+int ac_integrate_step(ac_handle *h, double dt);
+
+/*
+ * Fill the radius-3 halo of the current state (AC_LAYOUT_PADDED) with the
+ * periodic map of Sec. 3.3, s' = ((s - r) mod n) + r per axis: the six sides,
+ * twelve edges and eight corners.  A no-op for AC_LAYOUT_PERIODIC.
+ */
+int ac_periodic_halo(ac_handle *h);
+
+/*
+ * Reduce a quantity of the current state over all cells in binary64
+ * (AC_MAX, AC_MIN, AC_SUM, AC_RMS; quantity 0..7 or AC_Q_*), write the result
+ * to *out (host memory) and synchronise.  AC_ERR_NONFINITE if any per-cell
+ * value met is NaN or infinite (*out is still written).  Not in the paper (its
+ * timestep is constant, Sec. 5): energies and the CFL speed for monitoring.
+ */
+int ac_reduce(ac_handle *h, int op, int quantity, double *out);
+
+/*
+ * The forcing of step `step` for seed `seed` (not in the paper): wave vector
+ * k with 2 <= |k| <= 3, unit polarisation e perpendicular to k, phase phi in
+ * [0, 2 pi), drawn with the SplitMix64 counter generator.  The forcing adds
+ * force_amp * e * cos(2 pi sum_a k_a i_a / n_a + phi) to du/dt at cell i.
+ */
+int ac_forcing_draw(unsigned long long seed, unsigned long long step, int k[3], double e[3],
+                    double *phi);
+
+/* Fix the forcing for the following substeps (instead of the per-step draw);
+ * k == NULL returns to the per-step draw. */
+int ac_set_forcing(ac_handle *h, const int k[3], const double e[3], double phi);
+
+/* Step counter (completed full steps) and the next expected substep. */
+int ac_get_step(const ac_handle *h, unsigned long long *step, int *next_substep);
+
+/* Position the handle at substep `next_substep` (0..2) of step `step`, e.g. to
+ * resume from a checkpoint: load f with ac_load and w with ac_load_w first
+ * (ac_load resets the substep to 0).  The step's forcing is drawn again for
+ * `step` at the next substep. */
+int ac_set_step(ac_handle *h, unsigned long long step, int next_substep);
+
+/* Number of kernels the handle has launched so far. */
+int ac_launch_count(const ac_handle *h, unsigned long long *count);
+
+/* Text of an AC_* code; message of the last CUDA error seen by this thread. */
+const char *ac_strerror(int code);
+const char *ac_last_cuda_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* AC_H */

@@ -1,0 +1,306 @@
+"""ctypes binding of ``libac.so`` (declared in ``include/ac.h``).
+
+Same names as the C ABI; this module only marshals arguments.  Every step of
+the substep runs in the library's CUDA kernels.  PyTorch is used for device
+memory (``Simulation`` binds torch tensors with ``ac_bind_buffers``) and for
+the CUDA stream.  Loading fails loudly if the compiled library is missing:
+there is no CPU fallback.
+"""
+import ctypes
+import math
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libac.so")
+
+AC_OK = 0
+AC_ERR_ARG = -1
+AC_ERR_CUDA = -2
+AC_ERR_OOM = -3
+AC_ERR_NONFINITE = -4
+AC_ERR_TIMEOUT = -5
+AC_ERR_STATE = -6
+
+AC_LNRHO, AC_UX, AC_UY, AC_UZ, AC_SS, AC_AX, AC_AY, AC_AZ = range(8)
+AC_NFIELDS = 8
+AC_ALL = -1
+
+AC_FP64, AC_FP32, AC_FP32_W64 = 0, 1, 2
+AC_LAYOUT_PERIODIC, AC_LAYOUT_PADDED = 0, 1
+AC_MAX, AC_MIN, AC_SUM, AC_RMS = 0, 1, 2, 3
+AC_Q_UMAG, AC_Q_EKIN, AC_Q_EMAG, AC_Q_CFL = 8, 9, 10, 11
+
+
+class ac_grid(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
+                ("lx", ctypes.c_double), ("ly", ctypes.c_double), ("lz", ctypes.c_double),
+                ("layout", ctypes.c_int)]
+
+
+class ac_params(ctypes.Structure):
+    _fields_ = [("nu", ctypes.c_double), ("eta", ctypes.c_double), ("cs0", ctypes.c_double),
+                ("gamma", ctypes.c_double), ("cp", ctypes.c_double), ("lnrho0", ctypes.c_double),
+                ("force_amp", ctypes.c_double), ("seed", ctypes.c_ulonglong),
+                ("precision", ctypes.c_int)]
+
+
+class AcError(RuntimeError):
+    def __init__(self, code, where, value=None):
+        self.code = code
+        self.value = value
+        msg = "%s failed: %s" % (where, ac_strerror(code))
+        if code == AC_ERR_CUDA or code == AC_ERR_OOM:
+            msg += " (%s)" % ac_last_cuda_error()
+        super().__init__(msg)
+
+
+_lib = None
+_c = ctypes
+_vp = ctypes.c_void_p
+_pd = ctypes.POINTER(ctypes.c_double)
+
+
+def load_library(path=None):
+    """Load libac.so (raises OSError if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    p = path or LIB_PATH
+    if not os.path.exists(p):
+        raise OSError("libac.so not found at %s: build it with "
+                      "paper_2103_01597_gb300.build.build()" % p)
+    L = ctypes.CDLL(p)
+    sig = {
+        "ac_init": ([ctypes.POINTER(_vp), ctypes.POINTER(ac_grid), ctypes.POINTER(ac_params), _vp],
+                    _c.c_int),
+        "ac_quit": ([_vp], _c.c_int),
+        "ac_set_stream": ([_vp, _vp], _c.c_int),
+        "ac_bind_buffers": ([_vp, ctypes.POINTER(_vp)], _c.c_int),
+        "ac_field_elems": ([_vp, ctypes.POINTER(ctypes.c_size_t)], _c.c_int),
+        "ac_load": ([_vp, _c.c_int, _vp], _c.c_int),
+        "ac_store": ([_vp, _c.c_int, _vp], _c.c_int),
+        "ac_load_w": ([_vp, _c.c_int, _vp], _c.c_int),
+        "ac_store_w": ([_vp, _c.c_int, _vp], _c.c_int),
+        "ac_integrate_substep": ([_vp, _c.c_double, _c.c_int], _c.c_int),
+        "ac_integrate_step": ([_vp, _c.c_double], _c.c_int),
+        "ac_periodic_halo": ([_vp], _c.c_int),
+        "ac_reduce": ([_vp, _c.c_int, _c.c_int, _pd], _c.c_int),
+        "ac_forcing_draw": ([_c.c_ulonglong, _c.c_ulonglong, ctypes.POINTER(_c.c_int), _pd, _pd],
+                            _c.c_int),
+        "ac_set_forcing": ([_vp, ctypes.POINTER(_c.c_int), _pd, _c.c_double], _c.c_int),
+        "ac_get_step": ([_vp, ctypes.POINTER(_c.c_ulonglong), ctypes.POINTER(_c.c_int)], _c.c_int),
+        "ac_set_step": ([_vp, _c.c_ulonglong, _c.c_int], _c.c_int),
+        "ac_launch_count": ([_vp, ctypes.POINTER(_c.c_ulonglong)], _c.c_int),
+        "ac_strerror": ([_c.c_int], _c.c_char_p),
+        "ac_last_cuda_error": ([], _c.c_char_p),
+    }
+    for name, (args, res) in sig.items():
+        fn = getattr(L, name)
+        fn.argtypes = args
+        fn.restype = res
+    _lib = L
+    return L
+
+
+def _check(rc, where, value=None):
+    if rc != AC_OK:
+        raise AcError(rc, where, value)
+
+
+def ac_strerror(code):
+    return load_library().ac_strerror(code).decode()
+
+
+def ac_last_cuda_error():
+    return load_library().ac_last_cuda_error().decode()
+
+
+def make_grid(n, L=(2 * math.pi,) * 3, layout=AC_LAYOUT_PERIODIC):
+    return ac_grid(int(n[0]), int(n[1]), int(n[2]), float(L[0]), float(L[1]), float(L[2]),
+                   int(layout))
+
+
+def make_params(nu=5e-3, eta=5e-3, cs0=1.0, gamma=5.0 / 3.0, cp=1.0, lnrho0=0.0,
+                force_amp=0.0, seed=0, precision=AC_FP64):
+    return ac_params(nu, eta, cs0, gamma, cp, lnrho0, force_amp, seed, precision)
+
+
+def ac_init(grid, params, stream=None):
+    h = _vp()
+    _check(load_library().ac_init(ctypes.byref(h), ctypes.byref(grid), ctypes.byref(params),
+                                  _vp(stream or 0)), "ac_init")
+    return h
+
+
+def ac_quit(h):
+    _check(load_library().ac_quit(h), "ac_quit")
+
+
+def ac_set_stream(h, stream):
+    _check(load_library().ac_set_stream(h, _vp(stream or 0)), "ac_set_stream")
+
+
+def ac_bind_buffers(h, dev_ptrs):
+    assert len(dev_ptrs) == 24
+    arr = (_vp * 24)(*[int(p) for p in dev_ptrs])
+    _check(load_library().ac_bind_buffers(h, arr), "ac_bind_buffers")
+
+
+def ac_field_elems(h):
+    n = ctypes.c_size_t()
+    _check(load_library().ac_field_elems(h, ctypes.byref(n)), "ac_field_elems")
+    return n.value
+
+
+def _host_ptr(a, writable):
+    if isinstance(a, int):
+        return a
+    if hasattr(a, "data_ptr"):  # torch CPU tensor (e.g. pinned)
+        assert a.dtype.is_floating_point and a.element_size() == 8 and a.is_contiguous()
+        return a.data_ptr()
+    assert isinstance(a, np.ndarray) and a.dtype == np.float64 and a.flags.c_contiguous
+    assert a.flags.writeable or not writable
+    return a.ctypes.data
+
+
+def ac_load(h, field, host_src):
+    _check(load_library().ac_load(h, field, _host_ptr(host_src, False)), "ac_load")
+
+
+def ac_store(h, field, host_dst):
+    _check(load_library().ac_store(h, field, _host_ptr(host_dst, True)), "ac_store")
+
+
+def ac_load_w(h, field, host_src):
+    _check(load_library().ac_load_w(h, field, _host_ptr(host_src, False)), "ac_load_w")
+
+
+def ac_store_w(h, field, host_dst):
+    _check(load_library().ac_store_w(h, field, _host_ptr(host_dst, True)), "ac_store_w")
+
+
+def ac_integrate_substep(h, dt, s):
+    _check(load_library().ac_integrate_substep(h, float(dt), int(s)), "ac_integrate_substep")
+
+
+def ac_integrate_step(h, dt):
+    _check(load_library().ac_integrate_step(h, float(dt)), "ac_integrate_step")
+
+
+def ac_periodic_halo(h):
+    _check(load_library().ac_periodic_halo(h), "ac_periodic_halo")
+
+
+def ac_reduce(h, op, quantity):
+    out = ctypes.c_double()
+    rc = load_library().ac_reduce(h, int(op), int(quantity), ctypes.byref(out))
+    _check(rc, "ac_reduce", out.value)
+    return out.value
+
+
+def ac_forcing_draw(seed, step):
+    k = (ctypes.c_int * 3)()
+    e = (ctypes.c_double * 3)()
+    phi = ctypes.c_double()
+    _check(load_library().ac_forcing_draw(seed & (2 ** 64 - 1), step, k, e, ctypes.byref(phi)),
+           "ac_forcing_draw")
+    return tuple(k), tuple(e), phi.value
+
+
+def ac_set_forcing(h, k, e, phi):
+    if k is None:
+        _check(load_library().ac_set_forcing(h, None, None, 0.0), "ac_set_forcing")
+        return
+    kk = (ctypes.c_int * 3)(*[int(v) for v in k])
+    ee = (ctypes.c_double * 3)(*[float(v) for v in e])
+    _check(load_library().ac_set_forcing(h, kk, ee, float(phi)), "ac_set_forcing")
+
+
+def ac_get_step(h):
+    st = ctypes.c_ulonglong()
+    ns = ctypes.c_int()
+    _check(load_library().ac_get_step(h, ctypes.byref(st), ctypes.byref(ns)), "ac_get_step")
+    return st.value, ns.value
+
+
+def ac_set_step(h, step, next_substep=0):
+    _check(load_library().ac_set_step(h, int(step), int(next_substep)), "ac_set_step")
+
+
+def ac_launch_count(h):
+    n = ctypes.c_ulonglong()
+    _check(load_library().ac_launch_count(h, ctypes.byref(n)), "ac_launch_count")
+    return n.value
+
+
+class Simulation:
+    """A handle whose state lives in torch-owned device tensors.
+
+    ``state[b]`` (b = 0, 1) are the two alternating (8, elems) state buffers
+    and ``w`` the (8, elems) accumulator; the library's current state is
+    ``state[current]``.  Rows are padded to 16-byte multiples.
+    """
+
+    def __init__(self, n, L=(2 * math.pi,) * 3, layout=AC_LAYOUT_PERIODIC, precision=AC_FP64,
+                 nu=5e-3, eta=5e-3, cs0=1.0, gamma=5.0 / 3.0, cp=1.0, lnrho0=0.0,
+                 force_amp=0.0, seed=0, device="cuda", stream=None):
+        import torch
+        self.n = tuple(n)
+        self.precision = precision
+        self.layout = layout
+        if stream is None:
+            stream = torch.cuda.current_stream(device).cuda_stream
+        self.h = ac_init(make_grid(n, L, layout),
+                         make_params(nu, eta, cs0, gamma, cp, lnrho0, force_amp, seed, precision),
+                         stream)
+        self.elems = ac_field_elems(self.h)
+        fdt = torch.float64 if precision == AC_FP64 else torch.float32
+        wdt = torch.float32 if precision == AC_FP32 else torch.float64
+        row = (self.elems + 3) // 4 * 4
+        self.state = torch.zeros((2, 8, row), dtype=fdt, device=device)
+        self.w = torch.zeros((8, row), dtype=wdt, device=device)
+        ptrs = [self.state[b, q].data_ptr() for b in range(2) for q in range(8)]
+        ptrs += [self.w[q].data_ptr() for q in range(8)]
+        ac_bind_buffers(self.h, ptrs)
+        self._closed = False
+
+    def load(self, f):
+        f = np.ascontiguousarray(f, dtype=np.float64)
+        ac_load(self.h, AC_ALL, f)
+
+    def store(self):
+        nx, ny, nz = self.n
+        out = np.empty((8, nz, ny, nx))
+        ac_store(self.h, AC_ALL, out)
+        return out
+
+    def load_w(self, w):
+        ac_load_w(self.h, AC_ALL, np.ascontiguousarray(w, dtype=np.float64))
+
+    def store_w(self):
+        nx, ny, nz = self.n
+        out = np.empty((8, nz, ny, nx))
+        ac_store_w(self.h, AC_ALL, out)
+        return out
+
+    def substep(self, dt, s):
+        ac_integrate_substep(self.h, dt, s)
+
+    def step(self, dt):
+        ac_integrate_step(self.h, dt)
+
+    def reduce(self, op, quantity):
+        return ac_reduce(self.h, op, quantity)
+
+    def close(self):
+        if not self._closed:
+            ac_quit(self.h)
+            self._closed = True
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,550 @@
+// C-ABI implementation of libac.so (declarations and contracts in include/ac.h).
+#include <math.h>
+#include <stdint.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <new>
+
+#include "ac_internal.h"
+
+namespace ac {
+cudaError_t launch_substep_f64(const SubstepLaunch &L, cudaStream_t st, int *launches);
+cudaError_t launch_substep_f32(const SubstepLaunch &L, cudaStream_t st, int *launches);
+cudaError_t launch_substep_f32w64(const SubstepLaunch &L, cudaStream_t st, int *launches);
+}  // namespace ac
+
+using namespace ac;
+
+// Williamson (1980) third-order 2N-storage coefficients (Sec. 4 names the scheme).
+static const double RK_ALPHA[3] = {0.0, -5.0 / 9.0, -153.0 / 128.0};
+static const double RK_BETA[3] = {1.0 / 3.0, 15.0 / 16.0, 8.0 / 15.0};
+
+static thread_local char g_cuda_msg[256] = "";
+
+static int cuda_fail(cudaError_t e) {
+    snprintf(g_cuda_msg, sizeof g_cuda_msg, "%s: %s", cudaGetErrorName(e), cudaGetErrorString(e));
+    return e == cudaErrorMemoryAllocation ? AC_ERR_OOM : AC_ERR_CUDA;
+}
+
+#define CK(call)                                   \
+    do {                                           \
+        cudaError_t e_ = (call);                   \
+        if (e_ != cudaSuccess) return cuda_fail(e_); \
+    } while (0)
+
+struct ac_handle {
+    ac_grid grid;
+    ac_params params;
+    Geom g;
+    StencilCoefs coefs;
+    PhysConsts phys;
+    cudaStream_t stream;
+    int elem_f, elem_w;  // bytes per element of state and accumulator arrays
+    void *state[2][NF];  // alternating state buffers
+    void *w[NF];
+    int cur;             // index of the current state
+    int have_buffers;
+    void *owned_block;   // library-owned state allocation (NULL if bound)
+    double2 *ftab;       // forcing tables (double2 then float2)
+    double *partials;
+    unsigned int *flags;
+    double *result_dev;  // [value, flag word]
+    double *result_host; // page-locked copy of result_dev
+    double *stage;       // float64 staging for load/store
+    size_t stage_elems;
+    int next_s;
+    unsigned long long step;
+    int force_manual;
+    int force_k[3];
+    double force_e[3];
+    double force_phi;
+    int ftab_dirty;
+    int ftab_valid;
+    unsigned long long ftab_step;  // step whose draw the tables hold (per-step draw mode)
+    unsigned long long launches;
+};
+
+extern "C" const char *ac_strerror(int code) {
+    switch (code) {
+        case AC_OK: return "AC_OK: success";
+        case AC_ERR_ARG: return "AC_ERR_ARG: invalid argument";
+        case AC_ERR_CUDA: return "AC_ERR_CUDA: CUDA runtime error";
+        case AC_ERR_OOM: return "AC_ERR_OOM: out of memory";
+        case AC_ERR_NONFINITE: return "AC_ERR_NONFINITE: non-finite value met";
+        case AC_ERR_TIMEOUT: return "AC_ERR_TIMEOUT: bounded device wait ran out";
+        case AC_ERR_STATE: return "AC_ERR_STATE: call out of order";
+        default: return "unknown ac error code";
+    }
+}
+
+extern "C" const char *ac_last_cuda_error(void) { return g_cuda_msg; }
+
+static int valid_grid(const ac_grid *g) {
+    if (!g) return 0;
+    if (g->nx < 1 || g->ny < 1 || g->nz < 1) return 0;
+    if (!(g->lx > 0) || !(g->ly > 0) || !(g->lz > 0)) return 0;
+    if (!isfinite(g->lx) || !isfinite(g->ly) || !isfinite(g->lz)) return 0;
+    if (g->layout != AC_LAYOUT_PERIODIC && g->layout != AC_LAYOUT_PADDED) return 0;
+    // 64-bit cell counts; keep every per-axis index and padded extent in int range.
+    if (g->nx > (1 << 24) || g->ny > (1 << 24) || g->nz > (1 << 24)) return 0;
+    return 1;
+}
+
+static int valid_params(const ac_params *p) {
+    if (!p) return 0;
+    const double v[7] = {p->nu, p->eta, p->cs0, p->gamma, p->cp, p->lnrho0, p->force_amp};
+    for (int i = 0; i < 7; ++i)
+        if (!isfinite(v[i])) return 0;
+    if (p->nu < 0 || p->eta < 0 || p->cs0 <= 0 || p->gamma <= 1.0 || p->cp <= 0) return 0;
+    if (p->precision != AC_FP64 && p->precision != AC_FP32 && p->precision != AC_FP32_W64)
+        return 0;
+    return 1;
+}
+
+static void free_handle_memory(ac_handle *h) {
+    if (h->owned_block) cudaFree(h->owned_block);
+    if (h->ftab) cudaFree(h->ftab);
+    if (h->partials) cudaFree(h->partials);
+    if (h->flags) cudaFree(h->flags);
+    if (h->result_dev) cudaFree(h->result_dev);
+    if (h->result_host) cudaFreeHost(h->result_host);
+    if (h->stage) cudaFree(h->stage);
+}
+
+extern "C" int ac_init(ac_handle **out, const ac_grid *grid, const ac_params *params,
+                       void *stream) {
+    if (!out || !valid_grid(grid) || !valid_params(params)) return AC_ERR_ARG;
+    *out = nullptr;
+    ac_handle *h = new (std::nothrow) ac_handle();
+    if (!h) return AC_ERR_OOM;
+    h->grid = *grid;
+    h->params = *params;
+    h->g = make_geom(grid->nx, grid->ny, grid->nz, grid->layout);
+    const double dx[3] = {grid->lx / grid->nx, grid->ly / grid->ny, grid->lz / grid->nz};
+    h->coefs = make_coefs(dx);
+    h->phys = make_phys(*params);
+    h->stream = static_cast<cudaStream_t>(stream);
+    h->elem_f = params->precision == AC_FP64 ? 8 : 4;
+    h->elem_w = params->precision == AC_FP32 ? 4 : 8;
+    const int ntab = grid->nx + grid->ny + grid->nz;
+    cudaError_t e = cudaMalloc(&h->ftab, (size_t)ntab * (sizeof(double2) + sizeof(float2)));
+    if (e == cudaSuccess) e = cudaMalloc(&h->partials, sizeof(double) * reduce_max_blocks());
+    if (e == cudaSuccess) e = cudaMalloc(&h->flags, sizeof(unsigned int) * reduce_max_blocks());
+    if (e == cudaSuccess) e = cudaMalloc(&h->result_dev, 2 * sizeof(double));
+    if (e == cudaSuccess) e = cudaMallocHost(&h->result_host, 2 * sizeof(double));
+    if (e != cudaSuccess) {
+        int rc = cuda_fail(e);
+        free_handle_memory(h);
+        delete h;
+        return rc;
+    }
+    *out = h;
+    return AC_OK;
+}
+
+extern "C" int ac_quit(ac_handle *h) {
+    if (!h) return AC_OK;
+    cudaStreamSynchronize(h->stream);
+    free_handle_memory(h);
+    delete h;
+    return AC_OK;
+}
+
+extern "C" int ac_set_stream(ac_handle *h, void *stream) {
+    if (!h) return AC_ERR_ARG;
+    h->stream = static_cast<cudaStream_t>(stream);
+    return AC_OK;
+}
+
+extern "C" int ac_field_elems(const ac_handle *h, size_t *elems) {
+    if (!h || !elems) return AC_ERR_ARG;
+    *elems = (size_t)h->g.elems;
+    return AC_OK;
+}
+
+static size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+// Allocate the library-owned state on first use (zero-filled).
+static int ensure_state(ac_handle *h) {
+    if (h->have_buffers) return AC_OK;
+    const size_t nf = align_up((size_t)h->g.elems * h->elem_f, 256);
+    const size_t nw = align_up((size_t)h->g.elems * h->elem_w, 256);
+    const size_t total = 2 * NF * nf + NF * nw;
+    void *blk = nullptr;
+    CK(cudaMalloc(&blk, total));
+    cudaError_t e = cudaMemsetAsync(blk, 0, total, h->stream);
+    if (e != cudaSuccess) {
+        cudaFree(blk);
+        return cuda_fail(e);
+    }
+    char *p = static_cast<char *>(blk);
+    for (int b = 0; b < 2; ++b)
+        for (int q = 0; q < NF; ++q) {
+            h->state[b][q] = p;
+            p += nf;
+        }
+    for (int q = 0; q < NF; ++q) {
+        h->w[q] = p;
+        p += nw;
+    }
+    h->owned_block = blk;
+    h->have_buffers = 1;
+    h->cur = 0;
+    return AC_OK;
+}
+
+extern "C" int ac_bind_buffers(ac_handle *h, void *const dev_ptrs[24]) {
+    if (!h || !dev_ptrs) return AC_ERR_ARG;
+    for (int i = 0; i < 24; ++i)
+        if (!dev_ptrs[i] || ((uintptr_t)dev_ptrs[i] & 15u)) return AC_ERR_ARG;
+    if (h->owned_block) {
+        CK(cudaStreamSynchronize(h->stream));
+        cudaFree(h->owned_block);
+        h->owned_block = nullptr;
+    }
+    for (int q = 0; q < NF; ++q) {
+        h->state[0][q] = dev_ptrs[q];
+        h->state[1][q] = dev_ptrs[NF + q];
+        h->w[q] = dev_ptrs[2 * NF + q];
+    }
+    h->cur = 0;
+    h->have_buffers = 1;
+    return AC_OK;
+}
+
+static int ensure_stage(ac_handle *h, size_t *planes) {
+    const size_t plane = (size_t)h->g.nx * h->g.ny;
+    const size_t want_elems = (size_t)1 << 25;  // 256 MiB of float64 at most
+    size_t np = want_elems / plane;
+    if (np < 1) np = 1;
+    if (np > (size_t)h->g.nz) np = (size_t)h->g.nz;
+    const size_t need = np * plane;
+    if (h->stage_elems < need) {
+        if (h->stage) {
+            CK(cudaStreamSynchronize(h->stream));
+            cudaFree(h->stage);
+            h->stage = nullptr;
+            h->stage_elems = 0;
+        }
+        CK(cudaMalloc(&h->stage, need * sizeof(double)));
+        h->stage_elems = need;
+    }
+    *planes = np;
+    return AC_OK;
+}
+
+// Host float64 (unpadded) -> device array `dst` with element size `es`.
+static int load_array(ac_handle *h, void *dst, int es, const double *src) {
+    const size_t plane = (size_t)h->g.nx * h->g.ny;
+    if (es == 8 && !h->g.padded) {
+        CK(cudaMemcpyAsync(dst, src, plane * h->g.nz * sizeof(double), cudaMemcpyHostToDevice,
+                           h->stream));
+        return AC_OK;
+    }
+    size_t np;
+    int rc = ensure_stage(h, &np);
+    if (rc) return rc;
+    for (size_t z0 = 0; z0 < (size_t)h->g.nz; z0 += np) {
+        const size_t nzc = (z0 + np <= (size_t)h->g.nz) ? np : (size_t)h->g.nz - z0;
+        CK(cudaMemcpyAsync(h->stage, src + z0 * plane, nzc * plane * sizeof(double),
+                           cudaMemcpyHostToDevice, h->stream));
+        CK(launch_scatter(h->stage, dst, es, h->g, (int)z0, (int)nzc, h->stream));
+        h->launches++;
+    }
+    return AC_OK;
+}
+
+static int store_array(ac_handle *h, const void *src, int es, double *dst) {
+    const size_t plane = (size_t)h->g.nx * h->g.ny;
+    if (es == 8 && !h->g.padded) {
+        CK(cudaMemcpyAsync(dst, src, plane * h->g.nz * sizeof(double), cudaMemcpyDeviceToHost,
+                           h->stream));
+        return AC_OK;
+    }
+    size_t np;
+    int rc = ensure_stage(h, &np);
+    if (rc) return rc;
+    for (size_t z0 = 0; z0 < (size_t)h->g.nz; z0 += np) {
+        const size_t nzc = (z0 + np <= (size_t)h->g.nz) ? np : (size_t)h->g.nz - z0;
+        CK(launch_gather(src, es, h->g, (int)z0, (int)nzc, h->stage, h->stream));
+        h->launches++;
+        CK(cudaMemcpyAsync(dst + z0 * plane, h->stage, nzc * plane * sizeof(double),
+                           cudaMemcpyDeviceToHost, h->stream));
+    }
+    return AC_OK;
+}
+
+static int load_common(ac_handle *h, int field, const double *src, int to_w) {
+    if (!h || !src || field < AC_ALL || field >= NF) return AC_ERR_ARG;
+    int rc = ensure_state(h);
+    if (rc) return rc;
+    const size_t n = (size_t)h->g.nx * h->g.ny * h->g.nz;
+    const int q0 = field == AC_ALL ? 0 : field, q1 = field == AC_ALL ? NF : field + 1;
+    for (int q = q0; q < q1; ++q) {
+        const double *s = src + (field == AC_ALL ? (size_t)q * n : 0);
+        rc = to_w ? load_array(h, h->w[q], h->elem_w, s)
+                  : load_array(h, h->state[h->cur][q], h->elem_f, s);
+        if (rc) return rc;
+    }
+    if (!to_w) h->next_s = 0;
+    return AC_OK;
+}
+
+static int store_common(ac_handle *h, int field, double *dst, int from_w) {
+    if (!h || !dst || field < AC_ALL || field >= NF) return AC_ERR_ARG;
+    int rc = ensure_state(h);
+    if (rc) return rc;
+    const size_t n = (size_t)h->g.nx * h->g.ny * h->g.nz;
+    const int q0 = field == AC_ALL ? 0 : field, q1 = field == AC_ALL ? NF : field + 1;
+    for (int q = q0; q < q1; ++q) {
+        double *d = dst + (field == AC_ALL ? (size_t)q * n : 0);
+        rc = from_w ? store_array(h, h->w[q], h->elem_w, d)
+                    : store_array(h, h->state[h->cur][q], h->elem_f, d);
+        if (rc) return rc;
+    }
+    CK(cudaStreamSynchronize(h->stream));
+    return AC_OK;
+}
+
+extern "C" int ac_load(ac_handle *h, int field, const double *src) {
+    return load_common(h, field, src, 0);
+}
+extern "C" int ac_store(ac_handle *h, int field, double *dst) {
+    return store_common(h, field, dst, 0);
+}
+extern "C" int ac_load_w(ac_handle *h, int field, const double *src) {
+    return load_common(h, field, src, 1);
+}
+extern "C" int ac_store_w(ac_handle *h, int field, double *dst) {
+    return store_common(h, field, dst, 1);
+}
+
+extern "C" int ac_periodic_halo(ac_handle *h) {
+    if (!h) return AC_ERR_ARG;
+    if (!h->g.padded) return AC_OK;
+    int rc = ensure_state(h);
+    if (rc) return rc;
+    CK(launch_halo(h->params.precision, h->g, h->state[h->cur], h->stream));
+    h->launches++;
+    return AC_OK;
+}
+
+// ---- forcing --------------------------------------------------------------
+
+static uint64_t splitmix64(uint64_t seed, uint64_t counter) {
+    // SplitMix64 (Steele, Lea, Flood 2014): n-th output of the stream seeded with `seed`.
+    uint64_t z = seed + (counter + 1u) * UINT64_C(0x9E3779B97F4A7C15);
+    z = (z ^ (z >> 30)) * UINT64_C(0xBF58476D1CE4E5B9);
+    z = (z ^ (z >> 27)) * UINT64_C(0x94D049BB133111EB);
+    return z ^ (z >> 31);
+}
+
+static double unit_double(uint64_t x) { return (double)(x >> 11) * (1.0 / 9007199254740992.0); }
+
+extern "C" int ac_forcing_draw(unsigned long long seed, unsigned long long step, int k[3],
+                               double e[3], double *phi) {
+    if (!k || !e || !phi) return AC_ERR_ARG;
+    // The shell 4 <= |k|^2 <= 9, enumerated with kx, ky, kz ascending from -3 to 3.
+    int shell[343][3];
+    int count = 0;
+    for (int a = -3; a <= 3; ++a)
+        for (int b = -3; b <= 3; ++b)
+            for (int c = -3; c <= 3; ++c) {
+                const int k2 = a * a + b * b + c * c;
+                if (k2 >= 4 && k2 <= 9) {
+                    shell[count][0] = a;
+                    shell[count][1] = b;
+                    shell[count][2] = c;
+                    ++count;
+                }
+            }
+    const uint64_t base = 16ull * step;
+    const int pick = (int)(splitmix64(seed, base) % (uint64_t)count);
+    const int ki[3] = {shell[pick][0], shell[pick][1], shell[pick][2]};
+    const double kk[3] = {(double)ki[0], (double)ki[1], (double)ki[2]};
+    const double k2 = kk[0] * kk[0] + kk[1] * kk[1] + kk[2] * kk[2];
+    // A helper vector not parallel to k: up to four uniform draws in the cube, else an axis.
+    double v[3] = {0.0, 0.0, 0.0};
+    int ok = 0;
+    for (int t = 0; t < 4 && !ok; ++t) {
+        double c[3];
+        for (int a = 0; a < 3; ++a)
+            c[a] = 2.0 * unit_double(splitmix64(seed, base + 1 + 3 * t + a)) - 1.0;
+        const double x0 = kk[1] * c[2] - kk[2] * c[1];
+        const double x1 = kk[2] * c[0] - kk[0] * c[2];
+        const double x2 = kk[0] * c[1] - kk[1] * c[0];
+        const double xx = x0 * x0 + x1 * x1 + x2 * x2;
+        const double cc = c[0] * c[0] + c[1] * c[1] + c[2] * c[2];
+        if (cc >= 1.0 / 16.0 && xx >= 0.25 * k2 * cc) {
+            v[0] = c[0];
+            v[1] = c[1];
+            v[2] = c[2];
+            ok = 1;
+        }
+    }
+    if (!ok) {
+        int best = 0;
+        for (int a = 1; a < 3; ++a)
+            if (abs(ki[a]) < abs(ki[best])) best = a;
+        v[best] = 1.0;
+    }
+    const double p0 = kk[1] * v[2] - kk[2] * v[1];
+    const double p1 = kk[2] * v[0] - kk[0] * v[2];
+    const double p2 = kk[0] * v[1] - kk[1] * v[0];
+    const double pn = sqrt(p0 * p0 + p1 * p1 + p2 * p2);
+    k[0] = ki[0];
+    k[1] = ki[1];
+    k[2] = ki[2];
+    e[0] = p0 / pn;
+    e[1] = p1 / pn;
+    e[2] = p2 / pn;
+    *phi = 6.283185307179586476925286766559 * unit_double(splitmix64(seed, base + 13));
+    return AC_OK;
+}
+
+extern "C" int ac_set_forcing(ac_handle *h, const int k[3], const double e[3], double phi) {
+    if (!h) return AC_ERR_ARG;
+    if (!k) {
+        h->force_manual = 0;
+        h->ftab_valid = 0;
+        return AC_OK;
+    }
+    if (!e || !isfinite(phi) || !isfinite(e[0]) || !isfinite(e[1]) || !isfinite(e[2]))
+        return AC_ERR_ARG;
+    h->force_manual = 1;
+    for (int a = 0; a < 3; ++a) {
+        h->force_k[a] = k[a];
+        h->force_e[a] = e[a];
+    }
+    h->force_phi = phi;
+    h->ftab_dirty = 1;
+    h->ftab_valid = 0;
+    return AC_OK;
+}
+
+extern "C" int ac_get_step(const ac_handle *h, unsigned long long *step, int *next_substep) {
+    if (!h) return AC_ERR_ARG;
+    if (step) *step = h->step;
+    if (next_substep) *next_substep = h->next_s;
+    return AC_OK;
+}
+
+extern "C" int ac_set_step(ac_handle *h, unsigned long long step, int next_substep) {
+    if (!h || next_substep < 0 || next_substep > 2) return AC_ERR_ARG;
+    h->step = step;
+    h->next_s = next_substep;
+    return AC_OK;
+}
+
+extern "C" int ac_launch_count(const ac_handle *h, unsigned long long *count) {
+    if (!h || !count) return AC_ERR_ARG;
+    *count = h->launches;
+    return AC_OK;
+}
+
+// ---- integration ------------------------------------------------------------
+
+extern "C" int ac_integrate_substep(ac_handle *h, double dt, int s) {
+    if (!h || s < 0 || s > 2 || !isfinite(dt)) return AC_ERR_ARG;
+    if (s != h->next_s) return AC_ERR_STATE;
+    int rc = ensure_state(h);
+    if (rc) return rc;
+    const int forcing = h->params.force_amp != 0.0;
+    if (forcing) {
+        // Per-step draw: (k, e, phi) stay fixed over the three substeps of a step.
+        if (!h->force_manual && (!h->ftab_valid || h->ftab_step != h->step)) {
+            ac_forcing_draw(h->params.seed, h->step, h->force_k, h->force_e, &h->force_phi);
+            h->ftab_step = h->step;
+            h->ftab_dirty = 1;
+        }
+        if (h->ftab_dirty || !h->ftab_valid) {
+            CK(launch_forcing_table(h->g, h->force_k, h->force_phi, h->ftab, h->stream));
+            h->launches++;
+            h->ftab_dirty = 0;
+            h->ftab_valid = 1;
+        }
+    }
+    if (h->g.padded) {
+        CK(launch_halo(h->params.precision, h->g, h->state[h->cur], h->stream));
+        h->launches++;
+    }
+    SubstepLaunch L;
+    L.precision = h->params.precision;
+    L.g = h->g;
+    for (int q = 0; q < NF; ++q) {
+        L.fin[q] = h->state[h->cur][q];
+        L.fout[q] = h->state[1 - h->cur][q];
+        L.w[q] = h->w[q];
+    }
+    L.c = h->coefs;
+    L.ph = h->phys;
+    L.force.on = forcing;
+    L.force.tab = h->ftab;
+    for (int a = 0; a < 3; ++a) L.force.amp_e[a] = h->params.force_amp * h->force_e[a];
+    L.alpha = RK_ALPHA[s];
+    L.beta = RK_BETA[s];
+    L.dt = dt;
+    L.s = s;
+    int nl = 0;
+    cudaError_t e;
+    if (h->params.precision == AC_FP64)
+        e = launch_substep_f64(L, h->stream, &nl);
+    else if (h->params.precision == AC_FP32)
+        e = launch_substep_f32(L, h->stream, &nl);
+    else
+        e = launch_substep_f32w64(L, h->stream, &nl);
+    h->launches += nl;
+    if (e != cudaSuccess) return cuda_fail(e);
+    h->cur = 1 - h->cur;
+    h->next_s = (s + 1) % 3;
+    if (s == 2) h->step++;
+    return AC_OK;
+}
+
+extern "C" int ac_integrate_step(ac_handle *h, double dt) {
+    if (!h || !isfinite(dt)) return AC_ERR_ARG;
+    if (h->next_s != 0) return AC_ERR_STATE;
+    for (int s = 0; s < 3; ++s) {
+        int rc = ac_integrate_substep(h, dt, s);
+        if (rc) return rc;
+    }
+    return AC_OK;
+}
+
+// ---- reductions -------------------------------------------------------------
+
+extern "C" int ac_reduce(ac_handle *h, int op, int quantity, double *out) {
+    if (!h || !out || op < AC_MAX || op > AC_RMS || quantity < 0 || quantity > AC_Q_CFL)
+        return AC_ERR_ARG;
+    int rc = ensure_state(h);
+    if (rc) return rc;
+    if (h->g.padded) {  // derived quantities read neighbours through the halo
+        CK(launch_halo(h->params.precision, h->g, h->state[h->cur], h->stream));
+        h->launches++;
+    }
+    ReduceLaunch L;
+    L.precision = h->params.precision;
+    L.g = h->g;
+    for (int q = 0; q < NF; ++q) L.f[q] = h->state[h->cur][q];
+    L.c = h->coefs;
+    L.ph = h->phys;
+    L.op = op;
+    L.quantity = quantity;
+    L.partials = h->partials;
+    L.flags = h->flags;
+    L.result = h->result_dev;
+    L.blocks = reduce_max_blocks();
+    int nl = 0;
+    cudaError_t e = launch_reduce(L, h->stream, &nl);
+    h->launches += nl;
+    if (e != cudaSuccess) return cuda_fail(e);
+    CK(cudaMemcpyAsync(h->result_host, h->result_dev, 2 * sizeof(double), cudaMemcpyDeviceToHost,
+                       h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    *out = h->result_host[0];
+    unsigned int flag;
+    memcpy(&flag, &h->result_host[1], sizeof flag);
+    return flag ? AC_ERR_NONFINITE : AC_OK;
+}

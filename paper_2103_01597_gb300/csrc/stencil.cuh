@@ -1,0 +1,273 @@
+// Device-side stencil machinery: cell indexing with the periodic map of
+// Sec. 3.3 or a radius-3 halo, the sixth-order operators on the point set of
+// Sec. 4 Eq. 13, and the fused RHS (Eqs. B.1-B.4) + Runge-Kutta update of one
+// cell.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "ac_internal.h"
+
+namespace ac {
+
+// Coefficients and constants in the kernel's arithmetic type R.
+template <typename R>
+struct DevCoefs {
+    R d1[3][3];
+    R d2[3][4];
+    R dc[3][3];
+    R nu, eta, nu3, two_nu;  // nu / 3, 2 nu
+    R inv_cp, cs2_ref, gamma_cp, gm1, cp_gm1;
+};
+
+template <typename R>
+inline DevCoefs<R> to_dev(const StencilCoefs &c, const PhysConsts &p) {
+    DevCoefs<R> d;
+    for (int a = 0; a < 3; ++a) {
+        for (int m = 0; m < 3; ++m) {
+            d.d1[a][m] = (R)c.d1[a][m];
+            d.dc[a][m] = (R)c.dc[a][m];
+        }
+        for (int m = 0; m < 4; ++m) d.d2[a][m] = (R)c.d2[a][m];
+    }
+    d.nu = (R)p.nu;
+    d.eta = (R)p.eta;
+    d.nu3 = (R)(p.nu / 3.0);
+    d.two_nu = (R)(2.0 * p.nu);
+    d.inv_cp = (R)p.inv_cp;
+    d.cs2_ref = (R)p.cs2_ref;
+    d.gamma_cp = (R)p.gamma_cp;
+    d.gm1 = (R)p.gm1;
+    d.cp_gm1 = (R)p.cp_gm1;
+    return d;
+}
+
+// Periodic wrap of an index that is at most 3 cells outside [0, n).
+__device__ __forceinline__ int wrap_near(int v, int n) {
+    // n >= 1; v in [-3, n + 2]
+    while (v < 0) v += n;
+    while (v >= n) v -= n;
+    return v;
+}
+
+// Cell addressing without a halo: every offset is wrapped (Sec. 3.3 map).
+struct IdxPeriodic {
+    int xo[7];
+    long long yo[7];
+    long long zo[7];
+    __device__ __forceinline__ void set_xy(int i, int j, const Geom &g) {
+#pragma unroll
+        for (int d = 0; d < 7; ++d) {
+            xo[d] = wrap_near(i + d - 3, g.nx);
+            yo[d] = (long long)wrap_near(j + d - 3, g.ny) * g.px;
+        }
+    }
+    __device__ __forceinline__ void set_z(int k, const Geom &g) {
+#pragma unroll
+        for (int d = 0; d < 7; ++d) zo[d] = (long long)wrap_near(k + d - 3, g.nz) * g.pxy;
+    }
+    __device__ __forceinline__ long long operator()(int dx, int dy, int dz) const {
+        return zo[dz + 3] + yo[dy + 3] + xo[dx + 3];
+    }
+};
+
+// Cell addressing inside a padded array whose halo holds the periodic images.
+struct IdxPadded {
+    long long c, base;
+    int px;
+    long long pxy;
+    __device__ __forceinline__ void set_xy(int i, int j, const Geom &g) {
+        px = g.px;
+        pxy = g.pxy;
+        base = g.origin + (long long)j * g.px + i;
+        c = base;
+    }
+    __device__ __forceinline__ void set_z(int k, const Geom &g) { c = base + (long long)k * pxy; }
+    __device__ __forceinline__ long long operator()(int dx, int dy, int dz) const {
+        return c + dz * pxy + (long long)dy * px + dx;
+    }
+};
+
+template <typename R>
+__device__ __forceinline__ R ldg(const R *p) { return __ldg(p); }
+
+// ---- sixth-order operators (r = 3) ---------------------------------------
+
+// First derivative along axis AX: sum_m d1[m-1] (f_m - f_-m).
+template <int AX, typename R, class IX>
+__device__ __forceinline__ R op_d1(const R *__restrict__ f, const IX &ix, const R (&c)[3]) {
+    constexpr int ox = AX == 0, oy = AX == 1, oz = AX == 2;
+    const R a1 = ldg(f + ix(ox, oy, oz)) - ldg(f + ix(-ox, -oy, -oz));
+    const R a2 = ldg(f + ix(2 * ox, 2 * oy, 2 * oz)) - ldg(f + ix(-2 * ox, -2 * oy, -2 * oz));
+    const R a3 = ldg(f + ix(3 * ox, 3 * oy, 3 * oz)) - ldg(f + ix(-3 * ox, -3 * oy, -3 * oz));
+    return c[0] * a1 + c[1] * a2 + c[2] * a3;
+}
+
+// Second derivative along axis AX: d2[0] f_0 + sum_m d2[m] (f_m + f_-m).
+template <int AX, typename R, class IX>
+__device__ __forceinline__ R op_d2(const R *__restrict__ f, const IX &ix, R f0, const R (&c)[4]) {
+    constexpr int ox = AX == 0, oy = AX == 1, oz = AX == 2;
+    const R s1 = ldg(f + ix(ox, oy, oz)) + ldg(f + ix(-ox, -oy, -oz));
+    const R s2 = ldg(f + ix(2 * ox, 2 * oy, 2 * oz)) + ldg(f + ix(-2 * ox, -2 * oy, -2 * oz));
+    const R s3 = ldg(f + ix(3 * ox, 3 * oy, 3 * oz)) + ldg(f + ix(-3 * ox, -3 * oy, -3 * oz));
+    return c[0] * f0 + c[1] * s1 + c[2] * s2 + c[3] * s3;
+}
+
+// Mixed derivative in the plane of axes A < B from the face diagonals of Eq. 13:
+// sum_m dc[m-1] S_m, S_m = f(+m,+m) + f(-m,-m) - f(+m,-m) - f(-m,+m).
+template <int A, int B, typename R, class IX>
+__device__ __forceinline__ R op_dab(const R *__restrict__ f, const IX &ix, const R (&c)[3]) {
+    constexpr int ax = A == 0, ay = A == 1, az = A == 2;
+    constexpr int bx = B == 0, by = B == 1, bz = B == 2;
+    R S[3];
+#pragma unroll
+    for (int m = 1; m <= 3; ++m) {
+        const R pp = ldg(f + ix(m * (ax + bx), m * (ay + by), m * (az + bz)));
+        const R mm = ldg(f + ix(-m * (ax + bx), -m * (ay + by), -m * (az + bz)));
+        const R pm = ldg(f + ix(m * (ax - bx), m * (ay - by), m * (az - bz)));
+        const R mp = ldg(f + ix(-m * (ax - bx), -m * (ay - by), -m * (az - bz)));
+        S[m - 1] = (pp + mm) - (pm + mp);
+    }
+    return c[0] * S[0] + c[1] * S[1] + c[2] * S[2];
+}
+
+// Plane index of the axis pair (a, b): xy -> 0, xz -> 1, yz -> 2.
+template <int A, int B>
+struct Plane {
+    static constexpr int lo = A < B ? A : B;
+    static constexpr int hi = A < B ? B : A;
+    static constexpr int id = lo == 0 ? (hi == 1 ? 0 : 1) : 2;
+};
+
+// Second derivatives of one vector component V_C: its Laplacian, the pure
+// derivative along its own axis (d_CC V_C) and the two mixed derivatives
+// d_C d_b V_C (b != C) that enter grad(div V).
+template <int C, typename R, class IX>
+__device__ __forceinline__ void component_second(const R *__restrict__ f, const IX &ix, R f0,
+                                                 const DevCoefs<R> &k, R &lap, R &dcc,
+                                                 R &cross_b1, R &cross_b2) {
+    const R dxx = op_d2<0>(f, ix, f0, k.d2[0]);
+    const R dyy = op_d2<1>(f, ix, f0, k.d2[1]);
+    const R dzz = op_d2<2>(f, ix, f0, k.d2[2]);
+    lap = dxx + dyy + dzz;
+    constexpr int B1 = C == 0 ? 1 : 0;
+    constexpr int B2 = C == 2 ? 1 : 2;
+    dcc = C == 0 ? dxx : (C == 1 ? dyy : dzz);
+    cross_b1 = op_dab<(C < B1 ? C : B1), (C < B1 ? B1 : C)>(f, ix, k.dc[Plane<C, B1>::id]);
+    cross_b2 = op_dab<(C < B2 ? C : B2), (C < B2 ? B2 : C)>(f, ix, k.dc[Plane<C, B2>::id]);
+}
+
+template <typename R> __device__ __forceinline__ R dev_exp(R x);
+template <> __device__ __forceinline__ double dev_exp<double>(double x) { return exp(x); }
+template <> __device__ __forceinline__ float dev_exp<float>(float x) { return expf(x); }
+
+// RHS of Eqs. B.1-B.4 at one cell (mu0 = 1, zeta = H = C = K = 0), with the
+// forcing term `frc` added to du/dt.  Output order: Table B.1.
+template <typename R, class IX>
+__device__ __forceinline__ void cell_rhs(const R *const __restrict__ *f, const IX &ix,
+                                         const DevCoefs<R> &k, const R frc[3], R out[NF]) {
+    const long long c0 = ix(0, 0, 0);
+    const R lnrho = ldg(f[0] + c0);
+    const R u[3] = {ldg(f[1] + c0), ldg(f[2] + c0), ldg(f[3] + c0)};
+    const R ss = ldg(f[4] + c0);
+    const R aa[3] = {ldg(f[5] + c0), ldg(f[6] + c0), ldg(f[7] + c0)};
+
+    // First derivatives.
+    R gl[3], gs[3], gu[3][3], ga[3][3];
+    gl[0] = op_d1<0>(f[0], ix, k.d1[0]);
+    gl[1] = op_d1<1>(f[0], ix, k.d1[1]);
+    gl[2] = op_d1<2>(f[0], ix, k.d1[2]);
+    gs[0] = op_d1<0>(f[4], ix, k.d1[0]);
+    gs[1] = op_d1<1>(f[4], ix, k.d1[1]);
+    gs[2] = op_d1<2>(f[4], ix, k.d1[2]);
+#pragma unroll
+    for (int m = 0; m < 3; ++m) {
+        gu[m][0] = op_d1<0>(f[1 + m], ix, k.d1[0]);
+        gu[m][1] = op_d1<1>(f[1 + m], ix, k.d1[1]);
+        gu[m][2] = op_d1<2>(f[1 + m], ix, k.d1[2]);
+        ga[m][0] = op_d1<0>(f[5 + m], ix, k.d1[0]);
+        ga[m][1] = op_d1<1>(f[5 + m], ix, k.d1[1]);
+        ga[m][2] = op_d1<2>(f[5 + m], ix, k.d1[2]);
+    }
+
+    // Second derivatives: Laplacians and grad(div .) of u and A.
+    R lapu[3], lapa[3], gdu[3], gda[3];
+    {
+        R dcc, c1, c2;
+        component_second<0>(f[1], ix, u[0], k, lapu[0], dcc, c1, c2);  // c1 = d_xy u_x, c2 = d_xz u_x
+        gdu[0] = dcc;
+        gdu[1] = c1;
+        gdu[2] = c2;
+        component_second<1>(f[2], ix, u[1], k, lapu[1], dcc, c1, c2);  // c1 = d_xy u_y, c2 = d_yz u_y
+        gdu[0] += c1;
+        gdu[1] += dcc;
+        gdu[2] += c2;
+        component_second<2>(f[3], ix, u[2], k, lapu[2], dcc, c1, c2);  // c1 = d_xz u_z, c2 = d_yz u_z
+        gdu[0] += c1;
+        gdu[1] += c2;
+        gdu[2] += dcc;
+    }
+    {
+        R dcc, c1, c2;
+        component_second<0>(f[5], ix, aa[0], k, lapa[0], dcc, c1, c2);
+        gda[0] = dcc;
+        gda[1] = c1;
+        gda[2] = c2;
+        component_second<1>(f[6], ix, aa[1], k, lapa[1], dcc, c1, c2);
+        gda[0] += c1;
+        gda[1] += dcc;
+        gda[2] += c2;
+        component_second<2>(f[7], ix, aa[2], k, lapa[2], dcc, c1, c2);
+        gda[0] += c1;
+        gda[1] += c2;
+        gda[2] += dcc;
+    }
+
+    // Thermodynamics: c_s^2 = c_s0^2 exp(gamma s / c_p + (gamma-1)(ln rho - ln rho0)),
+    // 1/rho = exp(-ln rho), 1/T = c_p (gamma - 1) / c_s^2.
+    const R rho_inv = dev_exp<R>(-lnrho);
+    const R cs2 = k.cs2_ref * dev_exp<R>(k.gamma_cp * ss + k.gm1 * lnrho);
+    const R inv_T = k.cp_gm1 / cs2;
+
+    const R divu = gu[0][0] + gu[1][1] + gu[2][2];
+    const R third_div = divu * (R)(1.0 / 3.0);
+
+    // B = curl A, j = grad(div A) - lap A.
+    const R B[3] = {ga[2][1] - ga[1][2], ga[0][2] - ga[2][0], ga[1][0] - ga[0][1]};
+    const R J[3] = {gda[0] - lapa[0], gda[1] - lapa[1], gda[2] - lapa[2]};
+
+    // Traceless rate of strain S.
+    const R Sxx = gu[0][0] - third_div, Syy = gu[1][1] - third_div, Szz = gu[2][2] - third_div;
+    const R Sxy = (R)0.5 * (gu[0][1] + gu[1][0]);
+    const R Sxz = (R)0.5 * (gu[0][2] + gu[2][0]);
+    const R Syz = (R)0.5 * (gu[1][2] + gu[2][1]);
+    const R SS2 = Sxx * Sxx + Syy * Syy + Szz * Szz + (R)2 * (Sxy * Sxy + Sxz * Sxz + Syz * Syz);
+    const R SG[3] = {Sxx * gl[0] + Sxy * gl[1] + Sxz * gl[2],
+                     Sxy * gl[0] + Syy * gl[1] + Syz * gl[2],
+                     Sxz * gl[0] + Syz * gl[1] + Szz * gl[2]};
+
+    const R JxB[3] = {J[1] * B[2] - J[2] * B[1], J[2] * B[0] - J[0] * B[2],
+                      J[0] * B[1] - J[1] * B[0]};
+    const R UxB[3] = {u[1] * B[2] - u[2] * B[1], u[2] * B[0] - u[0] * B[2],
+                      u[0] * B[1] - u[1] * B[0]};
+    const R J2 = J[0] * J[0] + J[1] * J[1] + J[2] * J[2];
+
+    // Eq. B.1
+    out[0] = -(u[0] * gl[0] + u[1] * gl[1] + u[2] * gl[2]) - divu;
+    // Eq. B.2
+#pragma unroll
+    for (int m = 0; m < 3; ++m) {
+        const R adv = u[0] * gu[m][0] + u[1] * gu[m][1] + u[2] * gu[m][2];
+        const R press = cs2 * (gs[m] * k.inv_cp + gl[m]);
+        const R visc = k.nu * lapu[m] + k.nu3 * gdu[m] + k.two_nu * SG[m];
+        out[1 + m] = (visc - adv) - press + JxB[m] * rho_inv + frc[m];
+    }
+    // Eq. B.3: Ds/Dt = (eta j^2 + 2 rho nu S:S) / (rho T)
+    out[4] = -(u[0] * gs[0] + u[1] * gs[1] + u[2] * gs[2])
+           + (k.eta * J2 * rho_inv + k.two_nu * SS2) * inv_T;
+    // Eq. B.4
+#pragma unroll
+    for (int m = 0; m < 3; ++m) out[5 + m] = UxB[m] + k.eta * lapa[m];
+}
+
+}  // namespace ac

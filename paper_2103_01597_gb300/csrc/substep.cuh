@@ -1,0 +1,113 @@
+// Fused RHS + Runge-Kutta substep kernel (one pass over the grid), templated
+// on the field type R, the accumulator type W and the addressing IX.
+#pragma once
+
+#include "stencil.cuh"
+
+namespace ac {
+
+template <typename R> struct Vec2;
+template <> struct Vec2<double> { using type = double2; };
+template <> struct Vec2<float> { using type = float2; };
+
+template <typename R, typename W>
+struct SubstepArgs {
+    Geom g;
+    const R *fin[NF];
+    R *fout[NF];
+    W *w[NF];
+    DevCoefs<R> k;
+    W alpha, beta, dt;
+    int s0;      // substep 0: w is not read
+    int zchunk;  // cells along z per thread
+    int force_on;
+    const typename Vec2<R>::type *ftab;  // e^{i theta_x}, e^{i theta_y}, e^{i (theta_z + phi)}
+    R amp_e[3];
+};
+
+// Williamson 2N-storage update of one field at one cell:
+// w <- alpha w + dt rhs (w not read when s0), f_out <- f_in + beta w.
+template <typename R, typename W>
+__device__ __forceinline__ void rk_update(const SubstepArgs<R, W> &a, int q, long long o, R rhs) {
+    W wn = a.dt * (W)rhs;
+    if (!a.s0) wn = a.alpha * a.w[q][o] + wn;
+    a.w[q][o] = wn;
+    a.fout[q][o] = (R)((W)ldg(a.fin[q] + o) + a.beta * wn);
+}
+
+template <typename R, typename W, class IX>
+__global__ void __launch_bounds__(128) substep_kernel(const SubstepArgs<R, W> a) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y * blockDim.y + threadIdx.y;
+    if (i >= a.g.nx || j >= a.g.ny) return;
+    const int k0 = blockIdx.z * a.zchunk;
+    const int k1 = min(k0 + a.zchunk, a.g.nz);
+    using V2 = typename Vec2<R>::type;
+    IX ix;
+    ix.set_xy(i, j, a.g);
+    // Forcing phase factor of this (x, y) column: e^{i (theta_x + theta_y)}.
+    V2 exy = {(R)0, (R)0};
+    if (a.force_on) {
+        const V2 ex = a.ftab[i], ey = a.ftab[a.g.nx + j];
+        exy.x = ex.x * ey.x - ex.y * ey.y;
+        exy.y = ex.x * ey.y + ex.y * ey.x;
+    }
+    for (int kk = k0; kk < k1; ++kk) {
+        ix.set_z(kk, a.g);
+        R frc[3] = {(R)0, (R)0, (R)0};
+        if (a.force_on) {
+            const V2 ez = a.ftab[a.g.nx + a.g.ny + kk];
+            const R cph = exy.x * ez.x - exy.y * ez.y;  // cos(k . x + phi)
+            frc[0] = a.amp_e[0] * cph;
+            frc[1] = a.amp_e[1] * cph;
+            frc[2] = a.amp_e[2] * cph;
+        }
+        R rhs[NF];
+        cell_rhs<R>(a.fin, ix, a.k, frc, rhs);
+        const long long o = ix(0, 0, 0);
+#pragma unroll
+        for (int q = 0; q < NF; ++q) rk_update(a, q, o, rhs[q]);
+    }
+}
+
+template <typename R, typename W>
+cudaError_t launch_substep_t(const SubstepLaunch &L, cudaStream_t st, int *launches) {
+    SubstepArgs<R, W> a;
+    a.g = L.g;
+    for (int q = 0; q < NF; ++q) {
+        a.fin[q] = static_cast<const R *>(L.fin[q]);
+        a.fout[q] = static_cast<R *>(L.fout[q]);
+        a.w[q] = static_cast<W *>(L.w[q]);
+    }
+    a.k = to_dev<R>(L.c, L.ph);
+    a.alpha = (W)L.alpha;
+    a.beta = (W)L.beta;
+    a.dt = (W)L.dt;
+    a.s0 = L.s == 0;
+    a.force_on = L.force.on;
+    // The table block holds nx+ny+nz double2 entries followed by the same count of float2.
+    const long long ntab = (long long)L.g.nx + L.g.ny + L.g.nz;
+    if (sizeof(R) == 8)
+        a.ftab = reinterpret_cast<const typename Vec2<R>::type *>(L.force.tab);
+    else
+        a.ftab = reinterpret_cast<const typename Vec2<R>::type *>(L.force.tab + ntab);
+    for (int m = 0; m < 3; ++m) a.amp_e[m] = (R)L.force.amp_e[m];
+
+    const dim3 block(32, 4, 1);
+    const unsigned gx = (L.g.nx + block.x - 1) / block.x;
+    const unsigned gy = (L.g.ny + block.y - 1) / block.y;
+    // Enough z-slices for several waves of CTAs over 152 SMs, up to 16 cells per thread.
+    const long long xy_blocks = (long long)gx * gy;
+    int zchunk = (int)((xy_blocks * L.g.nz) / (8 * 152));
+    zchunk = zchunk < 1 ? 1 : (zchunk > 16 ? 16 : zchunk);
+    a.zchunk = zchunk;
+    const dim3 grid(gx, gy, (L.g.nz + zchunk - 1) / zchunk);
+    if (L.g.padded)
+        substep_kernel<R, W, IdxPadded><<<grid, block, 0, st>>>(a);
+    else
+        substep_kernel<R, W, IdxPeriodic><<<grid, block, 0, st>>>(a);
+    ++*launches;
+    return cudaGetLastError();
+}
+
+}  // namespace ac

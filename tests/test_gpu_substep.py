@@ -1,0 +1,289 @@
+"""GPU parity of the fused RK3 substep (through the C ABI) against the FP64 oracle.
+
+Tolerances:
+  * FP64: 1e-12 relative per field in the max norm (max|g - o| / max|o|), the
+    bound the method is held to; summation order and FMA contraction differ
+    between the kernel and the oracle, so results are not bitwise equal.
+  * FP32: f within 2e-6 and w within 2e-4 relative per field (see the design
+    notes: binary32 rounding of the stencil sums, amplified by the 1/dx^2 of the
+    second derivatives, on inputs already rounded to binary32).
+  * Shift equivariance and load/store round trips: bitwise.
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+from oracle import core
+from paper_2103_01597_gb300 import ac, build, synthetic
+
+from gpu_util import rel_err, sample_cells, ulp_err
+
+pytestmark = pytest.mark.gpu
+
+PHYS = dict(nu=5e-3, eta=5e-3, cs0=1.0, gamma=5.0 / 3.0, cp=1.0, lnrho0=0.0)
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    build.build()
+    ac.load_library()
+    torch.cuda.init()
+
+
+def _state(n, seed, amp=0.2):
+    f = synthetic.smooth_state(n, seed, amp=amp)
+    f += synthetic.noise_state(n, seed + 100, sigma=1e-3)
+    f[0] += 0.1 * synthetic.uniform_state(n, seed + 200)[0]
+    return f
+
+
+def _sim(n, L=(2 * math.pi,) * 3, precision=ac.AC_FP64, layout=ac.AC_LAYOUT_PERIODIC,
+         force_amp=0.0, seed=0, **phys):
+    kw = dict(PHYS)
+    kw.update(phys)
+    return ac.Simulation(n, L=L, layout=layout, precision=precision, force_amp=force_amp,
+                         seed=seed, **kw)
+
+
+def _oracle_params(n, L=(2 * math.pi,) * 3, forcing=None, **phys):
+    kw = dict(PHYS)
+    kw.update(phys)
+    return core.Params(n=n, L=L, forcing=forcing, **kw)
+
+
+SIZES = [(8, 8, 8), (16, 16, 16), (32, 32, 32), (8, 16, 24), (37, 21, 13), (5, 3, 7), (1, 12, 10)]
+
+
+@pytest.mark.parametrize("layout", [ac.AC_LAYOUT_PERIODIC, ac.AC_LAYOUT_PADDED])
+@pytest.mark.parametrize("n", SIZES)
+def test_fp64_substeps_match_oracle(n, layout):
+    L = (2 * math.pi, 3.0, 5.5)
+    phys = dict(nu=2e-2, eta=3e-2, cs0=1.1, gamma=1.4, cp=1.3, lnrho0=0.2)
+    sim = _sim(n, L=L, layout=layout, force_amp=0.05, seed=2, **phys)
+    f = _state(n, seed=sum(n) + layout)
+    sim.load(f)
+    dt = 1e-3
+    w = None
+    for s in range(3):
+        k, e, phi = ac.ac_forcing_draw(2, 0)
+        p = _oracle_params(n, L=L, forcing=core.Forcing(k, e, phi, 0.05), **phys)
+        fo, wo = core.substep(f, w, p, dt, s)
+        sim.substep(dt, s)
+        fg, wg = sim.store(), sim.store_w()
+        assert np.all(rel_err(fg, fo) <= 1e-12), (s, rel_err(fg, fo))
+        assert np.all(rel_err(wg, wo) <= 1e-12), (s, rel_err(wg, wo))
+        f, w = fg, wg  # next substep starts from the GPU's own state
+    sim.close()
+
+
+def test_fp64_step_config_32cube():
+    """One full step of the 32^3 configuration: noise of amplitude 1e-5 on u and
+    A, ln rho = s = 0, dt = 1e-3 (seeded)."""
+    n = (32, 32, 32)
+    sim = _sim(n)
+    f = synthetic.noise_state(n, seed=1)
+    sim.load(f)
+    sim.step(1e-3)
+    g = sim.store()
+    o = core.step(f, _oracle_params(n), 1e-3)
+    err = rel_err(g, o)
+    assert np.all(err <= 1e-12), err
+    # the paper's ulp metric on the O(1e-5) fields u, A (informational bound)
+    assert np.max(ulp_err(g[1:4], o[1:4])) < 64
+    assert sim.reduce(ac.AC_MAX, ac.AC_Q_UMAG) > 0
+    sim.close()
+
+
+def test_shift_equivariance_bitwise():
+    n = (24, 20, 18)
+    f = _state(n, seed=4)
+    shift = (5, 7, 3)
+    out = []
+    for sh in [(0, 0, 0), shift]:
+        sim = _sim(n)
+        sim.load(np.roll(f, shift=(sh[2], sh[1], sh[0]), axis=(1, 2, 3)))
+        sim.step(2e-3)
+        out.append(sim.store())
+        sim.close()
+    assert np.array_equal(np.roll(out[0], shift=(shift[2], shift[1], shift[0]), axis=(1, 2, 3)),
+                          out[1])
+
+
+def test_layouts_agree_bitwise():
+    n = (20, 12, 9)
+    f = _state(n, seed=8)
+    res = []
+    for layout in (ac.AC_LAYOUT_PERIODIC, ac.AC_LAYOUT_PADDED):
+        sim = _sim(n, layout=layout, force_amp=0.05, seed=5)
+        sim.load(f)
+        sim.step(1e-3)
+        res.append(sim.store())
+        sim.close()
+    assert np.array_equal(res[0], res[1])
+
+
+@pytest.mark.parametrize("precision,ftol,wtol", [(ac.AC_FP32, 2e-6, 2e-4),
+                                                  (ac.AC_FP32_W64, 2e-6, 2e-4)])
+def test_fp32_within_bound(precision, ftol, wtol):
+    n = (32, 24, 16)
+    sim = _sim(n, precision=precision, force_amp=0.05, seed=3)
+    f = _state(n, seed=12)
+    f32 = f.astype(np.float32).astype(np.float64)  # the device rounds the input to binary32
+    sim.load(f)
+    dt = 1e-3
+    w = None
+    fcur = f32
+    for s in range(3):
+        k, e, phi = ac.ac_forcing_draw(3, 0)
+        p = _oracle_params(n, forcing=core.Forcing(k, e, phi, 0.05))
+        fo, wo = core.substep(fcur, w, p, dt, s)
+        sim.substep(dt, s)
+        fg, wg = sim.store(), sim.store_w()
+        assert np.all(rel_err(fg, fo) <= ftol), (s, rel_err(fg, fo))
+        assert np.all(rel_err(wg, wo) <= wtol), (s, rel_err(wg, wo))
+        fcur, w = fg, wg
+    sim.close()
+
+
+def test_halo_fill_bitwise():
+    n = (11, 6, 9)
+    for precision in (ac.AC_FP64, ac.AC_FP32):
+        sim = _sim(n, layout=ac.AC_LAYOUT_PADDED, precision=precision)
+        f = _state(n, seed=2)
+        sim.load(f)
+        ac.ac_periodic_halo(sim.h)
+        torch.cuda.synchronize()
+        m = (n[2] + 6, n[1] + 6, n[0] + 6)
+        got = sim.state[0, :, :sim.elems].double().cpu().numpy().reshape((8,) + m)
+        for q in range(8):
+            interior = f[q].astype(np.float32).astype(np.float64) if precision else f[q]
+            assert np.array_equal(got[q], np.pad(interior, 3, mode="wrap"))
+        sim.close()
+
+
+def test_load_store_roundtrip():
+    n = (9, 7, 5)
+    f = _state(n, seed=6)
+    for precision in (ac.AC_FP64, ac.AC_FP32, ac.AC_FP32_W64):
+        for layout in (ac.AC_LAYOUT_PERIODIC, ac.AC_LAYOUT_PADDED):
+            sim = _sim(n, precision=precision, layout=layout)
+            sim.load(f)
+            sim.load_w(2 * f)
+            g, w = sim.store(), sim.store_w()
+            exp = f if precision == ac.AC_FP64 else f.astype(np.float32).astype(np.float64)
+            expw = 2 * f if precision != ac.AC_FP32 else (2 * f).astype(np.float32).astype(np.float64)
+            assert np.array_equal(g, exp) and np.array_equal(w, expw)
+            sim.close()
+
+
+def test_reductions_match_oracle():
+    n = (20, 16, 12)
+    sim = _sim(n)
+    f = _state(n, seed=9)
+    sim.load(f)
+    p = _oracle_params(n)
+    qmap = {ac.AC_Q_UMAG: "umag", ac.AC_Q_EKIN: "ekin", ac.AC_Q_EMAG: "emag", ac.AC_Q_CFL: "cfl"}
+    for quantity in list(range(8)) + list(qmap):
+        oq = qmap.get(quantity, quantity)
+        for op, oname in [(ac.AC_MAX, "max"), (ac.AC_MIN, "min"), (ac.AC_SUM, "sum"),
+                          (ac.AC_RMS, "rms")]:
+            g = sim.reduce(op, quantity)
+            o = core.reduce(f, p, oname, oq)
+            scale = np.sum(np.abs(core.quantity(f, p, oq))) if oname == "sum" else abs(o)
+            assert abs(g - o) <= 1e-12 * max(scale, 1e-300), (quantity, oname, g, o)
+    sim.close()
+
+
+def test_error_paths():
+    n = (8, 8, 8)
+    sim = _sim(n)
+    sim.load(_state(n, seed=1))
+    with pytest.raises(ac.AcError) as ei:
+        sim.substep(1e-3, 1)
+    assert ei.value.code == ac.AC_ERR_STATE
+    with pytest.raises(ac.AcError) as ei:
+        sim.substep(float("nan"), 0)
+    assert ei.value.code == ac.AC_ERR_ARG
+    sim.substep(1e-3, 0)
+    with pytest.raises(ac.AcError):
+        ac.ac_integrate_step(sim.h, 1e-3)  # mid-step
+    sim.substep(1e-3, 1)
+    sim.substep(1e-3, 2)
+    assert ac.ac_get_step(sim.h) == (1, 0)
+    bad = _state(n, seed=1)
+    bad[3][2, 2, 2] = np.nan
+    sim.load(bad)
+    with pytest.raises(ac.AcError) as ei:
+        sim.reduce(ac.AC_MAX, ac.AC_UZ)
+    assert ei.value.code == ac.AC_ERR_NONFINITE
+    assert ac.ac_launch_count(sim.h) > 0
+    sim.close()
+
+
+def test_nan_in_w_not_read_at_s0():
+    n = (8, 8, 8)
+    sim = _sim(n)
+    f = _state(n, seed=3)
+    sim.load(f)
+    sim.load_w(np.full_like(f, np.nan))
+    sim.substep(1e-3, 0)
+    assert np.all(np.isfinite(sim.store())) and np.all(np.isfinite(sim.store_w()))
+    sim.close()
+
+
+def test_checkpoint_resume_bitwise():
+    """Stop after substep 0 of the second step, store f and w, resume in a new
+    handle: the result after four steps equals the uninterrupted run bitwise."""
+    n = (16, 12, 10)
+    f = _state(n, seed=21)
+    ref = _sim(n, force_amp=0.05, seed=9)
+    ref.load(f)
+    for _ in range(4):
+        ref.step(1e-3)
+    out_ref = ref.store()
+    ref.close()
+    a = _sim(n, force_amp=0.05, seed=9)
+    a.load(f)
+    a.step(1e-3)
+    a.substep(1e-3, 0)
+    ck_f, ck_w = a.store(), a.store_w()
+    step, ns = ac.ac_get_step(a.h)
+    assert (step, ns) == (1, 1)
+    a.close()
+    b = _sim(n, force_amp=0.05, seed=9)
+    b.load(ck_f)
+    b.load_w(ck_w)
+    ac.ac_set_step(b.h, step, ns)
+    b.substep(1e-3, 1)
+    b.substep(1e-3, 2)
+    for _ in range(2):
+        b.step(1e-3)
+    assert np.array_equal(b.store(), out_ref)
+    b.close()
+
+
+@pytest.mark.parametrize("precision", [ac.AC_FP64])
+def test_full_size_256_sampled(precision):
+    """256^3 forced FP64, the timed configuration: every substep of one step at
+    sampled cells (random, corners and boundary layers) against the oracle."""
+    n = (256, 256, 256)
+    sim = _sim(n, precision=precision, force_amp=0.05, seed=2)
+    f = synthetic.noise_state(n, seed=2)
+    sim.load(f)
+    cells = sample_cells(n, 3000, seed=7)
+    w = None
+    k, e, phi = ac.ac_forcing_draw(2, 0)
+    p = _oracle_params(n, forcing=core.Forcing(k, e, phi, 0.05))
+    for s in range(3):
+        fo, wo = core.substep_cells(f, w, p, 1e-3, s, cells)
+        sim.substep(1e-3, s)
+        fg, wg = sim.store(), sim.store_w()
+        idx = (cells[:, 2], cells[:, 1], cells[:, 0])
+        gs = np.stack([fg[q][idx] for q in range(8)])
+        ws = np.stack([wg[q][idx] for q in range(8)])
+        assert np.all(rel_err(gs, fo) <= 1e-12), (s, rel_err(gs, fo))
+        assert np.all(rel_err(ws, wo) <= 1e-12), (s, rel_err(ws, wo))
+        f, w = fg, wg
+    sim.close()
