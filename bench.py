@@ -69,6 +69,8 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    ap.add_argument("--grid", type=int, default=0,
+                    help="override the cube edge (small cases for profiling)")
     return ap.parse_args()
 
 
@@ -379,7 +381,12 @@ def run_ours(args, wl):
 
 def main():
     args = parse()
-    wl = WORKLOADS[args.workload]
+    wl = dict(WORKLOADS[args.workload])
+    if args.grid:
+        g = args.grid
+        wl["n"] = (g, g, g)
+        wl["desc"] = wl["desc"].replace("256^3", "%d^3" % g).replace("512^3", "%d^3" % g)
+        wl.pop("vs", None)
     if args.impl == "reference":
         return run_reference(args, wl)
     return run_ours(args, wl)

@@ -90,10 +90,26 @@ def test_fp64_step_config_32cube():
     o = core.step(f, _oracle_params(n), 1e-3)
     err = rel_err(g, o)
     assert np.all(err <= 1e-12), err
-    # the paper's ulp metric on the O(1e-5) fields u, A (informational bound)
-    assert np.max(ulp_err(g[1:4], o[1:4])) < 64
     assert sim.reduce(ac.AC_MAX, ac.AC_Q_UMAG) > 0
     sim.close()
+
+
+def test_paper_ulp_metric_uniform_fields():
+    """The paper's own check (Sec. 5, Eqs. 14-15): one step from fields uniform
+    in [0, 1) with dt = 1.19209e-7, error against the CPU solver in ulps.  The
+    paper's solver pair had the same rounding order and met 2 ulp; here the
+    kernel fuses f + beta w into one FMA while the oracle rounds twice, which
+    differs by up to 1 ulp of the intermediate per substep, so 3 ulp over a step,
+    and 6 ulp of the final value when it falls into the next lower binade."""
+    n = (48, 40, 32)
+    sim = _sim(n)
+    f = synthetic.uniform_state(n, seed=0)
+    sim.load(f)
+    sim.step(1.19209e-7)
+    g = sim.store()
+    sim.close()
+    o = core.step(f, _oracle_params(n), 1.19209e-7)
+    assert np.max(ulp_err(g, o)) <= 6.0, np.max(ulp_err(g, o))
 
 
 def test_shift_equivariance_bitwise():
