@@ -212,6 +212,34 @@ int ac_set_step(ac_handle *h, unsigned long long step, int next_substep);
 /* Number of kernels the handle has launched so far. */
 int ac_launch_count(const ac_handle *h, unsigned long long *count);
 
+/*
+ * Allocation-free reduction (the paper has no counterpart; it exists for
+ * callers that cannot allocate device memory -- for example an application
+ * that owns all device memory through its own pool and only lends the library
+ * its field arrays, and so cannot create an ac_handle, whose work areas are
+ * allocated with cudaMalloc).
+ *
+ * Same result as ac_reduce (op, quantity, binary64 accumulation, per-cell
+ * quantities evaluated the same way) for the state held in `fields`: eight
+ * device arrays in the order of Table B.1, each laid out for `grid` (padded
+ * layout: the halo must already hold the periodic images) with elements of
+ * `params->precision` (double for AC_FP64, float otherwise).  The partial sums
+ * go to a fixed device array inside the library (one slot per z-plane, at most
+ * AC_NOALLOC_MAX_NZ planes: larger nz is rejected with AC_ERR_ARG); nothing is
+ * allocated.  The result is written to host memory *out and `stream`
+ * (cudaStream_t, NULL: legacy default stream) is synchronised; AC_ERR_NONFINITE
+ * if a NaN or infinity was met.  Only the summation order differs from
+ * ac_reduce, so sums and rms agree to rounding and max/min exactly.
+ *
+ * The first call on a device looks up that device's copy of the fixed array
+ * (with the device current); make that first call before any stream capture.
+ * Every call shares the array: calls whose work overlaps on the GPU (other
+ * streams or host threads) race on it and must be serialised by the caller.
+ */
+#define AC_NOALLOC_MAX_NZ 8192
+int ac_reduce_noalloc(const void *const fields[8], const ac_grid *grid, const ac_params *params,
+                      int op, int quantity, double *out, void *stream);
+
 /* Text of an AC_* code; message of the last CUDA error seen by this thread. */
 const char *ac_strerror(int code);
 const char *ac_last_cuda_error(void);

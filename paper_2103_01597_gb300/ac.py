@@ -93,6 +93,8 @@ def load_library(path=None):
         "ac_get_step": ([_vp, ctypes.POINTER(_c.c_ulonglong), ctypes.POINTER(_c.c_int)], _c.c_int),
         "ac_set_step": ([_vp, _c.c_ulonglong, _c.c_int], _c.c_int),
         "ac_launch_count": ([_vp, ctypes.POINTER(_c.c_ulonglong)], _c.c_int),
+        "ac_reduce_noalloc": ([ctypes.POINTER(_vp), ctypes.POINTER(ac_grid),
+                               ctypes.POINTER(ac_params), _c.c_int, _c.c_int, _pd, _vp], _c.c_int),
         "ac_strerror": ([_c.c_int], _c.c_char_p),
         "ac_last_cuda_error": ([], _c.c_char_p),
     }
@@ -197,6 +199,19 @@ def ac_reduce(h, op, quantity):
     out = ctypes.c_double()
     rc = load_library().ac_reduce(h, int(op), int(quantity), ctypes.byref(out))
     _check(rc, "ac_reduce", out.value)
+    return out.value
+
+
+def ac_reduce_noalloc(field_ptrs, grid, params, op, quantity, stream=None):
+    """Reduction over caller-held device arrays without any device allocation
+    (see include/ac.h); returns the value, raises AcError (with .value) on a
+    non-finite input."""
+    assert len(field_ptrs) == 8
+    arr = (_vp * 8)(*[int(p) for p in field_ptrs])
+    out = ctypes.c_double()
+    rc = load_library().ac_reduce_noalloc(arr, ctypes.byref(grid), ctypes.byref(params), int(op),
+                                          int(quantity), ctypes.byref(out), _vp(stream or 0))
+    _check(rc, "ac_reduce_noalloc", out.value)
     return out.value
 
 

@@ -28,6 +28,8 @@ static int cuda_fail(cudaError_t e) {
     return e == cudaErrorMemoryAllocation ? AC_ERR_OOM : AC_ERR_CUDA;
 }
 
+int ac::ac_report_cuda(cudaError_t e) { return cuda_fail(e); }
+
 #define CK(call)                                   \
     do {                                           \
         cudaError_t e_ = (call);                   \

@@ -108,4 +108,7 @@ struct ReduceLaunch {
 int reduce_max_blocks();
 cudaError_t launch_reduce(const ReduceLaunch &L, cudaStream_t st, int *launches);
 
+// Record a CUDA error for ac_last_cuda_error() and map it to an AC_ERR_* code.
+int ac_report_cuda(cudaError_t e);
+
 }  // namespace ac
