@@ -221,7 +221,7 @@ cudaError_t launch_gather(const void *src, int elem_size, const Geom &g, int z0,
 // deterministic for a given grid.
 // ---------------------------------------------------------------------------
 constexpr int RED_THREADS = 256;
-constexpr int RED_MAX_BLOCKS = 2 * 152;
+constexpr int RED_MAX_BLOCKS = 8 * 152;  // eight 256-thread CTAs per SM
 
 int reduce_max_blocks() { return RED_MAX_BLOCKS; }
 

@@ -91,41 +91,64 @@ struct IdxPadded {
 template <typename R>
 __device__ __forceinline__ R ldg(const R *p) { return __ldg(p); }
 
+// ---- field views -----------------------------------------------------------
+// A view returns one field's value at offset (dx, dy, dz) from the current cell;
+// the offsets are compile-time constants after unrolling.
+
+// Global memory through the read-only path, addressed by IX.
+template <typename R, class IX>
+struct GlobalView {
+    const R *__restrict__ f;
+    const IX &ix;
+    __device__ __forceinline__ R operator()(int dx, int dy, int dz) const {
+        return ldg(f + ix(dx, dy, dz));
+    }
+};
+
+// All eight fields of one cell in global memory.
+template <typename R, class IX>
+struct GlobalCell {
+    const R *const *f;
+    const IX &ix;
+    __device__ __forceinline__ GlobalView<R, IX> operator[](int q) const { return {f[q], ix}; }
+    __device__ __forceinline__ long long center() const { return ix(0, 0, 0); }
+};
+
 // ---- sixth-order operators (r = 3) ---------------------------------------
 
 // First derivative along axis AX: sum_m d1[m-1] (f_m - f_-m).
-template <int AX, typename R, class IX>
-__device__ __forceinline__ R op_d1(const R *__restrict__ f, const IX &ix, const R (&c)[3]) {
+template <int AX, typename R, class V>
+__device__ __forceinline__ R op_d1(const V &f, const R (&c)[3]) {
     constexpr int ox = AX == 0, oy = AX == 1, oz = AX == 2;
-    const R a1 = ldg(f + ix(ox, oy, oz)) - ldg(f + ix(-ox, -oy, -oz));
-    const R a2 = ldg(f + ix(2 * ox, 2 * oy, 2 * oz)) - ldg(f + ix(-2 * ox, -2 * oy, -2 * oz));
-    const R a3 = ldg(f + ix(3 * ox, 3 * oy, 3 * oz)) - ldg(f + ix(-3 * ox, -3 * oy, -3 * oz));
+    const R a1 = f(ox, oy, oz) - f(-ox, -oy, -oz);
+    const R a2 = f(2 * ox, 2 * oy, 2 * oz) - f(-2 * ox, -2 * oy, -2 * oz);
+    const R a3 = f(3 * ox, 3 * oy, 3 * oz) - f(-3 * ox, -3 * oy, -3 * oz);
     return c[0] * a1 + c[1] * a2 + c[2] * a3;
 }
 
 // Second derivative along axis AX: d2[0] f_0 + sum_m d2[m] (f_m + f_-m).
-template <int AX, typename R, class IX>
-__device__ __forceinline__ R op_d2(const R *__restrict__ f, const IX &ix, R f0, const R (&c)[4]) {
+template <int AX, typename R, class V>
+__device__ __forceinline__ R op_d2(const V &f, R f0, const R (&c)[4]) {
     constexpr int ox = AX == 0, oy = AX == 1, oz = AX == 2;
-    const R s1 = ldg(f + ix(ox, oy, oz)) + ldg(f + ix(-ox, -oy, -oz));
-    const R s2 = ldg(f + ix(2 * ox, 2 * oy, 2 * oz)) + ldg(f + ix(-2 * ox, -2 * oy, -2 * oz));
-    const R s3 = ldg(f + ix(3 * ox, 3 * oy, 3 * oz)) + ldg(f + ix(-3 * ox, -3 * oy, -3 * oz));
+    const R s1 = f(ox, oy, oz) + f(-ox, -oy, -oz);
+    const R s2 = f(2 * ox, 2 * oy, 2 * oz) + f(-2 * ox, -2 * oy, -2 * oz);
+    const R s3 = f(3 * ox, 3 * oy, 3 * oz) + f(-3 * ox, -3 * oy, -3 * oz);
     return c[0] * f0 + c[1] * s1 + c[2] * s2 + c[3] * s3;
 }
 
 // Mixed derivative in the plane of axes A < B from the face diagonals of Eq. 13:
 // sum_m dc[m-1] S_m, S_m = f(+m,+m) + f(-m,-m) - f(+m,-m) - f(-m,+m).
-template <int A, int B, typename R, class IX>
-__device__ __forceinline__ R op_dab(const R *__restrict__ f, const IX &ix, const R (&c)[3]) {
+template <int A, int B, typename R, class V>
+__device__ __forceinline__ R op_dab(const V &f, const R (&c)[3]) {
     constexpr int ax = A == 0, ay = A == 1, az = A == 2;
     constexpr int bx = B == 0, by = B == 1, bz = B == 2;
     R S[3];
 #pragma unroll
     for (int m = 1; m <= 3; ++m) {
-        const R pp = ldg(f + ix(m * (ax + bx), m * (ay + by), m * (az + bz)));
-        const R mm = ldg(f + ix(-m * (ax + bx), -m * (ay + by), -m * (az + bz)));
-        const R pm = ldg(f + ix(m * (ax - bx), m * (ay - by), m * (az - bz)));
-        const R mp = ldg(f + ix(-m * (ax - bx), -m * (ay - by), -m * (az - bz)));
+        const R pp = f(m * (ax + bx), m * (ay + by), m * (az + bz));
+        const R mm = f(-m * (ax + bx), -m * (ay + by), -m * (az + bz));
+        const R pm = f(m * (ax - bx), m * (ay - by), m * (az - bz));
+        const R mp = f(-m * (ax - bx), -m * (ay - by), -m * (az - bz));
         S[m - 1] = (pp + mm) - (pm + mp);
     }
     return c[0] * S[0] + c[1] * S[1] + c[2] * S[2];
@@ -142,19 +165,18 @@ struct Plane {
 // Second derivatives of one vector component V_C: its Laplacian, the pure
 // derivative along its own axis (d_CC V_C) and the two mixed derivatives
 // d_C d_b V_C (b != C) that enter grad(div V).
-template <int C, typename R, class IX>
-__device__ __forceinline__ void component_second(const R *__restrict__ f, const IX &ix, R f0,
-                                                 const DevCoefs<R> &k, R &lap, R &dcc,
-                                                 R &cross_b1, R &cross_b2) {
-    const R dxx = op_d2<0>(f, ix, f0, k.d2[0]);
-    const R dyy = op_d2<1>(f, ix, f0, k.d2[1]);
-    const R dzz = op_d2<2>(f, ix, f0, k.d2[2]);
+template <int C, typename R, class V>
+__device__ __forceinline__ void component_second(const V &f, R f0, const DevCoefs<R> &k, R &lap,
+                                                 R &dcc, R &cross_b1, R &cross_b2) {
+    const R dxx = op_d2<0>(f, f0, k.d2[0]);
+    const R dyy = op_d2<1>(f, f0, k.d2[1]);
+    const R dzz = op_d2<2>(f, f0, k.d2[2]);
     lap = dxx + dyy + dzz;
     constexpr int B1 = C == 0 ? 1 : 0;
     constexpr int B2 = C == 2 ? 1 : 2;
     dcc = C == 0 ? dxx : (C == 1 ? dyy : dzz);
-    cross_b1 = op_dab<(C < B1 ? C : B1), (C < B1 ? B1 : C)>(f, ix, k.dc[Plane<C, B1>::id]);
-    cross_b2 = op_dab<(C < B2 ? C : B2), (C < B2 ? B2 : C)>(f, ix, k.dc[Plane<C, B2>::id]);
+    cross_b1 = op_dab<(C < B1 ? C : B1), (C < B1 ? B1 : C)>(f, k.dc[Plane<C, B1>::id]);
+    cross_b2 = op_dab<(C < B2 ? C : B2), (C < B2 ? B2 : C)>(f, k.dc[Plane<C, B2>::id]);
 }
 
 template <typename R> __device__ __forceinline__ R dev_exp(R x);
@@ -163,61 +185,61 @@ template <> __device__ __forceinline__ float dev_exp<float>(float x) { return ex
 
 // RHS of Eqs. B.1-B.4 at one cell (mu0 = 1, zeta = H = C = K = 0), with the
 // forcing term `frc` added to du/dt.  Output order: Table B.1.
-template <typename R, class IX>
-__device__ __forceinline__ void cell_rhs(const R *const __restrict__ *f, const IX &ix,
-                                         const DevCoefs<R> &k, const R frc[3], R out[NF]) {
-    const long long c0 = ix(0, 0, 0);
-    const R lnrho = ldg(f[0] + c0);
-    const R u[3] = {ldg(f[1] + c0), ldg(f[2] + c0), ldg(f[3] + c0)};
-    const R ss = ldg(f[4] + c0);
-    const R aa[3] = {ldg(f[5] + c0), ldg(f[6] + c0), ldg(f[7] + c0)};
+// `f` is a cell accessor: f[q] is the view of field q around the cell.
+template <typename R, class CELL>
+__device__ __forceinline__ void cell_rhs(const CELL &f, const DevCoefs<R> &k, const R frc[3],
+                                         R out[NF]) {
+    const R lnrho = f[0](0, 0, 0);
+    const R u[3] = {f[1](0, 0, 0), f[2](0, 0, 0), f[3](0, 0, 0)};
+    const R ss = f[4](0, 0, 0);
+    const R aa[3] = {f[5](0, 0, 0), f[6](0, 0, 0), f[7](0, 0, 0)};
 
     // First derivatives.
     R gl[3], gs[3], gu[3][3], ga[3][3];
-    gl[0] = op_d1<0>(f[0], ix, k.d1[0]);
-    gl[1] = op_d1<1>(f[0], ix, k.d1[1]);
-    gl[2] = op_d1<2>(f[0], ix, k.d1[2]);
-    gs[0] = op_d1<0>(f[4], ix, k.d1[0]);
-    gs[1] = op_d1<1>(f[4], ix, k.d1[1]);
-    gs[2] = op_d1<2>(f[4], ix, k.d1[2]);
+    gl[0] = op_d1<0>(f[0], k.d1[0]);
+    gl[1] = op_d1<1>(f[0], k.d1[1]);
+    gl[2] = op_d1<2>(f[0], k.d1[2]);
+    gs[0] = op_d1<0>(f[4], k.d1[0]);
+    gs[1] = op_d1<1>(f[4], k.d1[1]);
+    gs[2] = op_d1<2>(f[4], k.d1[2]);
 #pragma unroll
     for (int m = 0; m < 3; ++m) {
-        gu[m][0] = op_d1<0>(f[1 + m], ix, k.d1[0]);
-        gu[m][1] = op_d1<1>(f[1 + m], ix, k.d1[1]);
-        gu[m][2] = op_d1<2>(f[1 + m], ix, k.d1[2]);
-        ga[m][0] = op_d1<0>(f[5 + m], ix, k.d1[0]);
-        ga[m][1] = op_d1<1>(f[5 + m], ix, k.d1[1]);
-        ga[m][2] = op_d1<2>(f[5 + m], ix, k.d1[2]);
+        gu[m][0] = op_d1<0>(f[1 + m], k.d1[0]);
+        gu[m][1] = op_d1<1>(f[1 + m], k.d1[1]);
+        gu[m][2] = op_d1<2>(f[1 + m], k.d1[2]);
+        ga[m][0] = op_d1<0>(f[5 + m], k.d1[0]);
+        ga[m][1] = op_d1<1>(f[5 + m], k.d1[1]);
+        ga[m][2] = op_d1<2>(f[5 + m], k.d1[2]);
     }
 
     // Second derivatives: Laplacians and grad(div .) of u and A.
     R lapu[3], lapa[3], gdu[3], gda[3];
     {
         R dcc, c1, c2;
-        component_second<0>(f[1], ix, u[0], k, lapu[0], dcc, c1, c2);  // c1 = d_xy u_x, c2 = d_xz u_x
+        component_second<0>(f[1], u[0], k, lapu[0], dcc, c1, c2);  // c1 = d_xy u_x, c2 = d_xz u_x
         gdu[0] = dcc;
         gdu[1] = c1;
         gdu[2] = c2;
-        component_second<1>(f[2], ix, u[1], k, lapu[1], dcc, c1, c2);  // c1 = d_xy u_y, c2 = d_yz u_y
+        component_second<1>(f[2], u[1], k, lapu[1], dcc, c1, c2);  // c1 = d_xy u_y, c2 = d_yz u_y
         gdu[0] += c1;
         gdu[1] += dcc;
         gdu[2] += c2;
-        component_second<2>(f[3], ix, u[2], k, lapu[2], dcc, c1, c2);  // c1 = d_xz u_z, c2 = d_yz u_z
+        component_second<2>(f[3], u[2], k, lapu[2], dcc, c1, c2);  // c1 = d_xz u_z, c2 = d_yz u_z
         gdu[0] += c1;
         gdu[1] += c2;
         gdu[2] += dcc;
     }
     {
         R dcc, c1, c2;
-        component_second<0>(f[5], ix, aa[0], k, lapa[0], dcc, c1, c2);
+        component_second<0>(f[5], aa[0], k, lapa[0], dcc, c1, c2);
         gda[0] = dcc;
         gda[1] = c1;
         gda[2] = c2;
-        component_second<1>(f[6], ix, aa[1], k, lapa[1], dcc, c1, c2);
+        component_second<1>(f[6], aa[1], k, lapa[1], dcc, c1, c2);
         gda[0] += c1;
         gda[1] += dcc;
         gda[2] += c2;
-        component_second<2>(f[7], ix, aa[2], k, lapa[2], dcc, c1, c2);
+        component_second<2>(f[7], aa[2], k, lapa[2], dcc, c1, c2);
         gda[0] += c1;
         gda[1] += c2;
         gda[2] += dcc;

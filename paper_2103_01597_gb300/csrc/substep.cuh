@@ -63,7 +63,8 @@ __global__ void __launch_bounds__(128) substep_kernel(const SubstepArgs<R, W> a)
             frc[2] = a.amp_e[2] * cph;
         }
         R rhs[NF];
-        cell_rhs<R>(a.fin, ix, a.k, frc, rhs);
+        const GlobalCell<R, IX> cell{a.fin, ix};
+        cell_rhs<R>(cell, a.k, frc, rhs);
         const long long o = ix(0, 0, 0);
 #pragma unroll
         for (int q = 0; q < NF; ++q) rk_update(a, q, o, rhs[q]);

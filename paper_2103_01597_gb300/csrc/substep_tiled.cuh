@@ -1,0 +1,280 @@
+// Shared-memory tiled, z-marching variant of the fused substep for binary32
+// fields (periodic layout).
+//
+// Each CTA owns a 32 x 8 column tile and walks a range of z.  A ring of
+// shared-memory plane tiles holds, for all eight fields, the tile plus its
+// radius-3 halo in x and y (x rounded out to 16-byte boundaries: columns
+// x0-4 .. x0+35); planes z-3 .. z+3 are resident while output plane z is
+// computed and the next planes stream in with cp.async.  Every stencil point
+// of Eq. 13 is then one shared-memory load at a compile-time offset.  The
+// periodic map of Sec. 3.3 is applied once per copied chunk.
+#pragma once
+
+#include "substep.cuh"
+
+namespace ac {
+
+constexpr int TT_X = 32;                  // tile width (one warp)
+constexpr int TT_Y = 8;                   // tile height
+constexpr int TT_ROW = TT_X + 8;          // floats per smem row: x0-4 .. x0+TT_X+3
+constexpr int TT_ROWS = TT_Y + 6;         // rows: y0-3 .. y0+TT_Y+2
+constexpr int TT_FIELD = TT_ROW * TT_ROWS;
+constexpr int TT_PLANE = NF * TT_FIELD;   // floats per plane slot
+constexpr int TT_PF = 2;                  // planes in flight beyond z+3
+constexpr int TT_NP = 7 + TT_PF;          // ring slots
+constexpr int TT_THREADS = TT_X * TT_Y;
+constexpr int TT_NW = TT_PF + 2;          // ring slots for the accumulator w of output planes
+// Copies per thread per plane: 16-byte chunks (x rounded to 16 B) or 4-byte elements.
+constexpr int TT_VCH = NF * TT_ROWS * (TT_ROW / 4);
+constexpr int TT_VPT = (TT_VCH + TT_THREADS - 1) / TT_THREADS;
+constexpr int TT_ECH = NF * TT_ROWS * TT_ROW;
+constexpr int TT_EPT = (TT_ECH + TT_THREADS - 1) / TT_THREADS;
+
+template <typename W>
+constexpr size_t tt_smem_bytes() {
+    return sizeof(float) * TT_NP * TT_PLANE + sizeof(W) * TT_NW * NF * TT_THREADS;
+}
+
+// The values on the cell's own z-column (dx = dy = 0) come from a per-thread
+// register queue of planes z-3 .. z+3; every other point from shared memory.
+template <typename R>
+struct SmemView {
+    const R *base;
+    const int (&slot)[7];
+    const R (&zq)[7];
+    __device__ __forceinline__ R operator()(int dx, int dy, int dz) const {
+        if (dx == 0 && dy == 0) return zq[dz + 3];
+        return base[slot[dz + 3] + dy * TT_ROW + dx];
+    }
+};
+
+template <typename R>
+struct SmemCell {
+    const R *cell;  // smem + (ty + 3) * TT_ROW + tx + 4
+    const int (&slot)[7];
+    const R (&zq)[NF][7];
+    __device__ __forceinline__ SmemView<R> operator[](int q) const {
+        return {cell + q * TT_FIELD, slot, zq[q]};
+    }
+};
+
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async8(void *smem, const void *gmem) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async4(void *smem, const void *gmem) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() {
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+}
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+__device__ __forceinline__ int wrap_mod(int v, int n) {
+    const int m = v % n;
+    return m < 0 ? m + n : m;
+}
+
+// Per-thread copy list of one plane tile: for each copy, its shared-memory
+// offset inside a ring slot and its source offset inside a z-plane (field base
+// pointer folded in).  The periodic map of Sec. 3.3 is applied here once; only
+// the z-plane offset changes from plane to plane.
+template <bool VEC>
+struct TileCopies {
+    static constexpr int N = VEC ? TT_VPT : TT_EPT;
+    int soff[N];
+    const float *src[N];
+    int n;
+    __device__ __forceinline__ void init(const float *const *fin, const Geom &g, int x0, int y0) {
+        const int tid = threadIdx.y * TT_X + threadIdx.x;
+        n = 0;
+        constexpr int CW = VEC ? 4 : 1;             // floats per copy
+        constexpr int CH = TT_ROW / CW;             // copies per row
+        constexpr int TOTAL = NF * TT_ROWS * CH;
+#pragma unroll
+        for (int u = 0; u < N; ++u) {
+            const int t = tid + u * TT_THREADS;
+            if (t < TOTAL) {
+                const int q = t / (TT_ROWS * CH);
+                const int rem = t - q * (TT_ROWS * CH);
+                const int r = rem / CH;
+                const int c = rem - r * CH;
+                const int gy = wrap_mod(y0 - 3 + r, g.ny);
+                const int gx = wrap_mod(x0 - 4 + CW * c, g.nx);
+                soff[u] = q * TT_FIELD + r * TT_ROW + CW * c;
+                src[u] = fin[q] + (long long)gy * g.px + gx;
+                n = u + 1;
+            }
+        }
+    }
+    // Issue the copies of plane p (wrapped) into `slot`.
+    __device__ __forceinline__ void issue(float *slot, const Geom &g, int p) const {
+        const long long zoff = (long long)wrap_mod(p, g.nz) * g.pxy;
+#pragma unroll
+        for (int u = 0; u < N; ++u)
+            if (u < n) {
+                if (VEC)
+                    cp_async16(slot + soff[u], src[u] + zoff);
+                else
+                    cp_async4(slot + soff[u], src[u] + zoff);
+            }
+    }
+};
+
+// Copy this thread's accumulator values of output plane z into a w ring slot.
+template <typename W>
+__device__ __forceinline__ void tile_load_w(W *wslot, W *const *w, const Geom &g, int i, int j,
+                                            int z, bool active) {
+    if (!active) return;
+    const int tid = threadIdx.y * TT_X + threadIdx.x;
+    const long long o = (long long)z * g.pxy + (long long)j * g.px + i;
+#pragma unroll
+    for (int q = 0; q < NF; ++q) {
+        if (sizeof(W) == 8) {
+            cp_async8(wslot + q * TT_THREADS + tid, w[q] + o);
+        } else {
+            cp_async4(wslot + q * TT_THREADS + tid, w[q] + o);
+        }
+    }
+}
+
+template <typename W, bool VEC>
+__global__ void __launch_bounds__(TT_THREADS, 1) substep_tiled_kernel(const SubstepArgs<float, W> a) {
+    extern __shared__ __align__(128) unsigned char tt_smem_raw[];
+    float *sm = reinterpret_cast<float *>(tt_smem_raw);
+    W *wring = reinterpret_cast<W *>(sm + TT_NP * TT_PLANE);
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    const int tid = ty * TT_X + tx;
+    const int x0 = blockIdx.x * TT_X, y0 = blockIdx.y * TT_Y;
+    const int z0 = blockIdx.z * a.zchunk;
+    const int z1 = min(z0 + a.zchunk, a.g.nz);
+    const int i = x0 + tx, j = y0 + ty;
+    const bool active = i < a.g.nx && j < a.g.ny;
+
+    float2 exy = make_float2(0.f, 0.f);
+    if (a.force_on && active) {
+        const float2 ex = a.ftab[i], ey = a.ftab[a.g.nx + j];
+        exy.x = ex.x * ey.x - ex.y * ey.y;
+        exy.y = ex.x * ey.y + ex.y * ey.x;
+    }
+    TileCopies<VEC> cp;
+    cp.init(a.fin, a.g, x0, y0);
+
+    // One commit group per plane p; it also carries w of output plane p - 3.
+    auto issue = [&](int p) {
+        if (p <= z1 + 2) cp.issue(sm + ((p - z0 + 3) % TT_NP) * TT_PLANE, a.g, p);
+        const int zw = p - 3;
+        if (!a.s0 && zw >= z0 && zw < z1)
+            tile_load_w<W>(wring + ((zw - z0) % TT_NW) * (NF * TT_THREADS), a.w, a.g, i, j, zw,
+                           active);
+        cp_async_commit();
+    };
+    for (int p = z0 - 3; p <= z0 + 3 + TT_PF; ++p) issue(p);
+
+    float zq[NF][7];  // z-column of this thread's cell: planes z-3 .. z+3
+    const float2 *ztab = a.ftab + a.g.nx + a.g.ny;
+    float2 ez_next = a.force_on ? ztab[z0] : make_float2(0.f, 0.f);
+    for (int z = z0; z < z1; ++z) {
+        const float2 ez = ez_next;  // forcing phase of plane z, loaded one plane ahead
+        if (a.force_on && z + 1 < z1) ez_next = ztab[z + 1];
+        cp_async_wait<TT_PF>();  // plane z+3 (and w of plane z) have landed for this thread
+        __syncthreads();         // ... and for every thread
+        int slot[7];
+#pragma unroll
+        for (int d = 0; d < 7; ++d) slot[d] = ((z - z0 + d) % TT_NP) * TT_PLANE;
+        const float *ctr = sm + (ty + 3) * TT_ROW + tx + 4;
+        if (z == z0) {
+#pragma unroll
+            for (int q = 0; q < NF; ++q)
+#pragma unroll
+                for (int d = 0; d < 7; ++d) zq[q][d] = ctr[slot[d] + q * TT_FIELD];
+        } else {
+#pragma unroll
+            for (int q = 0; q < NF; ++q) {
+#pragma unroll
+                for (int d = 0; d < 6; ++d) zq[q][d] = zq[q][d + 1];
+                zq[q][6] = ctr[slot[6] + q * TT_FIELD];
+            }
+        }
+        if (active) {
+            const SmemCell<float> cell{ctr, slot, zq};
+            float frc[3] = {0.f, 0.f, 0.f};
+            if (a.force_on) {
+                const float cph = exy.x * ez.x - exy.y * ez.y;
+                frc[0] = a.amp_e[0] * cph;
+                frc[1] = a.amp_e[1] * cph;
+                frc[2] = a.amp_e[2] * cph;
+            }
+            float rhs[NF];
+            cell_rhs<float>(cell, a.k, frc, rhs);
+            const long long o = (long long)z * a.g.pxy + (long long)j * a.g.px + i;
+            const W *wz = wring + ((z - z0) % TT_NW) * (NF * TT_THREADS) + tid;
+#pragma unroll
+            for (int q = 0; q < NF; ++q) {
+                W wn = a.dt * (W)rhs[q];
+                if (!a.s0) wn = a.alpha * wz[q * TT_THREADS] + wn;
+                a.w[q][o] = wn;
+                a.fout[q][o] = (float)((W)cell[q](0, 0, 0) + a.beta * wn);
+            }
+        }
+        __syncthreads();  // reads of plane z-3's slot and of w(z) are done before refilling
+        issue(z + 4 + TT_PF);
+    }
+    cp_async_wait<0>();
+}
+
+// Launch the tiled kernel for binary32 fields in the periodic layout.
+template <typename W>
+cudaError_t launch_substep_tiled_t(const SubstepLaunch &L, cudaStream_t st, int *launches) {
+    SubstepArgs<float, W> a;
+    a.g = L.g;
+    for (int q = 0; q < NF; ++q) {
+        a.fin[q] = static_cast<const float *>(L.fin[q]);
+        a.fout[q] = static_cast<float *>(L.fout[q]);
+        a.w[q] = static_cast<W *>(L.w[q]);
+    }
+    a.k = to_dev<float>(L.c, L.ph);
+    a.alpha = (W)L.alpha;
+    a.beta = (W)L.beta;
+    a.dt = (W)L.dt;
+    a.s0 = L.s == 0;
+    a.force_on = L.force.on;
+    const long long ntab = (long long)L.g.nx + L.g.ny + L.g.nz;
+    a.ftab = reinterpret_cast<const float2 *>(L.force.tab + ntab);
+    for (int m = 0; m < 3; ++m) a.amp_e[m] = (float)L.force.amp_e[m];
+
+    const unsigned gx = (L.g.nx + TT_X - 1) / TT_X;
+    const unsigned gy = (L.g.ny + TT_Y - 1) / TT_Y;
+    // z range per CTA: up to 128 planes, fewer until there are at least two CTAs per SM.
+    int zc = L.g.nz < 128 ? L.g.nz : 128;
+    while (zc > 16 && (long long)gx * gy * ((L.g.nz + zc - 1) / zc) < 2 * 152) zc = (zc + 1) / 2;
+    a.zchunk = zc;
+    const dim3 grid(gx, gy, (L.g.nz + zc - 1) / zc);
+    const dim3 block(TT_X, TT_Y, 1);
+    const bool vec = (L.g.nx % 4) == 0;
+    cudaError_t e;
+    const size_t smem = tt_smem_bytes<W>();
+    if (vec) {
+        e = cudaFuncSetAttribute(substep_tiled_kernel<W, true>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        substep_tiled_kernel<W, true><<<grid, block, smem, st>>>(a);
+    } else {
+        e = cudaFuncSetAttribute(substep_tiled_kernel<W, false>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        substep_tiled_kernel<W, false><<<grid, block, smem, st>>>(a);
+    }
+    ++*launches;
+    return cudaGetLastError();
+}
+
+}  // namespace ac

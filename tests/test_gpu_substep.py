@@ -140,11 +140,17 @@ def test_layouts_agree_bitwise():
     assert np.array_equal(res[0], res[1])
 
 
+FP32_SIZES = [(32, 24, 16), (37, 21, 13), (64, 40, 150), (4, 4, 4), (1, 12, 10), (36, 9, 40)]
+
+
+@pytest.mark.parametrize("layout", [ac.AC_LAYOUT_PERIODIC, ac.AC_LAYOUT_PADDED])
+@pytest.mark.parametrize("n", FP32_SIZES)
 @pytest.mark.parametrize("precision,ftol,wtol", [(ac.AC_FP32, 2e-6, 2e-4),
                                                   (ac.AC_FP32_W64, 2e-6, 2e-4)])
-def test_fp32_within_bound(precision, ftol, wtol):
-    n = (32, 24, 16)
-    sim = _sim(n, precision=precision, force_amp=0.05, seed=3)
+def test_fp32_within_bound(precision, ftol, wtol, n, layout):
+    """Periodic layout: the shared-memory tiled kernel (16-byte copies when
+    nx % 4 == 0, element copies otherwise; several z ranges for nz = 150)."""
+    sim = _sim(n, precision=precision, force_amp=0.05, seed=3, layout=layout)
     f = _state(n, seed=12)
     f32 = f.astype(np.float32).astype(np.float64)  # the device rounds the input to binary32
     sim.load(f)
@@ -157,6 +163,8 @@ def test_fp32_within_bound(precision, ftol, wtol):
         fo, wo = core.substep(fcur, w, p, dt, s)
         sim.substep(dt, s)
         fg, wg = sim.store(), sim.store_w()
+        print("fp32 n=%s s=%d max rel err f %.2e w %.2e" % (n, s, rel_err(fg, fo).max(),
+                                                           rel_err(wg, wo).max()))
         assert np.all(rel_err(fg, fo) <= ftol), (s, rel_err(fg, fo))
         assert np.all(rel_err(wg, wo) <= wtol), (s, rel_err(wg, wo))
         fcur, w = fg, wg
@@ -302,4 +310,32 @@ def test_full_size_256_sampled(precision):
         assert np.all(rel_err(gs, fo) <= 1e-12), (s, rel_err(gs, fo))
         assert np.all(rel_err(ws, wo) <= 1e-12), (s, rel_err(ws, wo))
         f, w = fg, wg
+    sim.close()
+
+
+def test_full_size_512_fp32_sampled():
+    """512^3 forced FP32, the timed FP32 configuration: substeps 0 and 1 at
+    sampled cells against the oracle run on the binary32-rounded state."""
+    n = (512, 512, 512)
+    sim = _sim(n, precision=ac.AC_FP32, force_amp=0.05, seed=3)
+    f = synthetic.noise_state(n, seed=3)
+    sim.load(f)
+    f = sim.store()  # the binary32 state the device holds, widened
+    cells = sample_cells(n, 2000, seed=8)
+    idx = (cells[:, 2], cells[:, 1], cells[:, 0])
+    k, e, phi = ac.ac_forcing_draw(3, 0)
+    p = _oracle_params(n, forcing=core.Forcing(k, e, phi, 0.05))
+    w = None
+    for s in range(2):
+        fo, wo = core.substep_cells(f, w, p, 1e-3, s, cells)
+        sim.substep(1e-3, s)
+        fg, wg = sim.store(), sim.store_w()
+        gs = np.stack([fg[q][idx] for q in range(8)])
+        ws = np.stack([wg[q][idx] for q in range(8)])
+        print("fp32 512^3 s=%d max rel err f %.2e w %.2e" % (s, rel_err(gs, fo).max(),
+                                                           rel_err(ws, wo).max()))
+        assert np.all(rel_err(gs, fo) <= 2e-6), (s, rel_err(gs, fo))
+        assert np.all(rel_err(ws, wo) <= 2e-4), (s, rel_err(ws, wo))
+        f, w = fg, wg
+        del fg, wg
     sim.close()
