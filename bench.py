@@ -37,7 +37,8 @@ UNIT = "Gcell-updates/s"
 # the physics of Eqs. B.1-B.4 with forcing, 40 in the Runge-Kutta update
 # (24 at substep 0, where w is not read).
 FLOPS_PER_CELL = {0: 743, 1: 759, 2: 759}
-# Algorithmic bytes per cell-substep: read f and w, write f and w (w not read at s = 0).
+# Algorithmic bytes per cell-substep: read f and w, write f and w, eight fields
+# each (w not read at s = 0).
 def bytes_per_cell(elem_f, elem_w, s):
     return 8 * (2 * elem_f + (2 if s else 1) * elem_w)
 
@@ -56,6 +57,12 @@ WORKLOADS = {
     "forced512_fp32": dict(n=(512, 512, 512), precision="fp32", force_amp=0.05, seed=3,
                            dt=1e-3, init="noise",
                            desc="512^3 periodic FP32 forced non-ideal MHD (FP64 reductions)"),
+    "ensemble64_fp32": dict(n=None, precision="fp32", force_amp=0.0, seed=4, dt=1e-3,
+                            init="noise", ensemble=True,
+                            desc="64 periodic boxes, per-axis sizes from {32,48,64,96,128}, "
+                                 "nu and eta log-uniform in [1e-3,1e-2] (seed 4), FP32, one "
+                                 "persistent launch per substep under a CUDA graph, tuned "
+                                 "work items"),
 }
 
 
@@ -68,6 +75,8 @@ def parse():
     ap.add_argument("--workload", default="forced256_fp64", choices=sorted(WORKLOADS))
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-compare", action="store_true",
+                    help="ensemble: skip the separate-launch and FP64 comparisons")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--fp64-peak", action="store_true",
                     help="also time a cuBLAS FP64 GEMM as a measured FP64 reference rate")
@@ -331,7 +340,7 @@ def run_ours(args, wl):
                 "alg_flops_per_cell_substep": FLOPS_PER_CELL}
     else:
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
-        bytes_s = {s: bytes_per_cell(elem_f, elem_w, s) * ncell / 8 for s in range(3)}
+        bytes_s = {s: bytes_per_cell(elem_f, elem_w, s) * ncell for s in range(3)}
         achieved = statistics.mean(bytes_s[s] / avg[s] for s in range(3)) / 1e9
         roof = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                 "frac": achieved / peaks["hbm_gbs"], "traffic": None,
@@ -381,16 +390,193 @@ def run_ours(args, wl):
     return 0
 
 
+def run_ensemble(args, wl):
+    """The batched ensemble: aggregate throughput of the graph-captured
+    persistent launch, beside 64 separate binary32 and binary64 launches and the
+    per-field binary32 error against binary64 after a few steps."""
+    import torch
+    from paper_2103_01597_gb300 import ac, build, synthetic
+    ws, rank, local = dist_setup(args)
+    torch.cuda.set_device(local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    if rank == 0:
+        build.build()
+    if dist:
+        dist.barrier()
+    spec = synthetic.ensemble(wl["seed"])
+    boxes = [(n, (2 * math.pi,) * 3, nu, eta) for n, nu, eta in spec]
+    ncell = sum(n[0] * n[1] * n[2] for n, _, _, _ in boxes)
+    states = [synthetic.noise_state(n, 100 + i) for i, (n, _, _, _) in enumerate(boxes)]
+    stream = torch.cuda.current_stream()
+    b = ac.Batch(boxes, stream=stream.cuda_stream)
+    for i, f in enumerate(states):
+        b.load(i, f)
+    dt = wl["dt"]
+    zc = ac.ac_batch_tune(b.b, dt)
+    ac.ac_batch_set_graph(b.b, True)
+    for _ in range(args.warmup):
+        b.step(dt)
+    torch.cuda.synchronize()
+    bus = None
+    try:
+        bus = torch.cuda.get_device_properties(local).pci_bus_id
+    except Exception:
+        pass
+    sampler = ClockSampler(bus) if rank == 0 else None
+    time.sleep(0.3 if sampler else 0)
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(2)] for _ in range(args.steps)]
+    l0 = ac.ac_batch_info(b.b)["launches"]
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    for it in range(args.steps):
+        evs[it][0].record(stream)
+        b.step(dt)
+        evs[it][1].record(stream)
+    t1.record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    elapsed = t0.elapsed_time(t1) / 1e3
+    launches = ac.ac_batch_info(b.b)["launches"] - l0
+    clocks = sampler.stop() if sampler else None
+    if dist:
+        tt = torch.tensor([elapsed], device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        elapsed = float(tt.item())
+    value = ws * ncell * 3 * args.steps / elapsed / 1e9
+    step_s = statistics.mean(e[0].elapsed_time(e[1]) / 1e3 for e in evs)
+    launch_s = step_s / 3
+    peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    alg = statistics.mean(bytes_per_cell(4, 4, s) for s in range(3)) * ncell
+    achieved = alg / launch_s / 1e9
+    roof = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+            "frac": achieved / peaks["hbm_gbs"], "traffic": None,
+            "kernel": "batch_substep_kernel<float> (persistent, graph-captured)",
+            "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)",
+            "avg_launch_ms": 1e3 * launch_s}
+
+    # 64 separate launches per substep: binary32 and binary64 single-box handles.
+    def separate(precision, steps=2):
+        sims = []
+        for i, (n, L, nu, eta) in enumerate(boxes):
+            sim = ac.Simulation(n, L=L, precision=precision, nu=nu, eta=eta,
+                                stream=stream.cuda_stream)
+            sim.load(states[i])
+            sims.append(sim)
+        for sim in sims:
+            sim.step(dt)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            for s in range(3):
+                for sim in sims:
+                    sim.substep(dt, s)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        t = e0.elapsed_time(e1) / 1e3
+        return sims, ncell * 3 * steps / t / 1e9
+
+    compare = {}
+    err = None
+    if rank == 0 and not args.no_compare:
+        s32, v32 = separate(ac.AC_FP32)
+        for sim in s32:
+            sim.close()
+        s64, v64 = separate(ac.AC_FP64)
+        compare = {"separate_fp32_launches_gcell_s": v32, "separate_fp64_launches_gcell_s": v64,
+                   "speedup_vs_separate_fp32": value / ws / v32,
+                   "speedup_vs_separate_fp64": value / ws / v64}
+        # binary32 batch vs binary64 handles after the same number of steps from the same state
+        nsteps = 5
+        for sim in s64:
+            sim.close()
+        bb = ac.Batch(boxes, stream=stream.cuda_stream)
+        errs = np.zeros(8)
+        for i, f in enumerate(states):
+            bb.load(i, f)
+        for _ in range(nsteps):
+            bb.step(dt)
+        for i, (n, L, nu, eta) in enumerate(boxes):
+            sim = ac.Simulation(n, L=L, precision=ac.AC_FP64, nu=nu, eta=eta,
+                                stream=stream.cuda_stream)
+            sim.load(states[i])
+            for _ in range(nsteps):
+                sim.step(dt)
+            r = sim.store()
+            g = bb.store(i)
+            sim.close()
+            for q in range(8):
+                den = np.max(np.abs(r[q]))
+                errs[q] = max(errs[q], np.max(np.abs(g[q] - r[q])) / den if den else 0.0)
+        bb.close()
+        err = {"steps": nsteps, "max_over_boxes_rel_err_per_field": errs.tolist()}
+
+    e2e = None
+    if args.e2e_steps > 0:
+        torch.cuda.synchronize()
+        ins = [torch.from_numpy(f.reshape(-1)).pin_memory() for f in states]
+        outs = [torch.empty_like(t).pin_memory() for t in ins]
+        tt0 = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            for i, t in enumerate(ins):
+                ac.ac_batch_load(b.b, i, ac.AC_ALL, t)
+            b.step(dt)
+            for i in range(len(boxes)):
+                ac.ac_batch_store(b.b, i, ac.AC_ALL, outs[i])
+        tt = time.perf_counter() - tt0
+        e2e = {"value": ncell * 3 * args.e2e_steps * ws / tt / 1e9, "unit": UNIT,
+               "h2d_bytes_per_step": 8 * ncell * 8, "d2h_bytes_per_step": 8 * ncell * 8,
+               "steps": args.e2e_steps}
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        n0 = boxes[0][0]
+        wl0 = dict(wl, n=n0, force_amp=0.0)
+        cpu = cpu_baseline(wl0, states[0], args.cpu_seconds)
+        cpu["sample"] += " (box 0 of the ensemble)"
+    b.close()
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
+                "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": 1e3 * elapsed / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": {"workload": wl["desc"], "boxes": len(boxes), "cells": ncell,
+                           "dt": dt, "tuned_item_z_extent": zc,
+                           "parallelism": "replicas" if ws > 1 else "single GPU",
+                           "l2": "inputs larger than L2 (%.1f GB of state resident)"
+                                 % (ncell * 24 * 4 / 1e9),
+                           "step": "3 persistent substep launches (graph replay)"},
+                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+                "clocks": clocks, "compare": compare, "fp32_vs_fp64": err}
+        print(json.dumps(line))
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
 def main():
     args = parse()
     wl = dict(WORKLOADS[args.workload])
-    if args.grid:
+    if args.grid and not wl.get("ensemble"):
         g = args.grid
         wl["n"] = (g, g, g)
         wl["desc"] = wl["desc"].replace("256^3", "%d^3" % g).replace("512^3", "%d^3" % g)
         wl.pop("vs", None)
     if args.impl == "reference":
+        if wl.get("ensemble"):
+            from paper_2103_01597_gb300 import synthetic
+            n0 = synthetic.ensemble(wl["seed"])[0][0]
+            wl = dict(wl, n=n0, desc=wl["desc"] + " (oracle sample: box 0)")
         return run_reference(args, wl)
+    if wl.get("ensemble"):
+        return run_ensemble(args, wl)
     return run_ours(args, wl)
 
 

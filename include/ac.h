@@ -212,6 +212,56 @@ int ac_set_step(ac_handle *h, unsigned long long step, int next_substep);
 /* Number of kernels the handle has launched so far. */
 int ac_launch_count(const ac_handle *h, unsigned long long *count);
 
+/* ---- batched ensemble ------------------------------------------------------
+ * Independent periodic boxes of uneven size integrated together (the paper
+ * notes that parameter scans inflate problem sizes, Sec. 4).  Each box carries
+ * its own grid and nu, eta; the other constants come from `common`.  One
+ * persistent kernel launch per substep covers every box: work items are
+ * (box, 32 x 8 column tile, z range), taken largest first from a device
+ * counter; each item computes exactly what the single-box binary32 kernel
+ * computes for those cells (same substep as ac_integrate_substep, no forcing).
+ * State: binary32 fields (AC_FP32, or AC_FP32_W64 with a binary64 accumulator);
+ * device memory is owned by the batch.  Limits: 1..AC_BATCH_MAX_BOXES boxes,
+ * 1..4096 cells per axis, nx a multiple of 4; force_amp must be 0.
+ */
+#define AC_BATCH_MAX_BOXES 128
+
+typedef struct {
+    int nx, ny, nz;      /* cells per axis                                       */
+    double lx, ly, lz;   /* box lengths                                          */
+    double nu, eta;      /* this box's viscosity and magnetic diffusivity        */
+} ac_box;
+
+typedef struct ac_batch ac_batch; /* opaque; owned by the library */
+
+int ac_batch_init(ac_batch **b, int nbox, const ac_box *boxes, const ac_params *common,
+                  void *stream);
+int ac_batch_quit(ac_batch *b);
+/* Host float64 <-> one box's current state (field 0..7 or AC_ALL, unpadded,
+ * x fastest) or accumulator; store synchronises the stream, load resets the
+ * substep counter to 0. */
+int ac_batch_load(ac_batch *b, int box, int field, const double *host_src);
+int ac_batch_store(ac_batch *b, int box, int field, double *host_dst);
+int ac_batch_load_w(ac_batch *b, int box, int field, const double *host_src);
+int ac_batch_store_w(ac_batch *b, int box, int field, double *host_dst);
+/* Substep s of every box (order rules of ac_integrate_substep). */
+int ac_batch_integrate_substep(ac_batch *b, double dt, int s);
+/* Substeps 0, 1, 2 of every box; with the graph enabled, the three launches
+ * (and the counter resets) are captured once per (dt, state buffer) into a
+ * CUDA graph and replayed. */
+int ac_batch_integrate_step(ac_batch *b, double dt);
+int ac_batch_set_graph(ac_batch *b, int enable);
+/* Autotuner: times substep 0 (which leaves the state unchanged) for work items
+ * of z extent 8, 16, 32, 64 and 128 and keeps the fastest (*zc_out).  With a
+ * cache path, a line "<device|boxes signature> <z extent>" is reused or
+ * appended.  Must be called at a step boundary (AC_ERR_STATE otherwise). */
+int ac_batch_tune(ac_batch *b, double dt, const char *cache_path, int *zc_out);
+/* Reduction of one box's state, as ac_reduce. */
+int ac_batch_reduce(ac_batch *b, int box, int op, int quantity, double *out);
+/* Total cells, work items, z extent of an item, persistent CTAs, launches so far. */
+int ac_batch_info(const ac_batch *b, long long *cells, int *items, int *zc, int *ctas,
+                  unsigned long long *launches);
+
 /*
  * Allocation-free reduction (the paper has no counterpart; it exists for
  * callers that cannot allocate device memory -- for example an application

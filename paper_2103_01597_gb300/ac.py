@@ -46,6 +46,15 @@ class ac_params(ctypes.Structure):
                 ("precision", ctypes.c_int)]
 
 
+class ac_box(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
+                ("lx", ctypes.c_double), ("ly", ctypes.c_double), ("lz", ctypes.c_double),
+                ("nu", ctypes.c_double), ("eta", ctypes.c_double)]
+
+
+AC_BATCH_MAX_BOXES = 128
+
+
 class AcError(RuntimeError):
     def __init__(self, code, where, value=None):
         self.code = code
@@ -95,6 +104,21 @@ def load_library(path=None):
         "ac_launch_count": ([_vp, ctypes.POINTER(_c.c_ulonglong)], _c.c_int),
         "ac_reduce_noalloc": ([ctypes.POINTER(_vp), ctypes.POINTER(ac_grid),
                                ctypes.POINTER(ac_params), _c.c_int, _c.c_int, _pd, _vp], _c.c_int),
+        "ac_batch_init": ([ctypes.POINTER(_vp), _c.c_int, ctypes.POINTER(ac_box),
+                           ctypes.POINTER(ac_params), _vp], _c.c_int),
+        "ac_batch_quit": ([_vp], _c.c_int),
+        "ac_batch_load": ([_vp, _c.c_int, _c.c_int, _vp], _c.c_int),
+        "ac_batch_store": ([_vp, _c.c_int, _c.c_int, _vp], _c.c_int),
+        "ac_batch_load_w": ([_vp, _c.c_int, _c.c_int, _vp], _c.c_int),
+        "ac_batch_store_w": ([_vp, _c.c_int, _c.c_int, _vp], _c.c_int),
+        "ac_batch_integrate_substep": ([_vp, _c.c_double, _c.c_int], _c.c_int),
+        "ac_batch_integrate_step": ([_vp, _c.c_double], _c.c_int),
+        "ac_batch_set_graph": ([_vp, _c.c_int], _c.c_int),
+        "ac_batch_tune": ([_vp, _c.c_double, _c.c_char_p, ctypes.POINTER(_c.c_int)], _c.c_int),
+        "ac_batch_reduce": ([_vp, _c.c_int, _c.c_int, _c.c_int, _pd], _c.c_int),
+        "ac_batch_info": ([_vp, ctypes.POINTER(_c.c_longlong), ctypes.POINTER(_c.c_int),
+                           ctypes.POINTER(_c.c_int), ctypes.POINTER(_c.c_int),
+                           ctypes.POINTER(_c.c_ulonglong)], _c.c_int),
         "ac_strerror": ([_c.c_int], _c.c_char_p),
         "ac_last_cuda_error": ([], _c.c_char_p),
     }
@@ -248,6 +272,123 @@ def ac_launch_count(h):
     n = ctypes.c_ulonglong()
     _check(load_library().ac_launch_count(h, ctypes.byref(n)), "ac_launch_count")
     return n.value
+
+
+# ---- batched ensemble --------------------------------------------------------
+
+def ac_batch_init(boxes, common, stream=None):
+    arr = (ac_box * len(boxes))(*boxes)
+    b = _vp()
+    _check(load_library().ac_batch_init(ctypes.byref(b), len(boxes), arr, ctypes.byref(common),
+                                        _vp(stream or 0)), "ac_batch_init")
+    return b
+
+
+def ac_batch_quit(b):
+    _check(load_library().ac_batch_quit(b), "ac_batch_quit")
+
+
+def ac_batch_load(b, box, field, host_src):
+    _check(load_library().ac_batch_load(b, box, field, _host_ptr(host_src, False)), "ac_batch_load")
+
+
+def ac_batch_store(b, box, field, host_dst):
+    _check(load_library().ac_batch_store(b, box, field, _host_ptr(host_dst, True)), "ac_batch_store")
+
+
+def ac_batch_load_w(b, box, field, host_src):
+    _check(load_library().ac_batch_load_w(b, box, field, _host_ptr(host_src, False)),
+           "ac_batch_load_w")
+
+
+def ac_batch_store_w(b, box, field, host_dst):
+    _check(load_library().ac_batch_store_w(b, box, field, _host_ptr(host_dst, True)),
+           "ac_batch_store_w")
+
+
+def ac_batch_integrate_substep(b, dt, s):
+    _check(load_library().ac_batch_integrate_substep(b, float(dt), int(s)),
+           "ac_batch_integrate_substep")
+
+
+def ac_batch_integrate_step(b, dt):
+    _check(load_library().ac_batch_integrate_step(b, float(dt)), "ac_batch_integrate_step")
+
+
+def ac_batch_set_graph(b, enable):
+    _check(load_library().ac_batch_set_graph(b, int(bool(enable))), "ac_batch_set_graph")
+
+
+def ac_batch_tune(b, dt, cache_path=None):
+    zc = ctypes.c_int()
+    cp = cache_path.encode() if cache_path else None
+    _check(load_library().ac_batch_tune(b, float(dt), cp, ctypes.byref(zc)), "ac_batch_tune")
+    return zc.value
+
+
+def ac_batch_reduce(b, box, op, quantity):
+    out = ctypes.c_double()
+    rc = load_library().ac_batch_reduce(b, box, int(op), int(quantity), ctypes.byref(out))
+    _check(rc, "ac_batch_reduce", out.value)
+    return out.value
+
+
+def ac_batch_info(b):
+    cells = ctypes.c_longlong()
+    items, zc, ctas = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    launches = ctypes.c_ulonglong()
+    _check(load_library().ac_batch_info(b, ctypes.byref(cells), ctypes.byref(items),
+                                        ctypes.byref(zc), ctypes.byref(ctas),
+                                        ctypes.byref(launches)), "ac_batch_info")
+    return dict(cells=cells.value, items=items.value, zc=zc.value, ctas=ctas.value,
+                launches=launches.value)
+
+
+class Batch:
+    """An ensemble of boxes: `boxes` is a list of (n, L, nu, eta)."""
+
+    def __init__(self, boxes, precision=AC_FP32, cs0=1.0, gamma=5.0 / 3.0, cp=1.0, lnrho0=0.0,
+                 stream=None):
+        self.specs = [(tuple(n), tuple(L), nu, eta) for n, L, nu, eta in boxes]
+        arr = [ac_box(n[0], n[1], n[2], L[0], L[1], L[2], nu, eta) for n, L, nu, eta in self.specs]
+        common = make_params(cs0=cs0, gamma=gamma, cp=cp, lnrho0=lnrho0, precision=precision)
+        if stream is None:
+            import torch
+            stream = torch.cuda.current_stream().cuda_stream
+        self.b = ac_batch_init(arr, common, stream)
+        self._closed = False
+
+    def load(self, box, f):
+        ac_batch_load(self.b, box, AC_ALL, np.ascontiguousarray(f, dtype=np.float64))
+
+    def store(self, box):
+        nx, ny, nz = self.specs[box][0]
+        out = np.empty((8, nz, ny, nx))
+        ac_batch_store(self.b, box, AC_ALL, out)
+        return out
+
+    def store_w(self, box):
+        nx, ny, nz = self.specs[box][0]
+        out = np.empty((8, nz, ny, nx))
+        ac_batch_store_w(self.b, box, AC_ALL, out)
+        return out
+
+    def step(self, dt):
+        ac_batch_integrate_step(self.b, dt)
+
+    def substep(self, dt, s):
+        ac_batch_integrate_substep(self.b, dt, s)
+
+    def close(self):
+        if not self._closed:
+            ac_batch_quit(self.b)
+            self._closed = True
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class Simulation:

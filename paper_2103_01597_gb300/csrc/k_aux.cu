@@ -225,27 +225,30 @@ constexpr int RED_MAX_BLOCKS = 8 * 152;  // eight 256-thread CTAs per SM
 
 int reduce_max_blocks() { return RED_MAX_BLOCKS; }
 
+// Rows of constant (y, z) are dealt to warps; lanes walk x.  The periodic
+// offsets of y and z are set once per row, those of x once per cell.
 template <typename R, class IX>
 __global__ void __launch_bounds__(RED_THREADS) reduce_kernel(PtrPack<const R> pk, Geom g,
                                                              DevCoefs<R> k, int op, int quantity,
                                                              double *partials,
                                                              unsigned int *flags) {
-    const long long plane = (long long)g.nx * g.ny;
-    const long long total = plane * g.nz;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const long long rows = (long long)g.ny * g.nz;
     double acc = red_init(op);
     unsigned int bad = 0;
-    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
-         t += (long long)gridDim.x * blockDim.x) {
-        const int kz = (int)(t / plane);
-        const long long rem = t - (long long)kz * plane;
-        const int j = (int)(rem / g.nx);
-        const int i = (int)(rem - (long long)j * g.nx);
+    for (long long row = (long long)blockIdx.x * (RED_THREADS / 32) + wid; row < rows;
+         row += (long long)gridDim.x * (RED_THREADS / 32)) {
+        const int kz = (int)(row / g.ny);
+        const int j = (int)(row - (long long)kz * g.ny);
         IX ix;
-        ix.set_xy(i, j, g);
+        ix.set_xy(0, j, g);
         ix.set_z(kz, g);
-        const double v = cell_quantity<R>(pk.p, ix, k, quantity);
-        if (!isfinite(v)) bad = 1;
-        acc = red_combine(op, acc, op == AC_RMS ? v * v : v);
+        for (int i = lane; i < g.nx; i += 32) {
+            ix.set_x(i, g);
+            const double v = cell_quantity<R>(pk.p, ix, k, quantity);
+            if (!isfinite(v)) bad = 1;
+            acc = red_combine(op, acc, op == AC_RMS ? v * v : v);
+        }
     }
     __shared__ double sh[RED_THREADS / 32];
     __shared__ unsigned int shb[RED_THREADS / 32];
@@ -254,7 +257,6 @@ __global__ void __launch_bounds__(RED_THREADS) reduce_kernel(PtrPack<const R> pk
         acc = red_combine(op, acc, __shfl_down_sync(0xffffffffu, acc, o));
         bad |= __shfl_down_sync(0xffffffffu, bad, o);
     }
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     if (lane == 0) {
         sh[wid] = acc;
         shb[wid] = bad;
@@ -304,7 +306,8 @@ static cudaError_t launch_reduce_t(const ReduceLaunch &L, cudaStream_t st, int *
     for (int q = 0; q < NF; ++q) pk.p[q] = static_cast<const R *>(L.f[q]);
     const DevCoefs<R> k = to_dev<R>(L.c, L.ph);
     const long long total = (long long)L.g.nx * L.g.ny * L.g.nz;
-    long long blocks = (total + RED_THREADS - 1) / RED_THREADS;
+    const long long rows = (long long)L.g.ny * L.g.nz;
+    long long blocks = (rows + RED_THREADS / 32 - 1) / (RED_THREADS / 32);
     if (blocks > L.blocks) blocks = L.blocks;
     if (blocks < 1) blocks = 1;
     if (L.g.padded)

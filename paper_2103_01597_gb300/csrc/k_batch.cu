@@ -1,0 +1,574 @@
+// Batched ensemble of independent periodic boxes (uneven sizes, per-box nu and
+// eta) advanced by one persistent kernel launch per Runge-Kutta substep.
+//
+// The paper notes that parameter scans inflate problem sizes (Sec. 4); here a
+// scan is a set of small boxes integrated together.  Work items are
+// (box, 32 x 8 column tile, z range); they are sorted by cost (largest first)
+// and taken by persistent CTAs from a device counter that a memset node resets
+// before every launch, so the kernel boundary is the only cross-CTA
+// synchronisation.  Each item runs the same tile body as the single-box
+// binary32 kernel, so every box's result is bitwise the single-box result.
+// The three substeps of a step can be captured into a CUDA graph, and the z
+// extent of the items is chosen by a measuring autotuner.
+#include <stdint.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <algorithm>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "substep_tiled.cuh"
+
+namespace ac {
+
+// One box of the ensemble as the kernel sees it (kernel-parameter space).
+struct BatchBox {
+    int nx, ny, nz, pad;
+    long long off;  // element offset of the box's first field in each pool
+    long long n;    // cells of the box (elements per field)
+    DevCoefs<float> k;
+};
+
+template <typename W>
+struct BatchArgs {
+    const float *fin;  // state pool read this substep
+    float *fout;       // state pool written this substep
+    W *w;              // accumulator pool
+    const int4 *items; // (box, x0, y0, z0 << 16 | z1)
+    unsigned int *counter;
+    int nitems;
+    int s0;
+    W alpha, beta, dt;
+    BatchBox box[AC_BATCH_MAX_BOXES];
+};
+
+// Argument adapter of one box inside the persistent kernel.
+template <typename W>
+struct TileBox {
+    const BatchArgs<W> &b;
+    const BatchBox &x;
+    Geom gg;
+    __device__ __forceinline__ TileBox(const BatchArgs<W> &b_, const BatchBox &x_) : b(b_), x(x_) {
+        gg.nx = x.nx;
+        gg.ny = x.ny;
+        gg.nz = x.nz;
+        gg.padded = 0;
+        gg.px = x.nx;
+        gg.pxy = (long long)x.nx * x.ny;
+        gg.origin = 0;
+        gg.elems = x.n;
+    }
+    __device__ __forceinline__ const float *fin(int q) const { return b.fin + x.off + q * x.n; }
+    __device__ __forceinline__ float *fout(int q) const { return b.fout + x.off + q * x.n; }
+    __device__ __forceinline__ W *w(int q) const { return b.w + x.off + q * x.n; }
+    __device__ __forceinline__ const Geom &g() const { return gg; }
+    __device__ __forceinline__ const DevCoefs<float> &k() const { return x.k; }
+    __device__ __forceinline__ W alpha() const { return b.alpha; }
+    __device__ __forceinline__ W beta() const { return b.beta; }
+    __device__ __forceinline__ W dt() const { return b.dt; }
+    __device__ __forceinline__ int s0() const { return b.s0; }
+    __device__ __forceinline__ int force_on() const { return 0; }
+    __device__ __forceinline__ const float2 *ftab() const { return nullptr; }
+    __device__ __forceinline__ float amp_e(int) const { return 0.f; }
+};
+
+template <typename W>
+__global__ void __launch_bounds__(TT_THREADS, 1) batch_substep_kernel(const __grid_constant__ BatchArgs<W> b) {
+    extern __shared__ __align__(128) unsigned char bt_smem_raw[];
+    __shared__ int item_sh;
+    for (;;) {
+        if (threadIdx.x == 0 && threadIdx.y == 0) item_sh = (int)atomicAdd(b.counter, 1u);
+        __syncthreads();
+        const int it = item_sh;
+        __syncthreads();  // every thread has read item_sh before it is overwritten
+        if (it >= b.nitems) break;
+        const int4 wi = b.items[it];
+        const TileBox<W> ta(b, b.box[wi.x]);
+        tiled_body<W, true>(ta, wi.y, wi.z, wi.w >> 16, wi.w & 0xffff, bt_smem_raw);
+    }
+}
+
+}  // namespace ac
+
+using namespace ac;
+
+static const double B_ALPHA[3] = {0.0, -5.0 / 9.0, -153.0 / 128.0};
+static const double B_BETA[3] = {1.0 / 3.0, 15.0 / 16.0, 8.0 / 15.0};
+
+struct ac_batch {
+    int nbox;
+    std::vector<ac_box> boxes;
+    ac_params common;
+    int precision;
+    int elem_w;
+    cudaStream_t stream;
+    std::vector<long long> off, n;
+    long long total;  // cells over all boxes
+    void *block;      // one allocation: two state pools, w pool
+    float *pool[2];
+    void *wpool;
+    int cur;
+    std::vector<DevCoefs<float>> coefs;
+    int4 *items_dev;
+    int nitems;
+    unsigned int *counter;
+    int zc;           // z extent of a work item (tuned)
+    int ctas;         // persistent CTAs
+    int next_s;
+    unsigned long long step;
+    int graph_on;
+    cudaStream_t cap_stream;
+    cudaGraphExec_t exec[2];
+    double graph_dt[2];
+    double *stage;
+    size_t stage_elems;
+    double *partials, *result_dev, *result_host;
+    unsigned int *flags;
+    unsigned long long launches;
+};
+
+#define BCK(call)                                      \
+    do {                                               \
+        cudaError_t e_ = (call);                       \
+        if (e_ != cudaSuccess) return ac_report_cuda(e_); \
+    } while (0)
+
+static int build_items(ac_batch *b, int zc) {
+    std::vector<int4> items;
+    std::vector<int> cost;
+    for (int bx = 0; bx < b->nbox; ++bx) {
+        const ac_box &x = b->boxes[bx];
+        const int z = std::min(zc, x.nz);
+        for (int z0 = 0; z0 < x.nz; z0 += z)
+            for (int y0 = 0; y0 < x.ny; y0 += TT_Y)
+                for (int x0 = 0; x0 < x.nx; x0 += TT_X) {
+                    const int z1 = std::min(z0 + z, x.nz);
+                    items.push_back(make_int4(bx, x0, y0, (z0 << 16) | z1));
+                    cost.push_back((z1 - z0 + 6) * std::min(TT_Y, x.ny - y0));
+                }
+    }
+    std::vector<int> order(items.size());
+    for (size_t i = 0; i < order.size(); ++i) order[i] = (int)i;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int c) { return cost[a] > cost[c]; });
+    std::vector<int4> sorted(items.size());
+    for (size_t i = 0; i < order.size(); ++i) sorted[i] = items[order[i]];
+    if (b->items_dev) {
+        BCK(cudaStreamSynchronize(b->stream));
+        cudaFree(b->items_dev);
+        b->items_dev = nullptr;
+    }
+    BCK(cudaMalloc(&b->items_dev, sizeof(int4) * sorted.size()));
+    BCK(cudaMemcpy(b->items_dev, sorted.data(), sizeof(int4) * sorted.size(),
+                   cudaMemcpyHostToDevice));
+    b->nitems = (int)sorted.size();
+    b->zc = zc;
+    for (int c = 0; c < 2; ++c)
+        if (b->exec[c]) {
+            cudaGraphExecDestroy(b->exec[c]);
+            b->exec[c] = nullptr;
+        }
+    return AC_OK;
+}
+
+template <typename W>
+static cudaError_t launch_batch_t(ac_batch *b, double dt, int s, int cur, cudaStream_t st) {
+    BatchArgs<W> a;
+    a.fin = b->pool[cur];
+    a.fout = b->pool[1 - cur];
+    a.w = static_cast<W *>(b->wpool);
+    a.items = b->items_dev;
+    a.counter = b->counter;
+    a.nitems = b->nitems;
+    a.s0 = s == 0;
+    a.alpha = (W)B_ALPHA[s];
+    a.beta = (W)B_BETA[s];
+    a.dt = (W)dt;
+    for (int i = 0; i < b->nbox; ++i) {
+        a.box[i].nx = b->boxes[i].nx;
+        a.box[i].ny = b->boxes[i].ny;
+        a.box[i].nz = b->boxes[i].nz;
+        a.box[i].pad = 0;
+        a.box[i].off = b->off[i];
+        a.box[i].n = b->n[i];
+        a.box[i].k = b->coefs[i];
+    }
+    cudaError_t e = cudaMemsetAsync(b->counter, 0, sizeof(unsigned int), st);
+    if (e != cudaSuccess) return e;
+    const size_t smem = tt_smem_bytes<W>();
+    e = cudaFuncSetAttribute(batch_substep_kernel<W>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem);
+    if (e != cudaSuccess) return e;
+    batch_substep_kernel<W><<<b->ctas, dim3(TT_X, TT_Y, 1), smem, st>>>(a);
+    return cudaGetLastError();
+}
+
+static cudaError_t launch_batch(ac_batch *b, double dt, int s, int cur, cudaStream_t st) {
+    if (b->precision == AC_FP32) return launch_batch_t<float>(b, dt, s, cur, st);
+    return launch_batch_t<double>(b, dt, s, cur, st);
+}
+
+static void free_batch(ac_batch *b) {
+    for (int c = 0; c < 2; ++c)
+        if (b->exec[c]) cudaGraphExecDestroy(b->exec[c]);
+    if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
+    if (b->block) cudaFree(b->block);
+    if (b->items_dev) cudaFree(b->items_dev);
+    if (b->counter) cudaFree(b->counter);
+    if (b->stage) cudaFree(b->stage);
+    if (b->partials) cudaFree(b->partials);
+    if (b->flags) cudaFree(b->flags);
+    if (b->result_dev) cudaFree(b->result_dev);
+    if (b->result_host) cudaFreeHost(b->result_host);
+}
+
+extern "C" int ac_batch_init(ac_batch **out, int nbox, const ac_box *boxes, const ac_params *common,
+                             void *stream) {
+    if (!out || !boxes || !common || nbox < 1 || nbox > AC_BATCH_MAX_BOXES) return AC_ERR_ARG;
+    *out = nullptr;
+    if (common->precision != AC_FP32 && common->precision != AC_FP32_W64) return AC_ERR_ARG;
+    if (common->force_amp != 0.0) return AC_ERR_ARG;
+    if (!(common->cs0 > 0) || !(common->gamma > 1.0) || !(common->cp > 0) ||
+        !isfinite(common->lnrho0))
+        return AC_ERR_ARG;
+    for (int i = 0; i < nbox; ++i) {
+        const ac_box &x = boxes[i];
+        if (x.nx < 1 || x.ny < 1 || x.nz < 1 || x.nx % 4 || x.nx > 4096 || x.ny > 4096 ||
+            x.nz > 4096)
+            return AC_ERR_ARG;
+        if (!(x.lx > 0) || !(x.ly > 0) || !(x.lz > 0) || !(x.nu >= 0) || !(x.eta >= 0) ||
+            !isfinite(x.nu) || !isfinite(x.eta))
+            return AC_ERR_ARG;
+    }
+    ac_batch *b = new (std::nothrow) ac_batch();
+    if (!b) return AC_ERR_OOM;
+    b->nbox = nbox;
+    b->boxes.assign(boxes, boxes + nbox);
+    b->common = *common;
+    b->precision = common->precision;
+    b->elem_w = common->precision == AC_FP32 ? 4 : 8;
+    b->stream = static_cast<cudaStream_t>(stream);
+    long long total = 0;
+    for (int i = 0; i < nbox; ++i) {
+        const ac_box &x = boxes[i];
+        b->off.push_back(8 * total);
+        b->n.push_back((long long)x.nx * x.ny * x.nz);
+        total += (long long)x.nx * x.ny * x.nz;
+        ac_params p = *common;
+        p.nu = x.nu;
+        p.eta = x.eta;
+        const double dx[3] = {x.lx / x.nx, x.ly / x.ny, x.lz / x.nz};
+        b->coefs.push_back(to_dev<float>(make_coefs(dx), make_phys(p)));
+    }
+    b->total = total;
+    const size_t fbytes = (size_t)8 * total * sizeof(float);
+    const size_t wbytes = (size_t)8 * total * b->elem_w;
+    cudaError_t e = cudaMalloc(&b->block, 2 * fbytes + wbytes);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b->block, 0, 2 * fbytes + wbytes, b->stream);
+    if (e == cudaSuccess) e = cudaMalloc(&b->counter, sizeof(unsigned int));
+    if (e == cudaSuccess) e = cudaMalloc(&b->partials, sizeof(double) * reduce_max_blocks());
+    if (e == cudaSuccess) e = cudaMalloc(&b->flags, sizeof(unsigned int) * reduce_max_blocks());
+    if (e == cudaSuccess) e = cudaMalloc(&b->result_dev, 2 * sizeof(double));
+    if (e == cudaSuccess) e = cudaMallocHost(&b->result_host, 2 * sizeof(double));
+    int dev = 0, sms = 152, occ = 1;
+    if (e == cudaSuccess) e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess) {
+        const size_t smem = b->precision == AC_FP32 ? tt_smem_bytes<float>() : tt_smem_bytes<double>();
+        if (b->precision == AC_FP32) {
+            e = cudaFuncSetAttribute(batch_substep_kernel<float>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e == cudaSuccess)
+                e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, batch_substep_kernel<float>,
+                                                                  TT_THREADS, smem);
+        } else {
+            e = cudaFuncSetAttribute(batch_substep_kernel<double>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e == cudaSuccess)
+                e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                    &occ, batch_substep_kernel<double>, TT_THREADS, smem);
+        }
+    }
+    if (e != cudaSuccess) {
+        int rc = ac_report_cuda(e);
+        free_batch(b);
+        delete b;
+        return rc;
+    }
+    b->pool[0] = static_cast<float *>(b->block);
+    b->pool[1] = reinterpret_cast<float *>(static_cast<char *>(b->block) + fbytes);
+    b->wpool = static_cast<char *>(b->block) + 2 * fbytes;
+    b->ctas = sms * (occ < 1 ? 1 : occ);
+    int rc = build_items(b, 64);
+    if (rc) {
+        free_batch(b);
+        delete b;
+        return rc;
+    }
+    *out = b;
+    return AC_OK;
+}
+
+extern "C" int ac_batch_quit(ac_batch *b) {
+    if (!b) return AC_OK;
+    cudaStreamSynchronize(b->stream);
+    free_batch(b);
+    delete b;
+    return AC_OK;
+}
+
+static int batch_stage(ac_batch *b, size_t need) {
+    if (b->stage_elems >= need) return AC_OK;
+    if (b->stage) {
+        BCK(cudaStreamSynchronize(b->stream));
+        cudaFree(b->stage);
+        b->stage = nullptr;
+        b->stage_elems = 0;
+    }
+    BCK(cudaMalloc(&b->stage, need * sizeof(double)));
+    b->stage_elems = need;
+    return AC_OK;
+}
+
+static Geom box_geom(const ac_box &x) { return make_geom(x.nx, x.ny, x.nz, AC_LAYOUT_PERIODIC); }
+
+static int batch_copy(ac_batch *b, int box, int field, double *host, int to_device, int w_arr) {
+    if (!b || !host || box < 0 || box >= b->nbox || field < AC_ALL || field >= NF) return AC_ERR_ARG;
+    const Geom g = box_geom(b->boxes[box]);
+    const long long n = b->n[box];
+    int rc = batch_stage(b, (size_t)n);
+    if (rc) return rc;
+    const int q0 = field == AC_ALL ? 0 : field, q1 = field == AC_ALL ? NF : field + 1;
+    for (int q = q0; q < q1; ++q) {
+        double *h = host + (field == AC_ALL ? (size_t)q * n : 0);
+        void *dev;
+        int es;
+        if (w_arr) {
+            es = b->elem_w;
+            dev = static_cast<char *>(b->wpool) + (size_t)(b->off[box] + q * n) * es;
+        } else {
+            es = 4;
+            dev = b->pool[b->cur] + b->off[box] + q * n;
+        }
+        if (to_device) {
+            BCK(cudaMemcpyAsync(b->stage, h, n * sizeof(double), cudaMemcpyHostToDevice, b->stream));
+            BCK(launch_scatter(b->stage, dev, es, g, 0, g.nz, b->stream));
+        } else {
+            BCK(launch_gather(dev, es, g, 0, g.nz, b->stage, b->stream));
+            BCK(cudaMemcpyAsync(h, b->stage, n * sizeof(double), cudaMemcpyDeviceToHost, b->stream));
+        }
+        b->launches++;
+    }
+    if (!to_device) BCK(cudaStreamSynchronize(b->stream));
+    else if (!w_arr) b->next_s = 0;
+    return AC_OK;
+}
+
+extern "C" int ac_batch_load(ac_batch *b, int box, int field, const double *host) {
+    return batch_copy(b, box, field, const_cast<double *>(host), 1, 0);
+}
+extern "C" int ac_batch_store(ac_batch *b, int box, int field, double *host) {
+    return batch_copy(b, box, field, host, 0, 0);
+}
+extern "C" int ac_batch_load_w(ac_batch *b, int box, int field, const double *host) {
+    return batch_copy(b, box, field, const_cast<double *>(host), 1, 1);
+}
+extern "C" int ac_batch_store_w(ac_batch *b, int box, int field, double *host) {
+    return batch_copy(b, box, field, host, 0, 1);
+}
+
+extern "C" int ac_batch_integrate_substep(ac_batch *b, double dt, int s) {
+    if (!b || s < 0 || s > 2 || !isfinite(dt)) return AC_ERR_ARG;
+    if (s != b->next_s) return AC_ERR_STATE;
+    BCK(launch_batch(b, dt, s, b->cur, b->stream));
+    b->launches++;
+    b->cur = 1 - b->cur;
+    b->next_s = (s + 1) % 3;
+    if (s == 2) b->step++;
+    return AC_OK;
+}
+
+// Capture the three substeps of a step that starts from state pool `cur`.
+static int capture_step(ac_batch *b, double dt, int cur) {
+    if (!b->cap_stream) BCK(cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking));
+    if (b->exec[cur]) {
+        cudaGraphExecDestroy(b->exec[cur]);
+        b->exec[cur] = nullptr;
+    }
+    BCK(cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal));
+    cudaError_t e = cudaSuccess;
+    int c = cur;
+    for (int s = 0; s < 3 && e == cudaSuccess; ++s) {
+        e = launch_batch(b, dt, s, c, b->cap_stream);
+        c = 1 - c;
+    }
+    cudaGraph_t graph = nullptr;
+    cudaError_t e2 = cudaStreamEndCapture(b->cap_stream, &graph);
+    if (e == cudaSuccess) e = e2;
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&b->exec[cur], graph, 0);
+    if (graph) cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return ac_report_cuda(e);
+    b->graph_dt[cur] = dt;
+    return AC_OK;
+}
+
+extern "C" int ac_batch_set_graph(ac_batch *b, int enable) {
+    if (!b) return AC_ERR_ARG;
+    b->graph_on = enable != 0;
+    return AC_OK;
+}
+
+extern "C" int ac_batch_integrate_step(ac_batch *b, double dt) {
+    if (!b || !isfinite(dt)) return AC_ERR_ARG;
+    if (b->next_s != 0) return AC_ERR_STATE;
+    if (!b->graph_on) {
+        for (int s = 0; s < 3; ++s) {
+            int rc = ac_batch_integrate_substep(b, dt, s);
+            if (rc) return rc;
+        }
+        return AC_OK;
+    }
+    if (!b->exec[b->cur] || b->graph_dt[b->cur] != dt) {
+        int rc = capture_step(b, dt, b->cur);
+        if (rc) return rc;
+    }
+    BCK(cudaGraphLaunch(b->exec[b->cur], b->stream));
+    b->launches += 3;
+    b->cur = 1 - b->cur;  // three substeps: an odd number of pool swaps
+    b->step++;
+    return AC_OK;
+}
+
+// Autotuner: time substep 0 (which reads only the current state, so the state
+// is unchanged) for each candidate z extent of the work items and keep the
+// fastest.  With a cache path, a line "<signature> <zc>" is read or appended.
+static std::string batch_signature(const ac_batch *b) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceProp prop;
+    memset(&prop, 0, sizeof prop);
+    cudaGetDeviceProperties(&prop, dev);
+    uint64_t h = 1469598103934665603ull;  // FNV-1a over the box sizes
+    for (const ac_box &x : b->boxes) {
+        const int v[3] = {x.nx, x.ny, x.nz};
+        for (int a = 0; a < 3; ++a) {
+            h ^= (uint64_t)(unsigned)v[a];
+            h *= 1099511628211ull;
+        }
+    }
+    char buf[256];
+    snprintf(buf, sizeof buf, "%s|sm%d|p%d|n%d|%016llx", prop.name, prop.multiProcessorCount,
+             b->precision, b->nbox, (unsigned long long)h);
+    std::string s(buf);
+    for (char &c : s)
+        if (c == ' ') c = '_';
+    return s;
+}
+
+extern "C" int ac_batch_tune(ac_batch *b, double dt, const char *cache_path, int *zc_out) {
+    if (!b || !isfinite(dt)) return AC_ERR_ARG;
+    if (b->next_s != 0) return AC_ERR_STATE;
+    const std::string sig = batch_signature(b);
+    if (cache_path) {
+        FILE *f = fopen(cache_path, "r");
+        if (f) {
+            char key[512];
+            int zc = 0;
+            int found = 0;
+            while (fscanf(f, "%511s %d", key, &zc) == 2)
+                if (sig == key && zc > 0) found = zc;
+            fclose(f);
+            if (found) {
+                int rc = build_items(b, found);
+                if (rc) return rc;
+                if (zc_out) *zc_out = found;
+                return AC_OK;
+            }
+        }
+    }
+    const int cand[5] = {8, 16, 32, 64, 128};
+    cudaEvent_t e0, e1;
+    BCK(cudaEventCreate(&e0));
+    BCK(cudaEventCreate(&e1));
+    float best = 1e30f;
+    int best_zc = b->zc;
+    for (int c = 0; c < 5; ++c) {
+        int rc = build_items(b, cand[c]);
+        if (rc) return rc;
+        BCK(launch_batch(b, dt, 0, b->cur, b->stream));  // warm-up
+        float tmin = 1e30f;
+        for (int r = 0; r < 3; ++r) {
+            BCK(cudaEventRecord(e0, b->stream));
+            BCK(launch_batch(b, dt, 0, b->cur, b->stream));
+            BCK(cudaEventRecord(e1, b->stream));
+            BCK(cudaEventSynchronize(e1));
+            float ms = 0.f;
+            BCK(cudaEventElapsedTime(&ms, e0, e1));
+            tmin = ms < tmin ? ms : tmin;
+        }
+        b->launches += 4;
+        if (tmin < best) {
+            best = tmin;
+            best_zc = cand[c];
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    int rc = build_items(b, best_zc);
+    if (rc) return rc;
+    if (cache_path) {
+        FILE *f = fopen(cache_path, "a");
+        if (f) {
+            fprintf(f, "%s %d\n", sig.c_str(), best_zc);
+            fclose(f);
+        }
+    }
+    if (zc_out) *zc_out = best_zc;
+    return AC_OK;
+}
+
+extern "C" int ac_batch_reduce(ac_batch *b, int box, int op, int quantity, double *out) {
+    if (!b || !out || box < 0 || box >= b->nbox || op < AC_MAX || op > AC_RMS || quantity < 0 ||
+        quantity > AC_Q_CFL)
+        return AC_ERR_ARG;
+    ReduceLaunch L;
+    L.precision = AC_FP32;
+    L.g = box_geom(b->boxes[box]);
+    for (int q = 0; q < NF; ++q) L.f[q] = b->pool[b->cur] + b->off[box] + q * b->n[box];
+    const ac_box &x = b->boxes[box];
+    const double dx[3] = {x.lx / x.nx, x.ly / x.ny, x.lz / x.nz};
+    ac_params p = b->common;
+    p.nu = x.nu;
+    p.eta = x.eta;
+    L.c = make_coefs(dx);
+    L.ph = make_phys(p);
+    L.op = op;
+    L.quantity = quantity;
+    L.partials = b->partials;
+    L.flags = b->flags;
+    L.result = b->result_dev;
+    L.blocks = reduce_max_blocks();
+    int nl = 0;
+    BCK(launch_reduce(L, b->stream, &nl));
+    b->launches += nl;
+    BCK(cudaMemcpyAsync(b->result_host, b->result_dev, 2 * sizeof(double), cudaMemcpyDeviceToHost,
+                        b->stream));
+    BCK(cudaStreamSynchronize(b->stream));
+    *out = b->result_host[0];
+    unsigned int flag;
+    memcpy(&flag, &b->result_host[1], sizeof flag);
+    return flag ? AC_ERR_NONFINITE : AC_OK;
+}
+
+extern "C" int ac_batch_info(const ac_batch *b, long long *cells, int *items, int *zc, int *ctas,
+                             unsigned long long *launches) {
+    if (!b) return AC_ERR_ARG;
+    if (cells) *cells = b->total;
+    if (items) *items = b->nitems;
+    if (zc) *zc = b->zc;
+    if (ctas) *ctas = b->ctas;
+    if (launches) *launches = b->launches;
+    return AC_OK;
+}

@@ -66,6 +66,10 @@ struct IdxPeriodic {
 #pragma unroll
         for (int d = 0; d < 7; ++d) zo[d] = (long long)wrap_near(k + d - 3, g.nz) * g.pxy;
     }
+    __device__ __forceinline__ void set_x(int i, const Geom &g) {
+#pragma unroll
+        for (int d = 0; d < 7; ++d) xo[d] = wrap_near(i + d - 3, g.nx);
+    }
     __device__ __forceinline__ long long operator()(int dx, int dy, int dz) const {
         return zo[dz + 3] + yo[dy + 3] + xo[dx + 3];
     }
@@ -73,16 +77,27 @@ struct IdxPeriodic {
 
 // Cell addressing inside a padded array whose halo holds the periodic images.
 struct IdxPadded {
-    long long c, base;
-    int px;
+    long long c;     // current cell
+    long long jrow;  // origin + j * px
+    long long row;   // jrow + k * pxy
+    int i, px;
     long long pxy;
-    __device__ __forceinline__ void set_xy(int i, int j, const Geom &g) {
+    __device__ __forceinline__ void set_xy(int i_, int j, const Geom &g) {
         px = g.px;
         pxy = g.pxy;
-        base = g.origin + (long long)j * g.px + i;
-        c = base;
+        i = i_;
+        jrow = g.origin + (long long)j * g.px;
+        row = jrow;
+        c = row + i;
     }
-    __device__ __forceinline__ void set_z(int k, const Geom &g) { c = base + (long long)k * pxy; }
+    __device__ __forceinline__ void set_z(int k, const Geom &) {
+        row = jrow + (long long)k * pxy;
+        c = row + i;
+    }
+    __device__ __forceinline__ void set_x(int i_, const Geom &) {
+        i = i_;
+        c = row + i;
+    }
     __device__ __forceinline__ long long operator()(int dx, int dy, int dz) const {
         return c + dz * pxy + (long long)dy * px + dx;
     }

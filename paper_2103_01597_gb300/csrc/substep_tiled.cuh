@@ -93,7 +93,8 @@ struct TileCopies {
     int soff[N];
     const float *src[N];
     int n;
-    __device__ __forceinline__ void init(const float *const *fin, const Geom &g, int x0, int y0) {
+    template <class TA>
+    __device__ __forceinline__ void init(const TA &ta, const Geom &g, int x0, int y0) {
         const int tid = threadIdx.y * TT_X + threadIdx.x;
         n = 0;
         constexpr int CW = VEC ? 4 : 1;             // floats per copy
@@ -110,7 +111,7 @@ struct TileCopies {
                 const int gy = wrap_mod(y0 - 3 + r, g.ny);
                 const int gx = wrap_mod(x0 - 4 + CW * c, g.nx);
                 soff[u] = q * TT_FIELD + r * TT_ROW + CW * c;
-                src[u] = fin[q] + (long long)gy * g.px + gx;
+                src[u] = ta.fin(q) + (long long)gy * g.px + gx;
                 n = u + 1;
             }
         }
@@ -130,8 +131,8 @@ struct TileCopies {
 };
 
 // Copy this thread's accumulator values of output plane z into a w ring slot.
-template <typename W>
-__device__ __forceinline__ void tile_load_w(W *wslot, W *const *w, const Geom &g, int i, int j,
+template <typename W, class TA>
+__device__ __forceinline__ void tile_load_w(W *wslot, const TA &ta, const Geom &g, int i, int j,
                                             int z, bool active) {
     if (!active) return;
     const int tid = threadIdx.y * TT_X + threadIdx.x;
@@ -139,52 +140,71 @@ __device__ __forceinline__ void tile_load_w(W *wslot, W *const *w, const Geom &g
 #pragma unroll
     for (int q = 0; q < NF; ++q) {
         if (sizeof(W) == 8) {
-            cp_async8(wslot + q * TT_THREADS + tid, w[q] + o);
+            cp_async8(wslot + q * TT_THREADS + tid, ta.w(q) + o);
         } else {
-            cp_async4(wslot + q * TT_THREADS + tid, w[q] + o);
+            cp_async4(wslot + q * TT_THREADS + tid, ta.w(q) + o);
         }
     }
 }
 
-template <typename W, bool VEC>
-__global__ void __launch_bounds__(TT_THREADS, 1) substep_tiled_kernel(const SubstepArgs<float, W> a) {
-    extern __shared__ __align__(128) unsigned char tt_smem_raw[];
-    float *sm = reinterpret_cast<float *>(tt_smem_raw);
+// Argument adapter of the single-box launch: eight field pointers per buffer.
+template <typename W>
+struct TileOne {
+    const SubstepArgs<float, W> &a;
+    __device__ __forceinline__ const float *fin(int q) const { return a.fin[q]; }
+    __device__ __forceinline__ float *fout(int q) const { return a.fout[q]; }
+    __device__ __forceinline__ W *w(int q) const { return a.w[q]; }
+    __device__ __forceinline__ const Geom &g() const { return a.g; }
+    __device__ __forceinline__ const DevCoefs<float> &k() const { return a.k; }
+    __device__ __forceinline__ W alpha() const { return a.alpha; }
+    __device__ __forceinline__ W beta() const { return a.beta; }
+    __device__ __forceinline__ W dt() const { return a.dt; }
+    __device__ __forceinline__ int s0() const { return a.s0; }
+    __device__ __forceinline__ int force_on() const { return a.force_on; }
+    __device__ __forceinline__ const float2 *ftab() const { return a.ftab; }
+    __device__ __forceinline__ float amp_e(int m) const { return a.amp_e[m]; }
+};
+
+// One output tile: columns [x0, x0+32) x [y0, y0+8), planes [z0, z1).
+template <typename W, bool VEC, class TA>
+__device__ __forceinline__ void tiled_body(const TA &ta, int x0, int y0, int z0, int z1,
+                                           unsigned char *smem_raw) {
+    float *sm = reinterpret_cast<float *>(smem_raw);
     W *wring = reinterpret_cast<W *>(sm + TT_NP * TT_PLANE);
+    const Geom &g = ta.g();
     const int tx = threadIdx.x, ty = threadIdx.y;
     const int tid = ty * TT_X + tx;
-    const int x0 = blockIdx.x * TT_X, y0 = blockIdx.y * TT_Y;
-    const int z0 = blockIdx.z * a.zchunk;
-    const int z1 = min(z0 + a.zchunk, a.g.nz);
     const int i = x0 + tx, j = y0 + ty;
-    const bool active = i < a.g.nx && j < a.g.ny;
+    const bool active = i < g.nx && j < g.ny;
+    const int force_on = ta.force_on();
+    const int s0 = ta.s0();
 
     float2 exy = make_float2(0.f, 0.f);
-    if (a.force_on && active) {
-        const float2 ex = a.ftab[i], ey = a.ftab[a.g.nx + j];
+    if (force_on && active) {
+        const float2 ex = ta.ftab()[i], ey = ta.ftab()[g.nx + j];
         exy.x = ex.x * ey.x - ex.y * ey.y;
         exy.y = ex.x * ey.y + ex.y * ey.x;
     }
     TileCopies<VEC> cp;
-    cp.init(a.fin, a.g, x0, y0);
+    cp.init(ta, g, x0, y0);
 
     // One commit group per plane p; it also carries w of output plane p - 3.
     auto issue = [&](int p) {
-        if (p <= z1 + 2) cp.issue(sm + ((p - z0 + 3) % TT_NP) * TT_PLANE, a.g, p);
+        if (p <= z1 + 2) cp.issue(sm + ((p - z0 + 3) % TT_NP) * TT_PLANE, g, p);
         const int zw = p - 3;
-        if (!a.s0 && zw >= z0 && zw < z1)
-            tile_load_w<W>(wring + ((zw - z0) % TT_NW) * (NF * TT_THREADS), a.w, a.g, i, j, zw,
+        if (!s0 && zw >= z0 && zw < z1)
+            tile_load_w<W>(wring + ((zw - z0) % TT_NW) * (NF * TT_THREADS), ta, g, i, j, zw,
                            active);
         cp_async_commit();
     };
     for (int p = z0 - 3; p <= z0 + 3 + TT_PF; ++p) issue(p);
 
     float zq[NF][7];  // z-column of this thread's cell: planes z-3 .. z+3
-    const float2 *ztab = a.ftab + a.g.nx + a.g.ny;
-    float2 ez_next = a.force_on ? ztab[z0] : make_float2(0.f, 0.f);
+    const float2 *ztab = force_on ? ta.ftab() + g.nx + g.ny : nullptr;
+    float2 ez_next = force_on ? ztab[z0] : make_float2(0.f, 0.f);
     for (int z = z0; z < z1; ++z) {
         const float2 ez = ez_next;  // forcing phase of plane z, loaded one plane ahead
-        if (a.force_on && z + 1 < z1) ez_next = ztab[z + 1];
+        if (force_on && z + 1 < z1) ez_next = ztab[z + 1];
         cp_async_wait<TT_PF>();  // plane z+3 (and w of plane z) have landed for this thread
         __syncthreads();         // ... and for every thread
         int slot[7];
@@ -207,28 +227,37 @@ __global__ void __launch_bounds__(TT_THREADS, 1) substep_tiled_kernel(const Subs
         if (active) {
             const SmemCell<float> cell{ctr, slot, zq};
             float frc[3] = {0.f, 0.f, 0.f};
-            if (a.force_on) {
+            if (force_on) {
                 const float cph = exy.x * ez.x - exy.y * ez.y;
-                frc[0] = a.amp_e[0] * cph;
-                frc[1] = a.amp_e[1] * cph;
-                frc[2] = a.amp_e[2] * cph;
+                frc[0] = ta.amp_e(0) * cph;
+                frc[1] = ta.amp_e(1) * cph;
+                frc[2] = ta.amp_e(2) * cph;
             }
             float rhs[NF];
-            cell_rhs<float>(cell, a.k, frc, rhs);
-            const long long o = (long long)z * a.g.pxy + (long long)j * a.g.px + i;
+            cell_rhs<float>(cell, ta.k(), frc, rhs);
+            const long long o = (long long)z * g.pxy + (long long)j * g.px + i;
             const W *wz = wring + ((z - z0) % TT_NW) * (NF * TT_THREADS) + tid;
 #pragma unroll
             for (int q = 0; q < NF; ++q) {
-                W wn = a.dt * (W)rhs[q];
-                if (!a.s0) wn = a.alpha * wz[q * TT_THREADS] + wn;
-                a.w[q][o] = wn;
-                a.fout[q][o] = (float)((W)cell[q](0, 0, 0) + a.beta * wn);
+                W wn = ta.dt() * (W)rhs[q];
+                if (!s0) wn = ta.alpha() * wz[q * TT_THREADS] + wn;
+                ta.w(q)[o] = wn;
+                ta.fout(q)[o] = (float)((W)zq[q][3] + ta.beta() * wn);
             }
         }
         __syncthreads();  // reads of plane z-3's slot and of w(z) are done before refilling
         issue(z + 4 + TT_PF);
     }
     cp_async_wait<0>();
+}
+
+template <typename W, bool VEC>
+__global__ void __launch_bounds__(TT_THREADS, 1) substep_tiled_kernel(const SubstepArgs<float, W> a) {
+    extern __shared__ __align__(128) unsigned char tt_smem_raw[];
+    const int z0 = blockIdx.z * a.zchunk;
+    const int z1 = min(z0 + a.zchunk, a.g.nz);
+    const TileOne<W> ta{a};
+    tiled_body<W, VEC>(ta, blockIdx.x * TT_X, blockIdx.y * TT_Y, z0, z1, tt_smem_raw);
 }
 
 // Launch the tiled kernel for binary32 fields in the periodic layout.
