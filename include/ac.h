@@ -172,6 +172,16 @@ int ac_integrate_substep(ac_handle *h, double dt, int s);
 int ac_integrate_step(ac_handle *h, double dt);
 
 /*
+ * Largest CFL speed |u| + sqrt(c_s^2 + |B|^2 / rho) over the cells of the state
+ * that the last substep 0 read (the state at the start of the step), computed
+ * by the substep kernel itself in the field precision (quantity AC_Q_CFL of
+ * ac_reduce, without a separate pass).  Synchronises the stream;
+ * AC_ERR_NONFINITE if a cell gave NaN or infinity.  0 before any substep 0.
+ * Not in the paper (constant dt, Sec. 5): for a CFL check of dt.
+ */
+int ac_last_cfl(ac_handle *h, double *out);
+
+/*
  * Fill the radius-3 halo of the current state (AC_LAYOUT_PADDED) with the
  * periodic map of Sec. 3.3, s' = ((s - r) mod n) + r per axis: the six sides,
  * twelve edges and eight corners.  A no-op for AC_LAYOUT_PERIODIC.

@@ -95,6 +95,7 @@ def load_library(path=None):
         "ac_integrate_substep": ([_vp, _c.c_double, _c.c_int], _c.c_int),
         "ac_integrate_step": ([_vp, _c.c_double], _c.c_int),
         "ac_periodic_halo": ([_vp], _c.c_int),
+        "ac_last_cfl": ([_vp, _pd], _c.c_int),
         "ac_reduce": ([_vp, _c.c_int, _c.c_int, _pd], _c.c_int),
         "ac_forcing_draw": ([_c.c_ulonglong, _c.c_ulonglong, ctypes.POINTER(_c.c_int), _pd, _pd],
                             _c.c_int),
@@ -213,6 +214,13 @@ def ac_integrate_substep(h, dt, s):
 
 def ac_integrate_step(h, dt):
     _check(load_library().ac_integrate_step(h, float(dt)), "ac_integrate_step")
+
+
+def ac_last_cfl(h):
+    out = ctypes.c_double()
+    rc = load_library().ac_last_cfl(h, ctypes.byref(out))
+    _check(rc, "ac_last_cfl", out.value)
+    return out.value
 
 
 def ac_periodic_halo(h):

@@ -54,6 +54,7 @@ struct ac_handle {
     unsigned int *flags;
     double *result_dev;  // [value, flag word]
     double *result_host; // page-locked copy of result_dev
+    unsigned long long *cfl_dev;  // max CFL speed of the last substep-0 input (bits of a double)
     double *stage;       // float64 staging for load/store
     size_t stage_elems;
     int next_s;
@@ -113,6 +114,7 @@ static void free_handle_memory(ac_handle *h) {
     if (h->result_dev) cudaFree(h->result_dev);
     if (h->result_host) cudaFreeHost(h->result_host);
     if (h->stage) cudaFree(h->stage);
+    if (h->cfl_dev) cudaFree(h->cfl_dev);
 }
 
 extern "C" int ac_init(ac_handle **out, const ac_grid *grid, const ac_params *params,
@@ -136,6 +138,8 @@ extern "C" int ac_init(ac_handle **out, const ac_grid *grid, const ac_params *pa
     if (e == cudaSuccess) e = cudaMalloc(&h->flags, sizeof(unsigned int) * reduce_max_blocks());
     if (e == cudaSuccess) e = cudaMalloc(&h->result_dev, 2 * sizeof(double));
     if (e == cudaSuccess) e = cudaMallocHost(&h->result_host, 2 * sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc(&h->cfl_dev, sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaMemset(h->cfl_dev, 0, sizeof(unsigned long long));
     if (e != cudaSuccess) {
         int rc = cuda_fail(e);
         free_handle_memory(h);
@@ -489,6 +493,11 @@ extern "C" int ac_integrate_substep(ac_handle *h, double dt, int s) {
     L.beta = RK_BETA[s];
     L.dt = dt;
     L.s = s;
+    L.cfl_max = nullptr;
+    if (s == 0) {  // the step's input state: record its max CFL speed on the way
+        CK(cudaMemsetAsync(h->cfl_dev, 0, sizeof(unsigned long long), h->stream));
+        L.cfl_max = h->cfl_dev;
+    }
     int nl = 0;
     cudaError_t e;
     if (h->params.precision == AC_FP64)
@@ -513,6 +522,15 @@ extern "C" int ac_integrate_step(ac_handle *h, double dt) {
         if (rc) return rc;
     }
     return AC_OK;
+}
+
+extern "C" int ac_last_cfl(ac_handle *h, double *out) {
+    if (!h || !out) return AC_ERR_ARG;
+    CK(cudaMemcpyAsync(h->result_host, h->cfl_dev, sizeof(unsigned long long),
+                       cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    *out = h->result_host[0];
+    return isfinite(*out) ? AC_OK : AC_ERR_NONFINITE;
 }
 
 // ---- reductions -------------------------------------------------------------

@@ -80,6 +80,7 @@ struct SubstepLaunch {
     ForceArgs force;
     double alpha, beta, dt;
     int s;
+    unsigned long long *cfl_max;  // substep 0: device word for the max CFL speed (or NULL)
 };
 
 cudaError_t launch_substep(const SubstepLaunch &L, cudaStream_t st, int *launches);

@@ -73,6 +73,7 @@ struct TileBox {
     __device__ __forceinline__ int force_on() const { return 0; }
     __device__ __forceinline__ const float2 *ftab() const { return nullptr; }
     __device__ __forceinline__ float amp_e(int) const { return 0.f; }
+    __device__ __forceinline__ unsigned long long *cfl_max() const { return nullptr; }
 };
 
 template <typename W>
@@ -87,7 +88,7 @@ __global__ void __launch_bounds__(TT_THREADS, 1) batch_substep_kernel(const __gr
         if (it >= b.nitems) break;
         const int4 wi = b.items[it];
         const TileBox<W> ta(b, b.box[wi.x]);
-        tiled_body<W, true>(ta, wi.y, wi.z, wi.w >> 16, wi.w & 0xffff, bt_smem_raw);
+        tiled_body<W, true, false>(ta, wi.y, wi.z, wi.w >> 16, wi.w & 0xffff, bt_smem_raw);
     }
 }
 

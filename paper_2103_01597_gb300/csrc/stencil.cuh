@@ -200,10 +200,12 @@ template <> __device__ __forceinline__ float dev_exp<float>(float x) { return ex
 
 // RHS of Eqs. B.1-B.4 at one cell (mu0 = 1, zeta = H = C = K = 0), with the
 // forcing term `frc` added to du/dt.  Output order: Table B.1.
-// `f` is a cell accessor: f[q] is the view of field q around the cell.
+// `f` is a cell accessor: f[q] is the view of field q around the cell.  With
+// `cfl` non-null, the fastest signal speed of the input state at the cell,
+// |u| + sqrt(c_s^2 + |B|^2 / rho) (mu0 = 1), is written there as well.
 template <typename R, class CELL>
 __device__ __forceinline__ void cell_rhs(const CELL &f, const DevCoefs<R> &k, const R frc[3],
-                                         R out[NF]) {
+                                         R out[NF], R *cfl = nullptr) {
     const R lnrho = f[0](0, 0, 0);
     const R u[3] = {f[1](0, 0, 0), f[2](0, 0, 0), f[3](0, 0, 0)};
     const R ss = f[4](0, 0, 0);
@@ -305,6 +307,30 @@ __device__ __forceinline__ void cell_rhs(const CELL &f, const DevCoefs<R> &k, co
     // Eq. B.4
 #pragma unroll
     for (int m = 0; m < 3; ++m) out[5 + m] = UxB[m] + k.eta * lapa[m];
+    if (cfl) {
+        const R b2 = B[0] * B[0] + B[1] * B[1] + B[2] * B[2];
+        const R u2 = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+        *cfl = sqrt(u2) + sqrt(cs2 + b2 * rho_inv);
+    }
+}
+
+// Block-wide max of a non-negative value folded into a global 64-bit word that
+// holds the bits of a binary64 (ordered like the values for non-negative
+// numbers; NaN bits compare above every finite value).
+__device__ __forceinline__ void block_max_to_global(double v, unsigned long long *gmax) {
+    __shared__ unsigned long long bmax;
+    const int tid = threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);
+    if (tid == 0) bmax = 0ull;
+    __syncthreads();
+    unsigned long long bits = (unsigned long long)__double_as_longlong(v);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long other = __shfl_xor_sync(0xffffffffu, bits, o);
+        bits = other > bits ? other : bits;
+    }
+    if ((tid & 31) == 0) atomicMax(&bmax, bits);
+    __syncthreads();
+    if (tid == 0) atomicMax(gmax, bmax);
 }
 
 }  // namespace ac

@@ -23,6 +23,7 @@ struct SubstepArgs {
     int force_on;
     const typename Vec2<R>::type *ftab;  // e^{i theta_x}, e^{i theta_y}, e^{i (theta_z + phi)}
     R amp_e[3];
+    unsigned long long *cfl_max;  // non-null at substep 0: max CFL speed of the input state
 };
 
 // Williamson 2N-storage update of one field at one cell:
@@ -35,11 +36,11 @@ __device__ __forceinline__ void rk_update(const SubstepArgs<R, W> &a, int q, lon
     a.fout[q][o] = (R)((W)ldg(a.fin[q] + o) + a.beta * wn);
 }
 
+// One (x, y) column of the tile: cells k0 .. k1-1 of the CTA's z range.  With
+// cfl_acc non-null the largest CFL speed of the input state is kept there.
 template <typename R, typename W, class IX>
-__global__ void __launch_bounds__(128) substep_kernel(const SubstepArgs<R, W> a) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    const int j = blockIdx.y * blockDim.y + threadIdx.y;
-    if (i >= a.g.nx || j >= a.g.ny) return;
+__device__ __forceinline__ void substep_column(const SubstepArgs<R, W> &a, int i, int j,
+                                               R *cfl_acc) {
     const int k0 = blockIdx.z * a.zchunk;
     const int k1 = min(k0 + a.zchunk, a.g.nz);
     using V2 = typename Vec2<R>::type;
@@ -64,10 +65,31 @@ __global__ void __launch_bounds__(128) substep_kernel(const SubstepArgs<R, W> a)
         }
         R rhs[NF];
         const GlobalCell<R, IX> cell{a.fin, ix};
-        cell_rhs<R>(cell, a.k, frc, rhs);
+        if (cfl_acc) {
+            R c;
+            cell_rhs<R>(cell, a.k, frc, rhs, &c);
+            *cfl_acc = (c > *cfl_acc || c != c) ? c : *cfl_acc;
+        } else {
+            cell_rhs<R>(cell, a.k, frc, rhs);
+        }
         const long long o = ix(0, 0, 0);
 #pragma unroll
         for (int q = 0; q < NF; ++q) rk_update(a, q, o, rhs[q]);
+    }
+}
+
+// CFL: also track the largest CFL speed of the input state (substep 0).
+template <typename R, typename W, class IX, bool CFL>
+__global__ void __launch_bounds__(128) substep_kernel(const SubstepArgs<R, W> a) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y * blockDim.y + threadIdx.y;
+    const bool active = i < a.g.nx && j < a.g.ny;
+    if (CFL) {
+        R cfl = (R)0;
+        if (active) substep_column<R, W, IX>(a, i, j, &cfl);
+        block_max_to_global((double)cfl, a.cfl_max);
+    } else if (active) {
+        substep_column<R, W, IX>(a, i, j, nullptr);
     }
 }
 
@@ -93,6 +115,7 @@ cudaError_t launch_substep_t(const SubstepLaunch &L, cudaStream_t st, int *launc
     else
         a.ftab = reinterpret_cast<const typename Vec2<R>::type *>(L.force.tab + ntab);
     for (int m = 0; m < 3; ++m) a.amp_e[m] = (R)L.force.amp_e[m];
+    a.cfl_max = L.cfl_max;
 
     const dim3 block(32, 4, 1);
     const unsigned gx = (L.g.nx + block.x - 1) / block.x;
@@ -103,10 +126,18 @@ cudaError_t launch_substep_t(const SubstepLaunch &L, cudaStream_t st, int *launc
     zchunk = zchunk < 1 ? 1 : (zchunk > 16 ? 16 : zchunk);
     a.zchunk = zchunk;
     const dim3 grid(gx, gy, (L.g.nz + zchunk - 1) / zchunk);
-    if (L.g.padded)
-        substep_kernel<R, W, IdxPadded><<<grid, block, 0, st>>>(a);
-    else
-        substep_kernel<R, W, IdxPeriodic><<<grid, block, 0, st>>>(a);
+    const bool cfl = a.cfl_max != nullptr;
+    if (L.g.padded) {
+        if (cfl)
+            substep_kernel<R, W, IdxPadded, true><<<grid, block, 0, st>>>(a);
+        else
+            substep_kernel<R, W, IdxPadded, false><<<grid, block, 0, st>>>(a);
+    } else {
+        if (cfl)
+            substep_kernel<R, W, IdxPeriodic, true><<<grid, block, 0, st>>>(a);
+        else
+            substep_kernel<R, W, IdxPeriodic, false><<<grid, block, 0, st>>>(a);
+    }
     ++*launches;
     return cudaGetLastError();
 }

@@ -163,10 +163,12 @@ struct TileOne {
     __device__ __forceinline__ int force_on() const { return a.force_on; }
     __device__ __forceinline__ const float2 *ftab() const { return a.ftab; }
     __device__ __forceinline__ float amp_e(int m) const { return a.amp_e[m]; }
+    __device__ __forceinline__ unsigned long long *cfl_max() const { return a.cfl_max; }
 };
 
-// One output tile: columns [x0, x0+32) x [y0, y0+8), planes [z0, z1).
-template <typename W, bool VEC, class TA>
+// One output tile: columns [x0, x0+32) x [y0, y0+8), planes [z0, z1).  CFL:
+// also fold the largest CFL speed of the input cells into ta.cfl_max().
+template <typename W, bool VEC, bool CFL, class TA>
 __device__ __forceinline__ void tiled_body(const TA &ta, int x0, int y0, int z0, int z1,
                                            unsigned char *smem_raw) {
     float *sm = reinterpret_cast<float *>(smem_raw);
@@ -178,6 +180,7 @@ __device__ __forceinline__ void tiled_body(const TA &ta, int x0, int y0, int z0,
     const bool active = i < g.nx && j < g.ny;
     const int force_on = ta.force_on();
     const int s0 = ta.s0();
+    float cfl = 0.f;
 
     float2 exy = make_float2(0.f, 0.f);
     if (force_on && active) {
@@ -234,7 +237,13 @@ __device__ __forceinline__ void tiled_body(const TA &ta, int x0, int y0, int z0,
                 frc[2] = ta.amp_e(2) * cph;
             }
             float rhs[NF];
-            cell_rhs<float>(cell, ta.k(), frc, rhs);
+            if (CFL) {
+                float c;
+                cell_rhs<float>(cell, ta.k(), frc, rhs, &c);
+                cfl = (c > cfl || c != c) ? c : cfl;
+            } else {
+                cell_rhs<float>(cell, ta.k(), frc, rhs);
+            }
             const long long o = (long long)z * g.pxy + (long long)j * g.px + i;
             const W *wz = wring + ((z - z0) % TT_NW) * (NF * TT_THREADS) + tid;
 #pragma unroll
@@ -249,15 +258,27 @@ __device__ __forceinline__ void tiled_body(const TA &ta, int x0, int y0, int z0,
         issue(z + 4 + TT_PF);
     }
     cp_async_wait<0>();
+    if (CFL) block_max_to_global((double)cfl, ta.cfl_max());
 }
 
-template <typename W, bool VEC>
+template <typename W, bool VEC, bool CFL>
 __global__ void __launch_bounds__(TT_THREADS, 1) substep_tiled_kernel(const SubstepArgs<float, W> a) {
     extern __shared__ __align__(128) unsigned char tt_smem_raw[];
     const int z0 = blockIdx.z * a.zchunk;
     const int z1 = min(z0 + a.zchunk, a.g.nz);
     const TileOne<W> ta{a};
-    tiled_body<W, VEC>(ta, blockIdx.x * TT_X, blockIdx.y * TT_Y, z0, z1, tt_smem_raw);
+    tiled_body<W, VEC, CFL>(ta, blockIdx.x * TT_X, blockIdx.y * TT_Y, z0, z1, tt_smem_raw);
+}
+
+template <typename W, bool VEC, bool CFL>
+static cudaError_t launch_tiled_variant(const SubstepArgs<float, W> &a, dim3 grid, dim3 block,
+                                        cudaStream_t st) {
+    const size_t smem = tt_smem_bytes<W>();
+    cudaError_t e = cudaFuncSetAttribute(substep_tiled_kernel<W, VEC, CFL>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    substep_tiled_kernel<W, VEC, CFL><<<grid, block, smem, st>>>(a);
+    return cudaGetLastError();
 }
 
 // Launch the tiled kernel for binary32 fields in the periodic layout.
@@ -279,6 +300,7 @@ cudaError_t launch_substep_tiled_t(const SubstepLaunch &L, cudaStream_t st, int 
     const long long ntab = (long long)L.g.nx + L.g.ny + L.g.nz;
     a.ftab = reinterpret_cast<const float2 *>(L.force.tab + ntab);
     for (int m = 0; m < 3; ++m) a.amp_e[m] = (float)L.force.amp_e[m];
+    a.cfl_max = L.cfl_max;
 
     const unsigned gx = (L.g.nx + TT_X - 1) / TT_X;
     const unsigned gy = (L.g.ny + TT_Y - 1) / TT_Y;
@@ -289,19 +311,15 @@ cudaError_t launch_substep_tiled_t(const SubstepLaunch &L, cudaStream_t st, int 
     const dim3 grid(gx, gy, (L.g.nz + zc - 1) / zc);
     const dim3 block(TT_X, TT_Y, 1);
     const bool vec = (L.g.nx % 4) == 0;
+    const bool cfl = a.cfl_max != nullptr;
     cudaError_t e;
-    const size_t smem = tt_smem_bytes<W>();
-    if (vec) {
-        e = cudaFuncSetAttribute(substep_tiled_kernel<W, true>,
-                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        substep_tiled_kernel<W, true><<<grid, block, smem, st>>>(a);
-    } else {
-        e = cudaFuncSetAttribute(substep_tiled_kernel<W, false>,
-                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        substep_tiled_kernel<W, false><<<grid, block, smem, st>>>(a);
-    }
+    if (vec)
+        e = cfl ? launch_tiled_variant<W, true, true>(a, grid, block, st)
+                : launch_tiled_variant<W, true, false>(a, grid, block, st);
+    else
+        e = cfl ? launch_tiled_variant<W, false, true>(a, grid, block, st)
+                : launch_tiled_variant<W, false, false>(a, grid, block, st);
+    if (e != cudaSuccess) return e;
     ++*launches;
     return cudaGetLastError();
 }

@@ -112,6 +112,29 @@ def test_paper_ulp_metric_uniform_fields():
     assert np.max(ulp_err(g, o)) <= 6.0, np.max(ulp_err(g, o))
 
 
+@pytest.mark.parametrize("precision,layout,tol", [(ac.AC_FP64, ac.AC_LAYOUT_PERIODIC, 1e-12),
+                                                  (ac.AC_FP64, ac.AC_LAYOUT_PADDED, 1e-12),
+                                                  (ac.AC_FP32, ac.AC_LAYOUT_PERIODIC, 1e-6),
+                                                  (ac.AC_FP32, ac.AC_LAYOUT_PADDED, 1e-6),
+                                                  (ac.AC_FP32_W64, ac.AC_LAYOUT_PERIODIC, 1e-6)])
+def test_fused_cfl_matches_reduction(precision, layout, tol):
+    """Substep 0 folds the max CFL speed of its input state into one word; it
+    equals the separate reduction (and the oracle) on that state."""
+    n = (36, 20, 24)
+    sim = _sim(n, precision=precision, layout=layout, force_amp=0.05, seed=4)
+    f = _state(n, seed=17)
+    f[6] += 0.3 * np.sin(np.arange(n[0]) * 2 * math.pi / n[0])[None, None, :]
+    sim.load(f)
+    ref = sim.reduce(ac.AC_MAX, ac.AC_Q_CFL)
+    sim.step(1e-3)
+    got = ac.ac_last_cfl(sim.h)
+    assert abs(got - ref) <= tol * ref, (got, ref)
+    if precision == ac.AC_FP64:
+        o = core.reduce(f, _oracle_params(n), "max", "cfl")
+        assert abs(got - o) <= 1e-12 * o
+    sim.close()
+
+
 def test_shift_equivariance_bitwise():
     n = (24, 20, 18)
     f = _state(n, seed=4)
