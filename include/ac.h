@@ -272,6 +272,59 @@ int ac_batch_reduce(ac_batch *b, int box, int op, int quantity, double *out);
 int ac_batch_info(const ac_batch *b, long long *cells, int *items, int *zc, int *ctas,
                   unsigned long long *launches);
 
+/* Device pointers of the current state's eight field arrays, with the
+ * handle's precision, layout and grid size (any of the outputs may be NULL). */
+int ac_get_state(const ac_handle *h, void *dev_ptrs[8], int *precision, int *layout, int n[3]);
+
+/* ---- learned closure for a 2x-coarser grid ---------------------------------
+ * The paper only mentions machine-learned reconstruction of turbulent flows
+ * from low-resolution data (Sec. 6); this closure is a reading of that remark:
+ * a three-layer 3-D conv net (8 -> 32 -> 32 -> 8 channels, 3x3x3 kernels,
+ * circular padding, ReLU after layers 1 and 2) maps a coarse state f (binary32,
+ * periodic layout, eight device arrays) to a correction
+ *     delta[c] = out_scale[c] * net(f / in_scale)[c].
+ * Convolutions run on the tensor cores with bfloat16 weights and activations
+ * and binary32 accumulation; master weights, gradients and Adam moments are
+ * binary32.  Parameters are one binary32 array of AC_CLOSURE_NPARAMS values:
+ * W1[32][8][3][3][3], b1[32], W2[32][32][3][3][3], b2[32], W3[8][32][3][3][3],
+ * b3[8]; a weight W[co][ci][kz][ky][kx] multiplies input channel ci at
+ * (z + kz - 1, y + ky - 1, x + kx - 1) (periodic).  Loss: mean squared error of
+ * the scaled output against target / out_scale over all cells and channels.
+ */
+#define AC_CLOSURE_NPARAMS 41544
+typedef struct ac_closure ac_closure; /* opaque; owned by the library */
+
+int ac_closure_init(ac_closure **c, int nx, int ny, int nz, void *stream);
+int ac_closure_quit(ac_closure *c);
+/* Host binary32 parameters in/out (set also clears the Adam moments). */
+int ac_closure_set_params(ac_closure *c, const float *host_params);
+int ac_closure_get_params(ac_closure *c, float *host_params);
+/* Gradients of the last ac_closure_backward, same layout as the parameters. */
+int ac_closure_get_grads(ac_closure *c, float *host_grads);
+/* Per-channel input and output scales (positive, finite). */
+int ac_closure_set_scales(ac_closure *c, const float in_scale[8], const float out_scale[8]);
+/* Correction of the coarse state `in` into `out` (device arrays, may not alias;
+ * out == NULL keeps the result inside the closure). */
+int ac_closure_forward(ac_closure *c, const float *const in[8], float *const out[8]);
+/* Forward, loss against `target` (physical units, device arrays) and
+ * gradients of every parameter; *loss (if non-NULL) synchronises. */
+int ac_closure_backward(ac_closure *c, const float *const in[8], const float *const target[8],
+                        double *loss);
+/* One Adam step (Kingma and Ba, bias-corrected) with the last gradients. */
+int ac_closure_adam_step(ac_closure *c, float lr, float beta1, float beta2, float eps);
+/* Add the correction of a binary32 periodic handle's current state to it, but
+ * only if every correction value is finite and at most `limit` in magnitude
+ * (the guard runs on the device; *applied, if non-NULL, synchronises). */
+int ac_closure_apply(ac_closure *c, ac_handle *h, double limit, int *applied);
+int ac_closure_launch_count(const ac_closure *c, unsigned long long *count);
+
+/* Full-weighting restriction of eight fine fields (nx, ny, nz even; binary64
+ * for AC_FP64, binary32 otherwise; periodic layout) to eight binary32 coarse
+ * arrays: coarse(I) = sum over d in {-1,0,1}^3 of prod_a w(d_a) fine(2I + d),
+ * w = (1/4, 1/2, 1/4).  Asynchronous on `stream`. */
+int ac_restrict(const void *const fine[8], int fine_precision, int nx, int ny, int nz,
+                float *const coarse[8], void *stream);
+
 /*
  * Allocation-free reduction (the paper has no counterpart; it exists for
  * callers that cannot allocate device memory -- for example an application

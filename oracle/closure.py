@@ -101,11 +101,14 @@ class Net:
         return h, acts
 
     def loss_and_grads(self, x, target, round_bf16=False):
+        """Mean squared error and its gradients.  With round_bf16, the output
+        gradient and the gradients passed back through each ReLU are rounded to
+        bfloat16 as well (they are the operands of the backward convolutions)."""
         r = bf16_round if round_bf16 else (lambda a: a)
         y, acts = self.forward(x, round_bf16)
         n = y.size
         loss = float(np.mean((y - target) ** 2))
-        dy = 2.0 * (y - target) / n
+        dy = r(2.0 * (y - target) / n)
         grads = [None] * len(self.params)
         for li in reversed(range(len(self.params))):
             W, b = self.params[li]
@@ -113,8 +116,24 @@ class Net:
             grads[li] = (dW, db)
             if li > 0:
                 da = conv3d_input_grad(dy, r(W))
-                dy = da * (acts[li] > 0)
+                dy = r(da * (acts[li] > 0))
         return loss, grads
+
+    def flat(self):
+        """Parameters as one vector: W1, b1, W2, b2, W3, b3 (row-major)."""
+        return np.concatenate([np.concatenate([W.ravel(), b.ravel()]) for W, b in self.params])
+
+    @staticmethod
+    def unflat(v, channels=(8, 32, 32, 8)):
+        params, o = [], 0
+        for cin, cout in zip(channels[:-1], channels[1:]):
+            nW = cout * cin * 27
+            W = np.array(v[o:o + nW], dtype=np.float64).reshape(cout, cin, 3, 3, 3)
+            o += nW
+            b = np.array(v[o:o + cout], dtype=np.float64)
+            o += cout
+            params.append((W, b))
+        return Net(params)
 
 
 class Adam:

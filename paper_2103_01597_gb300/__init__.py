@@ -10,7 +10,7 @@ compiled library.
 """
 import importlib
 
-__all__ = ["ac", "synthetic"]
+__all__ = ["ac", "closure", "synthetic"]
 
 
 def __getattr__(name):

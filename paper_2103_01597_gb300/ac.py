@@ -120,6 +120,22 @@ def load_library(path=None):
         "ac_batch_info": ([_vp, ctypes.POINTER(_c.c_longlong), ctypes.POINTER(_c.c_int),
                            ctypes.POINTER(_c.c_int), ctypes.POINTER(_c.c_int),
                            ctypes.POINTER(_c.c_ulonglong)], _c.c_int),
+        "ac_get_state": ([_vp, ctypes.POINTER(_vp), ctypes.POINTER(_c.c_int),
+                          ctypes.POINTER(_c.c_int), ctypes.POINTER(_c.c_int)], _c.c_int),
+        "ac_closure_init": ([ctypes.POINTER(_vp), _c.c_int, _c.c_int, _c.c_int, _vp], _c.c_int),
+        "ac_closure_quit": ([_vp], _c.c_int),
+        "ac_closure_set_params": ([_vp, ctypes.POINTER(_c.c_float)], _c.c_int),
+        "ac_closure_get_params": ([_vp, ctypes.POINTER(_c.c_float)], _c.c_int),
+        "ac_closure_get_grads": ([_vp, ctypes.POINTER(_c.c_float)], _c.c_int),
+        "ac_closure_set_scales": ([_vp, ctypes.POINTER(_c.c_float), ctypes.POINTER(_c.c_float)],
+                                  _c.c_int),
+        "ac_closure_forward": ([_vp, ctypes.POINTER(_vp), ctypes.POINTER(_vp)], _c.c_int),
+        "ac_closure_backward": ([_vp, ctypes.POINTER(_vp), ctypes.POINTER(_vp), _pd], _c.c_int),
+        "ac_closure_adam_step": ([_vp, _c.c_float, _c.c_float, _c.c_float, _c.c_float], _c.c_int),
+        "ac_closure_apply": ([_vp, _vp, _c.c_double, ctypes.POINTER(_c.c_int)], _c.c_int),
+        "ac_closure_launch_count": ([_vp, ctypes.POINTER(_c.c_ulonglong)], _c.c_int),
+        "ac_restrict": ([ctypes.POINTER(_vp), _c.c_int, _c.c_int, _c.c_int, _c.c_int,
+                         ctypes.POINTER(_vp), _vp], _c.c_int),
         "ac_strerror": ([_c.c_int], _c.c_char_p),
         "ac_last_cuda_error": ([], _c.c_char_p),
     }
@@ -279,6 +295,105 @@ def ac_set_step(h, step, next_substep=0):
 def ac_launch_count(h):
     n = ctypes.c_ulonglong()
     _check(load_library().ac_launch_count(h, ctypes.byref(n)), "ac_launch_count")
+    return n.value
+
+
+def ac_get_state(h):
+    ptrs = (_vp * 8)()
+    prec, layout = ctypes.c_int(), ctypes.c_int()
+    n = (ctypes.c_int * 3)()
+    _check(load_library().ac_get_state(h, ptrs, ctypes.byref(prec), ctypes.byref(layout), n),
+           "ac_get_state")
+    return [p or 0 for p in ptrs], prec.value, layout.value, tuple(n)
+
+
+# ---- learned closure -----------------------------------------------------------
+
+AC_CLOSURE_NPARAMS = 41544
+
+
+def _ptr8(ptrs):
+    assert len(ptrs) == 8
+    return (_vp * 8)(*[int(p) for p in ptrs])
+
+
+def _f32(a):
+    a = np.ascontiguousarray(a, dtype=np.float32)
+    return a, a.ctypes.data_as(ctypes.POINTER(ctypes.c_float))
+
+
+def ac_restrict(fine_ptrs, fine_precision, n_fine, coarse_ptrs, stream=None):
+    _check(load_library().ac_restrict(_ptr8(fine_ptrs), int(fine_precision), int(n_fine[0]),
+                                      int(n_fine[1]), int(n_fine[2]), _ptr8(coarse_ptrs),
+                                      _vp(stream or 0)), "ac_restrict")
+
+
+def ac_closure_init(n, stream=None):
+    c = _vp()
+    _check(load_library().ac_closure_init(ctypes.byref(c), int(n[0]), int(n[1]), int(n[2]),
+                                          _vp(stream or 0)), "ac_closure_init")
+    return c
+
+
+def ac_closure_quit(c):
+    _check(load_library().ac_closure_quit(c), "ac_closure_quit")
+
+
+def ac_closure_set_params(c, params):
+    a, p = _f32(params)
+    assert a.size == AC_CLOSURE_NPARAMS
+    _check(load_library().ac_closure_set_params(c, p), "ac_closure_set_params")
+
+
+def ac_closure_get_params(c):
+    a = np.empty(AC_CLOSURE_NPARAMS, dtype=np.float32)
+    _check(load_library().ac_closure_get_params(c, a.ctypes.data_as(ctypes.POINTER(ctypes.c_float))),
+           "ac_closure_get_params")
+    return a
+
+
+def ac_closure_get_grads(c):
+    a = np.empty(AC_CLOSURE_NPARAMS, dtype=np.float32)
+    _check(load_library().ac_closure_get_grads(c, a.ctypes.data_as(ctypes.POINTER(ctypes.c_float))),
+           "ac_closure_get_grads")
+    return a
+
+
+def ac_closure_set_scales(c, in_scale, out_scale):
+    a, pa = _f32(in_scale)
+    b, pb = _f32(out_scale)
+    _check(load_library().ac_closure_set_scales(c, pa, pb), "ac_closure_set_scales")
+
+
+def ac_closure_forward(c, in_ptrs, out_ptrs=None):
+    _check(load_library().ac_closure_forward(c, _ptr8(in_ptrs),
+                                             _ptr8(out_ptrs) if out_ptrs is not None else None),
+           "ac_closure_forward")
+
+
+def ac_closure_backward(c, in_ptrs, target_ptrs):
+    loss = ctypes.c_double()
+    rc = load_library().ac_closure_backward(c, _ptr8(in_ptrs), _ptr8(target_ptrs),
+                                            ctypes.byref(loss))
+    _check(rc, "ac_closure_backward", loss.value)
+    return loss.value
+
+
+def ac_closure_adam_step(c, lr, beta1=0.9, beta2=0.999, eps=1e-8):
+    _check(load_library().ac_closure_adam_step(c, float(lr), float(beta1), float(beta2), float(eps)),
+           "ac_closure_adam_step")
+
+
+def ac_closure_apply(c, h, limit):
+    applied = ctypes.c_int()
+    _check(load_library().ac_closure_apply(c, h, float(limit), ctypes.byref(applied)),
+           "ac_closure_apply")
+    return bool(applied.value)
+
+
+def ac_closure_launch_count(c):
+    n = ctypes.c_ulonglong()
+    _check(load_library().ac_closure_launch_count(c, ctypes.byref(n)), "ac_closure_launch_count")
     return n.value
 
 

@@ -444,6 +444,23 @@ extern "C" int ac_set_step(ac_handle *h, unsigned long long step, int next_subst
     return AC_OK;
 }
 
+extern "C" int ac_get_state(const ac_handle *h, void *dev_ptrs[8], int *precision, int *layout,
+                            int n[3]) {
+    if (!h) return AC_ERR_ARG;
+    if (dev_ptrs) {
+        if (!h->have_buffers) return AC_ERR_STATE;
+        for (int q = 0; q < NF; ++q) dev_ptrs[q] = h->state[h->cur][q];
+    }
+    if (precision) *precision = h->params.precision;
+    if (layout) *layout = h->grid.layout;
+    if (n) {
+        n[0] = h->grid.nx;
+        n[1] = h->grid.ny;
+        n[2] = h->grid.nz;
+    }
+    return AC_OK;
+}
+
 extern "C" int ac_launch_count(const ac_handle *h, unsigned long long *count) {
     if (!h || !count) return AC_ERR_ARG;
     *count = h->launches;

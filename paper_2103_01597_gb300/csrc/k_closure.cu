@@ -1,0 +1,758 @@
+// Learned closure for a 2x-coarser grid: restriction of a fine state, and a
+// three-layer 3-D conv net (8 -> 32 -> 32 -> 8 channels, 3x3x3 kernels,
+// circular padding, ReLU between layers) with its forward pass, hand-written
+// backward pass, Adam update and the guarded application of its correction to
+// a coarse state.  The paper only mentions machine-learned reconstruction of
+// turbulent flows from low-resolution data (Sec. 6); everything here is a
+// reading of that remark.
+//
+// Convolutions are implicit GEMMs on the tensor cores with bfloat16 operands
+// and binary32 accumulation (mma.sync m16n8k16): M = 128 cells of an x-row,
+// N = output channels, K = 27 taps x input channels.  The row tile with a
+// one-cell halo is staged once per (dy, dz) tap group and serves the three dx
+// taps by shifting the window.  Activations are channel-major [C][N]
+// (N = nx ny nz, x fastest), like the solver's fields.
+#include <cuda_bf16.h>
+#include <math.h>
+#include <stdint.h>
+#include <string.h>
+
+#include <new>
+
+#include "ac_internal.h"
+
+namespace ac {
+
+using bf16 = __nv_bfloat16;
+
+constexpr int CL_TM = 128;       // cells per CTA tile
+constexpr int CL_THREADS = 128;  // four warps, 32 cells each
+constexpr int CL_WG_CTAS = 64;   // CTAs per tap group in the weight-gradient kernel
+
+struct ConvGeom {
+    int nx, ny, nz;
+    long long n;  // cells
+};
+
+__device__ __forceinline__ int cl_wrap(int v, int n) {
+    int m = v % n;
+    return m < 0 ? m + n : m;
+}
+
+__device__ __forceinline__ void mma_bf16_16816(float (&d)[4], const unsigned (&a)[4],
+                                               const unsigned (&b)[2]) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 "
+        "{%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};\n"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
+__device__ __forceinline__ unsigned pack_bf16(bf16 lo, bf16 hi) {
+    return (unsigned)__bfloat16_as_ushort(lo) | ((unsigned)__bfloat16_as_ushort(hi) << 16);
+}
+
+enum { EPI_RELU_BF16 = 0, EPI_LINEAR_F32 = 1, EPI_MASK_BF16 = 2 };
+
+// y[co, p] = sum_{tap, ci} Wt[co][tap][ci] x[ci, p + off(tap)]  (+ epilogue):
+//   EPI_RELU_BF16:  max(y + bias, 0) as bfloat16 (hidden layers);
+//   EPI_LINEAR_F32: y + bias as binary32 (output layer);
+//   EPI_MASK_BF16:  y where mask > 0, else 0, as bfloat16 (input gradient
+//                   through a ReLU, with flipped/transposed weights).
+template <int CIN, int COUT, int EPI>
+__global__ void __launch_bounds__(CL_THREADS) conv_fwd_kernel(const bf16 *__restrict__ X,
+                                                              const bf16 *__restrict__ Wt,
+                                                              const float *__restrict__ bias,
+                                                              const bf16 *__restrict__ mask,
+                                                              void *__restrict__ Y, ConvGeom g) {
+    constexpr int PA = CIN + 8;  // padded pitches keep the fragment loads conflict-free
+    constexpr int KG = 3 * CIN;
+    constexpr int PB = KG + 8;
+    constexpr int NT = COUT / 8;
+    __shared__ __align__(16) bf16 As[(CL_TM + 2) * PA];
+    __shared__ __align__(16) bf16 Bs[COUT * PB];
+    const int segs = (g.nx + CL_TM - 1) / CL_TM;
+    const int row = blockIdx.x / segs;
+    const int seg = blockIdx.x - row * segs;
+    const int y = row % g.ny, z = row / g.ny;
+    const int x0 = seg * CL_TM;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int gq = lane >> 2, tq = lane & 3;
+    float acc[2][NT][4];
+#pragma unroll
+    for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+        for (int nt = 0; nt < NT; ++nt)
+#pragma unroll
+            for (int r = 0; r < 4; ++r) acc[mt][nt][r] = 0.f;
+
+    for (int grp = 0; grp < 9; ++grp) {
+        const int dz = grp / 3 - 1, dy = grp % 3 - 1;
+        const long long rbase = ((long long)cl_wrap(z + dz, g.nz) * g.ny + cl_wrap(y + dy, g.ny)) * g.nx;
+        __syncthreads();  // previous group's tiles are no longer read
+        for (int idx = tid; idx < CIN * (CL_TM + 2); idx += CL_THREADS) {
+            const int ci = idx / (CL_TM + 2);
+            const int c = idx - ci * (CL_TM + 2);
+            As[c * PA + ci] = X[(long long)ci * g.n + rbase + cl_wrap(x0 - 1 + c, g.nx)];
+        }
+        for (int idx = tid; idx < COUT * KG; idx += CL_THREADS) {
+            const int co = idx / KG;
+            const int r = idx - co * KG;
+            const int j = r / CIN, ci = r - j * CIN;
+            Bs[co * PB + r] = Wt[((long long)co * 27 + grp * 3 + j) * CIN + ci];
+        }
+        __syncthreads();
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {  // dx = j - 1: the window starts j cells into the halo tile
+#pragma unroll
+            for (int kk = 0; kk < CIN / 16; ++kk) {
+                unsigned a[2][4];
+#pragma unroll
+                for (int mt = 0; mt < 2; ++mt) {
+                    const int r0 = warp * 32 + mt * 16 + gq + j;
+                    const bf16 *p0 = As + r0 * PA + kk * 16 + 2 * tq;
+                    const bf16 *p1 = p0 + 8 * PA;
+                    a[mt][0] = *reinterpret_cast<const unsigned *>(p0);
+                    a[mt][1] = *reinterpret_cast<const unsigned *>(p1);
+                    a[mt][2] = *reinterpret_cast<const unsigned *>(p0 + 8);
+                    a[mt][3] = *reinterpret_cast<const unsigned *>(p1 + 8);
+                }
+#pragma unroll
+                for (int nt = 0; nt < NT; ++nt) {
+                    const bf16 *pb = Bs + (nt * 8 + gq) * PB + j * CIN + kk * 16 + 2 * tq;
+                    const unsigned b[2] = {*reinterpret_cast<const unsigned *>(pb),
+                                           *reinterpret_cast<const unsigned *>(pb + 8)};
+                    mma_bf16_16816(acc[0][nt], a[0], b);
+                    mma_bf16_16816(acc[1][nt], a[1], b);
+                }
+            }
+        }
+    }
+    const long long obase = ((long long)z * g.ny + y) * g.nx;
+#pragma unroll
+    for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+        for (int nt = 0; nt < NT; ++nt)
+#pragma unroll
+            for (int h = 0; h < 2; ++h)
+#pragma unroll
+                for (int c = 0; c < 2; ++c) {
+                    const int x = x0 + warp * 32 + mt * 16 + gq + 8 * h;
+                    if (x >= g.nx) continue;
+                    const int co = nt * 8 + 2 * tq + c;
+                    const long long o = (long long)co * g.n + obase + x;
+                    float v = acc[mt][nt][2 * h + c];
+                    if (EPI == EPI_RELU_BF16) {
+                        v = fmaxf(v + bias[co], 0.f);
+                        static_cast<bf16 *>(Y)[o] = __float2bfloat16_rn(v);
+                    } else if (EPI == EPI_LINEAR_F32) {
+                        static_cast<float *>(Y)[o] = v + bias[co];
+                    } else {
+                        v = __bfloat162float(mask[o]) > 0.f ? v : 0.f;
+                        static_cast<bf16 *>(Y)[o] = __float2bfloat16_rn(v);
+                    }
+                }
+}
+
+// Partial weight gradients of one tap group (blockIdx.y = dz, dy):
+// part[grp][cta][co][j * CIN + ci] = sum over this CTA's cells of
+// dZ[co, p] x[ci, p + off(dz, dy, j - 1)].  M = output channels (padded to 16),
+// N = 3 CIN, K = cells.
+template <int CIN, int COUT>
+__global__ void __launch_bounds__(CL_THREADS) conv_wgrad_kernel(const bf16 *__restrict__ dZ,
+                                                                const bf16 *__restrict__ X,
+                                                                float *__restrict__ part,
+                                                                ConvGeom g) {
+    constexpr int MT = (COUT + 15) / 16;
+    constexpr int KN = 3 * CIN;
+    constexpr int NT = KN / 8;
+    constexpr int NTW = (NT + 3) / 4;
+    constexpr int PD = CL_TM + 8;
+    constexpr int PX = CL_TM + 8;
+    __shared__ __align__(16) bf16 Ds[MT * 16 * PD];
+    __shared__ __align__(16) bf16 Xs[CIN * PX];
+    const int grp = blockIdx.y;
+    const int dz = grp / 3 - 1, dy = grp % 3 - 1;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int gq = lane >> 2, tq = lane & 3;
+    float acc[MT][NTW][4];
+#pragma unroll
+    for (int mt = 0; mt < MT; ++mt)
+#pragma unroll
+        for (int w = 0; w < NTW; ++w)
+#pragma unroll
+            for (int r = 0; r < 4; ++r) acc[mt][w][r] = 0.f;
+    const int segs = (g.nx + CL_TM - 1) / CL_TM;
+    const long long tiles = (long long)g.ny * g.nz * segs;
+    for (long long tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
+        const int row = (int)(tile / segs);
+        const int seg = (int)(tile - (long long)row * segs);
+        const int y = row % g.ny, z = row / g.ny;
+        const int x0 = seg * CL_TM;
+        const long long obase = ((long long)z * g.ny + y) * g.nx;
+        const long long rbase = ((long long)cl_wrap(z + dz, g.nz) * g.ny + cl_wrap(y + dy, g.ny)) * g.nx;
+        __syncthreads();
+        for (int idx = tid; idx < MT * 16 * CL_TM; idx += CL_THREADS) {
+            const int co = idx / CL_TM;
+            const int c = idx - co * CL_TM;
+            const int x = x0 + c;
+            Ds[co * PD + c] = (co < COUT && x < g.nx) ? dZ[(long long)co * g.n + obase + x]
+                                                      : __float2bfloat16_rn(0.f);
+        }
+        for (int idx = tid; idx < CIN * (CL_TM + 2); idx += CL_THREADS) {
+            const int ci = idx / (CL_TM + 2);
+            const int c = idx - ci * (CL_TM + 2);
+            Xs[ci * PX + c] = X[(long long)ci * g.n + rbase + cl_wrap(x0 - 1 + c, g.nx)];
+        }
+        __syncthreads();
+#pragma unroll
+        for (int ks = 0; ks < CL_TM / 16; ++ks) {
+            unsigned a[MT][4];
+#pragma unroll
+            for (int mt = 0; mt < MT; ++mt) {
+                const bf16 *p0 = Ds + (mt * 16 + gq) * PD + ks * 16 + 2 * tq;
+                const bf16 *p1 = p0 + 8 * PD;
+                a[mt][0] = *reinterpret_cast<const unsigned *>(p0);
+                a[mt][1] = *reinterpret_cast<const unsigned *>(p1);
+                a[mt][2] = *reinterpret_cast<const unsigned *>(p0 + 8);
+                a[mt][3] = *reinterpret_cast<const unsigned *>(p1 + 8);
+            }
+#pragma unroll
+            for (int w = 0; w < NTW; ++w) {
+                const int nt = warp + 4 * w;
+                if (nt >= NT) continue;
+                const int nn = nt * 8 + gq;
+                const int j = nn / CIN, ci = nn - (nn / CIN) * CIN;
+                const bf16 *px = Xs + ci * PX + ks * 16 + 2 * tq + j;
+                const unsigned b[2] = {pack_bf16(px[0], px[1]), pack_bf16(px[8], px[9])};
+#pragma unroll
+                for (int mt = 0; mt < MT; ++mt) mma_bf16_16816(acc[mt][w], a[mt], b);
+            }
+        }
+    }
+#pragma unroll
+    for (int mt = 0; mt < MT; ++mt)
+#pragma unroll
+        for (int w = 0; w < NTW; ++w) {
+            const int nt = warp + 4 * w;
+            if (nt >= NT) continue;
+#pragma unroll
+            for (int h = 0; h < 2; ++h)
+#pragma unroll
+                for (int c = 0; c < 2; ++c) {
+                    const int co = mt * 16 + gq + 8 * h;
+                    if (co >= COUT) continue;
+                    const int nn = nt * 8 + 2 * tq + c;
+                    part[(((long long)grp * gridDim.x + blockIdx.x) * COUT + co) * KN + nn] =
+                        acc[mt][w][2 * h + c];
+                }
+        }
+}
+
+// Sum the per-CTA partials into the gradient of W[co][ci][kz][ky][kx] (only the
+// first cin_real input channels exist).
+__global__ void wgrad_reduce_kernel(const float *__restrict__ part, int ctas, int cout, int cin,
+                                    int cin_real, float *__restrict__ gW) {
+    const int total = cout * cin_real * 27;
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < total; t += gridDim.x * blockDim.x) {
+        const int co = t / (cin_real * 27);
+        const int rem = t - co * cin_real * 27;
+        const int ci = rem / 27;
+        const int tap = rem - ci * 27;
+        const int grp = tap / 3, j = tap - grp * 3;
+        double s = 0.0;
+        for (int b = 0; b < ctas; ++b)
+            s += part[(((long long)grp * ctas + b) * cout + co) * (3 * cin) + j * cin + ci];
+        gW[t] = (float)s;
+    }
+}
+
+// db[co] = sum over cells of dZ[co, p] (one block per channel, fixed order).
+__global__ void bias_grad_kernel(const bf16 *__restrict__ dZ, long long n, float *__restrict__ gb) {
+    const int co = blockIdx.x;
+    double s = 0.0;
+    for (long long p = threadIdx.x; p < n; p += blockDim.x)
+        s += (double)__bfloat162float(dZ[(long long)co * n + p]);
+    __shared__ double sh[256];
+    sh[threadIdx.x] = s;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if ((int)threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) gb[co] = (float)sh[0];
+}
+
+// Network input: x[c] = f[c] / in_scale[c] as bfloat16 (channels 8..15 stay zero).
+struct F8 {
+    const float *p[8];
+};
+struct W8 {
+    float *p[8];
+};
+__global__ void pack_input_kernel(F8 f, const float *__restrict__ inv_scale, long long n,
+                                  bf16 *__restrict__ x) {
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < 8 * n;
+         t += (long long)gridDim.x * blockDim.x) {
+        const int c = (int)(t / n);
+        const long long p = t - c * n;
+        x[t] = __float2bfloat16_rn(f.p[c][p] * inv_scale[c]);
+    }
+}
+
+// Loss and output gradient: d = y - target / out_scale; loss partial sums of
+// d^2 (binary64); dY = 2 d / (8 n) as bfloat16.
+__global__ void loss_grad_kernel(const float *__restrict__ y, F8 tgt,
+                                 const float *__restrict__ inv_out, long long n,
+                                 bf16 *__restrict__ dy, double *__restrict__ partials) {
+    double acc = 0.0;
+    const float gsc = (float)(2.0 / (8.0 * (double)n));
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < 8 * n;
+         t += (long long)gridDim.x * blockDim.x) {
+        const int c = (int)(t / n);
+        const long long p = t - c * n;
+        const float d = y[t] - tgt.p[c][p] * inv_out[c];
+        acc += (double)d * (double)d;
+        dy[t] = __float2bfloat16_rn(gsc * d);
+    }
+    __shared__ double sh[256];
+    sh[threadIdx.x] = acc;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if ((int)threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) partials[blockIdx.x] = sh[0];
+}
+
+// out[c] = out_scale[c] * y[c]
+__global__ void scale_output_kernel(const float *__restrict__ y, const float *__restrict__ out_scale,
+                                    long long n, W8 out) {
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < 8 * n;
+         t += (long long)gridDim.x * blockDim.x) {
+        const int c = (int)(t / n);
+        out.p[c][t - c * n] = out_scale[c] * y[t];
+    }
+}
+
+// Guard: largest |out_scale * y| (NaN counts as larger than anything) into one word.
+__global__ void correction_max_kernel(const float *__restrict__ y,
+                                      const float *__restrict__ out_scale, long long n,
+                                      unsigned long long *gmax) {
+    double m = 0.0;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < 8 * n;
+         t += (long long)gridDim.x * blockDim.x) {
+        const int c = (int)(t / n);
+        const double v = fabs((double)(out_scale[c] * y[t]));
+        m = (v > m || v != v) ? v : m;
+    }
+    unsigned long long bits = (unsigned long long)__double_as_longlong(m);
+    for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long other = __shfl_xor_sync(0xffffffffu, bits, o);
+        bits = other > bits ? other : bits;
+    }
+    if ((threadIdx.x & 31) == 0) atomicMax(gmax, bits);
+}
+
+// f[c] += out_scale[c] * y[c], only if the guard word shows a finite maximum <= limit.
+__global__ void apply_correction_kernel(W8 f, const float *__restrict__ y,
+                                        const float *__restrict__ out_scale, long long n,
+                                        const unsigned long long *gmax, double limit) {
+    const double m = __longlong_as_double((long long)*gmax);
+    if (!(m <= limit)) return;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < 8 * n;
+         t += (long long)gridDim.x * blockDim.x) {
+        const int c = (int)(t / n);
+        f.p[c][t - c * n] += out_scale[c] * y[t];
+    }
+}
+
+// Adam (Kingma and Ba 2015) on the binary32 master parameters.
+__global__ void adam_kernel(float *__restrict__ p, float *__restrict__ m, float *__restrict__ v,
+                            const float *__restrict__ g, int n, float lr, float b1, float b2,
+                            float eps, float c1, float c2) {
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x) {
+        const float gt = g[t];
+        const float mt = b1 * m[t] + (1.f - b1) * gt;
+        const float vt = b2 * v[t] + (1.f - b2) * gt * gt;
+        m[t] = mt;
+        v[t] = vt;
+        p[t] -= lr * (mt / c1) / (sqrtf(vt / c2) + eps);
+    }
+}
+
+// bfloat16 weights from the master copy W[co][ci][tap]:
+//   forward layout    Wf[co][tap][ci_pad]   (ci >= cin stays zero);
+//   transposed layout Wb[ci][26 - tap][co_pad] for the input gradient.
+__global__ void prep_weights_kernel(const float *__restrict__ W, int cout, int cin, int cin_pad,
+                                    bf16 *__restrict__ wf, int cout_pad, bf16 *__restrict__ wb) {
+    const int total = cout * cin * 27;
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < total; t += gridDim.x * blockDim.x) {
+        const int co = t / (cin * 27);
+        const int rem = t - co * cin * 27;
+        const int ci = rem / 27;
+        const int tap = rem - ci * 27;
+        const bf16 w = __float2bfloat16_rn(W[t]);
+        wf[((long long)co * 27 + tap) * cin_pad + ci] = w;
+        if (wb) wb[((long long)ci * 27 + (26 - tap)) * cout_pad + co] = w;
+    }
+}
+
+// Full-weighting restriction: coarse(I) = sum_d w(d) fine(2I + d), w = (1/4, 1/2, 1/4)
+// per axis, periodic; binary64 accumulation, binary32 result.
+template <typename T>
+__global__ void restrict_kernel(const T *__restrict__ fine, int nxf, int nyf, int nzf,
+                                float *__restrict__ coarse) {
+    const int nxc = nxf / 2, nyc = nyf / 2, nzc = nzf / 2;
+    const long long total = (long long)nxc * nyc * nzc;
+    const double w[3] = {0.25, 0.5, 0.25};
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+         t += (long long)gridDim.x * blockDim.x) {
+        const int I = (int)(t % nxc);
+        const int J = (int)((t / nxc) % nyc);
+        const int K = (int)(t / ((long long)nxc * nyc));
+        double acc = 0.0;
+        for (int dk = -1; dk <= 1; ++dk)
+            for (int dj = -1; dj <= 1; ++dj)
+                for (int di = -1; di <= 1; ++di) {
+                    const long long idx =
+                        ((long long)cl_wrap(2 * K + dk, nzf) * nyf + cl_wrap(2 * J + dj, nyf)) * nxf +
+                        cl_wrap(2 * I + di, nxf);
+                    acc += w[di + 1] * w[dj + 1] * w[dk + 1] * (double)fine[idx];
+                }
+        coarse[t] = (float)acc;
+    }
+}
+
+}  // namespace ac
+
+using namespace ac;
+
+// Parameter layout (binary32, as in common deep-learning libraries):
+// W1[32][8][3][3][3], b1[32], W2[32][32][3][3][3], b2[32], W3[8][32][3][3][3], b3[8].
+static const int P_W1 = 0, P_B1 = 6912, P_W2 = 6944, P_B2 = 34592, P_W3 = 34624, P_B3 = 41536;
+
+struct ac_closure {
+    ConvGeom g;
+    cudaStream_t stream;
+    float *block;  // master params, m, v, grads, scales
+    float *params, *adam_m, *adam_v, *grads;
+    float *scales;  // [0..7] 1/in_scale, [8..15] out_scale, [16..23] 1/out_scale
+    float in_scale[8], out_scale[8];
+    bf16 *wf1, *wf2, *wf3, *wb3, *wb2;
+    bf16 *x0, *a1, *a2, *dy, *dz2, *dz1;
+    float *y;
+    float *part;
+    double *lossp;
+    double *loss_host;
+    unsigned long long *guard;
+    int adam_t;
+    int lossblocks;
+    unsigned long long launches;
+    void *act_block;
+};
+
+#define CCK(call)                                          \
+    do {                                                   \
+        cudaError_t e_ = (call);                           \
+        if (e_ != cudaSuccess) return ac_report_cuda(e_);  \
+    } while (0)
+
+static unsigned cl_grid(long long count, int threads = 256) {
+    long long b = (count + threads - 1) / threads;
+    return (unsigned)(b > 152 * 16 ? 152 * 16 : (b < 1 ? 1 : b));
+}
+
+static void free_closure(ac_closure *c) {
+    if (c->block) cudaFree(c->block);
+    if (c->act_block) cudaFree(c->act_block);
+    if (c->loss_host) cudaFreeHost(c->loss_host);
+}
+
+extern "C" int ac_closure_init(ac_closure **out, int nx, int ny, int nz, void *stream) {
+    if (!out || nx < 1 || ny < 1 || nz < 1 || nx > (1 << 20) || ny > (1 << 20) || nz > (1 << 20))
+        return AC_ERR_ARG;
+    *out = nullptr;
+    ac_closure *c = new (std::nothrow) ac_closure();
+    if (!c) return AC_ERR_OOM;
+    c->g.nx = nx;
+    c->g.ny = ny;
+    c->g.nz = nz;
+    c->g.n = (long long)nx * ny * nz;
+    c->stream = static_cast<cudaStream_t>(stream);
+    const long long n = c->g.n;
+    const size_t np = AC_CLOSURE_NPARAMS;
+    // params, m, v, grads, scales (24), bf16 weights (fwd and transposed layouts)
+    const size_t wbytes = 2 * (32 * 27 * 16 + 32 * 27 * 32 + 8 * 27 * 32 + 32 * 27 * 16 + 32 * 27 * 32);
+    const size_t fbytes = sizeof(float) * (4 * np + 64) + wbytes + 256;
+    c->lossblocks = 304;
+    const size_t part_floats = (size_t)9 * CL_WG_CTAS * 32 * 96;
+    const size_t abytes = 2 * (size_t)n * (16 + 32 + 32 + 16 + 32 + 32) + 4 * (size_t)n * 8 +
+                          4 * part_floats + 8 * (size_t)c->lossblocks + 8 + 1024;
+    cudaError_t e = cudaMalloc(&c->block, fbytes);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->block, 0, fbytes, c->stream);
+    if (e == cudaSuccess) e = cudaMalloc(&c->act_block, abytes);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->act_block, 0, abytes, c->stream);
+    if (e == cudaSuccess) e = cudaMallocHost(&c->loss_host, 2 * sizeof(double));
+    if (e != cudaSuccess) {
+        int rc = ac_report_cuda(e);
+        free_closure(c);
+        delete c;
+        return rc;
+    }
+    float *f = c->block;
+    c->params = f;
+    c->adam_m = f + np;
+    c->adam_v = f + 2 * np;
+    c->grads = f + 3 * np;
+    c->scales = f + 4 * np;
+    bf16 *w = reinterpret_cast<bf16 *>(f + 4 * np + 64);
+    c->wf1 = w;
+    c->wf2 = c->wf1 + 32 * 27 * 16;
+    c->wf3 = c->wf2 + 32 * 27 * 32;
+    c->wb3 = c->wf3 + 8 * 27 * 32;
+    c->wb2 = c->wb3 + 32 * 27 * 16;
+    char *a = static_cast<char *>(c->act_block);
+    c->x0 = reinterpret_cast<bf16 *>(a);
+    c->a1 = c->x0 + 16 * n;
+    c->a2 = c->a1 + 32 * n;
+    c->dy = c->a2 + 32 * n;
+    c->dz2 = c->dy + 16 * n;
+    c->dz1 = c->dz2 + 32 * n;
+    c->y = reinterpret_cast<float *>(c->dz1 + 32 * n);
+    c->part = c->y + 8 * n;
+    c->lossp = reinterpret_cast<double *>(c->part + part_floats);
+    c->guard = reinterpret_cast<unsigned long long *>(c->lossp + c->lossblocks);
+    for (int i = 0; i < 8; ++i) c->in_scale[i] = c->out_scale[i] = 1.f;
+    float sc[24];
+    for (int i = 0; i < 24; ++i) sc[i] = 1.f;
+    e = cudaMemcpyAsync(c->scales, sc, sizeof sc, cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) {
+        int rc = ac_report_cuda(e);
+        free_closure(c);
+        delete c;
+        return rc;
+    }
+    *out = c;
+    return AC_OK;
+}
+
+extern "C" int ac_closure_quit(ac_closure *c) {
+    if (!c) return AC_OK;
+    cudaStreamSynchronize(c->stream);
+    free_closure(c);
+    delete c;
+    return AC_OK;
+}
+
+static int prep_weights(ac_closure *c) {
+    prep_weights_kernel<<<32, 256, 0, c->stream>>>(c->params + P_W1, 32, 8, 16, c->wf1, 0, nullptr);
+    prep_weights_kernel<<<128, 256, 0, c->stream>>>(c->params + P_W2, 32, 32, 32, c->wf2, 32, c->wb2);
+    prep_weights_kernel<<<32, 256, 0, c->stream>>>(c->params + P_W3, 8, 32, 32, c->wf3, 16, c->wb3);
+    c->launches += 3;
+    CCK(cudaGetLastError());
+    return AC_OK;
+}
+
+extern "C" int ac_closure_set_params(ac_closure *c, const float *host) {
+    if (!c || !host) return AC_ERR_ARG;
+    for (int i = 0; i < AC_CLOSURE_NPARAMS; ++i)
+        if (!isfinite(host[i])) return AC_ERR_ARG;
+    CCK(cudaMemcpyAsync(c->params, host, sizeof(float) * AC_CLOSURE_NPARAMS, cudaMemcpyHostToDevice,
+                        c->stream));
+    CCK(cudaMemsetAsync(c->adam_m, 0, sizeof(float) * 2 * AC_CLOSURE_NPARAMS, c->stream));
+    c->adam_t = 0;
+    return prep_weights(c);
+}
+
+static int copy_out(ac_closure *c, const float *dev, float *host) {
+    if (!c || !host) return AC_ERR_ARG;
+    CCK(cudaMemcpyAsync(host, dev, sizeof(float) * AC_CLOSURE_NPARAMS, cudaMemcpyDeviceToHost,
+                        c->stream));
+    CCK(cudaStreamSynchronize(c->stream));
+    return AC_OK;
+}
+
+extern "C" int ac_closure_get_params(ac_closure *c, float *host) {
+    return c ? copy_out(c, c->params, host) : AC_ERR_ARG;
+}
+extern "C" int ac_closure_get_grads(ac_closure *c, float *host) {
+    return c ? copy_out(c, c->grads, host) : AC_ERR_ARG;
+}
+
+extern "C" int ac_closure_set_scales(ac_closure *c, const float in_scale[8], const float out_scale[8]) {
+    if (!c || !in_scale || !out_scale) return AC_ERR_ARG;
+    float sc[24];
+    for (int i = 0; i < 8; ++i) {
+        if (!(in_scale[i] > 0) || !(out_scale[i] > 0) || !isfinite(in_scale[i]) ||
+            !isfinite(out_scale[i]))
+            return AC_ERR_ARG;
+        c->in_scale[i] = in_scale[i];
+        c->out_scale[i] = out_scale[i];
+        sc[i] = 1.f / in_scale[i];
+        sc[8 + i] = out_scale[i];
+        sc[16 + i] = 1.f / out_scale[i];
+    }
+    CCK(cudaMemcpyAsync(c->scales, sc, sizeof sc, cudaMemcpyHostToDevice, c->stream));
+    CCK(cudaStreamSynchronize(c->stream));
+    return AC_OK;
+}
+
+static int run_forward(ac_closure *c, const float *const in[8]) {
+    const ConvGeom g = c->g;
+    F8 f;
+    for (int i = 0; i < 8; ++i) f.p[i] = in[i];
+    pack_input_kernel<<<cl_grid(8 * g.n), 256, 0, c->stream>>>(f, c->scales, g.n, c->x0);
+    const unsigned ctas = (unsigned)((long long)g.ny * g.nz * ((g.nx + CL_TM - 1) / CL_TM));
+    conv_fwd_kernel<16, 32, EPI_RELU_BF16><<<ctas, CL_THREADS, 0, c->stream>>>(
+        c->x0, c->wf1, c->params + P_B1, nullptr, c->a1, g);
+    conv_fwd_kernel<32, 32, EPI_RELU_BF16><<<ctas, CL_THREADS, 0, c->stream>>>(
+        c->a1, c->wf2, c->params + P_B2, nullptr, c->a2, g);
+    conv_fwd_kernel<32, 8, EPI_LINEAR_F32><<<ctas, CL_THREADS, 0, c->stream>>>(
+        c->a2, c->wf3, c->params + P_B3, nullptr, c->y, g);
+    c->launches += 4;
+    CCK(cudaGetLastError());
+    return AC_OK;
+}
+
+extern "C" int ac_closure_forward(ac_closure *c, const float *const in[8], float *const out[8]) {
+    if (!c || !in) return AC_ERR_ARG;
+    for (int i = 0; i < 8; ++i)
+        if (!in[i] || (out && !out[i])) return AC_ERR_ARG;
+    int rc = run_forward(c, in);
+    if (rc) return rc;
+    if (out) {
+        W8 o;
+        for (int i = 0; i < 8; ++i) o.p[i] = out[i];
+        scale_output_kernel<<<cl_grid(8 * c->g.n), 256, 0, c->stream>>>(c->y, c->scales + 8, c->g.n, o);
+        c->launches++;
+        CCK(cudaGetLastError());
+    }
+    return AC_OK;
+}
+
+extern "C" int ac_closure_backward(ac_closure *c, const float *const in[8],
+                                   const float *const target[8], double *loss) {
+    if (!c || !in || !target) return AC_ERR_ARG;
+    for (int i = 0; i < 8; ++i)
+        if (!in[i] || !target[i]) return AC_ERR_ARG;
+    int rc = run_forward(c, in);
+    if (rc) return rc;
+    const ConvGeom g = c->g;
+    F8 t;
+    for (int i = 0; i < 8; ++i) t.p[i] = target[i];
+    loss_grad_kernel<<<c->lossblocks, 256, 0, c->stream>>>(c->y, t, c->scales + 16, g.n, c->dy,
+                                                           c->lossp);
+    const unsigned ctas = (unsigned)((long long)g.ny * g.nz * ((g.nx + CL_TM - 1) / CL_TM));
+    // input gradients through conv3 and conv2 (ReLU masks from the stored activations)
+    conv_fwd_kernel<16, 32, EPI_MASK_BF16><<<ctas, CL_THREADS, 0, c->stream>>>(
+        c->dy, c->wb3, nullptr, c->a2, c->dz2, g);
+    conv_fwd_kernel<32, 32, EPI_MASK_BF16><<<ctas, CL_THREADS, 0, c->stream>>>(
+        c->dz2, c->wb2, nullptr, c->a1, c->dz1, g);
+    // weight gradients
+    const dim3 wg(CL_WG_CTAS, 9);
+    conv_wgrad_kernel<32, 8><<<wg, CL_THREADS, 0, c->stream>>>(c->dy, c->a2, c->part, g);
+    wgrad_reduce_kernel<<<32, 256, 0, c->stream>>>(c->part, CL_WG_CTAS, 8, 32, 32, c->grads + P_W3);
+    conv_wgrad_kernel<32, 32><<<wg, CL_THREADS, 0, c->stream>>>(c->dz2, c->a1, c->part, g);
+    wgrad_reduce_kernel<<<64, 256, 0, c->stream>>>(c->part, CL_WG_CTAS, 32, 32, 32, c->grads + P_W2);
+    conv_wgrad_kernel<16, 32><<<wg, CL_THREADS, 0, c->stream>>>(c->dz1, c->x0, c->part, g);
+    wgrad_reduce_kernel<<<32, 256, 0, c->stream>>>(c->part, CL_WG_CTAS, 32, 16, 8, c->grads + P_W1);
+    bias_grad_kernel<<<8, 256, 0, c->stream>>>(c->dy, g.n, c->grads + P_B3);
+    bias_grad_kernel<<<32, 256, 0, c->stream>>>(c->dz2, g.n, c->grads + P_B2);
+    bias_grad_kernel<<<32, 256, 0, c->stream>>>(c->dz1, g.n, c->grads + P_B1);
+    c->launches += 12;
+    CCK(cudaGetLastError());
+    if (loss) {
+        double *hp = static_cast<double *>(malloc(sizeof(double) * c->lossblocks));
+        if (!hp) return AC_ERR_OOM;
+        cudaError_t e = cudaMemcpyAsync(hp, c->lossp, sizeof(double) * c->lossblocks,
+                                        cudaMemcpyDeviceToHost, c->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+        if (e != cudaSuccess) {
+            free(hp);
+            return ac_report_cuda(e);
+        }
+        double s = 0.0;
+        for (int i = 0; i < c->lossblocks; ++i) s += hp[i];
+        free(hp);
+        *loss = s / (8.0 * (double)g.n);
+        if (!isfinite(*loss)) return AC_ERR_NONFINITE;
+    }
+    return AC_OK;
+}
+
+extern "C" int ac_closure_adam_step(ac_closure *c, float lr, float beta1, float beta2, float eps) {
+    if (!c || !(lr > 0) || !(beta1 >= 0 && beta1 < 1) || !(beta2 >= 0 && beta2 < 1) || !(eps > 0))
+        return AC_ERR_ARG;
+    c->adam_t++;
+    const float c1 = 1.f - powf(beta1, (float)c->adam_t);
+    const float c2 = 1.f - powf(beta2, (float)c->adam_t);
+    adam_kernel<<<64, 256, 0, c->stream>>>(c->params, c->adam_m, c->adam_v, c->grads,
+                                           AC_CLOSURE_NPARAMS, lr, beta1, beta2, eps, c1, c2);
+    c->launches++;
+    CCK(cudaGetLastError());
+    return prep_weights(c);
+}
+
+extern "C" int ac_closure_apply(ac_closure *c, ac_handle *h, double limit, int *applied) {
+    if (!c || !h || !(limit > 0)) return AC_ERR_ARG;
+    void *ptrs[8];
+    int precision = 0, layout = 0, n[3];
+    int rc = ac_get_state(h, ptrs, &precision, &layout, n);
+    if (rc) return rc;
+    if (precision == AC_FP64 || layout != AC_LAYOUT_PERIODIC || n[0] != c->g.nx ||
+        n[1] != c->g.ny || n[2] != c->g.nz)
+        return AC_ERR_ARG;
+    const float *in[8];
+    W8 f;
+    for (int i = 0; i < 8; ++i) {
+        in[i] = static_cast<const float *>(ptrs[i]);
+        f.p[i] = static_cast<float *>(ptrs[i]);
+    }
+    rc = run_forward(c, in);
+    if (rc) return rc;
+    CCK(cudaMemsetAsync(c->guard, 0, sizeof(unsigned long long), c->stream));
+    correction_max_kernel<<<cl_grid(8 * c->g.n), 256, 0, c->stream>>>(c->y, c->scales + 8, c->g.n,
+                                                                      c->guard);
+    apply_correction_kernel<<<cl_grid(8 * c->g.n), 256, 0, c->stream>>>(f, c->y, c->scales + 8,
+                                                                        c->g.n, c->guard, limit);
+    c->launches += 2;
+    CCK(cudaGetLastError());
+    if (applied) {
+        unsigned long long bits = 0;
+        CCK(cudaMemcpyAsync(c->loss_host, c->guard, sizeof bits, cudaMemcpyDeviceToHost, c->stream));
+        CCK(cudaStreamSynchronize(c->stream));
+        memcpy(&bits, c->loss_host, sizeof bits);
+        double m;
+        memcpy(&m, &bits, sizeof m);
+        *applied = m <= limit ? 1 : 0;
+    }
+    return AC_OK;
+}
+
+extern "C" int ac_closure_launch_count(const ac_closure *c, unsigned long long *count) {
+    if (!c || !count) return AC_ERR_ARG;
+    *count = c->launches;
+    return AC_OK;
+}
+
+extern "C" int ac_restrict(const void *const fine[8], int fine_precision, int nx, int ny, int nz,
+                           float *const coarse[8], void *stream) {
+    if (!fine || !coarse || nx < 2 || ny < 2 || nz < 2 || (nx | ny | nz) & 1) return AC_ERR_ARG;
+    if (fine_precision != AC_FP64 && fine_precision != AC_FP32 && fine_precision != AC_FP32_W64)
+        return AC_ERR_ARG;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const long long nc = (long long)(nx / 2) * (ny / 2) * (nz / 2);
+    for (int q = 0; q < 8; ++q) {
+        if (!fine[q] || !coarse[q]) return AC_ERR_ARG;
+        if (fine_precision == AC_FP64)
+            restrict_kernel<double><<<cl_grid(nc), 256, 0, st>>>(
+                static_cast<const double *>(fine[q]), nx, ny, nz, coarse[q]);
+        else
+            restrict_kernel<float><<<cl_grid(nc), 256, 0, st>>>(
+                static_cast<const float *>(fine[q]), nx, ny, nz, coarse[q]);
+    }
+    CCK(cudaGetLastError());
+    return AC_OK;
+}

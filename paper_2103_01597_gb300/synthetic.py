@@ -12,7 +12,9 @@ Recipes:
   * ``uniform_state``: every field i.i.d. uniform in [0, 1) -- the paper's own
                        benchmark initial condition (Sec. 5);
   * ``ensemble``:      box sizes drawn per axis from {32, 48, 64, 96, 128} and
-                       nu, eta log-uniform in [1e-3, 1e-2].
+                       nu, eta log-uniform in [1e-3, 1e-2];
+  * ``turbulent_state``: random-phase modes up to |k| = kmax with a power-law
+                       spectrum (learned-closure training data).
 """
 import numpy as np
 
@@ -50,6 +52,31 @@ def smooth_state(n, seed, amp=0.1):
             ph = g.random() * 2 * np.pi
             a = amp * g.random()
             f[q] += a * np.cos(2 * np.pi * (m[0] * i / nx + m[1] * j / ny + m[2] * k / nz) + ph)
+    return f
+
+
+def turbulent_state(n, seed, kmax=6, amp=0.3, slope=-5.0 / 3.0):
+    """Random-phase Fourier modes with 1 <= |k| <= kmax in every field (u and A at
+    amplitude `amp`, ln rho and s at amp / 4), mode amplitudes ~ |k|^(slope / 2)
+    (an energy spectrum ~ k^slope), normalised so each field has rms `amp`
+    (`amp / 4`).  Used for the learned-closure data: energy up to the scales
+    the coarse grid resolves."""
+    nx, ny, nz = n
+    g = _rng(seed)
+    kx = np.fft.fftfreq(nx, 1.0 / nx)
+    ky = np.fft.fftfreq(ny, 1.0 / ny)
+    kz = np.fft.fftfreq(nz, 1.0 / nz)
+    KZ, KY, KX = np.meshgrid(kz, ky, kx, indexing="ij")
+    kk = np.sqrt(KX ** 2 + KY ** 2 + KZ ** 2)
+    shell = (kk >= 1) & (kk <= kmax)
+    weight = np.where(shell, np.maximum(kk, 1.0) ** (slope / 2 - 1.0), 0.0)
+    f = np.zeros((NFIELDS, nz, ny, nx))
+    for q in range(NFIELDS):
+        spec = weight * np.exp(2j * np.pi * g.random(kk.shape)) * g.normal(1.0, 0.3, kk.shape)
+        field = np.real(np.fft.ifftn(spec))
+        rms = np.sqrt(np.mean(field ** 2))
+        a = amp if q in (1, 2, 3, 5, 6, 7) else amp / 4
+        f[q] = field * (a / rms if rms > 0 else 0.0)
     return f
 
 

@@ -1,0 +1,157 @@
+"""GPU tests of the learned closure (restriction, conv net forward, backward,
+Adam, guarded application) against the FP64 oracle, and of what training buys.
+
+Tolerances: restriction 1e-6 relative (binary32 output of a binary64 sum);
+forward and gradients 2e-2 relative per tensor in the max norm (bfloat16
+operands on both sides, binary32 vs binary64 accumulation and the occasional
+different bfloat16 rounding of an intermediate); Adam 1e-5.
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+from oracle import closure as oc
+from oracle import core
+from paper_2103_01597_gb300 import ac, build, synthetic
+from paper_2103_01597_gb300 import closure as cl
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    build.build()
+    ac.load_library()
+
+
+def _dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32).reshape(8, -1)).cuda()
+
+
+def _rows(t):
+    return [t[q].data_ptr() for q in range(8)]
+
+
+def _maxrel(g, o):
+    return float(np.max(np.abs(g - o)) / np.max(np.abs(o)))
+
+
+def test_restriction_matches_oracle():
+    nf = (16, 12, 20)
+    f = synthetic.smooth_state(nf, 3, amp=0.4) + synthetic.noise_state(nf, 4, 1e-2)
+    sim = ac.Simulation(nf, precision=ac.AC_FP64)
+    sim.load(f)
+    nc = (8, 6, 10)
+    out = torch.empty((8, 8 * 6 * 10), dtype=torch.float32, device="cuda")
+    ptrs, _, _, _ = ac.ac_get_state(sim.h)
+    ac.ac_restrict(ptrs, ac.AC_FP64, nf, _rows(out))
+    got = out.double().cpu().numpy().reshape(8, nc[2], nc[1], nc[0])
+    for q in range(8):
+        assert _maxrel(got[q], core.restrict(f[q])) <= 1e-6, q
+    sim.close()
+
+
+def _setup(n, seed):
+    net = oc.Net.init(seed)
+    params = net.flat().astype(np.float32)
+    net = oc.Net.unflat(params.astype(np.float64))  # the binary32 values the GPU holds
+    rng = np.random.default_rng(seed)
+    x = synthetic.turbulent_state(n, seed, kmax=3, amp=0.5).astype(np.float32).astype(np.float64)
+    in_scale = (0.5 + rng.random(8)).astype(np.float32)
+    out_scale = (0.01 + 0.1 * rng.random(8)).astype(np.float32)
+    return net, params, x, in_scale, out_scale
+
+
+@pytest.mark.parametrize("n", [(16, 12, 10), (40, 8, 6), (130, 3, 4)])
+def test_forward_matches_oracle(n):
+    net, params, x, ins, outs = _setup(n, 5)
+    c = cl.Closure(n, params=params)
+    c.set_scales(ins, outs)
+    got = c.correction(_dev(x)).double().cpu().numpy().reshape((8,) + x.shape[1:])
+    xn = x / ins.astype(np.float64)[:, None, None, None]
+    y, _ = net.forward(xn, round_bf16=True)
+    ref = y * outs.astype(np.float64)[:, None, None, None]
+    assert _maxrel(got, ref) <= 2e-2, _maxrel(got, ref)
+    c.close()
+
+
+def test_gradients_and_adam_match_oracle():
+    n = (16, 12, 10)
+    net, params, x, ins, outs = _setup(n, 6)
+    rng = np.random.default_rng(7)
+    tgt = (outs.astype(np.float64)[:, None, None, None]
+           * rng.standard_normal(x.shape)).astype(np.float32).astype(np.float64)
+    c = cl.Closure(n, params=params)
+    c.set_scales(ins, outs)
+    loss = c.loss(_dev(x), _dev(tgt))
+    g = ac.ac_closure_get_grads(c.c).astype(np.float64)
+    xn = x / ins.astype(np.float64)[:, None, None, None]
+    tn = tgt / outs.astype(np.float64)[:, None, None, None]
+    lo, go = net.loss_and_grads(xn, tn, round_bf16=True)
+    assert abs(loss - lo) <= 1e-3 * lo, (loss, lo)
+    go_flat = oc.Net(go).flat()
+    off = 0
+    for li, (W, b) in enumerate(go):
+        for arr in (W, b):
+            sz = arr.size
+            err = _maxrel(g[off:off + sz], go_flat[off:off + sz])
+            assert err <= 2e-2, (li, arr.shape, err)
+            off += sz
+    # one Adam step on the GPU's own gradients
+    ac.ac_closure_adam_step(c.c, 1e-3)
+    new = ac.ac_closure_get_params(c.c).astype(np.float64)
+    ad = oc.Adam([params.shape], lr=1e-3)
+    ref = ad.step([params.astype(np.float64)], [g])[0]
+    upd_g = new - params.astype(np.float64)
+    upd_o = ref - params.astype(np.float64)
+    assert np.max(np.abs(upd_g - upd_o)) <= 1e-4 * np.max(np.abs(upd_o))
+    c.close()
+
+
+def test_apply_guard():
+    n = (16, 8, 12)
+    net, params, x, ins, outs = _setup(n, 8)
+    sim = ac.Simulation(n, precision=ac.AC_FP32)
+    sim.load(x)
+    before = cl.current_state(sim).clone()
+    c = cl.Closure(n, params=params)
+    c.set_scales(ins, outs)
+    corr = c.correction(before.clone()).clone()
+    assert not c.apply(sim, limit=1e-9)  # larger than the limit: left unchanged
+    assert torch.equal(cl.current_state(sim), before)
+    assert c.apply(sim, limit=1e3)
+    after = cl.current_state(sim)
+    assert torch.allclose(after, before + corr, rtol=0, atol=1e-6)
+    sim.close()
+    c.close()
+
+
+def test_training_reduces_coarse_error():
+    """Fine 32^3 binary64 run restricted to 16^3: the trained closure predicts
+    the coarse step's defect on held-out pairs far better than zero (what the
+    plain coarse step without closure implies)."""
+    nf = (32, 32, 32)
+    f0 = synthetic.turbulent_state(nf, 21, kmax=6, amp=0.4)
+    pairs = cl.make_pairs(f0, nf, 48, 2e-3, seed=3, force_amp=0.05)
+    train, held = pairs[:40], pairs[40:]
+    ins = cl.channel_rms([p[0] for p in train])
+    outs = cl.channel_rms([p[1] for p in train])
+    c = cl.Closure((16, 16, 16), seed=1)
+    c.set_scales(ins, outs)
+    base = np.mean([c.loss(x, t) for x, t in held])
+    for it in range(600):
+        x, t = train[it % len(train)]
+        c.train_step(x, t, lr=2e-3 if it < 400 else 5e-4)
+    after = np.mean([c.loss(x, t) for x, t in held])
+    # relative defect left after the correction vs the defect itself
+    rel = []
+    for x, t in held:
+        corr = c.correction(x)
+        rel.append(float(torch.linalg.vector_norm(t - corr) / torch.linalg.vector_norm(t)))
+    print("closure: held-out loss %.3e -> %.3e, relative defect %.3f" % (base, after,
+                                                                         float(np.mean(rel))))
+    assert after < 0.5 * base
+    assert np.mean(rel) < 0.75
+    c.close()
