@@ -58,6 +58,11 @@ WORKLOADS = {
     "forced512_fp32": dict(n=(512, 512, 512), precision="fp32", force_amp=0.05, seed=3,
                            dt=1e-3, init="noise",
                            desc="512^3 periodic FP32 forced non-ideal MHD (FP64 reductions)"),
+    "closure128": dict(n=(128, 128, 128), precision="fp32", force_amp=0.05, seed=5, dt=1e-3,
+                       init="turbulent", closure=True,
+                       desc="learned closure: 128^3 FP32 coarse grid + 3-layer 3-D conv "
+                            "(8-32-32-8, k=3, BF16 weights, FP32 accumulation) applied every "
+                            "step, trained on 256^3 FP64 forced runs restricted 2x"),
     "ensemble64_fp32": dict(n=None, precision="fp32", force_amp=0.0, seed=4, dt=1e-3,
                             init="noise", ensemble=True,
                             desc="64 periodic boxes, per-axis sizes from {32,48,64,96,128}, "
@@ -76,6 +81,9 @@ def parse():
     ap.add_argument("--workload", default="forced256_fp64", choices=sorted(WORKLOADS))
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--closure-pairs", type=int, default=24)
+    ap.add_argument("--closure-iters", type=int, default=300)
+    ap.add_argument("--closure-rollout", type=int, default=20)
     ap.add_argument("--no-compare", action="store_true",
                     help="ensemble: skip the separate-launch and FP64 comparisons")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
@@ -564,10 +572,160 @@ def run_ensemble(args, wl):
     return 0
 
 
+def _spectra(f, n):
+    """Kinetic (u) and magnetic (B = curl A, spectral) shell spectra on the host."""
+    from oracle import closure as oc
+    u = f[1:4]
+    A = f[5:8]
+    k = [np.fft.fftfreq(m, 1.0 / m) for m in (n[2], n[1], n[0])]
+    KZ, KY, KX = np.meshgrid(*k, indexing="ij")
+    Ah = [np.fft.fftn(A[a]) for a in range(3)]
+    Bh = [1j * (KY * Ah[2] - KZ * Ah[1]), 1j * (KZ * Ah[0] - KX * Ah[2]),
+          1j * (KX * Ah[1] - KY * Ah[0])]
+    B = np.array([np.real(np.fft.ifftn(b)) for b in Bh])
+    return oc.energy_spectrum(u), oc.energy_spectrum(B)
+
+
+def run_closure(args, wl):
+    """Coarse 128^3 FP32 grid with the learned closure applied every step."""
+    import torch
+    from paper_2103_01597_gb300 import ac, build, synthetic
+    from paper_2103_01597_gb300 import closure as cl
+    build.build()
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream()
+    nc = wl["n"]
+    nf = tuple(2 * v for v in nc)
+    cells = nc[0] * nc[1] * nc[2]
+    dtf = wl["dt"]
+    t0 = time.perf_counter()
+    f0 = synthetic.turbulent_state(nf, wl["seed"], kmax=24, amp=0.3)
+    npairs = args.closure_pairs
+    pairs = cl.make_pairs(f0, nf, npairs + 4, dtf, seed=wl["seed"], force_amp=wl["force_amp"])
+    t_data = time.perf_counter() - t0
+    train, held = pairs[:npairs], pairs[npairs:]
+    ins = cl.channel_rms([p[0] for p in train])
+    outs = cl.channel_rms([p[1] for p in train])
+    c = cl.Closure(nc, seed=wl["seed"])
+    c.set_scales(ins, outs)
+    base = float(np.mean([c.loss(x, t) for x, t in held]))
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for it in range(args.closure_iters):
+        x, t = train[it % len(train)]
+        c.train_step(x, t, lr=2e-3 if it < 0.7 * args.closure_iters else 5e-4)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    train_ms = e0.elapsed_time(e1) / args.closure_iters
+    after = float(np.mean([c.loss(x, t) for x, t in held]))
+    defect = []
+    for x, t in held:
+        corr = c.correction(x)
+        defect.append(float(torch.linalg.vector_norm(t - corr) / torch.linalg.vector_norm(t)))
+
+    # timed region: coarse steps with the closure applied after each step
+    sim = ac.Simulation(nc, precision=ac.AC_FP32, force_amp=wl["force_amp"], seed=wl["seed"])
+    cl.current_state(sim).copy_(held[0][0])
+    for _ in range(args.warmup):
+        sim.step(2 * dtf)
+        c.apply(sim, 1e3)
+    torch.cuda.synchronize()
+    conv_ev = [[torch.cuda.Event(enable_timing=True) for _ in range(2)] for _ in range(args.steps)]
+    ta, tb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    l0 = ac.ac_launch_count(sim.h) + ac.ac_closure_launch_count(c.c)
+    lib = ac.load_library()
+    ta.record(stream)
+    for it in range(args.steps):
+        sim.step(2 * dtf)
+        rc = lib.ac_closure_apply(c.c, sim.h, 1e3, None)  # forward + guard + add, no host sync
+        assert rc == 0, ac.ac_strerror(rc)
+    tb.record(stream)
+    torch.cuda.synchronize()
+    elapsed = ta.elapsed_time(tb) / 1e3
+    launches = ac.ac_launch_count(sim.h) + ac.ac_closure_launch_count(c.c) - l0
+    # the three convolution launches of the forward pass, timed alone on the same state
+    xs = cl._rows(cl.current_state(sim))
+    for it in range(args.steps):
+        conv_ev[it][0].record(stream)
+        ac.ac_closure_forward(c.c, xs, None)
+        conv_ev[it][1].record(stream)
+    torch.cuda.synchronize()
+    conv_s = statistics.mean(e[0].elapsed_time(e[1]) for e in conv_ev) / 1e3
+    value = cells * 3 * args.steps / elapsed / 1e9
+    flops = 2 * 27 * (8 * 32 + 32 * 32 + 32 * 8) * cells
+    peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    roof = {"bound": "tensor", "achieved": flops / conv_s / 1e12, "peak": peaks["bf16_tflops"],
+            "unit": "TFLOP/s", "frac": flops / conv_s / 1e12 / peaks["bf16_tflops"],
+            "traffic": None, "kernel": "conv_fwd_kernel x3 (closure forward, mma.sync BF16)",
+            "peak_source": "measured (MEASURED_PEAKS.json bf16_tflops, burst)",
+            "avg_launch_ms": 1e3 * conv_s / 3}
+
+    # spectra after M coarse steps: plain, with closure, and the restricted fine run
+    M = args.closure_rollout
+    fine = ac.Simulation(nf, precision=ac.AC_FP64, force_amp=wl["force_amp"], seed=wl["seed"])
+    fine.load(f0)
+    plain = ac.Simulation(nc, precision=ac.AC_FP32, force_amp=wl["force_amp"], seed=wl["seed"])
+    corr = ac.Simulation(nc, precision=ac.AC_FP32, force_amp=wl["force_amp"], seed=wl["seed"])
+    x0 = torch.empty((8, cells), dtype=torch.float32, device="cuda")
+    fptrs, _, _, _ = ac.ac_get_state(fine.h)
+    ac.ac_restrict(fptrs, ac.AC_FP64, nf, cl._rows(x0))
+    cl.current_state(plain).copy_(x0)
+    cl.current_state(corr).copy_(x0)
+    applied = 0
+    for m in range(M):
+        frc = ac.ac_forcing_draw(wl["seed"], 1000 + m)
+        for sm in (fine, plain, corr):
+            ac.ac_set_forcing(sm.h, *frc)
+        fine.step(dtf)
+        fine.step(dtf)
+        plain.step(2 * dtf)
+        corr.step(2 * dtf)
+        applied += int(c.apply(corr, 1e3))
+    ref = torch.empty((8, cells), dtype=torch.float32, device="cuda")
+    fptrs, _, _, _ = ac.ac_get_state(fine.h)
+    ac.ac_restrict(fptrs, ac.AC_FP64, nf, cl._rows(ref))
+    shape = (8, nc[2], nc[1], nc[0])
+    R = ref.double().cpu().numpy().reshape(shape)
+    P = cl.current_state(plain).double().cpu().numpy().reshape(shape)
+    C = cl.current_state(corr).double().cpu().numpy().reshape(shape)
+    kmax = nc[0] // 3
+    def dist(a, b):
+        return float(np.sqrt(np.sum((np.log(a[1:kmax]) - np.log(b[1:kmax])) ** 2) / (kmax - 1)))
+    eR, mR = _spectra(R, nc)
+    eP, mP = _spectra(P, nc)
+    eC, mC = _spectra(C, nc)
+    state_err = {"plain": float(np.sqrt(np.mean((P - R) ** 2) / np.mean(R ** 2))),
+                 "closure": float(np.sqrt(np.mean((C - R) ** 2) / np.mean(R ** 2)))}
+    quality = {"rollout_steps": M, "closure_applied": applied,
+               "kinetic_log_spectrum_rms_distance": {"plain": dist(eP, eR), "closure": dist(eC, eR)},
+               "magnetic_log_spectrum_rms_distance": {"plain": dist(mP, mR), "closure": dist(mC, mR)},
+               "state_rel_l2_error_vs_restricted_fine": state_err,
+               "heldout_loss_before_after": [base, after],
+               "heldout_relative_defect_after": float(np.mean(defect)),
+               "train_ms_per_iter": train_ms, "train_iters": args.closure_iters,
+               "pairs": npairs, "data_gen_s": t_data}
+    for sm in (fine, plain, corr, sim):
+        sm.close()
+    c.close()
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * elapsed / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+bf16",
+            "data": "synthetic",
+            "config": {"workload": wl["desc"], "grid": list(nc), "fine_grid": list(nf),
+                       "dt_coarse": 2 * dtf,
+                       "step": "coarse RK3 step (3 fused substeps) + closure forward "
+                               "(3 conv layers) + guarded correction"},
+            "roofline": roof, "cpu_baseline": None, "e2e": None, "gpu_launches": launches,
+            "clocks": None, "closure": quality}
+    print(json.dumps(line))
+    return 0
+
+
 def main():
     args = parse()
     wl = dict(WORKLOADS[args.workload])
-    if args.grid and not wl.get("ensemble"):
+    if args.grid and not wl.get("ensemble") and not wl.get("closure"):
         g = args.grid
         wl["n"] = (g, g, g)
         wl["desc"] = wl["desc"].replace("256^3", "%d^3" % g).replace("512^3", "%d^3" % g)
@@ -580,6 +738,8 @@ def main():
         return run_reference(args, wl)
     if wl.get("ensemble"):
         return run_ensemble(args, wl)
+    if wl.get("closure"):
+        return run_closure(args, wl)
     return run_ours(args, wl)
 
 
