@@ -599,7 +599,7 @@ def run_closure(args, wl):
     cells = nc[0] * nc[1] * nc[2]
     dtf = wl["dt"]
     t0 = time.perf_counter()
-    f0 = synthetic.turbulent_state(nf, wl["seed"], kmax=24, amp=0.3)
+    f0 = synthetic.turbulent_state(nf, wl["seed"], kmax=16, amp=0.3)
     npairs = args.closure_pairs
     pairs = cl.make_pairs(f0, nf, npairs + 4, dtf, seed=wl["seed"], force_amp=wl["force_amp"])
     t_data = time.perf_counter() - t0

@@ -103,6 +103,7 @@ def make_pairs(f0, n_fine, npairs, dt_fine, seed=0, force_amp=0.0, warm_steps=0,
         ac.ac_restrict(fptrs, ac.AC_FP64, n_fine, _rows(x))
         fine.step(dt_fine)
         fine.step(dt_fine)
+        ac.ac_last_cfl(fine.h)  # raises if the fine run stopped being finite
         fptrs, _, _, _ = ac.ac_get_state(fine.h)
         ac.ac_restrict(fptrs, ac.AC_FP64, n_fine, _rows(nxt))
         current_state(coarse).copy_(x)

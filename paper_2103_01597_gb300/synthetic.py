@@ -56,11 +56,12 @@ def smooth_state(n, seed, amp=0.1):
 
 
 def turbulent_state(n, seed, kmax=6, amp=0.3, slope=-5.0 / 3.0):
-    """Random-phase Fourier modes with 1 <= |k| <= kmax in every field (u and A at
-    amplitude `amp`, ln rho and s at amp / 4), mode amplitudes ~ |k|^(slope / 2)
-    (an energy spectrum ~ k^slope), normalised so each field has rms `amp`
-    (`amp / 4`).  Used for the learned-closure data: energy up to the scales
-    the coarse grid resolves."""
+    """Random-phase Fourier modes with 1 <= |k| <= kmax, mode amplitudes
+    ~ |k|^(slope / 2 - 1) (a shell energy spectrum ~ k^slope).  u has rms `amp`;
+    A is drawn with an extra 1/|k| so that B = curl A (evaluated spectrally
+    here, for the normalisation only) has rms `amp`; ln rho and s have rms
+    amp / 4.  Used for the learned-closure data: energy up to the scales the
+    coarse grid resolves, signal speeds O(1)."""
     nx, ny, nz = n
     g = _rng(seed)
     kx = np.fft.fftfreq(nx, 1.0 / nx)
@@ -71,12 +72,26 @@ def turbulent_state(n, seed, kmax=6, amp=0.3, slope=-5.0 / 3.0):
     shell = (kk >= 1) & (kk <= kmax)
     weight = np.where(shell, np.maximum(kk, 1.0) ** (slope / 2 - 1.0), 0.0)
     f = np.zeros((NFIELDS, nz, ny, nx))
+    spectra = {}
     for q in range(NFIELDS):
         spec = weight * np.exp(2j * np.pi * g.random(kk.shape)) * g.normal(1.0, 0.3, kk.shape)
+        if q >= 5:
+            spec = spec / np.maximum(kk, 1.0)
+        spectra[q] = spec
         field = np.real(np.fft.ifftn(spec))
-        rms = np.sqrt(np.mean(field ** 2))
-        a = amp if q in (1, 2, 3, 5, 6, 7) else amp / 4
-        f[q] = field * (a / rms if rms > 0 else 0.0)
+        if q < 5:
+            rms = np.sqrt(np.mean(field ** 2))
+            a = amp if q in (1, 2, 3) else amp / 4
+            f[q] = field * (a / rms if rms > 0 else 0.0)
+        else:
+            f[q] = field
+    Ah = [np.fft.fftn(f[5 + a]) for a in range(3)]
+    B = [np.real(np.fft.ifftn(1j * (KY * Ah[2] - KZ * Ah[1]))),
+         np.real(np.fft.ifftn(1j * (KZ * Ah[0] - KX * Ah[2]))),
+         np.real(np.fft.ifftn(1j * (KX * Ah[1] - KY * Ah[0])))]
+    brms = np.sqrt(np.mean(B[0] ** 2 + B[1] ** 2 + B[2] ** 2) / 3)
+    if brms > 0:
+        f[5:8] *= amp / brms
     return f
 
 
