@@ -82,7 +82,7 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--closure-pairs", type=int, default=24)
-    ap.add_argument("--closure-iters", type=int, default=300)
+    ap.add_argument("--closure-iters", type=int, default=800)
     ap.add_argument("--closure-rollout", type=int, default=20)
     ap.add_argument("--no-compare", action="store_true",
                     help="ensemble: skip the separate-launch and FP64 comparisons")
@@ -599,7 +599,7 @@ def run_closure(args, wl):
     cells = nc[0] * nc[1] * nc[2]
     dtf = wl["dt"]
     t0 = time.perf_counter()
-    f0 = synthetic.turbulent_state(nf, wl["seed"], kmax=16, amp=0.3)
+    f0 = synthetic.turbulent_state(nf, wl["seed"], kmax=48, amp=0.3)
     npairs = args.closure_pairs
     pairs = cl.make_pairs(f0, nf, npairs + 4, dtf, seed=wl["seed"], force_amp=wl["force_amp"])
     t_data = time.perf_counter() - t0
