@@ -168,6 +168,27 @@ int ac_store_w(ac_handle *h, int field, double *host_dst);
  */
 int ac_integrate_substep(ac_handle *h, double dt, int s);
 
+/*
+ * Arithmetic of the stencil sums for AC_FP64.  AC_STENCIL_AUTO (default): exact
+ * integer sums whenever they apply (binary64 fields, periodic layout, equal
+ * spacing dx = dy = dz), plain binary64 sums otherwise.  With integer sums each
+ * field group (ln rho; u; s; A) is first written as int64 fixed point with one
+ * power-of-two scale per group (|F| <= 2^44, resolution 2^-45 of the group's
+ * largest |f|); every stencil numerator and every sum of numerators with a
+ * common coefficient is then exact and only one int64 -> binary64 conversion
+ * and one multiplication per derivative term run on the FP64 pipe.  The result
+ * stays within the same 1e-12 relative bound of the exact-rounding definition.
+ * AC_STENCIL_FP64: binary64 arithmetic throughout.  AC_STENCIL_FIXED: integer
+ * sums, AC_ERR_ARG where they do not apply.  Extra device memory for integer
+ * sums: one int64 copy of the eight fields, allocated on first use.
+ */
+#define AC_STENCIL_AUTO 0
+#define AC_STENCIL_FP64 1
+#define AC_STENCIL_FIXED 2
+int ac_set_stencil_mode(ac_handle *h, int mode);
+/* *fixed = 1 if the next substeps use integer stencil sums. */
+int ac_get_stencil_path(const ac_handle *h, int *fixed);
+
 /* Substeps 0, 1, 2 with the same dt (one full Runge-Kutta step). */
 int ac_integrate_step(ac_handle *h, double dt);
 

@@ -30,6 +30,7 @@ AC_ALL = -1
 AC_FP64, AC_FP32, AC_FP32_W64 = 0, 1, 2
 AC_LAYOUT_PERIODIC, AC_LAYOUT_PADDED = 0, 1
 AC_MAX, AC_MIN, AC_SUM, AC_RMS = 0, 1, 2, 3
+AC_STENCIL_AUTO, AC_STENCIL_FP64, AC_STENCIL_FIXED = 0, 1, 2
 AC_Q_UMAG, AC_Q_EKIN, AC_Q_EMAG, AC_Q_CFL = 8, 9, 10, 11
 
 
@@ -96,6 +97,8 @@ def load_library(path=None):
         "ac_integrate_step": ([_vp, _c.c_double], _c.c_int),
         "ac_periodic_halo": ([_vp], _c.c_int),
         "ac_last_cfl": ([_vp, _pd], _c.c_int),
+        "ac_set_stencil_mode": ([_vp, _c.c_int], _c.c_int),
+        "ac_get_stencil_path": ([_vp, ctypes.POINTER(_c.c_int)], _c.c_int),
         "ac_reduce": ([_vp, _c.c_int, _c.c_int, _pd], _c.c_int),
         "ac_forcing_draw": ([_c.c_ulonglong, _c.c_ulonglong, ctypes.POINTER(_c.c_int), _pd, _pd],
                             _c.c_int),
@@ -230,6 +233,16 @@ def ac_integrate_substep(h, dt, s):
 
 def ac_integrate_step(h, dt):
     _check(load_library().ac_integrate_step(h, float(dt)), "ac_integrate_step")
+
+
+def ac_set_stencil_mode(h, mode):
+    _check(load_library().ac_set_stencil_mode(h, int(mode)), "ac_set_stencil_mode")
+
+
+def ac_get_stencil_path(h):
+    fixed = ctypes.c_int()
+    _check(load_library().ac_get_stencil_path(h, ctypes.byref(fixed)), "ac_get_stencil_path")
+    return bool(fixed.value)
 
 
 def ac_last_cfl(h):

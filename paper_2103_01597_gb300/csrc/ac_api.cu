@@ -55,6 +55,9 @@ struct ac_handle {
     double *result_dev;  // [value, flag word]
     double *result_host; // page-locked copy of result_dev
     unsigned long long *cfl_dev;  // max CFL speed of the last substep-0 input (bits of a double)
+    int stencil_mode;             // AC_STENCIL_*
+    long long *fx_block;          // int64 copies of the fields (integer stencil sums)
+    unsigned long long *fx_gmax;  // group maxima of |f| (bits of doubles)
     double *stage;       // float64 staging for load/store
     size_t stage_elems;
     int next_s;
@@ -115,6 +118,8 @@ static void free_handle_memory(ac_handle *h) {
     if (h->result_host) cudaFreeHost(h->result_host);
     if (h->stage) cudaFree(h->stage);
     if (h->cfl_dev) cudaFree(h->cfl_dev);
+    if (h->fx_block) cudaFree(h->fx_block);
+    if (h->fx_gmax) cudaFree(h->fx_gmax);
 }
 
 extern "C" int ac_init(ac_handle **out, const ac_grid *grid, const ac_params *params,
@@ -430,6 +435,28 @@ extern "C" int ac_set_forcing(ac_handle *h, const int k[3], const double e[3], d
     return AC_OK;
 }
 
+// Integer stencil sums apply to binary64 fields on a periodic grid with equal
+// spacing on every axis (so numerators of different axes share a coefficient).
+static int fx_applicable(const ac_handle *h) {
+    const double dx = h->grid.lx / h->grid.nx, dy = h->grid.ly / h->grid.ny,
+                 dz = h->grid.lz / h->grid.nz;
+    return h->params.precision == AC_FP64 && h->grid.layout == AC_LAYOUT_PERIODIC && dx == dy &&
+           dy == dz;
+}
+
+extern "C" int ac_set_stencil_mode(ac_handle *h, int mode) {
+    if (!h || mode < AC_STENCIL_AUTO || mode > AC_STENCIL_FIXED) return AC_ERR_ARG;
+    if (mode == AC_STENCIL_FIXED && !fx_applicable(h)) return AC_ERR_ARG;
+    h->stencil_mode = mode;
+    return AC_OK;
+}
+
+extern "C" int ac_get_stencil_path(const ac_handle *h, int *fixed) {
+    if (!h || !fixed) return AC_ERR_ARG;
+    *fixed = h->stencil_mode != AC_STENCIL_FP64 && fx_applicable(h);
+    return AC_OK;
+}
+
 extern "C" int ac_get_step(const ac_handle *h, unsigned long long *step, int *next_substep) {
     if (!h) return AC_ERR_ARG;
     if (step) *step = h->step;
@@ -510,6 +537,18 @@ extern "C" int ac_integrate_substep(ac_handle *h, double dt, int s) {
     L.beta = RK_BETA[s];
     L.dt = dt;
     L.s = s;
+    L.use_fx = h->stencil_mode != AC_STENCIL_FP64 && fx_applicable(h);
+    L.dx = h->grid.lx / h->grid.nx;
+    L.fx_gmax = nullptr;
+    for (int q = 0; q < NF; ++q) L.fxF[q] = nullptr;
+    if (L.use_fx) {
+        if (!h->fx_block) {
+            CK(cudaMalloc(&h->fx_block, (size_t)NF * h->g.elems * sizeof(long long)));
+            CK(cudaMalloc(&h->fx_gmax, 4 * sizeof(unsigned long long)));
+        }
+        for (int q = 0; q < NF; ++q) L.fxF[q] = h->fx_block + (size_t)q * h->g.elems;
+        L.fx_gmax = h->fx_gmax;
+    }
     L.cfl_max = nullptr;
     if (s == 0) {  // the step's input state: record its max CFL speed on the way
         CK(cudaMemsetAsync(h->cfl_dev, 0, sizeof(unsigned long long), h->stream));

@@ -81,6 +81,12 @@ struct SubstepLaunch {
     double alpha, beta, dt;
     int s;
     unsigned long long *cfl_max;  // substep 0: device word for the max CFL speed (or NULL)
+    // binary64 with integer stencil sums (cubic periodic grids): int64 copies of
+    // the fields and four group-max words; use_fx = 0 selects plain binary64 sums.
+    int use_fx;
+    long long *fxF[NF];
+    unsigned long long *fx_gmax;
+    double dx;
 };
 
 cudaError_t launch_substep(const SubstepLaunch &L, cudaStream_t st, int *launches);

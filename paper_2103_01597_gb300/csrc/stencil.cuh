@@ -200,6 +200,66 @@ template <> __device__ __forceinline__ float dev_exp<float>(float x) { return ex
 
 // RHS of Eqs. B.1-B.4 at one cell (mu0 = 1, zeta = H = C = K = 0), with the
 // forcing term `frc` added to du/dt.  Output order: Table B.1.
+// Eqs. B.1-B.4 at one cell given the centre values and the derivative terms:
+// gl, gs, gu[m][a] first derivatives of ln rho, s, u_m; B = curl A; viscl =
+// nu (lap u + grad(div u) / 3); lapa = lap A; J = grad(div A) - lap A (mu0 = 1).
+template <typename R>
+__device__ __forceinline__ void cell_physics(R lnrho, const R (&u)[3], R ss, const R (&gl)[3],
+                                             const R (&gs)[3], const R (&gu)[3][3],
+                                             const R (&B)[3], const R (&viscl)[3],
+                                             const R (&lapa)[3], const R (&J)[3],
+                                             const DevCoefs<R> &k, const R frc[3], R out[NF],
+                                             R *cfl) {
+    // Thermodynamics: c_s^2 = c_s0^2 exp(gamma s / c_p + (gamma-1)(ln rho - ln rho0)),
+    // 1/rho = exp(-ln rho), 1/T = c_p (gamma - 1) / c_s^2.
+    const R rho_inv = dev_exp<R>(-lnrho);
+    const R cs2 = k.cs2_ref * dev_exp<R>(k.gamma_cp * ss + k.gm1 * lnrho);
+    const R inv_T = k.cp_gm1 / cs2;
+
+    const R divu = gu[0][0] + gu[1][1] + gu[2][2];
+    const R third_div = divu * (R)(1.0 / 3.0);
+
+
+    // Traceless rate of strain S.
+    const R Sxx = gu[0][0] - third_div, Syy = gu[1][1] - third_div, Szz = gu[2][2] - third_div;
+    const R Sxy = (R)0.5 * (gu[0][1] + gu[1][0]);
+    const R Sxz = (R)0.5 * (gu[0][2] + gu[2][0]);
+    const R Syz = (R)0.5 * (gu[1][2] + gu[2][1]);
+    const R SS2 = Sxx * Sxx + Syy * Syy + Szz * Szz + (R)2 * (Sxy * Sxy + Sxz * Sxz + Syz * Syz);
+    const R SG[3] = {Sxx * gl[0] + Sxy * gl[1] + Sxz * gl[2],
+                     Sxy * gl[0] + Syy * gl[1] + Syz * gl[2],
+                     Sxz * gl[0] + Syz * gl[1] + Szz * gl[2]};
+
+    const R JxB[3] = {J[1] * B[2] - J[2] * B[1], J[2] * B[0] - J[0] * B[2],
+                      J[0] * B[1] - J[1] * B[0]};
+    const R UxB[3] = {u[1] * B[2] - u[2] * B[1], u[2] * B[0] - u[0] * B[2],
+                      u[0] * B[1] - u[1] * B[0]};
+    const R J2 = J[0] * J[0] + J[1] * J[1] + J[2] * J[2];
+
+    // Eq. B.1
+    out[0] = -(u[0] * gl[0] + u[1] * gl[1] + u[2] * gl[2]) - divu;
+    // Eq. B.2
+#pragma unroll
+    for (int m = 0; m < 3; ++m) {
+        const R adv = u[0] * gu[m][0] + u[1] * gu[m][1] + u[2] * gu[m][2];
+        const R press = cs2 * (gs[m] * k.inv_cp + gl[m]);
+        const R visc = viscl[m] + k.two_nu * SG[m];
+        out[1 + m] = (visc - adv) - press + JxB[m] * rho_inv + frc[m];
+    }
+    // Eq. B.3: Ds/Dt = (eta j^2 + 2 rho nu S:S) / (rho T)
+    out[4] = -(u[0] * gs[0] + u[1] * gs[1] + u[2] * gs[2])
+           + (k.eta * J2 * rho_inv + k.two_nu * SS2) * inv_T;
+    // Eq. B.4
+#pragma unroll
+    for (int m = 0; m < 3; ++m) out[5 + m] = UxB[m] + k.eta * lapa[m];
+    if (cfl) {
+        const R b2 = B[0] * B[0] + B[1] * B[1] + B[2] * B[2];
+        const R u2 = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+        *cfl = sqrt(u2) + sqrt(cs2 + b2 * rho_inv);
+    }
+}
+
+
 // `f` is a cell accessor: f[q] is the view of field q around the cell.  With
 // `cfl` non-null, the fastest signal speed of the input state at the cell,
 // |u| + sqrt(c_s^2 + |B|^2 / rho) (mu0 = 1), is written there as well.
@@ -262,56 +322,13 @@ __device__ __forceinline__ void cell_rhs(const CELL &f, const DevCoefs<R> &k, co
         gda[2] += dcc;
     }
 
-    // Thermodynamics: c_s^2 = c_s0^2 exp(gamma s / c_p + (gamma-1)(ln rho - ln rho0)),
-    // 1/rho = exp(-ln rho), 1/T = c_p (gamma - 1) / c_s^2.
-    const R rho_inv = dev_exp<R>(-lnrho);
-    const R cs2 = k.cs2_ref * dev_exp<R>(k.gamma_cp * ss + k.gm1 * lnrho);
-    const R inv_T = k.cp_gm1 / cs2;
-
-    const R divu = gu[0][0] + gu[1][1] + gu[2][2];
-    const R third_div = divu * (R)(1.0 / 3.0);
-
-    // B = curl A, j = grad(div A) - lap A.
+    // B = curl A, j = grad(div A) - lap A, nu (lap u + grad(div u) / 3).
     const R B[3] = {ga[2][1] - ga[1][2], ga[0][2] - ga[2][0], ga[1][0] - ga[0][1]};
     const R J[3] = {gda[0] - lapa[0], gda[1] - lapa[1], gda[2] - lapa[2]};
-
-    // Traceless rate of strain S.
-    const R Sxx = gu[0][0] - third_div, Syy = gu[1][1] - third_div, Szz = gu[2][2] - third_div;
-    const R Sxy = (R)0.5 * (gu[0][1] + gu[1][0]);
-    const R Sxz = (R)0.5 * (gu[0][2] + gu[2][0]);
-    const R Syz = (R)0.5 * (gu[1][2] + gu[2][1]);
-    const R SS2 = Sxx * Sxx + Syy * Syy + Szz * Szz + (R)2 * (Sxy * Sxy + Sxz * Sxz + Syz * Syz);
-    const R SG[3] = {Sxx * gl[0] + Sxy * gl[1] + Sxz * gl[2],
-                     Sxy * gl[0] + Syy * gl[1] + Syz * gl[2],
-                     Sxz * gl[0] + Syz * gl[1] + Szz * gl[2]};
-
-    const R JxB[3] = {J[1] * B[2] - J[2] * B[1], J[2] * B[0] - J[0] * B[2],
-                      J[0] * B[1] - J[1] * B[0]};
-    const R UxB[3] = {u[1] * B[2] - u[2] * B[1], u[2] * B[0] - u[0] * B[2],
-                      u[0] * B[1] - u[1] * B[0]};
-    const R J2 = J[0] * J[0] + J[1] * J[1] + J[2] * J[2];
-
-    // Eq. B.1
-    out[0] = -(u[0] * gl[0] + u[1] * gl[1] + u[2] * gl[2]) - divu;
-    // Eq. B.2
+    R viscl[3];
 #pragma unroll
-    for (int m = 0; m < 3; ++m) {
-        const R adv = u[0] * gu[m][0] + u[1] * gu[m][1] + u[2] * gu[m][2];
-        const R press = cs2 * (gs[m] * k.inv_cp + gl[m]);
-        const R visc = k.nu * lapu[m] + k.nu3 * gdu[m] + k.two_nu * SG[m];
-        out[1 + m] = (visc - adv) - press + JxB[m] * rho_inv + frc[m];
-    }
-    // Eq. B.3: Ds/Dt = (eta j^2 + 2 rho nu S:S) / (rho T)
-    out[4] = -(u[0] * gs[0] + u[1] * gs[1] + u[2] * gs[2])
-           + (k.eta * J2 * rho_inv + k.two_nu * SS2) * inv_T;
-    // Eq. B.4
-#pragma unroll
-    for (int m = 0; m < 3; ++m) out[5 + m] = UxB[m] + k.eta * lapa[m];
-    if (cfl) {
-        const R b2 = B[0] * B[0] + B[1] * B[1] + B[2] * B[2];
-        const R u2 = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
-        *cfl = sqrt(u2) + sqrt(cs2 + b2 * rho_inv);
-    }
+    for (int m = 0; m < 3; ++m) viscl[m] = k.nu * lapu[m] + k.nu3 * gdu[m];
+    cell_physics<R>(lnrho, u, ss, gl, gs, gu, B, viscl, lapa, J, k, frc, out, cfl);
 }
 
 // Block-wide max of a non-negative value folded into a global 64-bit word that

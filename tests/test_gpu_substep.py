@@ -78,6 +78,62 @@ def test_fp64_substeps_match_oracle(n, layout):
     sim.close()
 
 
+CUBIC = [(8, 8, 8), (16, 12, 20), (37, 21, 13), (1, 12, 10), (64, 64, 64)]
+
+
+@pytest.mark.parametrize("mode", [ac.AC_STENCIL_FIXED, ac.AC_STENCIL_FP64])
+@pytest.mark.parametrize("n", CUBIC)
+def test_fp64_equal_spacing_substeps_match_oracle(n, mode):
+    """Equal spacing on every axis: the integer stencil sums apply (FIXED) and must
+    meet the same 1e-12 bar as plain binary64 sums (FP64), every substep."""
+    h = 0.3
+    L = tuple(h * v for v in n)
+    phys = dict(nu=2e-2, eta=3e-2, cs0=1.1, gamma=1.4, cp=1.3, lnrho0=0.2)
+    sim = _sim(n, L=L, force_amp=0.05, seed=2, **phys)
+    ac.ac_set_stencil_mode(sim.h, mode)
+    assert ac.ac_get_stencil_path(sim.h) == (mode == ac.AC_STENCIL_FIXED)
+    f = _state(n, seed=sum(n) + 7)
+    f[1:4] *= 3.0  # u and A with unequal magnitudes within their group
+    f[7] *= 1e-3
+    sim.load(f)
+    dt = 1e-3
+    w = None
+    for s in range(3):
+        k, e, phi = ac.ac_forcing_draw(2, 0)
+        p = _oracle_params(n, L=L, forcing=core.Forcing(k, e, phi, 0.05), **phys)
+        fo, wo = core.substep(f, w, p, dt, s)
+        sim.substep(dt, s)
+        fg, wg = sim.store(), sim.store_w()
+        assert np.all(rel_err(fg, fo) <= 1e-12), (s, rel_err(fg, fo))
+        assert np.all(rel_err(wg, wo) <= 1e-12), (s, rel_err(wg, wo))
+        f, w = fg, wg
+    sim.close()
+
+
+def test_fixed_path_rejected_where_it_does_not_apply():
+    sim = _sim((8, 8, 8), L=(1.0, 2.0, 1.0))
+    with pytest.raises(ac.AcError):
+        ac.ac_set_stencil_mode(sim.h, ac.AC_STENCIL_FIXED)
+    assert not ac.ac_get_stencil_path(sim.h)
+    sim.close()
+
+
+def test_shift_equivariance_fixed_path_bitwise():
+    n = (24, 24, 24)
+    f = _state(n, seed=14)
+    shift = (5, 7, 3)
+    out = []
+    for sh in [(0, 0, 0), shift]:
+        sim = _sim(n)
+        assert ac.ac_get_stencil_path(sim.h)
+        sim.load(np.roll(f, shift=(sh[2], sh[1], sh[0]), axis=(1, 2, 3)))
+        sim.step(2e-3)
+        out.append(sim.store())
+        sim.close()
+    assert np.array_equal(np.roll(out[0], shift=(shift[2], shift[1], shift[0]), axis=(1, 2, 3)),
+                          out[1])
+
+
 def test_fp64_step_config_32cube():
     """One full step of the 32^3 configuration: noise of amplitude 1e-5 on u and
     A, ln rho = s = 0, dt = 1e-3 (seeded)."""
