@@ -173,9 +173,10 @@ int ac_integrate_substep(ac_handle *h, double dt, int s);
  * integer sums whenever they apply (binary64 fields, periodic layout, equal
  * spacing dx = dy = dz), plain binary64 sums otherwise.  With integer sums each
  * field group (ln rho; u; s; A) is first written as int64 fixed point with one
- * power-of-two scale per group (|F| <= 2^44, resolution 2^-45 of the group's
- * largest |f|); every stencil numerator and every sum of numerators with a
- * common coefficient is then exact and only one int64 -> binary64 conversion
+ * power-of-two scale per group (|F| <= 2^50, resolution 2^-51 of the group's
+ * largest |f|, i.e. four binary64 units in the last place at that magnitude);
+ * every stencil numerator and every sum of numerators with a common
+ * coefficient is then exact and only one int64 -> binary64 conversion
  * and one multiplication per derivative term run on the FP64 pipe.  The result
  * stays within the same 1e-12 relative bound of the exact-rounding definition.
  * AC_STENCIL_FP64: binary64 arithmetic throughout.  AC_STENCIL_FIXED: integer

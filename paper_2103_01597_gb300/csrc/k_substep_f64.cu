@@ -32,6 +32,7 @@ cudaError_t launch_substep_f64(const SubstepLaunch &L, cudaStream_t st, int *lau
     a.cfl_max = L.cfl_max;
     FxCoefs fc;
     fc.inv60dx = 1.0 / (60.0 * L.dx);
+    fc.nu180 = L.ph.nu / (180.0 * L.dx * L.dx);
     fc.nu2160 = L.ph.nu / (2160.0 * L.dx * L.dx);
     fc.inv180dx2 = 1.0 / (180.0 * L.dx * L.dx);
     fc.inv720dx2 = 1.0 / (720.0 * L.dx * L.dx);

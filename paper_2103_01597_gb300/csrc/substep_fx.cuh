@@ -4,16 +4,15 @@
 // bound by its FP64 instruction count, most of which (about 400 of 600 per
 // cell) are the additions and multiplications of the 54 stencils of Eq. 13.
 // Here each field group (ln rho; u; s; A) is first written as int64 fixed
-// point with one power-of-two scale per group, F = round(f 2^(44 - e)) with
-// max |f| < 2^e, so |F| <= 2^44.  Every stencil numerator -- and every sum of
-// numerators that share a coefficient (curl A, lap u + grad(div u) / 3,
-// lap A, grad(div A) - lap A) -- is then an exact integer on the integer
-// pipes (|numerator| < 2^60), and only one int64 -> binary64 conversion and
-// one multiplication per derivative term remain on the FP64 pipe.  The
-// quantisation error, 2^-45 of the group's largest magnitude, is below the
-// rounding of the binary64 stencil sums it replaces by about a factor of
-// four; the centre values used by the physics and the Runge-Kutta update are
-// the binary64 state itself.  The physics of Eqs. B.1-B.4 is unchanged
+// point with one power-of-two scale per group, F = round(f 2^(50 - e)) with
+// max |f| < 2^e, so |F| <= 2^50.  Every stencil numerator -- and every sum of
+// numerators that share a coefficient (curl A, lap u, grad(div u), lap A,
+// grad(div A)) -- is then an exact integer on the integer pipes (largest:
+// 6744 |F| < 2^63), and only one int64 -> binary64 conversion and one
+// multiplication per derivative term remain on the FP64 pipe.  The
+// quantisation step, 2^-50 of the group's largest magnitude, is four binary64
+// units in the last place at that magnitude; the centre values used by the
+// physics and the Runge-Kutta update are the binary64 state itself.  The physics of Eqs. B.1-B.4 is unchanged
 // binary64 code (cell_physics).
 #pragma once
 
@@ -21,7 +20,7 @@
 
 namespace ac {
 
-constexpr int FX_BITS = 44;
+constexpr int FX_BITS = 50;
 
 // Field -> group: 0 = ln rho, 1 = u, 2 = s, 3 = A.
 __host__ __device__ __forceinline__ int fx_group(int q) {
@@ -70,7 +69,7 @@ __global__ void fx_max_kernel(FxPtrs p, long long n, unsigned long long *gmax) {
     }
 }
 
-// F = round(f 2^(44 - e)) by integer operations on the binary64 bits (round
+// F = round(f 2^(50 - e)) by integer operations on the binary64 bits (round
 // half up in magnitude); values below the resolution become 0.
 __global__ void fx_quantize_kernel(FxPtrs p, long long n, const unsigned long long *gmax) {
     int e[4];
@@ -84,7 +83,7 @@ __global__ void fx_quantize_kernel(FxPtrs p, long long n, const unsigned long lo
             const int eb = (int)((b >> 52) & 0x7ff);
             long long v = 0;
             if (eb != 0 && eb != 0x7ff) {
-                const int sh = 1031 + e[fx_group(q)] - eb;  // right shift of the 53-bit significand
+                const int sh = 1075 - FX_BITS + e[fx_group(q)] - eb;  // right shift of the significand
                 if (sh > 0 && sh < 62) {
                     const long long mant = (b & 0xfffffffffffffll) | 0x10000000000000ll;
                     v = (mant + (1ll << (sh - 1))) >> sh;
@@ -134,13 +133,14 @@ __device__ __forceinline__ long long ndab(const V &F) {
     return 270 * S[0] - 27 * S[1] + 2 * S[2];
 }
 
-// Coefficients of the converted numerators; the group scales 2^(e - 44) are
+// Coefficients of the converted numerators; the group scales 2^(e - FX_BITS) are
 // read from the max words on the device.
 struct FxCoefs {
-    double inv60dx;    // 1 / (60 dx)
-    double nu2160;     // nu / (2160 dx^2): nu (lap u + grad(div u) / 3)
+    double inv60dx;    // 1 / (60 dx): first derivatives
+    double nu180;      // nu / (180 dx^2): nu lap u
+    double nu2160;     // nu / (2160 dx^2): nu grad(div u) / 3
     double inv180dx2;  // 1 / (180 dx^2): lap A
-    double inv720dx2;  // 1 / (720 dx^2): grad(div A) - lap A
+    double inv720dx2;  // 1 / (720 dx^2): grad(div A)
 };
 
 template <class IX, bool CFL>
@@ -157,9 +157,10 @@ __global__ void __launch_bounds__(128) substep_fx_kernel(const SubstepArgs<doubl
         for (int gq = 0; gq < 4; ++gq) sc[gq] = fx_pow2(fx_exponent(gmax[gq]) - FX_BITS);
         const double c1[4] = {sc[0] * fc.inv60dx, sc[1] * fc.inv60dx, sc[2] * fc.inv60dx,
                               sc[3] * fc.inv60dx};
-        const double cvisc = sc[1] * fc.nu2160;
-        const double clap = sc[3] * fc.inv180dx2;
-        const double cj = sc[3] * fc.inv720dx2;
+        const double clu = sc[1] * fc.nu180;
+        const double cgu = sc[1] * fc.nu2160;
+        const double cla = sc[3] * fc.inv180dx2;
+        const double cga = sc[3] * fc.inv720dx2;
         const int k0 = blockIdx.z * a.zchunk;
         const int k1 = min(k0 + a.zchunk, a.g.nz);
         IX ix;
@@ -201,63 +202,65 @@ __global__ void __launch_bounds__(128) substep_fx_kernel(const SubstepArgs<doubl
             B[0] = (double)(nd1<1>(Fa[2]) - nd1<2>(Fa[1])) * c1[3];
             B[1] = (double)(nd1<2>(Fa[0]) - nd1<0>(Fa[2])) * c1[3];
             B[2] = (double)(nd1<0>(Fa[1]) - nd1<1>(Fa[0])) * c1[3];
-            // nu (lap u_i + grad(div u)_i / 3) = nu / (2160 dx^2) x
-            //   [16 N2_ii(u_i) + 12 N2_jj(u_i) + 12 N2_kk(u_i) + NX_ij(u_j) + NX_ik(u_k)]
-            long long V[3];
+            // lap u_i = sum_a N2_aa(u_i) / (180 dx^2);
+            // grad(div u)_i = [4 N2_ii(u_i) + NX_ij(u_j) + NX_ik(u_k)] / (720 dx^2)
+            long long LU[3], GU[3];
             {
                 const long long c0 = Fu[0](0, 0, 0);
                 const long long xx = nd2<0>(Fu[0], c0), yy = nd2<1>(Fu[0], c0), zz = nd2<2>(Fu[0], c0);
-                V[0] = 16 * xx + 12 * yy + 12 * zz;
-                V[1] = ndab<0, 1>(Fu[0]);
-                V[2] = ndab<0, 2>(Fu[0]);
+                LU[0] = xx + yy + zz;
+                GU[0] = 4 * xx;
+                GU[1] = ndab<0, 1>(Fu[0]);
+                GU[2] = ndab<0, 2>(Fu[0]);
             }
             {
                 const long long c0 = Fu[1](0, 0, 0);
                 const long long xx = nd2<0>(Fu[1], c0), yy = nd2<1>(Fu[1], c0), zz = nd2<2>(Fu[1], c0);
-                V[1] += 12 * xx + 16 * yy + 12 * zz;
-                V[0] += ndab<0, 1>(Fu[1]);
-                V[2] += ndab<1, 2>(Fu[1]);
+                LU[1] = xx + yy + zz;
+                GU[1] += 4 * yy;
+                GU[0] += ndab<0, 1>(Fu[1]);
+                GU[2] += ndab<1, 2>(Fu[1]);
             }
             {
                 const long long c0 = Fu[2](0, 0, 0);
                 const long long xx = nd2<0>(Fu[2], c0), yy = nd2<1>(Fu[2], c0), zz = nd2<2>(Fu[2], c0);
-                V[2] += 12 * xx + 12 * yy + 16 * zz;
-                V[0] += ndab<0, 2>(Fu[2]);
-                V[1] += ndab<1, 2>(Fu[2]);
+                LU[2] = xx + yy + zz;
+                GU[2] += 4 * zz;
+                GU[0] += ndab<0, 2>(Fu[2]);
+                GU[1] += ndab<1, 2>(Fu[2]);
             }
-            // lap A_i = sum_a N2_aa(A_i) / (180 dx^2);
-            // j_i = [NX_ij(A_j) + NX_ik(A_k) - 4 N2_jj(A_i) - 4 N2_kk(A_i)] / (720 dx^2)
-            long long LA[3], JN[3];
+            // the same two sums for A; j = grad(div A) - lap A
+            long long LA[3], GA[3];
             {
                 const long long c0 = Fa[0](0, 0, 0);
                 const long long xx = nd2<0>(Fa[0], c0), yy = nd2<1>(Fa[0], c0), zz = nd2<2>(Fa[0], c0);
                 LA[0] = xx + yy + zz;
-                JN[0] = -4 * (yy + zz);
-                JN[1] = ndab<0, 1>(Fa[0]);
-                JN[2] = ndab<0, 2>(Fa[0]);
+                GA[0] = 4 * xx;
+                GA[1] = ndab<0, 1>(Fa[0]);
+                GA[2] = ndab<0, 2>(Fa[0]);
             }
             {
                 const long long c0 = Fa[1](0, 0, 0);
                 const long long xx = nd2<0>(Fa[1], c0), yy = nd2<1>(Fa[1], c0), zz = nd2<2>(Fa[1], c0);
                 LA[1] = xx + yy + zz;
-                JN[1] += -4 * (xx + zz);
-                JN[0] += ndab<0, 1>(Fa[1]);
-                JN[2] += ndab<1, 2>(Fa[1]);
+                GA[1] += 4 * yy;
+                GA[0] += ndab<0, 1>(Fa[1]);
+                GA[2] += ndab<1, 2>(Fa[1]);
             }
             {
                 const long long c0 = Fa[2](0, 0, 0);
                 const long long xx = nd2<0>(Fa[2], c0), yy = nd2<1>(Fa[2], c0), zz = nd2<2>(Fa[2], c0);
                 LA[2] = xx + yy + zz;
-                JN[2] += -4 * (xx + yy);
-                JN[0] += ndab<0, 2>(Fa[2]);
-                JN[1] += ndab<1, 2>(Fa[2]);
+                GA[2] += 4 * zz;
+                GA[0] += ndab<0, 2>(Fa[2]);
+                GA[1] += ndab<1, 2>(Fa[2]);
             }
             double viscl[3], lapa[3], J[3];
 #pragma unroll
             for (int m = 0; m < 3; ++m) {
-                viscl[m] = (double)V[m] * cvisc;
-                lapa[m] = (double)LA[m] * clap;
-                J[m] = (double)JN[m] * cj;
+                viscl[m] = (double)LU[m] * clu + (double)GU[m] * cgu;
+                lapa[m] = (double)LA[m] * cla;
+                J[m] = (double)GA[m] * cga - lapa[m];
             }
             // centre values: the binary64 state
             const double lnrho = ldg(a.fin[0] + o);
