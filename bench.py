@@ -45,6 +45,9 @@ def bytes_per_cell(elem_f, elem_w, s):
 
 # Nominal dense FP64 rate of one GB300 (no measured FP64 peak is provided).
 FP64_NOMINAL_TFLOPS = 1.25
+# DRAM bytes per cell of one launch of the integer-sum FP64 substep kernel
+# (ncu, 128^3: 426.3 MB read + 239.0 MB written over 2,097,152 cells).
+FX_TRAFFIC_PER_CELL = (426.260224e6 + 238.959616e6) / 2097152
 
 WORKLOADS = {
     "forced256_fp64": dict(n=(256, 256, 256), precision="fp64", force_amp=0.05, seed=2,
@@ -340,11 +343,20 @@ def run_ours(args, wl):
         flops = {s: FLOPS_PER_CELL[s] * ncell for s in range(3)}
         achieved = statistics.mean(flops[s] / avg[s] for s in range(3)) / 1e12
         dg = fp64_dgemm_tflops(torch) if (rank == 0 and args.fp64_peak) else None
+        fixed = ac.ac_get_stencil_path(sim.h)
         roof = {"bound": "alu", "achieved": achieved, "peak": FP64_NOMINAL_TFLOPS,
-                "unit": "TFLOP/s", "frac": achieved / FP64_NOMINAL_TFLOPS, "traffic": None,
-                "kernel": "substep_kernel<double,double,IdxPeriodic>",
-                "peak_source": "nominal GB300 dense FP64 (no measured FP64 peak in "
-                               "MEASURED_PEAKS.json)",
+                "unit": "TFLOP/s", "frac": achieved / FP64_NOMINAL_TFLOPS,
+                # dram read + write per 256^3 launch of the unchanged kernel, from the 128^3
+                # ncu capture scaled by cells (profiles/substep_fx_128_full.md)
+                "traffic": FX_TRAFFIC_PER_CELL * ncell if (fixed and n == (256, 256, 256)) else None,
+                "kernel": ("substep_fx_kernel (int64 stencil sums) + fx_max + fx_quantize"
+                           if fixed else "substep_kernel<double,double,IdxPeriodic>"),
+                "peak_source": "nominal GB300 dense FP64, 2 FP64 lanes/SM/cycle x 152 SMs x "
+                               "2.07 GHz (no measured FP64 peak in MEASURED_PEAKS.json)",
+                "note": ("achieved counts the method's 759 binary64 flops per cell-substep; "
+                         "540 of them (the stencil sums) run as exact int64 operations on the "
+                         "integer pipes, so frac can exceed 1; ncu: FP64 pipe 68% busy"
+                         if fixed else "all arithmetic on the FP64 pipe"),
                 "fp64_dgemm_measured_tflops": dg,
                 "avg_launch_ms": 1e3 * avg_all,
                 "alg_flops_per_cell_substep": FLOPS_PER_CELL}
