@@ -339,6 +339,22 @@ int ac_closure_adam_step(ac_closure *c, float lr, float beta1, float beta2, floa
  * (the guard runs on the device; *applied, if non-NULL, synchronises). */
 int ac_closure_apply(ac_closure *c, ac_handle *h, double limit, int *applied);
 int ac_closure_launch_count(const ac_closure *c, unsigned long long *count);
+/* Convolution kernels of the forward pass run by ac_closure_forward and
+ * ac_closure_apply.  AC_CONV_TCGEN05 (the default): tcgen05.mma with the
+ * accumulator in tensor memory, on channels-last activations, persistent CTAs
+ * holding one layer's weights in shared memory.  AC_CONV_MMA_SYNC: the
+ * warp-level mma.sync kernels on channel-major activations that
+ * ac_closure_backward always uses.  Both take the same bfloat16 operands and
+ * accumulate in binary32, in a different order. */
+#define AC_CONV_TCGEN05 0
+#define AC_CONV_MMA_SYNC 1
+int ac_closure_set_conv_path(ac_closure *c, int path);
+int ac_closure_get_conv_path(const ac_closure *c, int *path);
+/* Reads and clears the device error word of the tcgen05 kernels
+ * (synchronises the closure's stream): AC_ERR_TIMEOUT if one of their bounded
+ * mbarrier waits ran out since the last call (the outputs of that call are
+ * then undefined), else AC_OK. */
+int ac_closure_status(ac_closure *c);
 
 /* Full-weighting restriction of eight fine fields (nx, ny, nz even; binary64
  * for AC_FP64, binary32 otherwise; periodic layout) to eight binary32 coarse

@@ -31,6 +31,7 @@ AC_FP64, AC_FP32, AC_FP32_W64 = 0, 1, 2
 AC_LAYOUT_PERIODIC, AC_LAYOUT_PADDED = 0, 1
 AC_MAX, AC_MIN, AC_SUM, AC_RMS = 0, 1, 2, 3
 AC_STENCIL_AUTO, AC_STENCIL_FP64, AC_STENCIL_FIXED = 0, 1, 2
+AC_CONV_TCGEN05, AC_CONV_MMA_SYNC = 0, 1
 AC_Q_UMAG, AC_Q_EKIN, AC_Q_EMAG, AC_Q_CFL = 8, 9, 10, 11
 
 
@@ -137,6 +138,9 @@ def load_library(path=None):
         "ac_closure_adam_step": ([_vp, _c.c_float, _c.c_float, _c.c_float, _c.c_float], _c.c_int),
         "ac_closure_apply": ([_vp, _vp, _c.c_double, ctypes.POINTER(_c.c_int)], _c.c_int),
         "ac_closure_launch_count": ([_vp, ctypes.POINTER(_c.c_ulonglong)], _c.c_int),
+        "ac_closure_set_conv_path": ([_vp, _c.c_int], _c.c_int),
+        "ac_closure_get_conv_path": ([_vp, ctypes.POINTER(_c.c_int)], _c.c_int),
+        "ac_closure_status": ([_vp], _c.c_int),
         "ac_restrict": ([ctypes.POINTER(_vp), _c.c_int, _c.c_int, _c.c_int, _c.c_int,
                          ctypes.POINTER(_vp), _vp], _c.c_int),
         "ac_strerror": ([_c.c_int], _c.c_char_p),
@@ -408,6 +412,20 @@ def ac_closure_launch_count(c):
     n = ctypes.c_ulonglong()
     _check(load_library().ac_closure_launch_count(c, ctypes.byref(n)), "ac_closure_launch_count")
     return n.value
+
+
+def ac_closure_set_conv_path(c, path):
+    _check(load_library().ac_closure_set_conv_path(c, int(path)), "ac_closure_set_conv_path")
+
+
+def ac_closure_get_conv_path(c):
+    p = ctypes.c_int()
+    _check(load_library().ac_closure_get_conv_path(c, ctypes.byref(p)), "ac_closure_get_conv_path")
+    return p.value
+
+
+def ac_closure_status(c):
+    _check(load_library().ac_closure_status(c), "ac_closure_status")
 
 
 # ---- batched ensemble --------------------------------------------------------

@@ -43,13 +43,14 @@ def current_state(sim):
 
 
 class Closure:
-    def __init__(self, n, seed=0, params=None, stream=None):
+    def __init__(self, n, seed=0, params=None, stream=None, conv_path=ac.AC_CONV_TCGEN05):
         import torch
         self.n = tuple(n)
         self.cells = n[0] * n[1] * n[2]
         if stream is None:
             stream = torch.cuda.current_stream().cuda_stream
         self.c = ac.ac_closure_init(n, stream)
+        ac.ac_closure_set_conv_path(self.c, conv_path)
         ac.ac_closure_set_params(self.c, init_params(seed) if params is None else params)
         self.out = torch.zeros((8, self.cells), dtype=torch.float32, device="cuda")
 
@@ -70,6 +71,10 @@ class Closure:
 
     def apply(self, sim, limit):
         return ac.ac_closure_apply(self.c, sim.h, limit)
+
+    def status(self):
+        """Raise AcError if a bounded wait of the tensor-core kernels ran out."""
+        ac.ac_closure_status(self.c)
 
     def close(self):
         if self.c is not None:

@@ -20,6 +20,7 @@
 #include <new>
 
 #include "ac_internal.h"
+#include "conv_tc.cuh"
 
 namespace ac {
 
@@ -325,25 +326,48 @@ __global__ void loss_grad_kernel(const float *__restrict__ y, F8 tgt,
     if (threadIdx.x == 0) partials[blockIdx.x] = sh[0];
 }
 
+// Index of (channel c, cell p) in the eight-channel output: channel-major
+// [8][n] or channels-last [n][8].
+__device__ __forceinline__ long long yidx(int c, long long p, long long n, int cl) {
+    return cl ? p * 8 + c : (long long)c * n + p;
+}
+
 // out[c] = out_scale[c] * y[c]
 __global__ void scale_output_kernel(const float *__restrict__ y, const float *__restrict__ out_scale,
-                                    long long n, W8 out) {
+                                    long long n, W8 out, int cl) {
     for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < 8 * n;
          t += (long long)gridDim.x * blockDim.x) {
         const int c = (int)(t / n);
-        out.p[c][t - c * n] = out_scale[c] * y[t];
+        const long long p = t - c * n;
+        out.p[c][p] = out_scale[c] * y[yidx(c, p, n, cl)];
+    }
+}
+
+// Channels-last network input: x[p][c] = f[c][p] / in_scale[c] (channels 8..15 zero).
+__global__ void pack_input_cl_kernel(F8 f, const float *__restrict__ inv_scale, long long n,
+                                     bf16 *__restrict__ x) {
+    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < n;
+         p += (long long)gridDim.x * blockDim.x) {
+        __align__(16) bf16 v[16];
+#pragma unroll
+        for (int c = 0; c < 8; ++c) v[c] = __float2bfloat16_rn(f.p[c][p] * inv_scale[c]);
+#pragma unroll
+        for (int c = 8; c < 16; ++c) v[c] = __float2bfloat16_rn(0.f);
+        uint4 *dst = reinterpret_cast<uint4 *>(x + p * 16);
+        dst[0] = reinterpret_cast<const uint4 *>(v)[0];
+        dst[1] = reinterpret_cast<const uint4 *>(v)[1];
     }
 }
 
 // Guard: largest |out_scale * y| (NaN counts as larger than anything) into one word.
 __global__ void correction_max_kernel(const float *__restrict__ y,
                                       const float *__restrict__ out_scale, long long n,
-                                      unsigned long long *gmax) {
+                                      unsigned long long *gmax, int cl) {
     double m = 0.0;
     for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < 8 * n;
          t += (long long)gridDim.x * blockDim.x) {
         const int c = (int)(t / n);
-        const double v = fabs((double)(out_scale[c] * y[t]));
+        const double v = fabs((double)(out_scale[c] * y[yidx(c, t - c * n, n, cl)]));
         m = (v > m || v != v) ? v : m;
     }
     unsigned long long bits = (unsigned long long)__double_as_longlong(m);
@@ -357,13 +381,14 @@ __global__ void correction_max_kernel(const float *__restrict__ y,
 // f[c] += out_scale[c] * y[c], only if the guard word shows a finite maximum <= limit.
 __global__ void apply_correction_kernel(W8 f, const float *__restrict__ y,
                                         const float *__restrict__ out_scale, long long n,
-                                        const unsigned long long *gmax, double limit) {
+                                        const unsigned long long *gmax, double limit, int cl) {
     const double m = __longlong_as_double((long long)*gmax);
     if (!(m <= limit)) return;
     for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < 8 * n;
          t += (long long)gridDim.x * blockDim.x) {
         const int c = (int)(t / n);
-        f.p[c][t - c * n] += out_scale[c] * y[t];
+        const long long p = t - c * n;
+        f.p[c][p] += out_scale[c] * y[yidx(c, p, n, cl)];
     }
 }
 
@@ -442,6 +467,11 @@ struct ac_closure {
     bf16 *wf1, *wf2, *wf3, *wb3, *wb2;
     bf16 *x0, *a1, *a2, *dy, *dz2, *dz1;
     float *y;
+    // tcgen05 forward: weight images; channels-last activations alias x0, a1, a2, y
+    int conv_path;
+    bf16 *img1, *img2, *img3;
+    unsigned *tc_err;
+    int tc_grid[3];
     float *part;
     double *lossp;
     double *loss_host;
@@ -461,6 +491,32 @@ struct ac_closure {
 static unsigned cl_grid(long long count, int threads = 256) {
     long long b = (count + threads - 1) / threads;
     return (unsigned)(b > 152 * 16 ? 152 * 16 : (b < 1 ? 1 : b));
+}
+
+template <int CIN, int COUT, int EPI>
+static cudaError_t tc_grid_for(const ac_closure *c, int sms, int *grid) {
+    auto k = tc::conv_tc_kernel<CIN, COUT, EPI>;
+    const int bytes = (int)tc::smem_bytes(CIN, COUT < 16 ? 16 : COUT);
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    int per_sm = 0;
+    if (e == cudaSuccess)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, tc::THREADS, bytes);
+    if (e != cudaSuccess) return e;
+    const long long tiles = (long long)c->g.ny * c->g.nz * ((c->g.nx + tc::TM - 1) / tc::TM);
+    long long g = (long long)(per_sm < 1 ? 1 : per_sm) * sms;
+    *grid = (int)(g < tiles ? g : tiles);
+    return cudaSuccess;
+}
+
+// Dynamic shared memory limits and persistent grid sizes of the three layers.
+static cudaError_t tc_setup(ac_closure *c) {
+    int dev = 0, sms = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess) e = tc_grid_for<16, 32, tc::EPI_RELU_BF16>(c, sms, &c->tc_grid[0]);
+    if (e == cudaSuccess) e = tc_grid_for<32, 32, tc::EPI_RELU_BF16>(c, sms, &c->tc_grid[1]);
+    if (e == cudaSuccess) e = tc_grid_for<32, 8, tc::EPI_LINEAR_F32>(c, sms, &c->tc_grid[2]);
+    return e;
 }
 
 static void free_closure(ac_closure *c) {
@@ -483,7 +539,8 @@ extern "C" int ac_closure_init(ac_closure **out, int nx, int ny, int nz, void *s
     const long long n = c->g.n;
     const size_t np = AC_CLOSURE_NPARAMS;
     // params, m, v, grads, scales (24), bf16 weights (fwd and transposed layouts)
-    const size_t wbytes = 2 * (32 * 27 * 16 + 32 * 27 * 32 + 8 * 27 * 32 + 32 * 27 * 16 + 32 * 27 * 32);
+    const size_t wbytes = 2 * (32 * 27 * 16 + 32 * 27 * 32 + 8 * 27 * 32 + 32 * 27 * 16 + 32 * 27 * 32) +
+                          2 * (27 * 16 * 32 + 27 * 32 * 32 + 27 * 32 * 16);
     const size_t fbytes = sizeof(float) * (4 * np + 64) + wbytes + 256;
     c->lossblocks = 304;
     const size_t part_floats = (size_t)9 * CL_WG_CTAS * 32 * 96;
@@ -512,6 +569,9 @@ extern "C" int ac_closure_init(ac_closure **out, int nx, int ny, int nz, void *s
     c->wf3 = c->wf2 + 32 * 27 * 32;
     c->wb3 = c->wf3 + 8 * 27 * 32;
     c->wb2 = c->wb3 + 32 * 27 * 16;
+    c->img1 = c->wb2 + 32 * 27 * 32;  // byte offsets stay multiples of 16
+    c->img2 = c->img1 + 27 * 16 * 32;
+    c->img3 = c->img2 + 27 * 32 * 32;
     char *a = static_cast<char *>(c->act_block);
     c->x0 = reinterpret_cast<bf16 *>(a);
     c->a1 = c->x0 + 16 * n;
@@ -523,11 +583,13 @@ extern "C" int ac_closure_init(ac_closure **out, int nx, int ny, int nz, void *s
     c->part = c->y + 8 * n;
     c->lossp = reinterpret_cast<double *>(c->part + part_floats);
     c->guard = reinterpret_cast<unsigned long long *>(c->lossp + c->lossblocks);
+    c->tc_err = reinterpret_cast<unsigned *>(c->guard + 1);
     for (int i = 0; i < 8; ++i) c->in_scale[i] = c->out_scale[i] = 1.f;
     float sc[24];
     for (int i = 0; i < 24; ++i) sc[i] = 1.f;
     e = cudaMemcpyAsync(c->scales, sc, sizeof sc, cudaMemcpyHostToDevice, c->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e == cudaSuccess) e = tc_setup(c);
     if (e != cudaSuccess) {
         int rc = ac_report_cuda(e);
         free_closure(c);
@@ -550,7 +612,10 @@ static int prep_weights(ac_closure *c) {
     prep_weights_kernel<<<32, 256, 0, c->stream>>>(c->params + P_W1, 32, 8, 16, c->wf1, 0, nullptr);
     prep_weights_kernel<<<128, 256, 0, c->stream>>>(c->params + P_W2, 32, 32, 32, c->wf2, 32, c->wb2);
     prep_weights_kernel<<<32, 256, 0, c->stream>>>(c->params + P_W3, 8, 32, 32, c->wf3, 16, c->wb3);
-    c->launches += 3;
+    tc::conv_tc_prep_kernel<<<64, 256, 0, c->stream>>>(c->params + P_W1, 32, 8, 16, 32, c->img1);
+    tc::conv_tc_prep_kernel<<<128, 256, 0, c->stream>>>(c->params + P_W2, 32, 32, 32, 32, c->img2);
+    tc::conv_tc_prep_kernel<<<64, 256, 0, c->stream>>>(c->params + P_W3, 8, 32, 32, 16, c->img3);
+    c->launches += 6;
     CCK(cudaGetLastError());
     return AC_OK;
 }
@@ -616,16 +681,77 @@ static int run_forward(ac_closure *c, const float *const in[8]) {
     return AC_OK;
 }
 
+template <int CIN, int COUT, int EPI>
+static void launch_tc(const ac_closure *c, int grid, const bf16 *x, const bf16 *img, const float *bias,
+                      void *y) {
+    tc::ConvTcArgs a;
+    a.x = x;
+    a.w = img;
+    a.bias = bias;
+    a.y = y;
+    a.nx = c->g.nx;
+    a.ny = c->g.ny;
+    a.nz = c->g.nz;
+    a.tiles = (int)((long long)c->g.ny * c->g.nz * ((c->g.nx + tc::TM - 1) / tc::TM));
+    a.err = c->tc_err;
+    tc::conv_tc_kernel<CIN, COUT, EPI>
+        <<<grid, tc::THREADS, tc::smem_bytes(CIN, COUT < 16 ? 16 : COUT), c->stream>>>(a);
+}
+
+// Forward pass on the tcgen05 kernels; leaves channels-last [n][8] binary32 in c->y.
+static int run_forward_tc(ac_closure *c, const float *const in[8]) {
+    const ConvGeom g = c->g;
+    F8 f;
+    for (int i = 0; i < 8; ++i) f.p[i] = in[i];
+    pack_input_cl_kernel<<<cl_grid(g.n), 256, 0, c->stream>>>(f, c->scales, g.n, c->x0);
+    launch_tc<16, 32, tc::EPI_RELU_BF16>(c, c->tc_grid[0], c->x0, c->img1, c->params + P_B1, c->a1);
+    launch_tc<32, 32, tc::EPI_RELU_BF16>(c, c->tc_grid[1], c->a1, c->img2, c->params + P_B2, c->a2);
+    launch_tc<32, 8, tc::EPI_LINEAR_F32>(c, c->tc_grid[2], c->a2, c->img3, c->params + P_B3, c->y);
+    c->launches += 4;
+    CCK(cudaGetLastError());
+    return AC_OK;
+}
+
+// Inference forward on the selected path; *cl = 1 if c->y is channels-last.
+static int run_inference(ac_closure *c, const float *const in[8], int *cl) {
+    *cl = c->conv_path == AC_CONV_TCGEN05;
+    return *cl ? run_forward_tc(c, in) : run_forward(c, in);
+}
+
+extern "C" int ac_closure_set_conv_path(ac_closure *c, int path) {
+    if (!c || (path != AC_CONV_TCGEN05 && path != AC_CONV_MMA_SYNC)) return AC_ERR_ARG;
+    c->conv_path = path;
+    return AC_OK;
+}
+
+extern "C" int ac_closure_get_conv_path(const ac_closure *c, int *path) {
+    if (!c || !path) return AC_ERR_ARG;
+    *path = c->conv_path;
+    return AC_OK;
+}
+
+extern "C" int ac_closure_status(ac_closure *c) {
+    if (!c) return AC_ERR_ARG;
+    unsigned err = 0;
+    CCK(cudaMemcpyAsync(c->loss_host, c->tc_err, sizeof err, cudaMemcpyDeviceToHost, c->stream));
+    CCK(cudaMemsetAsync(c->tc_err, 0, sizeof err, c->stream));
+    CCK(cudaStreamSynchronize(c->stream));
+    memcpy(&err, c->loss_host, sizeof err);
+    return err ? AC_ERR_TIMEOUT : AC_OK;
+}
+
 extern "C" int ac_closure_forward(ac_closure *c, const float *const in[8], float *const out[8]) {
     if (!c || !in) return AC_ERR_ARG;
     for (int i = 0; i < 8; ++i)
         if (!in[i] || (out && !out[i])) return AC_ERR_ARG;
-    int rc = run_forward(c, in);
+    int cl = 0;
+    int rc = run_inference(c, in, &cl);
     if (rc) return rc;
     if (out) {
         W8 o;
         for (int i = 0; i < 8; ++i) o.p[i] = out[i];
-        scale_output_kernel<<<cl_grid(8 * c->g.n), 256, 0, c->stream>>>(c->y, c->scales + 8, c->g.n, o);
+        scale_output_kernel<<<cl_grid(8 * c->g.n), 256, 0, c->stream>>>(c->y, c->scales + 8, c->g.n, o,
+                                                                        cl);
         c->launches++;
         CCK(cudaGetLastError());
     }
@@ -710,13 +836,14 @@ extern "C" int ac_closure_apply(ac_closure *c, ac_handle *h, double limit, int *
         in[i] = static_cast<const float *>(ptrs[i]);
         f.p[i] = static_cast<float *>(ptrs[i]);
     }
-    rc = run_forward(c, in);
+    int cl = 0;
+    rc = run_inference(c, in, &cl);
     if (rc) return rc;
     CCK(cudaMemsetAsync(c->guard, 0, sizeof(unsigned long long), c->stream));
     correction_max_kernel<<<cl_grid(8 * c->g.n), 256, 0, c->stream>>>(c->y, c->scales + 8, c->g.n,
-                                                                      c->guard);
+                                                                      c->guard, cl);
     apply_correction_kernel<<<cl_grid(8 * c->g.n), 256, 0, c->stream>>>(f, c->y, c->scales + 8,
-                                                                        c->g.n, c->guard, limit);
+                                                                        c->g.n, c->guard, limit, cl);
     c->launches += 2;
     CCK(cudaGetLastError());
     if (applied) {

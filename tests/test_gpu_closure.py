@@ -64,16 +64,56 @@ def _setup(n, seed):
     return net, params, x, in_scale, out_scale
 
 
-@pytest.mark.parametrize("n", [(16, 12, 10), (40, 8, 6), (130, 3, 4)])
-def test_forward_matches_oracle(n):
+PATHS = [ac.AC_CONV_TCGEN05, ac.AC_CONV_MMA_SYNC]
+
+
+# one x-row tile, ragged tiles, several tiles per row, odd sizes, a single cell
+@pytest.mark.parametrize("path", PATHS)
+@pytest.mark.parametrize("n", [(16, 12, 10), (40, 8, 6), (130, 3, 4), (300, 2, 3), (7, 5, 3),
+                               (1, 1, 1)])
+def test_forward_matches_oracle(n, path):
     net, params, x, ins, outs = _setup(n, 5)
-    c = cl.Closure(n, params=params)
+    c = cl.Closure(n, params=params, conv_path=path)
     c.set_scales(ins, outs)
     got = c.correction(_dev(x)).double().cpu().numpy().reshape((8,) + x.shape[1:])
+    c.status()
     xn = x / ins.astype(np.float64)[:, None, None, None]
     y, _ = net.forward(xn, round_bf16=True)
     ref = y * outs.astype(np.float64)[:, None, None, None]
     assert _maxrel(got, ref) <= 2e-2, _maxrel(got, ref)
+    c.close()
+
+
+def test_forward_paths_agree_at_64_cubed():
+    """The tcgen05 and mma.sync forward passes on a 64^3 grid (32 768 tiles of
+    a row each on the persistent grid): same bfloat16 operands, different
+    accumulation order, so agreement to bfloat16 rounding of the hidden
+    activations."""
+    n = (64, 64, 64)
+    net, params, x, ins, outs = _setup(n, 9)
+    xs = _dev(x)
+    outs_ = []
+    for path in PATHS:
+        c = cl.Closure(n, params=params, conv_path=path)
+        c.set_scales(ins, outs)
+        outs_.append(c.correction(xs).double().cpu().numpy())
+        c.status()
+        c.close()
+    assert _maxrel(outs_[0], outs_[1]) <= 1e-2, _maxrel(outs_[0], outs_[1])
+    # every cell against the oracle
+    xn = x / ins.astype(np.float64)[:, None, None, None]
+    y, _ = net.forward(xn, round_bf16=True)
+    ref = (y * outs.astype(np.float64)[:, None, None, None]).reshape(8, -1)
+    assert _maxrel(outs_[0], ref) <= 2e-2, _maxrel(outs_[0], ref)
+
+
+def test_conv_path_selection():
+    c = cl.Closure((8, 8, 8))
+    assert ac.ac_closure_get_conv_path(c.c) == ac.AC_CONV_TCGEN05
+    ac.ac_closure_set_conv_path(c.c, ac.AC_CONV_MMA_SYNC)
+    assert ac.ac_closure_get_conv_path(c.c) == ac.AC_CONV_MMA_SYNC
+    with pytest.raises(ac.AcError):
+        ac.ac_closure_set_conv_path(c.c, 7)
     c.close()
 
 
@@ -110,13 +150,14 @@ def test_gradients_and_adam_match_oracle():
     c.close()
 
 
-def test_apply_guard():
+@pytest.mark.parametrize("path", PATHS)
+def test_apply_guard(path):
     n = (16, 8, 12)
     net, params, x, ins, outs = _setup(n, 8)
     sim = ac.Simulation(n, precision=ac.AC_FP32)
     sim.load(x)
     before = cl.current_state(sim).clone()
-    c = cl.Closure(n, params=params)
+    c = cl.Closure(n, params=params, conv_path=path)
     c.set_scales(ins, outs)
     corr = c.correction(before.clone()).clone()
     assert not c.apply(sim, limit=1e-9)  # larger than the limit: left unchanged
