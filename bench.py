@@ -66,6 +66,11 @@ WORKLOADS = {
                        desc="learned closure: 128^3 FP32 coarse grid + 3-layer 3-D conv "
                             "(8-32-32-8, k=3, BF16 weights, FP32 accumulation) applied every "
                             "step, trained on 256^3 FP64 forced runs restricted 2x"),
+    "closure_forward256": dict(n=(256, 256, 256), precision="fp32", force_amp=0.0, seed=7,
+                               init="turbulent", closure_forward=True,
+                               desc="learned-closure inference on a 256^3 FP32 state: input "
+                                    "pack, 3-D conv 8-32-32-8 (k=3, circular, BF16 operands, "
+                                    "FP32 accumulation, tcgen05) and output scaling"),
     "ensemble64_fp32": dict(n=None, precision="fp32", force_amp=0.0, seed=4, dt=1e-3,
                             init="noise", ensemble=True,
                             desc="64 periodic boxes, per-axis sizes from {32,48,64,96,128}, "
@@ -680,8 +685,7 @@ def run_closure(args, wl):
             "peak_source": "measured (MEASURED_PEAKS.json bf16_tflops, burst)",
             "avg_launch_ms": 1e3 * conv_s / 3,
             "forward_ms": {k: 1e3 * v for k, v in fwd_s.items()},
-            "note": "algorithmic flops count the 8 real input channels; the tensor cores "
-                    "also multiply the 8 zero channels of the 16-wide first-layer input"}
+            "note": "algorithmic flops (8 real input and output channels)"}
 
     # spectra after M coarse steps: plain, with closure, and the restricted fine run
     M = args.closure_rollout
@@ -744,6 +748,189 @@ def run_closure(args, wl):
     return 0
 
 
+# ---------------------------------------------------------------------------
+# learned-closure inference
+# ---------------------------------------------------------------------------
+CF_METRIC = "closure forward throughput"
+CF_UNIT = "Gcell/s"
+# algorithmic flops per cell of the three layers (real channels: 8 -> 32 -> 32
+# -> 8; the tensor cores also multiply padding, which is not counted)
+CF_FLOPS = {1: 2 * 27 * 8 * 32, 2: 2 * 27 * 32 * 32, 3: 2 * 27 * 32 * 8}
+# algorithmic flops per cell (8 real input channels, 8 real output channels)
+CF_ALGO_FLOPS = 2 * 27 * (8 * 32 + 32 * 32 + 32 * 8)
+
+
+def _closure_oracle_sample(params, n, seed):
+    from oracle import closure as oc
+    net = oc.Net.unflat(np.asarray(params, dtype=np.float64))
+    x = np.random.default_rng(seed).standard_normal((8, n, n, n))
+    t0 = time.perf_counter()
+    net.forward(x, round_bf16=True)
+    return time.perf_counter() - t0, n ** 3
+
+
+def run_closure_forward(args, wl):
+    """Inference throughput of the learned closure (ac_closure_forward: input
+    pack, three convolution launches, output scaling) on a 256^3 state; the
+    dominant kernel is the 32 -> 32 layer."""
+    import torch
+    from paper_2103_01597_gb300 import ac, build, synthetic
+    from paper_2103_01597_gb300 import closure as cl
+    ws, rank, local = dist_setup(args)
+    torch.cuda.set_device(local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    if rank == 0:
+        build.build()
+    if dist:
+        dist.barrier()
+    n = wl["n"]
+    cells = n[0] * n[1] * n[2]
+    f = synthetic.turbulent_state(n, wl["seed"], kmax=48, amp=0.3).astype(np.float32).reshape(8, -1)
+    rms = np.sqrt(np.mean(f.astype(np.float64) ** 2, axis=1))
+    ins = np.maximum(rms, 1e-6).astype(np.float32)
+    outs = (1e-2 * ins).astype(np.float32)
+    stream = torch.cuda.current_stream()
+    xs = torch.from_numpy(f).cuda()
+    out = torch.empty_like(xs)
+    c = cl.Closure(n, seed=wl["seed"], stream=stream.cuda_stream)
+    c.set_scales(ins, outs)
+    rin, rout = cl._rows(xs), cl._rows(out)
+    lib = ac.load_library()
+    pin, pout = ac._ptr8(rin), ac._ptr8(rout)
+    for _ in range(args.warmup):
+        assert lib.ac_closure_forward(c.c, pin, pout) == 0
+    torch.cuda.synchronize()
+    bus = None
+    try:
+        bus = torch.cuda.get_device_properties(local).pci_bus_id
+    except Exception:
+        pass
+    sampler = ClockSampler(bus) if rank == 0 else None
+    time.sleep(0.3 if sampler else 0)
+    l0 = ac.ac_closure_launch_count(c.c)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ta, tb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ta.record(stream)
+    for _ in range(args.steps):
+        rc = lib.ac_closure_forward(c.c, pin, pout)
+        assert rc == 0, ac.ac_strerror(rc)
+    tb.record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    elapsed = ta.elapsed_time(tb) / 1e3
+    clocks = sampler.stop() if sampler else None
+    launches = ac.ac_closure_launch_count(c.c) - l0
+    c.status()
+    if dist:
+        t = torch.tensor([elapsed], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        elapsed = float(t.item())
+    value = ws * cells * args.steps / elapsed / 1e9
+
+    # per-launch device times (events around each launch, on the closure's stream)
+    per = {}
+    for path, name in ((ac.AC_CONV_TCGEN05, "tcgen05"), (ac.AC_CONV_MMA_SYNC, "mma_sync")):
+        ac.ac_closure_set_conv_path(c.c, path)
+        ac.ac_closure_forward_timings(c.c, rin, rout)
+        rows = [ac.ac_closure_forward_timings(c.c, rin, rout) for _ in range(max(3, args.steps))]
+        per[name] = [statistics.mean(r[i] for r in rows) for i in range(5)]
+    ac.ac_closure_set_conv_path(c.c, ac.AC_CONV_TCGEN05)
+    ms2 = per["tcgen05"][2]
+    peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    ach = CF_FLOPS[2] * cells / (ms2 / 1e3) / 1e12
+    layers = {name: {"ms": {k: v for k, v in zip(("pack", "conv1", "conv2", "conv3", "scale"),
+                                                 per[name])},
+                     "conv_tflops": {"conv%d" % l: CF_FLOPS[l] * cells / (per[name][l] / 1e3) / 1e12
+                                     for l in (1, 2, 3)}}
+              for name in per}
+    roof = {"bound": "tensor", "achieved": ach, "peak": peaks["bf16_tflops"], "unit": "TFLOP/s",
+            "frac": ach / peaks["bf16_tflops"], "traffic": None,
+            "kernel": "conv_tc_kernel<32,32> (layer 2, tcgen05.mma BF16, TMEM accumulators)",
+            "per_unit": "2*27*32*32 = 55296 flops per cell", "units_per_launch": cells,
+            "avg_launch_ms": ms2,
+            "peak_source": "measured (MEASURED_PEAKS.json bf16_tflops, burst)",
+            "launches": layers}
+
+    # end to end through the public call: pinned host state in, correction out
+    hin = torch.from_numpy(f).pin_memory()
+    hout = torch.empty_like(hin).pin_memory()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ne = max(2, args.e2e_steps)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(ne):
+        xs.copy_(hin, non_blocking=True)
+        assert lib.ac_closure_forward(c.c, pin, pout) == 0
+        hout.copy_(out, non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e = {"value": ws * cells * ne / (e0.elapsed_time(e1) / 1e3) / 1e9, "unit": CF_UNIT,
+           "h2d_bytes_per_step": 8 * cells * 4, "d2h_bytes_per_step": 8 * cells * 4,
+           "steps": ne}
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        params = ac.ac_closure_get_params(c.c)
+        dt, cu = _closure_oracle_sample(params, 48, 1)
+        cpu = {"value": cu / dt / 1e9, "unit": CF_UNIT, "cores": os.cpu_count(), "kind": "oracle",
+               "sample": "closure forward of a 48^3 state (numpy FP64 oracle, BF16-rounded "
+                         "operands, BLAS threads as numpy sets them)", "seconds": dt}
+    c.close()
+    if rank == 0:
+        line = {"metric": CF_METRIC, "value": value, "unit": CF_UNIT, "n_gpus": ws,
+                "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": 1e3 * elapsed / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "bf16 x bf16 -> f32",
+                "data": "synthetic",
+                "config": {"workload": wl["desc"], "grid": list(n),
+                           "parallelism": "replicas" if ws > 1 else "single GPU",
+                           "l2": "inputs larger than L2 (state 0.54 GB, each activation "
+                                 "0.5-1.1 GB)",
+                           "algorithmic_flops_per_cell": CF_ALGO_FLOPS,
+                           "step": "one ac_closure_forward (pack + 3 conv + scale)"},
+                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+                "clocks": clocks}
+        print(json.dumps(line))
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+def run_closure_forward_reference(args, wl):
+    """The oracle arm of the closure-inference workload: the numpy FP64 forward
+    on a 32^3 sample per step."""
+    ws, rank, _ = dist_setup(args)
+    if rank != 0:
+        return 0
+    from paper_2103_01597_gb300 import closure as cl
+    params = cl.init_params(wl["seed"])
+    for _ in range(args.warmup):
+        _closure_oracle_sample(params, 32, 0)
+    tot, cu = 0.0, 0
+    for i in range(args.steps):
+        dt, c = _closure_oracle_sample(params, 32, i)
+        tot += dt
+        cu += c
+    value = cu / tot / 1e9
+    line = {"impl": "reference", "metric": CF_METRIC, "value": value, "unit": CF_UNIT,
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * tot / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": wl["desc"], "grid": list(wl["n"]),
+                       "sample_per_step": "closure forward of a 32^3 state"},
+            "cpu_baseline": {"value": value, "unit": CF_UNIT, "cores": os.cpu_count(),
+                             "kind": "oracle", "sample": "per step: a 32^3 forward"},
+            "e2e": {"value": value, "unit": CF_UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
 def main():
     args = parse()
     wl = dict(WORKLOADS[args.workload])
@@ -757,7 +944,11 @@ def main():
             from paper_2103_01597_gb300 import synthetic
             n0 = synthetic.ensemble(wl["seed"])[0][0]
             wl = dict(wl, n=n0, desc=wl["desc"] + " (oracle sample: box 0)")
+        if wl.get("closure_forward"):
+            return run_closure_forward_reference(args, wl)
         return run_reference(args, wl)
+    if wl.get("closure_forward"):
+        return run_closure_forward(args, wl)
     if wl.get("ensemble"):
         return run_ensemble(args, wl)
     if wl.get("closure"):

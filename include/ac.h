@@ -328,6 +328,11 @@ int ac_closure_set_scales(ac_closure *c, const float in_scale[8], const float ou
 /* Correction of the coarse state `in` into `out` (device arrays, may not alias;
  * out == NULL keeps the result inside the closure). */
 int ac_closure_forward(ac_closure *c, const float *const in[8], float *const out[8]);
+/* As ac_closure_forward (out required), and ms[0..4] receives the device time
+ * of each of its five launches (input pack, convolution layers 1, 2, 3, output
+ * scale) from CUDA events on the closure's stream; synchronises. */
+int ac_closure_forward_timings(ac_closure *c, const float *const in[8], float *const out[8],
+                               float ms[5]);
 /* Forward, loss against `target` (physical units, device arrays) and
  * gradients of every parameter; *loss (if non-NULL) synchronises. */
 int ac_closure_backward(ac_closure *c, const float *const in[8], const float *const target[8],

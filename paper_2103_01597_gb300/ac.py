@@ -134,6 +134,8 @@ def load_library(path=None):
         "ac_closure_set_scales": ([_vp, ctypes.POINTER(_c.c_float), ctypes.POINTER(_c.c_float)],
                                   _c.c_int),
         "ac_closure_forward": ([_vp, ctypes.POINTER(_vp), ctypes.POINTER(_vp)], _c.c_int),
+        "ac_closure_forward_timings": ([_vp, ctypes.POINTER(_vp), ctypes.POINTER(_vp),
+                                        ctypes.POINTER(_c.c_float)], _c.c_int),
         "ac_closure_backward": ([_vp, ctypes.POINTER(_vp), ctypes.POINTER(_vp), _pd], _c.c_int),
         "ac_closure_adam_step": ([_vp, _c.c_float, _c.c_float, _c.c_float, _c.c_float], _c.c_int),
         "ac_closure_apply": ([_vp, _vp, _c.c_double, ctypes.POINTER(_c.c_int)], _c.c_int),
@@ -386,6 +388,15 @@ def ac_closure_forward(c, in_ptrs, out_ptrs=None):
     _check(load_library().ac_closure_forward(c, _ptr8(in_ptrs),
                                              _ptr8(out_ptrs) if out_ptrs is not None else None),
            "ac_closure_forward")
+
+
+def ac_closure_forward_timings(c, in_ptrs, out_ptrs):
+    """Forward into out_ptrs; returns the device ms of its five launches
+    (input pack, conv layers 1-3, output scale)."""
+    ms = (ctypes.c_float * 5)()
+    _check(load_library().ac_closure_forward_timings(c, _ptr8(in_ptrs), _ptr8(out_ptrs), ms),
+           "ac_closure_forward_timings")
+    return list(ms)
 
 
 def ac_closure_backward(c, in_ptrs, target_ptrs):

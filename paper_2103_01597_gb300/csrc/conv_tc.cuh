@@ -1,22 +1,32 @@
 // 3-D convolution (3x3x3 taps, circular padding) as an implicit GEMM on the
 // fifth-generation tensor cores: tcgen05.mma with bfloat16 operands from
-// shared memory and a binary32 accumulator in tensor memory (TMEM).
+// shared memory, staged by the tensor memory accelerator (TMA), and binary32
+// accumulators in tensor memory (TMEM).
 //
-// Activations are channels-last bfloat16, x[p][c] (p = cell, x fastest).  A CTA
-// computes 128 cells of one x-row (GEMM M = 128) for all output channels
-// (N = COUT, padded to 16).  K = 27 taps x CIN: for each tap, the 128 source
-// cells (shifted by the tap, wrapped periodically) are copied with 16-byte
-// cp.async into the canonical K-major no-swizzle layout (core matrices of
-// 8 cells x 8 channels, 128 contiguous bytes), and one elected thread issues
-// CIN/16 MMAs of K = 16.  A tiles are double-buffered: the copy of tap t+1
-// overlaps the MMAs of tap t, and a buffer is refilled only after the MMAs
-// that read it have signalled their mbarrier (tcgen05.commit).  The weights
-// of the layer stay in shared memory in the same layout.  The epilogue reads
-// the accumulator with tcgen05.ld (one row per thread) and applies bias and
-// ReLU.  Every wait is bounded: on timeout the kernel records an error word,
-// stops issuing, still frees its TMEM, and returns.
+// Activation layout ("row-planar", RP): bfloat16, for each row (y, z) and each
+// group kc of 8 channels a plane of nx + 2 cells x 16 bytes, the cells being
+// x = nx-1, 0, 1, ..., nx-1, 0 (the periodic x halo stored with the row):
+//     a[(((z * ny + y) * KC + kc) * (nx + 2) + x + 1) * 8 + c]  = channel 8 kc + c.
+// A TMA box of 8 channels x 130 cells x KC planes then lands in shared memory
+// as KC planes of 130 consecutive 16-byte rows, which is the canonical K-major
+// no-swizzle operand layout (core matrices of 8 cells x 8 channels) with
+// M-direction core-matrix stride 128 bytes and K-direction stride 2080 bytes;
+// the three dx taps of a row are the same operand started 0, 1 or 2 cells in.
+//
+// An output tile is 128 cells of one x-row (GEMM M = 128) for all output
+// channels (N = COUT, padded to 16); K = 27 taps x CIN.  Warp roles in a
+// persistent CTA: warp 4 (one thread) issues the TMA copies of z-slices
+// (rows y-1, y, y+1 of one plane) into a six-slice ring; warp 5 (one thread)
+// issues the MMAs of each tile into one of two TMEM accumulators and signals
+// completion with tcgen05.commit; warps 0-3 read an accumulator back
+// (tcgen05.ld, one TMEM lane per thread), add the bias, apply ReLU and store.
+// A CTA marches along z through column segments, so each staged slice serves
+// three tiles.  Every wait is bounded: on timeout a role records an error
+// word and stops, the others run out of their own bounded waits, and TMEM is
+// still freed.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_bf16.h>
 #include <stdint.h>
 
@@ -25,9 +35,11 @@ namespace tc {
 
 using bf16 = __nv_bfloat16;
 
-constexpr int TM = 128;          // cells per CTA (GEMM M)
-constexpr int THREADS = 128;     // four warps: one TMEM lane quadrant each
+constexpr int TM = 128;          // cells per tile (GEMM M)
+constexpr int THREADS = 192;     // warps 0-3 epilogue (one TMEM lane quadrant each), 4 TMA, 5 MMA
 constexpr int CORE = 128;        // bytes of one core matrix (8 rows x 16 B)
+constexpr int PLANE = (TM + 2) * 16;  // bytes of one staged 8-channel plane (130 cells)
+constexpr int NBUF = 6;          // z-slices in the shared-memory ring
 constexpr unsigned WAIT_LIMIT = 1u << 24;  // polls of an mbarrier before giving up
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
@@ -142,188 +154,394 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
     for (int c = 0; c < 32; ++c) v[c] = __uint_as_float(r[c]);
 }
 
-__device__ __forceinline__ void cp16(void *smem, const void *gmem) {
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(smem_u32(smem)), "l"(gmem)
+// 32 lanes x 16 columns of binary32 from TMEM.
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+        "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
+          "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr)
+        : "memory");
+    asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+#pragma unroll
+    for (int c = 0; c < 16; ++c) v[c] = __uint_as_float(r[c]);
+}
+
+// Zero 32 lanes x NB (16 or 32) columns of TMEM and wait for the stores.
+template <int NB>
+__device__ __forceinline__ void tmem_zero(uint32_t taddr) {
+    const uint32_t z = 0;
+    if (NB == 32)
+        asm volatile(
+            "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], "
+            "{%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,"
+            "%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1};\n" ::"r"(taddr),
+            "r"(z)
+            : "memory");
+    else
+        asm volatile(
+            "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], "
+            "{%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1};\n" ::"r"(taddr),
+            "r"(z)
+            : "memory");
+    asm volatile("tcgen05.wait::st.sync.aligned;\n" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(smem_u32(bar)) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(bar)),
+                 "r"(bytes)
                  : "memory");
 }
-__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_wait() {
-    asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+
+// 5-D tiled TMA load of one box into shared memory, completing on `bar`.
+__device__ __forceinline__ void tma_load_5d(void *dst, const CUtensorMap *map, uint64_t *bar, int c0,
+                                            int c1, int c2, int c3, int c4) {
+    asm volatile(
+        "cp.async.bulk.tensor.5d.shared::cluster.global.tile.mbarrier::complete_tx::bytes "
+        "[%0], [%1, {%3, %4, %5, %6, %7}], [%2];\n" ::"r"(smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(c0), "r"(c1), "r"(c2),
+        "r"(c3), "r"(c4)
+        : "memory");
+}
+
+// Untiled bulk copy global -> shared (16-byte aligned, size a multiple of 16).
+__device__ __forceinline__ void bulk_load(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
+            smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
 }
 
 enum { EPI_RELU_BF16 = 0, EPI_LINEAR_F32 = 1 };
 
-constexpr int APITCH = (TM + 8) * 16;  // bytes of one 8-channel plane of an A tile (130 rows used)
+// Bytes of one staged row (KC planes, rounded up so rows stay 128-byte aligned).
+__host__ __device__ constexpr int row_bytes(int cin) { return ((cin / 8) * PLANE + 127) / 128 * 128; }
 
-// Bytes of dynamic shared memory: layer weights and two A tiles.
-__host__ __device__ constexpr size_t smem_bytes(int cin, int npad) {
-    return (size_t)27 * cin * npad * 2 + 2 * (size_t)(cin / 8) * APITCH;
+// Bytes of the kz-stacked weight image (nb accumulator columns per tile): nine
+// (ky, kx) taps x cin channels, or, for cin = 8, five tap pairs x 16 channels.
+__host__ __device__ constexpr int w_bytes(int cin, int nb) {
+    return cin == 8 ? 10 * 3 * nb * 16 : 9 * cin * 3 * nb * 2;
+}
+
+// Bytes of dynamic shared memory: the weight image and the slice ring.
+__host__ __device__ constexpr size_t smem_bytes(int cin, int nb) {
+    return (size_t)w_bytes(cin, nb) + (size_t)NBUF * 3 * row_bytes(cin);
+}
+
+// Layers with 8 input channels fill the K = 16 of an MMA with two taps of one
+// slice: the pairs (tap a, tap b) below, tap = 3 dy + dx, the second core-matrix
+// column of K lying (offset of b - offset of a) bytes after the first.  The last
+// pair repeats tap 7 with zero weights.
+__host__ __device__ constexpr int pair_tap(int p, int h) {
+    return h == 0 ? (p < 4 ? 2 * p : 7) : (p < 4 ? 2 * p + 1 : 8);
 }
 
 struct ConvTcArgs {
-    const bf16 *x;        // [cells][CIN] channels-last input
     const bf16 *w;        // weights in the shared-memory image order (see prep)
     const float *bias;    // [COUT]
-    void *y;              // [cells][COUT] bf16 (ReLU) or binary32 (linear)
+    void *y;              // output: RP bfloat16 (ReLU layers) or [cells][COUT] binary32 (linear)
     int nx, ny, nz;
-    int tiles;            // ny * nz * ceil(nx / TM)
+    int zc;               // tiles per column segment (z extent of a chunk)
     unsigned *err;        // set non-zero if a bounded wait ran out
 };
 
-// Persistent: CTA b computes tiles b, b + gridDim.x, ...  A tile is 128 cells
-// of one x-row.  The nine (dy, dz) source rows of a tile are staged one after
-// another, each with a one-cell halo on both sides (130 cells); the three dx
-// taps of a row read the same staged rows through descriptors whose start is
-// shifted by 0, 1 or 2 cells (16 bytes each): in the no-swizzle K-major layout
-// with 128-byte M-direction core-matrix stride the M rows of a plane are
-// simply consecutive 16-byte rows.  Staged row groups are double-buffered
-// across tiles, so the copy of the next group always overlaps the MMAs of the
-// current one.
+__device__ __forceinline__ int wrapi(int v, int n) {
+    if (v >= 0 && v < n) return v;
+    const int m = v % n;
+    return m < 0 ? m + n : m;
+}
+
+// Column segments: g = chunk * ncols + col (chunk-major, so that the CTAs of
+// one wave work in the same z-chunk and share its slices in L2), col = y * segs
+// + seg; a segment is the tiles z = chunk * zc ... of column col.
+struct Segment {
+    int y, seg, z0, len;
+};
+
+__device__ __forceinline__ Segment segment_of(long long g, const ConvTcArgs &a, int segs) {
+    const long long ncols = (long long)a.ny * segs;
+    const int chunk = (int)(g / ncols);
+    const int col = (int)(g - chunk * ncols);
+    Segment s;
+    s.y = col / segs;
+    s.seg = col - s.y * segs;
+    s.z0 = chunk * a.zc;
+    s.len = min(a.zc, a.nz - s.z0);
+    return s;
+}
+
+// Persistent CTA g-loop over column segments b, b + G, ...  Slices are numbered
+// in the order the CTA stages them (a segment of L tiles stages L + 2: planes
+// z0-1 .. z0+L); slice s lives in ring buffer s % NBUF, as that buffer's
+// (s / NBUF)-th fill.
 //
-// Weight image: w[((((tap * KC + kc) * NG + ng) * 8 + r) * 8 + c] holds
-// W[co = 8 ng + r][ci = 8 kc + c][tap], zero for co >= COUT or ci >= cin_real.
+// One MMA batch per slice.  Slice j of a segment (plane z0 + j - 1) feeds the
+// tiles j-2, j-1, j of the segment that exist (dz = +1, 0, -1).  The weight
+// image stacks the three kz blocks along N, [W(kz=2); W(kz=1); W(kz=0)], NB
+// rows each, so the contributions of one slice to up to three tiles are one
+// MMA of N = 3 NB (fewer at segment ends) whose accumulator is three
+// consecutive NB-column blocks of TMEM: tile t of the CTA owns block t % R.
+// Because one MMA both opens a tile and adds to older ones, MMAs always
+// accumulate, and blocks are zero when handed over: zeroed once at start and
+// again by the epilogue after it reads a tile.  Barriers, each waited on in
+// phase order:
+//   full[b]  : TMA bytes of a fill landed (producer expect_tx, TMA complete_tx);
+//   empty[b] : the MMAs reading a fill have finished (tcgen05.commit);
+//   accf[k]  : the tile in block k is complete (commit after its third slice);
+//   acce[k]  : the four epilogue warps have read and re-zeroed block k;
+//   wbar     : the layer's weight image landed;
+//   fin      : every MMA of the CTA has finished (before TMEM is freed).
+//
+// Weight image: w[(((kq * NGS + ng) * 8 + r) * 8 + c], NGS = 3 NB / 8, holds for
+// stack row 8 ng + r = (2 - kz) NB + co the weight W[co][ci][kz][dyx] (dyx =
+// 3 ky + kx) of K-chunk kq: kq = dyx * KC + kc and ci = 8 kc + c, or for
+// CIN = 8, kq = 2 p + h, dyx = pair_tap(p, h) and ci = c; zero for co >= COUT,
+// ci >= cin_real and the zero half of the last pair.
+constexpr int RBLK = 8;  // TMEM accumulator blocks per CTA
+
 template <int CIN, int COUT, int EPI>
-__global__ void __launch_bounds__(THREADS) conv_tc_kernel(const ConvTcArgs a) {
-    constexpr int NPAD = COUT < 16 ? 16 : COUT;
-    constexpr int KC = CIN / 8;     // core-matrix columns along K per tap
-    constexpr int NG = NPAD / 8;    // core-matrix rows along N
-    constexpr int A_BYTES = KC * APITCH;
-    constexpr int W_BYTES = 27 * KC * NG * CORE;
-    constexpr uint32_t IDESC = idesc_bf16(TM, NPAD);
-    static_assert(CIN % 16 == 0 && COUT % 8 == 0 && COUT <= 32, "shape");
+__global__ void __launch_bounds__(THREADS, 1)
+    conv_tc_kernel(const __grid_constant__ CUtensorMap xmap, const ConvTcArgs a) {
+    constexpr int NB = COUT < 16 ? 16 : COUT;  // accumulator columns per tile
+    constexpr int KC = CIN / 8;                // core-matrix columns along K per tap
+    constexpr bool PAIR = CIN == 8;            // two taps per MMA
+    constexpr int NGS = 3 * NB / 8;            // core-matrix rows of the kz stack
+    constexpr int ROW = row_bytes(CIN);
+    constexpr int SLICE = 3 * ROW;
+    constexpr int W_BYTES = w_bytes(CIN, NB);
+    constexpr uint32_t SLICE_TX = 3 * KC * PLANE;
+    constexpr uint32_t TCOLS = RBLK * NB;      // 256 or 128 TMEM columns
+    static_assert((CIN % 16 == 0 || CIN == 8) && COUT % 8 == 0 && COUT <= 32, "shape");
     extern __shared__ __align__(1024) unsigned char smem[];
-    __shared__ uint64_t bar[2];
+    __shared__ uint64_t full[NBUF], empty[NBUF], accf[RBLK], acce[RBLK], wbar, fin;
     __shared__ uint32_t tmem_base;
     unsigned char *Ws = smem;
-    unsigned char *As = smem + W_BYTES;
-    const int tid = threadIdx.x, warp = tid >> 5;
+    unsigned char *Ss = smem + W_BYTES;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int segs = (a.nx + TM - 1) / TM;
-    const int mine = a.tiles > (int)blockIdx.x ? (a.tiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
-    const int groups = 9 * mine;
+    const long long nseg = (long long)((a.nz + a.zc - 1) / a.zc) * a.ny * segs;
 
-    if (warp == 0) tmem_alloc(&tmem_base, 32);
-    if (tid == 0) {
-        mbar_init(&bar[0], 1);
-        mbar_init(&bar[1], 1);
+    if (warp == 0) tmem_alloc(&tmem_base, TCOLS);
+    if (threadIdx.x == 128) {
+        for (int b = 0; b < NBUF; ++b) {
+            mbar_init(&full[b], 1);
+            mbar_init(&empty[b], 1);
+        }
+        for (int b = 0; b < RBLK; ++b) {
+            mbar_init(&accf[b], 1);
+            mbar_init(&acce[b], 4);
+        }
+        mbar_init(&wbar, 1);
+        mbar_init(&fin, 1);
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
     }
-    for (int i = tid; i < W_BYTES / 16; i += THREADS)
-        cp16(Ws + 16 * i, reinterpret_cast<const unsigned char *>(a.w) + 16 * i);
-
-    // Stage source row group G (tile G / 9, dz dy = G % 9) into buffer G & 1.
-    auto load_group = [&](int G) {
-        const int tile = (int)blockIdx.x + (G / 9) * (int)gridDim.x;
-        const int grp = G % 9;
-        const int row = tile / segs, seg = tile - row * segs;
-        const int y = row % a.ny, z = row / a.ny;
-        const int dz = grp / 3 - 1, dy = grp % 3 - 1;
-        int yy = (y + dy) % a.ny, zz = (z + dz) % a.nz;
-        yy = yy < 0 ? yy + a.ny : yy;
-        zz = zz < 0 ? zz + a.nz : zz;
-        const long long rbase = ((long long)zz * a.ny + yy) * a.nx;
-        unsigned char *dst = As + (G & 1) * A_BYTES;
-        for (int i = tid; i < (TM + 2) * KC; i += THREADS) {
-            const int c = i / KC, kc = i - c * KC;  // consecutive threads: one cell's chunks
-            int xx = (seg * TM - 1 + c) % a.nx;
-            xx = xx < 0 ? xx + a.nx : xx;
-            cp16(dst + kc * APITCH + c * 16, a.x + (rbase + xx) * CIN + 8 * kc);
-        }
-    };
-
-    if (groups > 0) load_group(0);
-    cp_commit();
     __syncthreads();  // barriers initialised, TMEM address published
     tc_fence_after_sync();
     const uint32_t tmem = tmem_base;
-    bool abort = false;
-    for (int G = 0; G < groups; ++G) {
-        if (G + 1 < groups) {
-            if (G >= 1) {  // the MMAs of group G-1 read the buffer group G+1 goes to
-                const bool ok = mbar_wait(&bar[(G - 1) & 1], ((G - 1) >> 1) & 1);
-                if (__syncthreads_or(!ok)) {
-                    abort = true;
-                    break;
+    if (warp < 4) {  // every accumulator block starts at zero
+        for (int k = 0; k < RBLK; ++k) tmem_zero<NB>(tmem + ((uint32_t)(warp * 32) << 16) + k * NB);
+        tc_fence_before_sync();
+    }
+    __syncthreads();
+    tc_fence_after_sync();
+
+    if (warp == 4) {
+        if (lane == 0) {  // ---- TMA producer
+            mbar_expect_tx(&wbar, W_BYTES);
+            bulk_load(Ws, a.w, W_BYTES, &wbar);
+            long long s = 0;
+            bool ok = true;
+            for (long long g = blockIdx.x; g < nseg && ok; g += gridDim.x) {
+                const Segment sg = segment_of(g, a, segs);
+                for (int j = 0; j < sg.len + 2; ++j, ++s) {
+                    const int b = (int)(s % NBUF);
+                    const long long k = s / NBUF;
+                    if (k > 0 && !mbar_wait(&empty[b], (unsigned)((k - 1) & 1))) {
+                        ok = false;
+                        break;
+                    }
+                    mbar_expect_tx(&full[b], SLICE_TX);
+                    const int z = wrapi(sg.z0 + j - 1, a.nz);
+                    unsigned char *dst = Ss + b * SLICE;
+#pragma unroll
+                    for (int r = 0; r < 3; ++r)
+                        tma_load_5d(dst + r * ROW, &xmap, &full[b], 0, sg.seg * TM, 0,
+                                    wrapi(sg.y + r - 1, a.ny), z);
                 }
             }
-            load_group(G + 1);
+            if (!ok) atomicExch(a.err, 1u);
+            // no copy may be in flight when the CTA exits: wait for each buffer's last fill
+            mbar_wait(&wbar, 0);
+            for (int b = 0; b < NBUF; ++b)
+                if (s > b) mbar_wait(&full[b], (unsigned)(((s - 1 - b) / NBUF) & 1));
         }
-        cp_commit();
-        cp_wait<1>();          // group G (and the weights) have landed for this thread
-        fence_proxy_async_smem();
-        __syncthreads();       // ... for every thread; the last epilogue's TMEM reads are done
-        const int grp = G % 9;
-        if (tid == 0) {
-            tc_fence_after_sync();
-            const uint32_t abase = smem_u32(As + (G & 1) * A_BYTES);
+    } else if (warp == 5) {
+        if (lane == 0) {  // ---- MMA issuer
+            bool ok = mbar_wait(&wbar, 0);
+            long long s = 0;  // slices consumed
+            int it0 = 0;      // CTA tile index of the segment's first tile
             const uint32_t wbase = smem_u32(Ws);
+            for (long long g = blockIdx.x; g < nseg && ok; g += gridDim.x) {
+                const Segment sg = segment_of(g, a, segs);
+                const int L = sg.len;
+                for (int j = 0; j < L + 2; ++j, ++s) {
+                    const int b = (int)(s % NBUF);
+                    ok = mbar_wait(&full[b], (unsigned)((s / NBUF) & 1));
+                    const int tn = it0 + j;  // tile first touched by this slice
+                    if (ok && j < L && tn >= RBLK)
+                        ok = mbar_wait(&acce[tn % RBLK], (unsigned)((tn / RBLK - 1) & 1));
+                    if (!ok) break;
+                    tc_fence_after_sync();
+                    const int ta = j - 2 > 0 ? j - 2 : 0;
+                    const int tb = j < L - 1 ? j : L - 1;
+                    // split the tile run at the end of the TMEM ring
+                    const int k0 = (it0 + ta) % RBLK;
+                    const int n1 = (tb - ta + 1) < (RBLK - k0) ? (tb - ta + 1) : (RBLK - k0);
+                    const uint32_t sbase = smem_u32(Ss + b * SLICE);
+                    for (int piece = 0; piece < 2; ++piece) {
+                        const int t0 = piece == 0 ? ta : ta + n1;
+                        const int cnt = piece == 0 ? n1 : tb - ta + 1 - n1;
+                        if (cnt <= 0) continue;
+                        const uint32_t dtm = tmem + (uint32_t)(((it0 + t0) % RBLK) * NB);
+                        const int stack0 = t0 - j + 2;  // kz block of the first tile
+                        const uint32_t idesc = idesc_bf16(TM, cnt * NB);
+                        // descriptors of the first operands; every other MMA adds a
+                        // compile-time byte offset / 16 to the start-address field
+                        const uint64_t b0 =
+                            smem_desc(wbase + stack0 * (NB / 8) * CORE, NGS * CORE, CORE);
+                        if constexpr (PAIR) {
+                            const uint64_t a0 = smem_desc(sbase, 0, CORE);
 #pragma unroll
-            for (int j = 0; j < 3; ++j)
+                            for (int p = 0; p < 5; ++p) {
+                                const int ta0 = pair_tap(p, 0), tb0 = pair_tap(p, 1);
+                                const uint32_t off = (ta0 / 3) * ROW + (ta0 % 3) * 16;
+                                const uint32_t lbo = (tb0 / 3) * ROW + (tb0 % 3) * 16 - off;
+                                const uint64_t ad = a0 + (off >> 4) + ((uint64_t)(lbo >> 4) << 16);
+                                const uint64_t bd = b0 + ((2 * p * NGS * CORE) >> 4);
+                                mma_bf16(dtm, ad, bd, idesc, 1u);
+                            }
+                        } else {
+                            const uint64_t a0 = smem_desc(sbase, PLANE, CORE);
 #pragma unroll
-                for (int kk = 0; kk < CIN / 16; ++kk) {
-                    const int tap = grp * 3 + j;
-                    const uint64_t ad = smem_desc(abase + j * 16 + kk * 2 * APITCH, APITCH, CORE);
-                    const uint64_t bd =
-                        smem_desc(wbase + ((tap * KC + 2 * kk) * NG) * CORE, NG * CORE, CORE);
-                    mma_bf16(tmem, ad, bd, IDESC, (grp > 0 || j > 0 || kk > 0) ? 1u : 0u);
+                            for (int dy = 0; dy < 3; ++dy)
+#pragma unroll
+                                for (int dx = 0; dx < 3; ++dx)
+#pragma unroll
+                                    for (int kk = 0; kk < CIN / 16; ++kk) {
+                                        const int dyx = dy * 3 + dx;
+                                        const uint64_t ad =
+                                            a0 + ((dy * ROW + dx * 16 + kk * 2 * PLANE) >> 4);
+                                        const uint64_t bd =
+                                            b0 + (((dyx * KC + 2 * kk) * NGS * CORE) >> 4);
+                                        mma_bf16(dtm, ad, bd, idesc, 1u);
+                                    }
+                        }
+                    }
+                    mma_commit(&empty[b]);
+                    if (j >= 2) mma_commit(&accf[(it0 + j - 2) % RBLK]);  // its third slice
                 }
-            mma_commit(&bar[G & 1]);
-        }
-        if (grp == 8) {  // tile complete: epilogue
-            const bool ok = mbar_wait(&bar[G & 1], (G >> 1) & 1);
-            if (__syncthreads_or(!ok)) {
-                abort = true;
-                break;
+                it0 += L;
             }
-            tc_fence_after_sync();
-            float v[32];
-            tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16), v);
-            tc_fence_before_sync();
-            const int tile = (int)blockIdx.x + (G / 9) * (int)gridDim.x;
-            const int row = tile / segs, seg = tile - row * segs;
-            const int y = row % a.ny, z = row / a.ny;
-            const int x = seg * TM + warp * 32 + (tid & 31);
-            if (x < a.nx) {
-                const long long p = ((long long)z * a.ny + y) * a.nx + x;
+            if (!ok) atomicExch(a.err, 1u);
+            // no MMA may be in flight when TMEM is freed: a final commit covers all
+            mma_commit(&fin);
+            mbar_wait(&fin, 0);
+        }
+    } else {  // ---- epilogue: warps 0-3, TMEM lanes 32 warp .. 32 warp + 31
+        float bias[COUT];
+#pragma unroll
+        for (int c = 0; c < COUT; ++c) bias[c] = a.bias[c];
+        int it = 0;
+        bool ok = true;
+        for (long long g = blockIdx.x; g < nseg && ok; g += gridDim.x) {
+            const Segment sg = segment_of(g, a, segs);
+            const int x = sg.seg * TM + warp * 32 + lane;
+            for (int i = 0; i < sg.len; ++i, ++it) {
+                const int kb = it % RBLK;
+                ok = __all_sync(0xffffffffu, mbar_wait(&accf[kb], (unsigned)((it / RBLK) & 1)));
+                if (!ok) break;
+                tc_fence_after_sync();
+                const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(kb * NB);
+                float v[NB];
+                if constexpr (NB == 32)
+                    tmem_ld32(taddr, v);
+                else
+                    tmem_ld16(taddr, v);
+                tmem_zero<NB>(taddr);
+                tc_fence_before_sync();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&acce[kb]);
+                if (x >= a.nx) continue;
+                const int z = sg.z0 + i;
                 if (EPI == EPI_RELU_BF16) {
                     __align__(16) bf16 o[COUT];
 #pragma unroll
-                    for (int c = 0; c < COUT; ++c)
-                        o[c] = __float2bfloat16_rn(fmaxf(v[c] + a.bias[c], 0.f));
-                    uint4 *dst = reinterpret_cast<uint4 *>(static_cast<bf16 *>(a.y) + p * COUT);
+                    for (int c = 0; c < COUT; ++c) o[c] = __float2bfloat16_rn(fmaxf(v[c] + bias[c], 0.f));
+                    bf16 *Y = static_cast<bf16 *>(a.y);
 #pragma unroll
-                    for (int c = 0; c < COUT / 8; ++c) dst[c] = reinterpret_cast<const uint4 *>(o)[c];
+                    for (int kc = 0; kc < COUT / 8; ++kc) {
+                        const uint4 val = reinterpret_cast<const uint4 *>(o)[kc];
+                        bf16 *plane =
+                            Y + ((((long long)z * a.ny + sg.y) * (COUT / 8) + kc) * (a.nx + 2)) * 8;
+                        *reinterpret_cast<uint4 *>(plane + (long long)(x + 1) * 8) = val;
+                        if (x == 0) *reinterpret_cast<uint4 *>(plane + (long long)(a.nx + 1) * 8) = val;
+                        if (x == a.nx - 1) *reinterpret_cast<uint4 *>(plane) = val;
+                    }
                 } else {
+                    const long long p = ((long long)z * a.ny + sg.y) * a.nx + x;
                     __align__(16) float o[COUT];
 #pragma unroll
-                    for (int c = 0; c < COUT; ++c) o[c] = v[c] + a.bias[c];
-                    float4 *dst = reinterpret_cast<float4 *>(static_cast<float *>(a.y) + p * COUT);
+                    for (int c = 0; c < COUT; ++c) o[c] = v[c] + bias[c];
+                    float4 *d = reinterpret_cast<float4 *>(static_cast<float *>(a.y) + p * COUT);
 #pragma unroll
-                    for (int c = 0; c < COUT / 4; ++c) dst[c] = reinterpret_cast<const float4 *>(o)[c];
+                    for (int c = 0; c < COUT / 4; ++c) d[c] = reinterpret_cast<const float4 *>(o)[c];
                 }
             }
         }
+        if (!ok && lane == 0) atomicExch(a.err, 1u);
     }
-    cp_wait<0>();
-    if (abort && tid == 0) atomicExch(a.err, 1u);
     tc_fence_before_sync();
     __syncthreads();
-    if (warp == 0) tmem_dealloc(tmem, 32);
+    if (warp == 0) tmem_dealloc(tmem, TCOLS);
 }
 
-// Weight image for conv_tc_kernel from binary32 W[cout][cin_real][27].
+// Weight image for conv_tc_kernel from binary32 W[cout][cin_real][27] (tap =
+// 9 kz + 3 ky + kx); nb = accumulator columns per tile (COUT padded to 16);
+// cin = 8 gives the tap-pair image.
 __global__ void conv_tc_prep_kernel(const float *__restrict__ W, int cout, int cin_real, int cin,
-                                    int npad, bf16 *__restrict__ img) {
-    const int KC = cin / 8, NG = npad / 8;
-    const int total = 27 * cin * npad;
+                                    int nb, bf16 *__restrict__ img) {
+    const int KC = cin / 8, NGS = 3 * nb / 8;
+    const bool pair = cin == 8;
+    const int total = (pair ? 10 : 9 * KC) * NGS * 64;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x) {
         const int c = i & 7, r = (i >> 3) & 7;
-        const int rest = i >> 6;  // (tap * KC + kc) * NG + ng
-        const int ng = rest % NG;
-        const int kc = (rest / NG) % KC;
-        const int tap = rest / (NG * KC);
-        const int co = 8 * ng + r, ci = 8 * kc + c;
-        const float v = (co < cout && ci < cin_real) ? W[((long long)co * cin_real + ci) * 27 + tap] : 0.f;
+        const int rest = i >> 6;  // kq * NGS + ng
+        const int ng = rest % NGS;
+        const int kq = rest / NGS;
+        int dyx, ci;
+        bool live = true;
+        if (pair) {
+            const int p = kq >> 1, h = kq & 1;
+            dyx = pair_tap(p, h);
+            ci = c;
+            live = !(p == 4 && h == 0);
+        } else {
+            dyx = kq / KC;
+            ci = 8 * (kq % KC) + c;
+        }
+        const int row = 8 * ng + r;
+        const int kz = 2 - row / nb, co = row % nb;
+        const float v = (live && co < cout && ci < cin_real)
+                            ? W[((long long)co * cin_real + ci) * 27 + kz * 9 + dyx]
+                            : 0.f;
         img[i] = __float2bfloat16_rn(v);
     }
 }

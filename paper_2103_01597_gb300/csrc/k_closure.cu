@@ -12,7 +12,9 @@
 // one-cell halo is staged once per (dy, dz) tap group and serves the three dx
 // taps by shifting the window.  Activations are channel-major [C][N]
 // (N = nx ny nz, x fastest), like the solver's fields.
+#include <cuda.h>
 #include <cuda_bf16.h>
+#include <cudaTypedefs.h>
 #include <math.h>
 #include <stdint.h>
 #include <string.h>
@@ -293,11 +295,12 @@ struct W8 {
 };
 __global__ void pack_input_kernel(F8 f, const float *__restrict__ inv_scale, long long n,
                                   bf16 *__restrict__ x) {
-    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < 8 * n;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < 16 * n;
          t += (long long)gridDim.x * blockDim.x) {
         const int c = (int)(t / n);
         const long long p = t - c * n;
-        x[t] = __float2bfloat16_rn(f.p[c][p] * inv_scale[c]);
+        // channels 8..15 are zero padding (the buffer is shared with the row-planar layout)
+        x[t] = c < 8 ? __float2bfloat16_rn(f.p[c][p] * inv_scale[c]) : __float2bfloat16_rn(0.f);
     }
 }
 
@@ -326,36 +329,50 @@ __global__ void loss_grad_kernel(const float *__restrict__ y, F8 tgt,
     if (threadIdx.x == 0) partials[blockIdx.x] = sh[0];
 }
 
-// Index of (channel c, cell p) in the eight-channel output: channel-major
-// [8][n] or channels-last [n][8].
-__device__ __forceinline__ long long yidx(int c, long long p, long long n, int cl) {
-    return cl ? p * 8 + c : (long long)c * n + p;
+// Eight binary32 output channels of cell p: channel-major y[c * n + p] or
+// channels-last y[p * 8 + c] (two 16-byte loads).
+__device__ __forceinline__ void load8(const float *__restrict__ y, long long p, long long n, int cl,
+                                      float (&v)[8]) {
+    if (cl) {
+        const float4 a = reinterpret_cast<const float4 *>(y + p * 8)[0];
+        const float4 b = reinterpret_cast<const float4 *>(y + p * 8)[1];
+        v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
+        v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
+    } else {
+#pragma unroll
+        for (int c = 0; c < 8; ++c) v[c] = y[(long long)c * n + p];
+    }
 }
 
 // out[c] = out_scale[c] * y[c]
 __global__ void scale_output_kernel(const float *__restrict__ y, const float *__restrict__ out_scale,
                                     long long n, W8 out, int cl) {
-    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < 8 * n;
-         t += (long long)gridDim.x * blockDim.x) {
-        const int c = (int)(t / n);
-        const long long p = t - c * n;
-        out.p[c][p] = out_scale[c] * y[yidx(c, p, n, cl)];
+    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < n;
+         p += (long long)gridDim.x * blockDim.x) {
+        float v[8];
+        load8(y, p, n, cl, v);
+#pragma unroll
+        for (int c = 0; c < 8; ++c) out.p[c][p] = out_scale[c] * v[c];
     }
 }
 
-// Channels-last network input: x[p][c] = f[c][p] / in_scale[c] (channels 8..15 zero).
-__global__ void pack_input_cl_kernel(F8 f, const float *__restrict__ inv_scale, long long n,
-                                     bf16 *__restrict__ x) {
+// Row-planar network input for the tensor-memory kernels (layout in conv_tc.cuh,
+// one plane of 8 channels): f[c] / in_scale[c] as bfloat16; cells x = 0 and
+// nx - 1 are also written to the periodic halo slots.
+__global__ void pack_input_rp_kernel(F8 f, const float *__restrict__ inv_scale, int nx,
+                                     long long n, bf16 *__restrict__ x) {
     for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < n;
          p += (long long)gridDim.x * blockDim.x) {
-        __align__(16) bf16 v[16];
+        const long long row = p / nx;  // z * ny + y
+        const int xi = (int)(p - row * nx);
+        __align__(16) bf16 v[8];
 #pragma unroll
         for (int c = 0; c < 8; ++c) v[c] = __float2bfloat16_rn(f.p[c][p] * inv_scale[c]);
-#pragma unroll
-        for (int c = 8; c < 16; ++c) v[c] = __float2bfloat16_rn(0.f);
-        uint4 *dst = reinterpret_cast<uint4 *>(x + p * 16);
-        dst[0] = reinterpret_cast<const uint4 *>(v)[0];
-        dst[1] = reinterpret_cast<const uint4 *>(v)[1];
+        const uint4 val = *reinterpret_cast<const uint4 *>(v);
+        uint4 *p0 = reinterpret_cast<uint4 *>(x + row * (nx + 2) * 8);
+        p0[xi + 1] = val;
+        if (xi == 0) p0[nx + 1] = val;
+        if (xi == nx - 1) p0[0] = val;
     }
 }
 
@@ -364,11 +381,15 @@ __global__ void correction_max_kernel(const float *__restrict__ y,
                                       const float *__restrict__ out_scale, long long n,
                                       unsigned long long *gmax, int cl) {
     double m = 0.0;
-    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < 8 * n;
-         t += (long long)gridDim.x * blockDim.x) {
-        const int c = (int)(t / n);
-        const double v = fabs((double)(out_scale[c] * y[yidx(c, t - c * n, n, cl)]));
-        m = (v > m || v != v) ? v : m;
+    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < n;
+         p += (long long)gridDim.x * blockDim.x) {
+        float v[8];
+        load8(y, p, n, cl, v);
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+            const double a = fabs((double)(out_scale[c] * v[c]));
+            m = (a > m || a != a) ? a : m;
+        }
     }
     unsigned long long bits = (unsigned long long)__double_as_longlong(m);
     for (int o = 16; o > 0; o >>= 1) {
@@ -384,11 +405,12 @@ __global__ void apply_correction_kernel(W8 f, const float *__restrict__ y,
                                         const unsigned long long *gmax, double limit, int cl) {
     const double m = __longlong_as_double((long long)*gmax);
     if (!(m <= limit)) return;
-    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < 8 * n;
-         t += (long long)gridDim.x * blockDim.x) {
-        const int c = (int)(t / n);
-        const long long p = t - c * n;
-        f.p[c][p] += out_scale[c] * y[yidx(c, p, n, cl)];
+    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < n;
+         p += (long long)gridDim.x * blockDim.x) {
+        float v[8];
+        load8(y, p, n, cl, v);
+#pragma unroll
+        for (int c = 0; c < 8; ++c) f.p[c][p] += out_scale[c] * v[c];
     }
 }
 
@@ -467,11 +489,14 @@ struct ac_closure {
     bf16 *wf1, *wf2, *wf3, *wb3, *wb2;
     bf16 *x0, *a1, *a2, *dy, *dz2, *dz1;
     float *y;
-    // tcgen05 forward: weight images; channels-last activations alias x0, a1, a2, y
+    // tcgen05 forward: weight images, tensor maps of the row-planar inputs of the
+    // three layers (x0, a1, a2 hold the row-planar activations on this path)
     int conv_path;
     bf16 *img1, *img2, *img3;
     unsigned *tc_err;
     int tc_grid[3];
+    int tc_zc;
+    CUtensorMap tc_map[3];
     float *part;
     double *lossp;
     double *loss_host;
@@ -502,20 +527,51 @@ static cudaError_t tc_grid_for(const ac_closure *c, int sms, int *grid) {
     if (e == cudaSuccess)
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, tc::THREADS, bytes);
     if (e != cudaSuccess) return e;
-    const long long tiles = (long long)c->g.ny * c->g.nz * ((c->g.nx + tc::TM - 1) / tc::TM);
+    // an SM's 512 TMEM columns bound the resident CTAs too (each allocates RBLK blocks)
+    const int tcols = tc::RBLK * (COUT < 16 ? 16 : COUT);
+    if (per_sm > 512 / tcols) per_sm = 512 / tcols;
+    const long long segs = (long long)((c->g.nz + c->tc_zc - 1) / c->tc_zc) * c->g.ny *
+                           ((c->g.nx + tc::TM - 1) / tc::TM);
     long long g = (long long)(per_sm < 1 ? 1 : per_sm) * sms;
-    *grid = (int)(g < tiles ? g : tiles);
+    *grid = (int)(g < segs ? g : segs);
     return cudaSuccess;
 }
 
-// Dynamic shared memory limits and persistent grid sizes of the three layers.
+// Tensor map of a row-planar activation with KC groups of 8 channels: dims
+// (8 channels, nx + 2 cells, KC, ny, nz), box (8, 130, KC, 1, 1).
+static cudaError_t tc_encode(PFN_cuTensorMapEncodeTiled_v12000 enc, const ac_closure *c, void *base,
+                             int kc, CUtensorMap *map) {
+    const cuuint64_t nxp = (cuuint64_t)c->g.nx + 2;
+    const cuuint64_t dims[5] = {8, nxp, (cuuint64_t)kc, (cuuint64_t)c->g.ny, (cuuint64_t)c->g.nz};
+    const cuuint64_t strides[4] = {16, 16 * nxp, 16 * nxp * kc, 16 * nxp * kc * c->g.ny};
+    const cuuint32_t box[5] = {8, tc::TM + 2, (cuuint32_t)kc, 1, 1};
+    const cuuint32_t estr[5] = {1, 1, 1, 1, 1};
+    const CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, base, dims, strides, box, estr,
+                           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                           CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+// Dynamic shared memory limits, persistent grid sizes and tensor maps of the
+// three layers.
 static cudaError_t tc_setup(ac_closure *c) {
     int dev = 0, sms = 0;
+    c->tc_zc = c->g.nz < 16 ? c->g.nz : 16;
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (e == cudaSuccess) e = tc_grid_for<16, 32, tc::EPI_RELU_BF16>(c, sms, &c->tc_grid[0]);
+    if (e == cudaSuccess) e = tc_grid_for<8, 32, tc::EPI_RELU_BF16>(c, sms, &c->tc_grid[0]);
     if (e == cudaSuccess) e = tc_grid_for<32, 32, tc::EPI_RELU_BF16>(c, sms, &c->tc_grid[1]);
     if (e == cudaSuccess) e = tc_grid_for<32, 8, tc::EPI_LINEAR_F32>(c, sms, &c->tc_grid[2]);
+    void *fn = nullptr;
+    cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+    if (e == cudaSuccess)
+        e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q);
+    if (e == cudaSuccess && (q != cudaDriverEntryPointSuccess || !fn)) e = cudaErrorNotSupported;
+    if (e != cudaSuccess) return e;
+    auto enc = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+    e = tc_encode(enc, c, c->x0, 1, &c->tc_map[0]);
+    if (e == cudaSuccess) e = tc_encode(enc, c, c->a1, 4, &c->tc_map[1]);
+    if (e == cudaSuccess) e = tc_encode(enc, c, c->a2, 4, &c->tc_map[2]);
     return e;
 }
 
@@ -544,8 +600,11 @@ extern "C" int ac_closure_init(ac_closure **out, int nx, int ny, int nz, void *s
     const size_t fbytes = sizeof(float) * (4 * np + 64) + wbytes + 256;
     c->lossblocks = 304;
     const size_t part_floats = (size_t)9 * CL_WG_CTAS * 32 * 96;
-    const size_t abytes = 2 * (size_t)n * (16 + 32 + 32 + 16 + 32 + 32) + 4 * (size_t)n * 8 +
-                          4 * part_floats + 8 * (size_t)c->lossblocks + 8 + 1024;
+    // x0, a1, a2 hold either channel-major [C][n] or row-planar [rows][C/8][nx+2][8]
+    // activations: sized for the larger (row-planar, np2 cells per channel)
+    const long long np2 = (long long)(nx + 2) * ny * nz;
+    const size_t abytes = 2 * (size_t)np2 * (16 + 32 + 32) + 2 * (size_t)n * (16 + 32 + 32) +
+                          4 * (size_t)n * 8 + 4 * part_floats + 8 * (size_t)c->lossblocks + 8 + 1024;
     cudaError_t e = cudaMalloc(&c->block, fbytes);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->block, 0, fbytes, c->stream);
     if (e == cudaSuccess) e = cudaMalloc(&c->act_block, abytes);
@@ -574,9 +633,9 @@ extern "C" int ac_closure_init(ac_closure **out, int nx, int ny, int nz, void *s
     c->img3 = c->img2 + 27 * 32 * 32;
     char *a = static_cast<char *>(c->act_block);
     c->x0 = reinterpret_cast<bf16 *>(a);
-    c->a1 = c->x0 + 16 * n;
-    c->a2 = c->a1 + 32 * n;
-    c->dy = c->a2 + 32 * n;
+    c->a1 = c->x0 + 16 * np2;
+    c->a2 = c->a1 + 32 * np2;
+    c->dy = c->a2 + 32 * np2;
     c->dz2 = c->dy + 16 * n;
     c->dz1 = c->dz2 + 32 * n;
     c->y = reinterpret_cast<float *>(c->dz1 + 32 * n);
@@ -612,7 +671,7 @@ static int prep_weights(ac_closure *c) {
     prep_weights_kernel<<<32, 256, 0, c->stream>>>(c->params + P_W1, 32, 8, 16, c->wf1, 0, nullptr);
     prep_weights_kernel<<<128, 256, 0, c->stream>>>(c->params + P_W2, 32, 32, 32, c->wf2, 32, c->wb2);
     prep_weights_kernel<<<32, 256, 0, c->stream>>>(c->params + P_W3, 8, 32, 32, c->wf3, 16, c->wb3);
-    tc::conv_tc_prep_kernel<<<64, 256, 0, c->stream>>>(c->params + P_W1, 32, 8, 16, 32, c->img1);
+    tc::conv_tc_prep_kernel<<<16, 256, 0, c->stream>>>(c->params + P_W1, 32, 8, 8, 32, c->img1);
     tc::conv_tc_prep_kernel<<<128, 256, 0, c->stream>>>(c->params + P_W2, 32, 32, 32, 32, c->img2);
     tc::conv_tc_prep_kernel<<<64, 256, 0, c->stream>>>(c->params + P_W3, 8, 32, 32, 16, c->img3);
     c->launches += 6;
@@ -664,58 +723,74 @@ extern "C" int ac_closure_set_scales(ac_closure *c, const float in_scale[8], con
     return AC_OK;
 }
 
-static int run_forward(ac_closure *c, const float *const in[8]) {
+// ev (optional): events recorded before the input pack and after the pack and
+// each convolution launch (five of the six that ac_closure_forward_timings uses).
+static inline void mark(cudaEvent_t *ev, int i, cudaStream_t st) {
+    if (ev) cudaEventRecord(ev[i], st);
+}
+
+static int run_forward(ac_closure *c, const float *const in[8], cudaEvent_t *ev = nullptr) {
     const ConvGeom g = c->g;
     F8 f;
     for (int i = 0; i < 8; ++i) f.p[i] = in[i];
-    pack_input_kernel<<<cl_grid(8 * g.n), 256, 0, c->stream>>>(f, c->scales, g.n, c->x0);
+    mark(ev, 0, c->stream);
+    pack_input_kernel<<<cl_grid(16 * g.n), 256, 0, c->stream>>>(f, c->scales, g.n, c->x0);
+    mark(ev, 1, c->stream);
     const unsigned ctas = (unsigned)((long long)g.ny * g.nz * ((g.nx + CL_TM - 1) / CL_TM));
     conv_fwd_kernel<16, 32, EPI_RELU_BF16><<<ctas, CL_THREADS, 0, c->stream>>>(
         c->x0, c->wf1, c->params + P_B1, nullptr, c->a1, g);
+    mark(ev, 2, c->stream);
     conv_fwd_kernel<32, 32, EPI_RELU_BF16><<<ctas, CL_THREADS, 0, c->stream>>>(
         c->a1, c->wf2, c->params + P_B2, nullptr, c->a2, g);
+    mark(ev, 3, c->stream);
     conv_fwd_kernel<32, 8, EPI_LINEAR_F32><<<ctas, CL_THREADS, 0, c->stream>>>(
         c->a2, c->wf3, c->params + P_B3, nullptr, c->y, g);
+    mark(ev, 4, c->stream);
     c->launches += 4;
     CCK(cudaGetLastError());
     return AC_OK;
 }
 
 template <int CIN, int COUT, int EPI>
-static void launch_tc(const ac_closure *c, int grid, const bf16 *x, const bf16 *img, const float *bias,
-                      void *y) {
+static void launch_tc(const ac_closure *c, int layer, const bf16 *img, const float *bias, void *y) {
     tc::ConvTcArgs a;
-    a.x = x;
     a.w = img;
     a.bias = bias;
     a.y = y;
     a.nx = c->g.nx;
     a.ny = c->g.ny;
     a.nz = c->g.nz;
-    a.tiles = (int)((long long)c->g.ny * c->g.nz * ((c->g.nx + tc::TM - 1) / tc::TM));
+    a.zc = c->tc_zc;
     a.err = c->tc_err;
     tc::conv_tc_kernel<CIN, COUT, EPI>
-        <<<grid, tc::THREADS, tc::smem_bytes(CIN, COUT < 16 ? 16 : COUT), c->stream>>>(a);
+        <<<c->tc_grid[layer], tc::THREADS, tc::smem_bytes(CIN, COUT < 16 ? 16 : COUT), c->stream>>>(
+            c->tc_map[layer], a);
 }
 
-// Forward pass on the tcgen05 kernels; leaves channels-last [n][8] binary32 in c->y.
-static int run_forward_tc(ac_closure *c, const float *const in[8]) {
+// Forward pass on the tcgen05 kernels (row-planar activations in x0, a1, a2);
+// leaves channels-last [n][8] binary32 in c->y.
+static int run_forward_tc(ac_closure *c, const float *const in[8], cudaEvent_t *ev = nullptr) {
     const ConvGeom g = c->g;
     F8 f;
     for (int i = 0; i < 8; ++i) f.p[i] = in[i];
-    pack_input_cl_kernel<<<cl_grid(g.n), 256, 0, c->stream>>>(f, c->scales, g.n, c->x0);
-    launch_tc<16, 32, tc::EPI_RELU_BF16>(c, c->tc_grid[0], c->x0, c->img1, c->params + P_B1, c->a1);
-    launch_tc<32, 32, tc::EPI_RELU_BF16>(c, c->tc_grid[1], c->a1, c->img2, c->params + P_B2, c->a2);
-    launch_tc<32, 8, tc::EPI_LINEAR_F32>(c, c->tc_grid[2], c->a2, c->img3, c->params + P_B3, c->y);
+    mark(ev, 0, c->stream);
+    pack_input_rp_kernel<<<cl_grid(g.n), 256, 0, c->stream>>>(f, c->scales, g.nx, g.n, c->x0);
+    mark(ev, 1, c->stream);
+    launch_tc<8, 32, tc::EPI_RELU_BF16>(c, 0, c->img1, c->params + P_B1, c->a1);
+    mark(ev, 2, c->stream);
+    launch_tc<32, 32, tc::EPI_RELU_BF16>(c, 1, c->img2, c->params + P_B2, c->a2);
+    mark(ev, 3, c->stream);
+    launch_tc<32, 8, tc::EPI_LINEAR_F32>(c, 2, c->img3, c->params + P_B3, c->y);
+    mark(ev, 4, c->stream);
     c->launches += 4;
     CCK(cudaGetLastError());
     return AC_OK;
 }
 
 // Inference forward on the selected path; *cl = 1 if c->y is channels-last.
-static int run_inference(ac_closure *c, const float *const in[8], int *cl) {
+static int run_inference(ac_closure *c, const float *const in[8], int *cl, cudaEvent_t *ev = nullptr) {
     *cl = c->conv_path == AC_CONV_TCGEN05;
-    return *cl ? run_forward_tc(c, in) : run_forward(c, in);
+    return *cl ? run_forward_tc(c, in, ev) : run_forward(c, in, ev);
 }
 
 extern "C" int ac_closure_set_conv_path(ac_closure *c, int path) {
@@ -750,12 +825,42 @@ extern "C" int ac_closure_forward(ac_closure *c, const float *const in[8], float
     if (out) {
         W8 o;
         for (int i = 0; i < 8; ++i) o.p[i] = out[i];
-        scale_output_kernel<<<cl_grid(8 * c->g.n), 256, 0, c->stream>>>(c->y, c->scales + 8, c->g.n, o,
+        scale_output_kernel<<<cl_grid(c->g.n), 256, 0, c->stream>>>(c->y, c->scales + 8, c->g.n, o,
                                                                         cl);
         c->launches++;
         CCK(cudaGetLastError());
     }
     return AC_OK;
+}
+
+extern "C" int ac_closure_forward_timings(ac_closure *c, const float *const in[8],
+                                          float *const out[8], float ms[5]) {
+    if (!c || !in || !out || !ms) return AC_ERR_ARG;
+    for (int i = 0; i < 8; ++i)
+        if (!in[i] || !out[i]) return AC_ERR_ARG;
+    cudaEvent_t ev[6] = {};
+    int rc = AC_OK;
+    cudaError_t e = cudaSuccess;
+    for (int i = 0; i < 6 && e == cudaSuccess; ++i) e = cudaEventCreate(&ev[i]);
+    if (e == cudaSuccess) {
+        int cl = 0;
+        rc = run_inference(c, in, &cl, ev);
+        if (rc == AC_OK) {
+            W8 o;
+            for (int i = 0; i < 8; ++i) o.p[i] = out[i];
+            scale_output_kernel<<<cl_grid(c->g.n), 256, 0, c->stream>>>(c->y, c->scales + 8,
+                                                                            c->g.n, o, cl);
+            c->launches++;
+            e = cudaGetLastError();
+            if (e == cudaSuccess) e = cudaEventRecord(ev[5], c->stream);
+            if (e == cudaSuccess) e = cudaEventSynchronize(ev[5]);
+            for (int i = 0; i < 5 && e == cudaSuccess; ++i) e = cudaEventElapsedTime(&ms[i], ev[i], ev[i + 1]);
+        }
+    }
+    for (int i = 0; i < 6; ++i)
+        if (ev[i]) cudaEventDestroy(ev[i]);
+    if (rc == AC_OK && e != cudaSuccess) rc = ac_report_cuda(e);
+    return rc;
 }
 
 extern "C" int ac_closure_backward(ac_closure *c, const float *const in[8],
@@ -840,9 +945,9 @@ extern "C" int ac_closure_apply(ac_closure *c, ac_handle *h, double limit, int *
     rc = run_inference(c, in, &cl);
     if (rc) return rc;
     CCK(cudaMemsetAsync(c->guard, 0, sizeof(unsigned long long), c->stream));
-    correction_max_kernel<<<cl_grid(8 * c->g.n), 256, 0, c->stream>>>(c->y, c->scales + 8, c->g.n,
+    correction_max_kernel<<<cl_grid(c->g.n), 256, 0, c->stream>>>(c->y, c->scales + 8, c->g.n,
                                                                       c->guard, cl);
-    apply_correction_kernel<<<cl_grid(8 * c->g.n), 256, 0, c->stream>>>(f, c->y, c->scales + 8,
+    apply_correction_kernel<<<cl_grid(c->g.n), 256, 0, c->stream>>>(f, c->y, c->scales + 8,
                                                                         c->g.n, c->guard, limit, cl);
     c->launches += 2;
     CCK(cudaGetLastError());
