@@ -329,8 +329,9 @@ int ac_closure_set_scales(ac_closure *c, const float in_scale[8], const float ou
  * out == NULL keeps the result inside the closure). */
 int ac_closure_forward(ac_closure *c, const float *const in[8], float *const out[8]);
 /* As ac_closure_forward (out required), and ms[0..4] receives the device time
- * of each of its five launches (input pack, convolution layers 1, 2, 3, output
- * scale) from CUDA events on the closure's stream; synchronises. */
+ * of each of its launches (input pack, convolution layers 1, 2, 3, output
+ * scaling) from CUDA events on the closure's stream; synchronises.  On the
+ * tcgen05 path layer 3 scales in its epilogue and ms[4] is the empty interval. */
 int ac_closure_forward_timings(ac_closure *c, const float *const in[8], float *const out[8],
                                float ms[5]);
 /* Forward, loss against `target` (physical units, device arrays) and

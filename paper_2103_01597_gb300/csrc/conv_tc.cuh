@@ -4,14 +4,17 @@
 // accumulators in tensor memory (TMEM).
 //
 // Activation layout ("row-planar", RP): bfloat16, for each row (y, z) and each
-// group kc of 8 channels a plane of nx + 2 cells x 16 bytes, the cells being
-// x = nx-1, 0, 1, ..., nx-1, 0 (the periodic x halo stored with the row):
-//     a[(((z * ny + y) * KC + kc) * (nx + 2) + x + 1) * 8 + c]  = channel 8 kc + c.
-// A TMA box of 8 channels x 130 cells x KC planes then lands in shared memory
-// as KC planes of 130 consecutive 16-byte rows, which is the canonical K-major
-// no-swizzle operand layout (core matrices of 8 cells x 8 channels) with
-// M-direction core-matrix stride 128 bytes and K-direction stride 2080 bytes;
-// the three dx taps of a row are the same operand started 0, 1 or 2 cells in.
+// group kc of 8 channels a plane of nxp = roundup(nx + 2, 8) cells x 16 bytes,
+// the first nx + 2 being x = nx-1, 0, 1, ..., nx-1, 0 (the periodic x halo is
+// stored with the row; the rest is padding):
+//     a[(((z * ny + y) * KC + kc) * nxp + x + 1) * 8 + c]  = channel 8 kc + c.
+// The TMA sees a plane as rows of 128 bytes (8 cells x 8 channels), so every
+// request is a whole line.  A box of 17 such rows x KC planes lands in shared
+// memory as KC planes of 136 consecutive 16-byte cell rows, which is the
+// canonical K-major no-swizzle operand layout (core matrices of 8 cells x 8
+// channels) with M-direction core-matrix stride 128 bytes and K-direction
+// stride 2176 bytes; the three dx taps of a row are the same operand started
+// 0, 1 or 2 cells in (rows 130..135 are staged but never read).
 //
 // An output tile is 128 cells of one x-row (GEMM M = 128) for all output
 // channels (N = COUT, padded to 16); K = 27 taps x CIN.  Warp roles in a
@@ -38,7 +41,8 @@ using bf16 = __nv_bfloat16;
 constexpr int TM = 128;          // cells per tile (GEMM M)
 constexpr int THREADS = 192;     // warps 0-3 epilogue (one TMEM lane quadrant each), 4 TMA, 5 MMA
 constexpr int CORE = 128;        // bytes of one core matrix (8 rows x 16 B)
-constexpr int PLANE = (TM + 2) * 16;  // bytes of one staged 8-channel plane (130 cells)
+constexpr int PCELLS = TM + 8;          // cells of a staged plane (130 used)
+constexpr int PLANE = PCELLS * 16;      // bytes of one staged 8-channel plane
 constexpr int NBUF = 6;          // z-slices in the shared-memory ring
 constexpr unsigned WAIT_LIMIT = 1u << 24;  // polls of an mbarrier before giving up
 
@@ -66,6 +70,35 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, unsigned parity) {
         if (done) return true;
     }
     return false;
+}
+
+// Non-blocking test of one mbarrier phase.
+__device__ __forceinline__ bool mbar_test(uint32_t bar_addr, unsigned parity) {
+    uint32_t done;
+    asm volatile(
+        "{\n .reg .pred p;\n"
+        " mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(bar_addr), "r"(parity)
+        : "memory");
+    return done != 0;
+}
+
+// Wait for the mbarrier phases (addr[k], par[k]) whose bit k is set in
+// `pending`, all at once: the tests of one round are independent, so their
+// shared-memory latencies overlap.  False on timeout.
+template <int N>
+__device__ __forceinline__ bool mbar_wait_all(const uint32_t (&addr)[N], const unsigned (&par)[N],
+                                              uint32_t pending) {
+    for (unsigned it = 0; it < WAIT_LIMIT && pending; ++it) {
+        uint32_t done = 0;
+#pragma unroll
+        for (int k = 0; k < N; ++k)
+            if ((pending >> k) & 1u) done |= (uint32_t)mbar_test(addr[k], par[k]) << k;
+        pending &= ~done;
+    }
+    return pending == 0;
 }
 
 __device__ __forceinline__ void fence_proxy_async_smem() {
@@ -220,10 +253,16 @@ __device__ __forceinline__ void bulk_load(void *dst, const void *src, uint32_t b
         : "memory");
 }
 
-enum { EPI_RELU_BF16 = 0, EPI_LINEAR_F32 = 1 };
+// Epilogues: ReLU to row-planar bfloat16 (hidden layers), or the network output
+// scaled per channel to eight binary32 channel-major arrays (optionally with the
+// largest |value|, NaN counting as largest, folded into a guard word).
+enum { EPI_RELU_BF16 = 0, EPI_SCALED_F32 = 1 };
 
 // Bytes of one staged row (KC planes, rounded up so rows stay 128-byte aligned).
-__host__ __device__ constexpr int row_bytes(int cin) { return ((cin / 8) * PLANE + 127) / 128 * 128; }
+__host__ __device__ constexpr int row_bytes(int cin) { return (cin / 8) * PLANE; }
+
+// Padded row length (cells) of the row-planar layout.
+__host__ __device__ constexpr int rp_cells(int nx) { return (nx + 2 + 7) / 8 * 8; }
 
 // Bytes of the kz-stacked weight image (nb accumulator columns per tile): nine
 // (ky, kx) taps x cin channels, or, for cin = 8, five tap pairs x 16 channels.
@@ -247,7 +286,10 @@ __host__ __device__ constexpr int pair_tap(int p, int h) {
 struct ConvTcArgs {
     const bf16 *w;        // weights in the shared-memory image order (see prep)
     const float *bias;    // [COUT]
-    void *y;              // output: RP bfloat16 (ReLU layers) or [cells][COUT] binary32 (linear)
+    bf16 *y;              // EPI_RELU_BF16: row-planar output
+    float *out[8];        // EPI_SCALED_F32: channel c to out[c][cell]
+    const float *out_scale;        // EPI_SCALED_F32: [8]
+    unsigned long long *gmax;      // EPI_SCALED_F32: guard word (binary64 bits), or null
     int nx, ny, nz;
     int zc;               // tiles per column segment (z extent of a chunk)
     unsigned *err;        // set non-zero if a bounded wait ran out
@@ -288,7 +330,8 @@ __device__ __forceinline__ Segment segment_of(long long g, const ConvTcArgs &a, 
 // image stacks the three kz blocks along N, [W(kz=2); W(kz=1); W(kz=0)], NB
 // rows each, so the contributions of one slice to up to three tiles are one
 // MMA of N = 3 NB (fewer at segment ends) whose accumulator is three
-// consecutive NB-column blocks of TMEM: tile t of the CTA owns block t % R.
+// consecutive NB-column blocks of TMEM: tile i of a segment owns block i, so
+// the window of a slice never wraps (a segment has at most RBLK tiles).
 // Because one MMA both opens a tile and adds to older ones, MMAs always
 // accumulate, and blocks are zero when handed over: zeroed once at start and
 // again by the epilogue after it reads a tile.  Barriers, each waited on in
@@ -305,7 +348,8 @@ __device__ __forceinline__ Segment segment_of(long long g, const ConvTcArgs &a, 
 // 3 ky + kx) of K-chunk kq: kq = dyx * KC + kc and ci = 8 kc + c, or for
 // CIN = 8, kq = 2 p + h, dyx = pair_tap(p, h) and ci = c; zero for co >= COUT,
 // ci >= cin_real and the zero half of the last pair.
-constexpr int RBLK = 8;  // TMEM accumulator blocks per CTA
+constexpr int RBLK = 16;  // TMEM accumulator blocks per CTA (>= tiles per segment, <= 32)
+constexpr int GROUP = 3;  // slices the MMA issuer waits for at once (<= NBUF / 2)
 
 template <int CIN, int COUT, int EPI>
 __global__ void __launch_bounds__(THREADS, 1)
@@ -373,7 +417,7 @@ __global__ void __launch_bounds__(THREADS, 1)
                     unsigned char *dst = Ss + b * SLICE;
 #pragma unroll
                     for (int r = 0; r < 3; ++r)
-                        tma_load_5d(dst + r * ROW, &xmap, &full[b], 0, sg.seg * TM, 0,
+                        tma_load_5d(dst + r * ROW, &xmap, &full[b], 0, sg.seg * (TM / 8), 0,
                                     wrapi(sg.y + r - 1, a.ny), z);
                 }
             }
@@ -387,68 +431,78 @@ __global__ void __launch_bounds__(THREADS, 1)
         if (lane == 0) {  // ---- MMA issuer
             bool ok = mbar_wait(&wbar, 0);
             long long s = 0;  // slices consumed
-            int it0 = 0;      // CTA tile index of the segment's first tile
+            // per TMEM block: bit k of `used` = block k has held a tile, bit k of
+            // `par` = parity of the number of tiles it has held (registers, not an
+            // indexed array: local memory would sit on the issue path)
+            uint32_t used = 0, par = 0;
             const uint32_t wbase = smem_u32(Ws);
             for (long long g = blockIdx.x; g < nseg && ok; g += gridDim.x) {
                 const Segment sg = segment_of(g, a, segs);
                 const int L = sg.len;
                 for (int j = 0; j < L + 2; ++j, ++s) {
                     const int b = (int)(s % NBUF);
-                    ok = mbar_wait(&full[b], (unsigned)((s / NBUF) & 1));
-                    const int tn = it0 + j;  // tile first touched by this slice
-                    if (ok && j < L && tn >= RBLK)
-                        ok = mbar_wait(&acce[tn % RBLK], (unsigned)((tn / RBLK - 1) & 1));
-                    if (!ok) break;
-                    tc_fence_after_sync();
+                    if (j % GROUP == 0) {
+                        // one combined wait for the next GROUP slices: each landed,
+                        // and each tile they open has been read out of its block
+                        uint32_t addr[2 * GROUP];
+                        unsigned want[2 * GROUP];
+                        uint32_t pending = 0;
+#pragma unroll
+                        for (int q = 0; q < GROUP; ++q) {
+                            const long long sq = s + q;
+                            const int jq = j + q;
+                            addr[2 * q] = smem_u32(&full[sq % NBUF]);
+                            want[2 * q] = (unsigned)((sq / NBUF) & 1);
+                            addr[2 * q + 1] = smem_u32(&acce[jq < RBLK ? jq : 0]);
+                            want[2 * q + 1] = ((par >> jq) & 1u) ^ 1u;
+                            if (jq < L + 2) pending |= 1u << (2 * q);
+                            if (jq < L && ((used >> jq) & 1u)) pending |= 1u << (2 * q + 1);
+                        }
+                        ok = mbar_wait_all(addr, want, pending);
+                        if (!ok) break;
+                        tc_fence_after_sync();
+                    }
+                    if (j < L) {  // tile j opens in block j
+                        used |= 1u << j;
+                        par ^= 1u << j;
+                    }
                     const int ta = j - 2 > 0 ? j - 2 : 0;
                     const int tb = j < L - 1 ? j : L - 1;
-                    // split the tile run at the end of the TMEM ring
-                    const int k0 = (it0 + ta) % RBLK;
-                    const int n1 = (tb - ta + 1) < (RBLK - k0) ? (tb - ta + 1) : (RBLK - k0);
                     const uint32_t sbase = smem_u32(Ss + b * SLICE);
-                    for (int piece = 0; piece < 2; ++piece) {
-                        const int t0 = piece == 0 ? ta : ta + n1;
-                        const int cnt = piece == 0 ? n1 : tb - ta + 1 - n1;
-                        if (cnt <= 0) continue;
-                        const uint32_t dtm = tmem + (uint32_t)(((it0 + t0) % RBLK) * NB);
-                        const int stack0 = t0 - j + 2;  // kz block of the first tile
-                        const uint32_t idesc = idesc_bf16(TM, cnt * NB);
-                        // descriptors of the first operands; every other MMA adds a
-                        // compile-time byte offset / 16 to the start-address field
-                        const uint64_t b0 =
-                            smem_desc(wbase + stack0 * (NB / 8) * CORE, NGS * CORE, CORE);
-                        if constexpr (PAIR) {
-                            const uint64_t a0 = smem_desc(sbase, 0, CORE);
+                    const uint32_t dtm = tmem + (uint32_t)(ta * NB);
+                    const int stack0 = ta - j + 2;  // kz block of the first tile
+                    const uint32_t idesc = idesc_bf16(TM, (tb - ta + 1) * NB);
+                    // descriptors of the first operands; every other MMA adds a
+                    // compile-time byte offset / 16 to the start-address field
+                    const uint64_t b0 = smem_desc(wbase + stack0 * (NB / 8) * CORE, NGS * CORE, CORE);
+                    if constexpr (PAIR) {
+                        const uint64_t a0 = smem_desc(sbase, 0, CORE);
 #pragma unroll
-                            for (int p = 0; p < 5; ++p) {
-                                const int ta0 = pair_tap(p, 0), tb0 = pair_tap(p, 1);
-                                const uint32_t off = (ta0 / 3) * ROW + (ta0 % 3) * 16;
-                                const uint32_t lbo = (tb0 / 3) * ROW + (tb0 % 3) * 16 - off;
-                                const uint64_t ad = a0 + (off >> 4) + ((uint64_t)(lbo >> 4) << 16);
-                                const uint64_t bd = b0 + ((2 * p * NGS * CORE) >> 4);
-                                mma_bf16(dtm, ad, bd, idesc, 1u);
-                            }
-                        } else {
-                            const uint64_t a0 = smem_desc(sbase, PLANE, CORE);
-#pragma unroll
-                            for (int dy = 0; dy < 3; ++dy)
-#pragma unroll
-                                for (int dx = 0; dx < 3; ++dx)
-#pragma unroll
-                                    for (int kk = 0; kk < CIN / 16; ++kk) {
-                                        const int dyx = dy * 3 + dx;
-                                        const uint64_t ad =
-                                            a0 + ((dy * ROW + dx * 16 + kk * 2 * PLANE) >> 4);
-                                        const uint64_t bd =
-                                            b0 + (((dyx * KC + 2 * kk) * NGS * CORE) >> 4);
-                                        mma_bf16(dtm, ad, bd, idesc, 1u);
-                                    }
+                        for (int p = 0; p < 5; ++p) {
+                            const int ta0 = pair_tap(p, 0), tb0 = pair_tap(p, 1);
+                            const uint32_t off = (ta0 / 3) * ROW + (ta0 % 3) * 16;
+                            const uint32_t lbo = (tb0 / 3) * ROW + (tb0 % 3) * 16 - off;
+                            const uint64_t ad = a0 + (off >> 4) + ((uint64_t)(lbo >> 4) << 16);
+                            const uint64_t bd = b0 + ((2 * p * NGS * CORE) >> 4);
+                            mma_bf16(dtm, ad, bd, idesc, 1u);
                         }
+                    } else {
+                        const uint64_t a0 = smem_desc(sbase, PLANE, CORE);
+#pragma unroll
+                        for (int dy = 0; dy < 3; ++dy)
+#pragma unroll
+                            for (int dx = 0; dx < 3; ++dx)
+#pragma unroll
+                                for (int kk = 0; kk < CIN / 16; ++kk) {
+                                    const int dyx = dy * 3 + dx;
+                                    const uint64_t ad = a0 + ((dy * ROW + dx * 16 + kk * 2 * PLANE) >> 4);
+                                    const uint64_t bd = b0 + (((dyx * KC + 2 * kk) * NGS * CORE) >> 4);
+                                    mma_bf16(dtm, ad, bd, idesc, 1u);
+                                }
                     }
                     mma_commit(&empty[b]);
-                    if (j >= 2) mma_commit(&accf[(it0 + j - 2) % RBLK]);  // its third slice
+                    if (j >= 2) mma_commit(&accf[j - 2]);  // tile j-2 has had its third slice
                 }
-                it0 += L;
             }
             if (!ok) atomicExch(a.err, 1u);
             // no MMA may be in flight when TMEM is freed: a final commit covers all
@@ -459,14 +513,16 @@ __global__ void __launch_bounds__(THREADS, 1)
         float bias[COUT];
 #pragma unroll
         for (int c = 0; c < COUT; ++c) bias[c] = a.bias[c];
-        int it = 0;
+        double gm = 0.0;  // EPI_SCALED_F32: this thread's largest |output|
+        uint32_t par = 0;  // bit k: parity of the tiles block k has held so far
         bool ok = true;
         for (long long g = blockIdx.x; g < nseg && ok; g += gridDim.x) {
             const Segment sg = segment_of(g, a, segs);
             const int x = sg.seg * TM + warp * 32 + lane;
-            for (int i = 0; i < sg.len; ++i, ++it) {
-                const int kb = it % RBLK;
-                ok = __all_sync(0xffffffffu, mbar_wait(&accf[kb], (unsigned)((it / RBLK) & 1)));
+            for (int i = 0; i < sg.len; ++i) {
+                const int kb = i;
+                ok = __all_sync(0xffffffffu, mbar_wait(&accf[kb], (par >> kb) & 1u));
+                par ^= 1u << kb;
                 if (!ok) break;
                 tc_fence_after_sync();
                 const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(kb * NB);
@@ -485,28 +541,37 @@ __global__ void __launch_bounds__(THREADS, 1)
                     __align__(16) bf16 o[COUT];
 #pragma unroll
                     for (int c = 0; c < COUT; ++c) o[c] = __float2bfloat16_rn(fmaxf(v[c] + bias[c], 0.f));
-                    bf16 *Y = static_cast<bf16 *>(a.y);
+                    bf16 *Y = a.y;
 #pragma unroll
                     for (int kc = 0; kc < COUT / 8; ++kc) {
                         const uint4 val = reinterpret_cast<const uint4 *>(o)[kc];
                         bf16 *plane =
-                            Y + ((((long long)z * a.ny + sg.y) * (COUT / 8) + kc) * (a.nx + 2)) * 8;
+                            Y + ((((long long)z * a.ny + sg.y) * (COUT / 8) + kc) * rp_cells(a.nx)) * 8;
                         *reinterpret_cast<uint4 *>(plane + (long long)(x + 1) * 8) = val;
                         if (x == 0) *reinterpret_cast<uint4 *>(plane + (long long)(a.nx + 1) * 8) = val;
                         if (x == a.nx - 1) *reinterpret_cast<uint4 *>(plane) = val;
                     }
                 } else {
                     const long long p = ((long long)z * a.ny + sg.y) * a.nx + x;
-                    __align__(16) float o[COUT];
 #pragma unroll
-                    for (int c = 0; c < COUT; ++c) o[c] = v[c] + bias[c];
-                    float4 *d = reinterpret_cast<float4 *>(static_cast<float *>(a.y) + p * COUT);
-#pragma unroll
-                    for (int c = 0; c < COUT / 4; ++c) d[c] = reinterpret_cast<const float4 *>(o)[c];
+                    for (int c = 0; c < COUT; ++c) {
+                        const float val = a.out_scale[c] * (v[c] + bias[c]);
+                        a.out[c][p] = val;
+                        const double m = fabs((double)val);
+                        gm = (m > gm || m != m) ? m : gm;
+                    }
                 }
             }
         }
         if (!ok && lane == 0) atomicExch(a.err, 1u);
+        if (EPI == EPI_SCALED_F32 && a.gmax) {
+            unsigned long long bits = (unsigned long long)__double_as_longlong(gm);
+            for (int o = 16; o > 0; o >>= 1) {
+                const unsigned long long other = __shfl_xor_sync(0xffffffffu, bits, o);
+                bits = other > bits ? other : bits;
+            }
+            if (lane == 0) atomicMax(a.gmax, bits);
+        }
     }
     tc_fence_before_sync();
     __syncthreads();

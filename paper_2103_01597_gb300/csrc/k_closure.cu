@@ -329,30 +329,13 @@ __global__ void loss_grad_kernel(const float *__restrict__ y, F8 tgt,
     if (threadIdx.x == 0) partials[blockIdx.x] = sh[0];
 }
 
-// Eight binary32 output channels of cell p: channel-major y[c * n + p] or
-// channels-last y[p * 8 + c] (two 16-byte loads).
-__device__ __forceinline__ void load8(const float *__restrict__ y, long long p, long long n, int cl,
-                                      float (&v)[8]) {
-    if (cl) {
-        const float4 a = reinterpret_cast<const float4 *>(y + p * 8)[0];
-        const float4 b = reinterpret_cast<const float4 *>(y + p * 8)[1];
-        v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
-        v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
-    } else {
-#pragma unroll
-        for (int c = 0; c < 8; ++c) v[c] = y[(long long)c * n + p];
-    }
-}
-
-// out[c] = out_scale[c] * y[c]
+// out[c] = out_scale[c] * y[c] (y channel-major [8][n])
 __global__ void scale_output_kernel(const float *__restrict__ y, const float *__restrict__ out_scale,
-                                    long long n, W8 out, int cl) {
-    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < n;
-         p += (long long)gridDim.x * blockDim.x) {
-        float v[8];
-        load8(y, p, n, cl, v);
-#pragma unroll
-        for (int c = 0; c < 8; ++c) out.p[c][p] = out_scale[c] * v[c];
+                                    long long n, W8 out) {
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < 8 * n;
+         t += (long long)gridDim.x * blockDim.x) {
+        const int c = (int)(t / n);
+        out.p[c][t - c * n] = out_scale[c] * y[t];
     }
 }
 
@@ -369,7 +352,7 @@ __global__ void pack_input_rp_kernel(F8 f, const float *__restrict__ inv_scale, 
 #pragma unroll
         for (int c = 0; c < 8; ++c) v[c] = __float2bfloat16_rn(f.p[c][p] * inv_scale[c]);
         const uint4 val = *reinterpret_cast<const uint4 *>(v);
-        uint4 *p0 = reinterpret_cast<uint4 *>(x + row * (nx + 2) * 8);
+        uint4 *p0 = reinterpret_cast<uint4 *>(x + row * tc::rp_cells(nx) * 8);
         p0[xi + 1] = val;
         if (xi == 0) p0[nx + 1] = val;
         if (xi == nx - 1) p0[0] = val;
@@ -379,17 +362,13 @@ __global__ void pack_input_rp_kernel(F8 f, const float *__restrict__ inv_scale, 
 // Guard: largest |out_scale * y| (NaN counts as larger than anything) into one word.
 __global__ void correction_max_kernel(const float *__restrict__ y,
                                       const float *__restrict__ out_scale, long long n,
-                                      unsigned long long *gmax, int cl) {
+                                      unsigned long long *gmax) {
     double m = 0.0;
-    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < n;
-         p += (long long)gridDim.x * blockDim.x) {
-        float v[8];
-        load8(y, p, n, cl, v);
-#pragma unroll
-        for (int c = 0; c < 8; ++c) {
-            const double a = fabs((double)(out_scale[c] * v[c]));
-            m = (a > m || a != a) ? a : m;
-        }
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < 8 * n;
+         t += (long long)gridDim.x * blockDim.x) {
+        const int c = (int)(t / n);
+        const double v = fabs((double)(out_scale[c] * y[t]));
+        m = (v > m || v != v) ? v : m;
     }
     unsigned long long bits = (unsigned long long)__double_as_longlong(m);
     for (int o = 16; o > 0; o >>= 1) {
@@ -399,18 +378,17 @@ __global__ void correction_max_kernel(const float *__restrict__ y,
     if ((threadIdx.x & 31) == 0) atomicMax(gmax, bits);
 }
 
-// f[c] += out_scale[c] * y[c], only if the guard word shows a finite maximum <= limit.
+// f[c] += s[c] * y[c] (s = out_scale, or 1 where y is already scaled: s == null),
+// only if the guard word shows a finite maximum <= limit.
 __global__ void apply_correction_kernel(W8 f, const float *__restrict__ y,
                                         const float *__restrict__ out_scale, long long n,
-                                        const unsigned long long *gmax, double limit, int cl) {
+                                        const unsigned long long *gmax, double limit) {
     const double m = __longlong_as_double((long long)*gmax);
     if (!(m <= limit)) return;
-    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < n;
-         p += (long long)gridDim.x * blockDim.x) {
-        float v[8];
-        load8(y, p, n, cl, v);
-#pragma unroll
-        for (int c = 0; c < 8; ++c) f.p[c][p] += out_scale[c] * v[c];
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < 8 * n;
+         t += (long long)gridDim.x * blockDim.x) {
+        const int c = (int)(t / n);
+        f.p[c][t - c * n] += (out_scale ? out_scale[c] : 1.f) * y[t];
     }
 }
 
@@ -538,13 +516,13 @@ static cudaError_t tc_grid_for(const ac_closure *c, int sms, int *grid) {
 }
 
 // Tensor map of a row-planar activation with KC groups of 8 channels: dims
-// (8 channels, nx + 2 cells, KC, ny, nz), box (8, 130, KC, 1, 1).
+// (64 = 8 cells x 8 channels, nxp / 8, KC, ny, nz), box (64, 17, KC, 1, 1).
 static cudaError_t tc_encode(PFN_cuTensorMapEncodeTiled_v12000 enc, const ac_closure *c, void *base,
                              int kc, CUtensorMap *map) {
-    const cuuint64_t nxp = (cuuint64_t)c->g.nx + 2;
-    const cuuint64_t dims[5] = {8, nxp, (cuuint64_t)kc, (cuuint64_t)c->g.ny, (cuuint64_t)c->g.nz};
-    const cuuint64_t strides[4] = {16, 16 * nxp, 16 * nxp * kc, 16 * nxp * kc * c->g.ny};
-    const cuuint32_t box[5] = {8, tc::TM + 2, (cuuint32_t)kc, 1, 1};
+    const cuuint64_t nxp = (cuuint64_t)tc::rp_cells(c->g.nx);
+    const cuuint64_t dims[5] = {64, nxp / 8, (cuuint64_t)kc, (cuuint64_t)c->g.ny, (cuuint64_t)c->g.nz};
+    const cuuint64_t strides[4] = {128, 16 * nxp, 16 * nxp * kc, 16 * nxp * kc * c->g.ny};
+    const cuuint32_t box[5] = {64, tc::PCELLS / 8, (cuuint32_t)kc, 1, 1};
     const cuuint32_t estr[5] = {1, 1, 1, 1, 1};
     const CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, base, dims, strides, box, estr,
                            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
@@ -556,12 +534,12 @@ static cudaError_t tc_encode(PFN_cuTensorMapEncodeTiled_v12000 enc, const ac_clo
 // three layers.
 static cudaError_t tc_setup(ac_closure *c) {
     int dev = 0, sms = 0;
-    c->tc_zc = c->g.nz < 16 ? c->g.nz : 16;
+    c->tc_zc = c->g.nz < tc::RBLK ? c->g.nz : tc::RBLK;  // a segment fits the TMEM blocks
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e == cudaSuccess) e = tc_grid_for<8, 32, tc::EPI_RELU_BF16>(c, sms, &c->tc_grid[0]);
     if (e == cudaSuccess) e = tc_grid_for<32, 32, tc::EPI_RELU_BF16>(c, sms, &c->tc_grid[1]);
-    if (e == cudaSuccess) e = tc_grid_for<32, 8, tc::EPI_LINEAR_F32>(c, sms, &c->tc_grid[2]);
+    if (e == cudaSuccess) e = tc_grid_for<32, 8, tc::EPI_SCALED_F32>(c, sms, &c->tc_grid[2]);
     void *fn = nullptr;
     cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
     if (e == cudaSuccess)
@@ -602,7 +580,7 @@ extern "C" int ac_closure_init(ac_closure **out, int nx, int ny, int nz, void *s
     const size_t part_floats = (size_t)9 * CL_WG_CTAS * 32 * 96;
     // x0, a1, a2 hold either channel-major [C][n] or row-planar [rows][C/8][nx+2][8]
     // activations: sized for the larger (row-planar, np2 cells per channel)
-    const long long np2 = (long long)(nx + 2) * ny * nz;
+    const long long np2 = (long long)tc::rp_cells(nx) * ny * nz;
     const size_t abytes = 2 * (size_t)np2 * (16 + 32 + 32) + 2 * (size_t)n * (16 + 32 + 32) +
                           4 * (size_t)n * 8 + 4 * part_floats + 8 * (size_t)c->lossblocks + 8 + 1024;
     cudaError_t e = cudaMalloc(&c->block, fbytes);
@@ -752,11 +730,15 @@ static int run_forward(ac_closure *c, const float *const in[8], cudaEvent_t *ev 
 }
 
 template <int CIN, int COUT, int EPI>
-static void launch_tc(const ac_closure *c, int layer, const bf16 *img, const float *bias, void *y) {
+static void launch_tc(const ac_closure *c, int layer, const bf16 *img, const float *bias, bf16 *y,
+                      float *const out[8] = nullptr, unsigned long long *gmax = nullptr) {
     tc::ConvTcArgs a;
     a.w = img;
     a.bias = bias;
     a.y = y;
+    for (int i = 0; i < 8; ++i) a.out[i] = out ? out[i] : nullptr;
+    a.out_scale = c->scales + 8;
+    a.gmax = gmax;
     a.nx = c->g.nx;
     a.ny = c->g.ny;
     a.nz = c->g.nz;
@@ -768,11 +750,15 @@ static void launch_tc(const ac_closure *c, int layer, const bf16 *img, const flo
 }
 
 // Forward pass on the tcgen05 kernels (row-planar activations in x0, a1, a2);
-// leaves channels-last [n][8] binary32 in c->y.
-static int run_forward_tc(ac_closure *c, const float *const in[8], cudaEvent_t *ev = nullptr) {
+// layer 3 writes out_scale * net(...) channel-major to out[0..7] (the closure's
+// own y when out is null) and, if gmax is given, folds the largest |value| into it.
+static int run_forward_tc(ac_closure *c, const float *const in[8], float *const out[8],
+                          unsigned long long *gmax, cudaEvent_t *ev = nullptr) {
     const ConvGeom g = c->g;
     F8 f;
     for (int i = 0; i < 8; ++i) f.p[i] = in[i];
+    float *own[8];
+    for (int i = 0; i < 8; ++i) own[i] = c->y + (long long)i * g.n;
     mark(ev, 0, c->stream);
     pack_input_rp_kernel<<<cl_grid(g.n), 256, 0, c->stream>>>(f, c->scales, g.nx, g.n, c->x0);
     mark(ev, 1, c->stream);
@@ -780,17 +766,34 @@ static int run_forward_tc(ac_closure *c, const float *const in[8], cudaEvent_t *
     mark(ev, 2, c->stream);
     launch_tc<32, 32, tc::EPI_RELU_BF16>(c, 1, c->img2, c->params + P_B2, c->a2);
     mark(ev, 3, c->stream);
-    launch_tc<32, 8, tc::EPI_LINEAR_F32>(c, 2, c->img3, c->params + P_B3, c->y);
+    launch_tc<32, 8, tc::EPI_SCALED_F32>(c, 2, c->img3, c->params + P_B3, nullptr, out ? out : own,
+                                         gmax);
     mark(ev, 4, c->stream);
     c->launches += 4;
     CCK(cudaGetLastError());
     return AC_OK;
 }
 
-// Inference forward on the selected path; *cl = 1 if c->y is channels-last.
-static int run_inference(ac_closure *c, const float *const in[8], int *cl, cudaEvent_t *ev = nullptr) {
-    *cl = c->conv_path == AC_CONV_TCGEN05;
-    return *cl ? run_forward_tc(c, in, ev) : run_forward(c, in, ev);
+// Inference on the selected path: the scaled correction in out (or the closure's
+// own y when null); ev, if given, brackets the five launches of the mma.sync path
+// (on the tcgen05 path the fifth, the output scaling, is empty).
+static int run_inference(ac_closure *c, const float *const in[8], float *const out[8],
+                         cudaEvent_t *ev = nullptr) {
+    if (c->conv_path == AC_CONV_TCGEN05) {
+        int rc = run_forward_tc(c, in, out, nullptr, ev);
+        mark(ev, 5, c->stream);
+        return rc;
+    }
+    int rc = run_forward(c, in, ev);
+    if (rc == AC_OK && out) {
+        W8 o;
+        for (int i = 0; i < 8; ++i) o.p[i] = out[i];
+        scale_output_kernel<<<cl_grid(8 * c->g.n), 256, 0, c->stream>>>(c->y, c->scales + 8, c->g.n, o);
+        c->launches++;
+        CCK(cudaGetLastError());
+    }
+    mark(ev, 5, c->stream);
+    return rc;
 }
 
 extern "C" int ac_closure_set_conv_path(ac_closure *c, int path) {
@@ -819,18 +822,7 @@ extern "C" int ac_closure_forward(ac_closure *c, const float *const in[8], float
     if (!c || !in) return AC_ERR_ARG;
     for (int i = 0; i < 8; ++i)
         if (!in[i] || (out && !out[i])) return AC_ERR_ARG;
-    int cl = 0;
-    int rc = run_inference(c, in, &cl);
-    if (rc) return rc;
-    if (out) {
-        W8 o;
-        for (int i = 0; i < 8; ++i) o.p[i] = out[i];
-        scale_output_kernel<<<cl_grid(c->g.n), 256, 0, c->stream>>>(c->y, c->scales + 8, c->g.n, o,
-                                                                        cl);
-        c->launches++;
-        CCK(cudaGetLastError());
-    }
-    return AC_OK;
+    return run_inference(c, in, out);
 }
 
 extern "C" int ac_closure_forward_timings(ac_closure *c, const float *const in[8],
@@ -843,17 +835,9 @@ extern "C" int ac_closure_forward_timings(ac_closure *c, const float *const in[8
     cudaError_t e = cudaSuccess;
     for (int i = 0; i < 6 && e == cudaSuccess; ++i) e = cudaEventCreate(&ev[i]);
     if (e == cudaSuccess) {
-        int cl = 0;
-        rc = run_inference(c, in, &cl, ev);
+        rc = run_inference(c, in, out, ev);
         if (rc == AC_OK) {
-            W8 o;
-            for (int i = 0; i < 8; ++i) o.p[i] = out[i];
-            scale_output_kernel<<<cl_grid(c->g.n), 256, 0, c->stream>>>(c->y, c->scales + 8,
-                                                                            c->g.n, o, cl);
-            c->launches++;
-            e = cudaGetLastError();
-            if (e == cudaSuccess) e = cudaEventRecord(ev[5], c->stream);
-            if (e == cudaSuccess) e = cudaEventSynchronize(ev[5]);
+            e = cudaEventSynchronize(ev[5]);
             for (int i = 0; i < 5 && e == cudaSuccess; ++i) e = cudaEventElapsedTime(&ms[i], ev[i], ev[i + 1]);
         }
     }
@@ -941,15 +925,22 @@ extern "C" int ac_closure_apply(ac_closure *c, ac_handle *h, double limit, int *
         in[i] = static_cast<const float *>(ptrs[i]);
         f.p[i] = static_cast<float *>(ptrs[i]);
     }
-    int cl = 0;
-    rc = run_inference(c, in, &cl);
-    if (rc) return rc;
     CCK(cudaMemsetAsync(c->guard, 0, sizeof(unsigned long long), c->stream));
-    correction_max_kernel<<<cl_grid(c->g.n), 256, 0, c->stream>>>(c->y, c->scales + 8, c->g.n,
-                                                                      c->guard, cl);
-    apply_correction_kernel<<<cl_grid(c->g.n), 256, 0, c->stream>>>(f, c->y, c->scales + 8,
-                                                                        c->g.n, c->guard, limit, cl);
-    c->launches += 2;
+    const float *yscale = nullptr;  // y already scaled (tcgen05 path)
+    if (c->conv_path == AC_CONV_TCGEN05) {
+        rc = run_forward_tc(c, in, nullptr, c->guard);
+        if (rc) return rc;
+    } else {
+        rc = run_forward(c, in);
+        if (rc) return rc;
+        correction_max_kernel<<<cl_grid(8 * c->g.n), 256, 0, c->stream>>>(c->y, c->scales + 8,
+                                                                          c->g.n, c->guard);
+        c->launches++;
+        yscale = c->scales + 8;
+    }
+    apply_correction_kernel<<<cl_grid(8 * c->g.n), 256, 0, c->stream>>>(f, c->y, yscale, c->g.n,
+                                                                        c->guard, limit);
+    c->launches++;
     CCK(cudaGetLastError());
     if (applied) {
         unsigned long long bits = 0;
