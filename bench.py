@@ -758,6 +758,9 @@ CF_UNIT = "Gcell/s"
 CF_FLOPS = {1: 2 * 27 * 8 * 32, 2: 2 * 27 * 32 * 32, 3: 2 * 27 * 32 * 8}
 # algorithmic flops per cell (8 real input channels, 8 real output channels)
 CF_ALGO_FLOPS = 2 * 27 * (8 * 32 + 32 * 32 + 32 * 8)
+# DRAM bytes per cell of one launch of the 32 -> 32 tcgen05 layer (ncu, 128^3:
+# 144.9 MB read + 92.9 MB written over 2,097,152 cells)
+CF_TRAFFIC_PER_CELL = (144.932864e6 + 92.878848e6) / 2097152
 
 
 def _closure_oracle_sample(params, n, seed):
@@ -850,7 +853,8 @@ def run_closure_forward(args, wl):
                                      for l in (1, 2, 3)}}
               for name in per}
     roof = {"bound": "tensor", "achieved": ach, "peak": peaks["bf16_tflops"], "unit": "TFLOP/s",
-            "frac": ach / peaks["bf16_tflops"], "traffic": None,
+            "frac": ach / peaks["bf16_tflops"], "traffic": CF_TRAFFIC_PER_CELL * cells,
+            "traffic_note": "dram read + write bytes per launch, ncu at 128^3 scaled by cells",
             "kernel": "conv_tc_kernel<32,32> (layer 2, tcgen05.mma BF16, TMEM accumulators)",
             "per_unit": "2*27*32*32 = 55296 flops per cell", "units_per_launch": cells,
             "avg_launch_ms": ms2,
