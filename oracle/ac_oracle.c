@@ -10,7 +10,8 @@
  *
  * Everything here is written for a reader checking it against the paper:
  *   - the stencil point set is Sec. 4, Eq. 13 (axes and face diagonals,
- *     radius r = 3, i.e. sixth order, Sec. 4);
+ *     radius r = 3, i.e. sixth order, Sec. 4); radii 1, 2 and 4 (orders 2, 4,
+ *     8) use the same kind of point set (a widening beyond the paper);
  *   - the equations are Appendix B, Eqs. B.1-B.4 with the symbols of
  *     Tables B.1 and B.2;
  *   - time integration is the third-order 2N-storage Runge-Kutta scheme of
@@ -48,6 +49,7 @@ typedef struct {
     int64_t force_k[3];    /* integer wave vector of this step's forcing      */
     double force_e[3];     /* unit polarisation vector, perpendicular to k    */
     double force_phi;      /* phase of this step's forcing                     */
+    int64_t radius;        /* stencil radius r (order 2r): 1, 2, 3 or 4       */
 } oracle_params;
 
 /* ------------------------------------------------------------------------ */
@@ -90,46 +92,83 @@ static double diag_pt(const double *f, const oracle_params *p, const int64_t c[3
 }
 
 /* ------------------------------------------------------------------------ */
-/* Sixth-order central differences on the point set of Eq. 13 (r = 3).       */
-/* Reading: the paper prints no coefficients; these are the standard        */
-/* sixth-order central ones (unique for the given points and order).        */
+/* Central differences of order 2r on the point set of Eq. 13 (r = 3: sixth   */
+/* order, Sec. 4).  Reading: the paper prints no coefficients; these are the */
+/* standard central ones, the unique weights on the points 0, +-1 .. +-r     */
+/* exact for polynomials of degree 2r (first derivative) and 2r + 1 (second  */
+/* derivative).  Closed form (Fornberg 1988), with w_m on (f_m - f_-m) and   */
+/* a_m on (f_m + f_-m):                                                      */
+/*   w_m = (-1)^(m+1) (r!)^2 / (m (r-m)! (r+m)!),   a_m = 2 w_m / m,         */
+/*   a_0 = -2 (a_1 + ... + a_r).                                             */
+/* For r = 3: w = (3/4, -3/20, 1/60) = (45, -9, 1)/60 and                    */
+/* a = (3/2, -3/20, 1/90), a_0 = -49/18.                                     */
 /* ------------------------------------------------------------------------ */
 
-/* First derivative along axis a:
- *   [45 (f_1 - f_-1) - 9 (f_2 - f_-2) + (f_3 - f_-3)] / (60 dx_a). */
-static double d1(const double *f, const oracle_params *p, const int64_t c[3], int a)
+static double factorial(int k)
 {
-    double d1v = axis_pt(f, p, c, a, 1) - axis_pt(f, p, c, a, -1);
-    double d2v = axis_pt(f, p, c, a, 2) - axis_pt(f, p, c, a, -2);
-    double d3v = axis_pt(f, p, c, a, 3) - axis_pt(f, p, c, a, -3);
-    return (45.0 * d1v - 9.0 * d2v + d3v) / (60.0 * p->dx[a]);
+    double f = 1.0;
+    for (int i = 2; i <= k; ++i)
+        f *= i; /* exact: k <= 8 */
+    return f;
 }
 
-/* Second derivative along axis a:
- *   [-49/18 f_0 + 3/2 (f_1 + f_-1) - 3/20 (f_2 + f_-2) + 1/90 (f_3 + f_-3)] / dx_a^2. */
+/* w_m of the first derivative (one rounding: numerator and denominator are
+ * exact integers). */
+static double w_first(int r, int m)
+{
+    double num = factorial(r) * factorial(r);
+    double den = (double)m * factorial(r - m) * factorial(r + m);
+    return (m % 2 ? num : -num) / den;
+}
+
+/* a_m (m >= 1) of the second derivative. */
+static double w_second(int r, int m)
+{
+    double num = 2.0 * factorial(r) * factorial(r);
+    double den = (double)m * (double)m * factorial(r - m) * factorial(r + m);
+    return (m % 2 ? num : -num) / den;
+}
+
+/* First derivative along axis a: sum_m w_m (f_m - f_-m) / dx_a. */
+static double d1(const double *f, const oracle_params *p, const int64_t c[3], int a)
+{
+    const int r = (int)p->radius;
+    double sum = 0.0;
+    for (int m = 1; m <= r; ++m)
+        sum += w_first(r, m) * (axis_pt(f, p, c, a, m) - axis_pt(f, p, c, a, -m));
+    return sum / p->dx[a];
+}
+
+/* Second derivative along axis a: [a_0 f_0 + sum_m a_m (f_m + f_-m)] / dx_a^2. */
 static double d2(const double *f, const oracle_params *p, const int64_t c[3], int a)
 {
-    double f0 = axis_pt(f, p, c, a, 0);
-    double s1 = axis_pt(f, p, c, a, 1) + axis_pt(f, p, c, a, -1);
-    double s2 = axis_pt(f, p, c, a, 2) + axis_pt(f, p, c, a, -2);
-    double s3 = axis_pt(f, p, c, a, 3) + axis_pt(f, p, c, a, -3);
-    double num = -49.0 / 18.0 * f0 + 1.5 * s1 - 0.15 * s2 + s3 / 90.0;
-    return num / (p->dx[a] * p->dx[a]);
+    const int r = (int)p->radius;
+    double a0 = 0.0, sum = 0.0;
+    for (int m = 1; m <= r; ++m) {
+        a0 -= 2.0 * w_second(r, m);
+        sum += w_second(r, m) * (axis_pt(f, p, c, a, m) + axis_pt(f, p, c, a, -m));
+    }
+    return (a0 * axis_pt(f, p, c, a, 0) + sum) / (p->dx[a] * p->dx[a]);
 }
 
 /* Mixed derivative d^2 f / (dx_a dx_b), a != b, from the face diagonals only
  * (Eq. 13 holds no other off-axis points):
- *   [270 S_1 - 27 S_2 + 2 S_3] / (720 dx_a dx_b),
- *   S_m = f(+m,+m) + f(-m,-m) - f(+m,-m) - f(-m,+m) in the (a, b) plane. */
+ *   sum_m a_m S_m / (4 dx_a dx_b),
+ *   S_m = f(+m,+m) + f(-m,-m) - f(+m,-m) - f(-m,+m) in the (a, b) plane.
+ * Along the two diagonals S_m = 2 sum_k m^2k / (2k)! (D+^2k - D-^2k) f with
+ * D+- = dx_a d_a +- dx_b d_b, and D+^2 - D-^2 = 4 dx_a dx_b d_a d_b: the same
+ * moment conditions as the second derivative, hence the weights a_m
+ * (r = 3: [270 S_1 - 27 S_2 + 2 S_3] / (720 dx_a dx_b)). */
 static double dab(const double *f, const oracle_params *p, const int64_t c[3], int a, int b)
 {
-    double S[4];
-    for (int64_t m = 1; m <= 3; ++m) {
-        S[m] = diag_pt(f, p, c, a, m, b, m) + diag_pt(f, p, c, a, -m, b, -m)
-             - diag_pt(f, p, c, a, m, b, -m) - diag_pt(f, p, c, a, -m, b, m);
+    const int r = (int)p->radius;
+    double sum = 0.0;
+    for (int64_t m = 1; m <= r; ++m) {
+        double S = diag_pt(f, p, c, a, m, b, m) + diag_pt(f, p, c, a, -m, b, -m)
+                 - diag_pt(f, p, c, a, m, b, -m) - diag_pt(f, p, c, a, -m, b, m);
+        sum += w_second(r, (int)m) * S;
     }
-    double num = 270.0 * S[1] - 27.0 * S[2] + 2.0 * S[3];
-    return num / (720.0 * p->dx[a] * p->dx[b]);
+    return sum / (4.0 * p->dx[a] * p->dx[b]);
 }
 
 /* Second derivative d^2 f / (dx_a dx_b) for any pair (a, b). */

@@ -7,9 +7,41 @@ products (x fastest, so the x factor is the last one), and the RHS of
 Eqs. B.1-B.4 is assembled from whole-grid vectors.  It shares no code with the
 C oracle; the two are compared on grids of 8^3 cells or fewer.
 """
+from fractions import Fraction
+
 import numpy as np
 
 NF = 8
+
+
+def _solve_exact(A, b):
+    """Solve the square system A x = b exactly (Fractions, Gauss-Jordan)."""
+    n = len(b)
+    M = [[Fraction(v) for v in row] + [Fraction(b[i])] for i, row in enumerate(A)]
+    for c in range(n):
+        piv = next(r for r in range(c, n) if M[r][c] != 0)
+        M[c], M[piv] = M[piv], M[c]
+        M[c] = [v / M[c][c] for v in M[c]]
+        for r in range(n):
+            if r != c and M[r][c] != 0:
+                M[r] = [vr - M[r][c] * vc for vr, vc in zip(M[r], M[c])]
+    return [M[i][n] for i in range(n)]
+
+
+def central_weights(r):
+    """Weights of the order-2r central differences from their defining moment
+    conditions (Taylor expansion of f(x +- m h)), solved exactly:
+      first derivative  sum_m w_m (f_m - f_-m) / h:  2 sum_m w_m m = 1 and
+                        sum_m w_m m^k = 0 for odd k = 3 .. 2r-1;
+      second derivative sum_m a_m (f_m + f_-m - 2 f_0) / h^2:  sum_m a_m m^2 = 1
+                        and sum_m a_m m^k = 0 for even k = 4 .. 2r.
+    Returns (w, a) as lists of Fractions indexed by m - 1."""
+    ms = range(1, r + 1)
+    A1 = [[m ** k for m in ms] for k in range(1, 2 * r, 2)]
+    b1 = [Fraction(1, 2)] + [0] * (r - 1)
+    A2 = [[m ** k for m in ms] for k in range(2, 2 * r + 1, 2)]
+    b2 = [1] + [0] * (r - 1)
+    return _solve_exact(A1, b1), _solve_exact(A2, b2)
 
 
 def _shift(n, m):
@@ -31,44 +63,49 @@ def _axis_op(n3, a, M1):
 
 
 class Operators:
-    """Sixth-order derivative matrices on an (nx, ny, nz) periodic grid."""
+    """Derivative matrices of order 2r (default: sixth, r = 3) on an
+    (nx, ny, nz) periodic grid; the mixed derivative uses the face diagonals,
+    sum_m a_m S_m / (4 dx_a dx_b), S_m expanding like 4 m^2 dx_a dx_b d_a d_b
+    plus the same higher moments as the axis second difference."""
 
-    def __init__(self, n3, dx3):
+    def __init__(self, n3, dx3, order=6):
         self.n3 = tuple(n3)
         self.dx = tuple(dx3)
+        r = order // 2
+        w, aw = central_weights(r)
+        c1 = {m: float(w[m - 1]) for m in range(1, r + 1)}
+        c2 = {m: float(aw[m - 1]) for m in range(1, r + 1)}
+        c0 = float(-2 * sum(aw))
         T = {}
         for a in range(3):
-            for m in range(-3, 4):
+            for m in range(-r, r + 1):
                 T[a, m] = _axis_op(self.n3, a, _shift(self.n3[a], m))
         self.T = T
-        c1 = {1: 45.0, 2: -9.0, 3: 1.0}
         self.D1 = []
         for a in range(3):
-            M = sum(c1[m] * (T[a, m] - T[a, -m]) for m in (1, 2, 3))
-            self.D1.append(M / (60.0 * self.dx[a]))
-        c2 = {1: 1.5, 2: -0.15, 3: 1.0 / 90.0}
+            M = sum(c1[m] * (T[a, m] - T[a, -m]) for m in range(1, r + 1))
+            self.D1.append(M / self.dx[a])
         N = T[0, 0].shape[0]
         self.D2 = {}
         for a in range(3):
-            M = -49.0 / 18.0 * np.eye(N) + sum(c2[m] * (T[a, m] + T[a, -m]) for m in (1, 2, 3))
+            M = c0 * np.eye(N) + sum(c2[m] * (T[a, m] + T[a, -m]) for m in range(1, r + 1))
             self.D2[a, a] = M / self.dx[a] ** 2
-        cx = {1: 270.0, 2: -27.0, 3: 2.0}
         for a in range(3):
             for b in range(3):
                 if a == b:
                     continue
                 M = np.zeros((N, N))
-                for m in (1, 2, 3):
+                for m in range(1, r + 1):
                     S = (T[a, m] @ T[b, m] + T[a, -m] @ T[b, -m]
                          - T[a, m] @ T[b, -m] - T[a, -m] @ T[b, m])
-                    M += cx[m] * S
-                self.D2[a, b] = M / (720.0 * self.dx[a] * self.dx[b])
+                    M += c2[m] * S
+                self.D2[a, b] = M / (4.0 * self.dx[a] * self.dx[b])
 
 
 def rhs(f, p, ops=None):
     """RHS of Eqs. B.1-B.4 with whole-grid vectors; f: (8, nz, ny, nx)."""
     if ops is None:
-        ops = Operators(p.n, p.dx)
+        ops = Operators(p.n, p.dx, getattr(p, "order", 6))
     shape = f.shape[1:]
     v = [f[q].ravel() for q in range(NF)]
     lnrho, s = v[0], v[4]

@@ -26,7 +26,7 @@ class _CParams(ctypes.Structure):
     _fields_ = [("n", _i64 * 3), ("dx", _f64 * 3), ("nu", _f64), ("eta", _f64),
                 ("cs0", _f64), ("gamma", _f64), ("cp", _f64), ("lnrho0", _f64),
                 ("force_on", _i64), ("force_amp", _f64), ("force_k", _i64 * 3),
-                ("force_e", _f64 * 3), ("force_phi", _f64)]
+                ("force_e", _f64 * 3), ("force_phi", _f64), ("radius", _i64)]
 
 
 @dataclass
@@ -50,6 +50,7 @@ class Params:
     cp: float = 1.0
     lnrho0: float = 0.0
     forcing: Forcing = field(default=None)
+    order: int = 6                 # stencil order 2r (Sec. 4 uses 6; 2, 4, 8 widen it)
 
     @property
     def dx(self):
@@ -62,6 +63,9 @@ class Params:
             cp.dx[a] = float(self.dx[a])
         cp.nu, cp.eta, cp.cs0 = self.nu, self.eta, self.cs0
         cp.gamma, cp.cp, cp.lnrho0 = self.gamma, self.cp, self.lnrho0
+        if self.order not in (2, 4, 6, 8):
+            raise ValueError("stencil order must be 2, 4, 6 or 8")
+        cp.radius = self.order // 2
         if self.forcing is not None:
             cp.force_on = 1
             cp.force_amp = self.forcing.amp
