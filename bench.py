@@ -38,6 +38,12 @@ UNIT = "Gcell-updates/s"
 # the physics of Eqs. B.1-B.4 with forcing, 40 in the Runge-Kutta update
 # (24 at substep 0, where w is not read).
 FLOPS_PER_CELL = {0: 743, 1: 759, 2: 759}
+
+
+# The same count at stencil order 2r: a first derivative takes 3r - 1 flops, a
+# second 3r + 1, a mixed one 5r - 1, so the 54 stencils take 186 r - 18.
+def flops_per_cell(order, s):
+    return 186 * (order // 2) - 18 + 24 + 155 + (24 if s == 0 else 40)
 # Algorithmic bytes per cell-substep: read f and w, write f and w, eight fields
 # each (w not read at s = 0).
 def bytes_per_cell(elem_f, elem_w, s):
@@ -89,6 +95,8 @@ def parse():
     ap.add_argument("--workload", default="forced256_fp64", choices=sorted(WORKLOADS))
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--stencil-order", type=int, default=6, choices=[2, 4, 6, 8],
+                    help="central-difference order of the substep (the paper's is 6)")
     ap.add_argument("--closure-pairs", type=int, default=24)
     ap.add_argument("--closure-iters", type=int, default=800)
     ap.add_argument("--closure-rollout", type=int, default=20)
@@ -189,7 +197,7 @@ def oracle_sample(wl, f, planes):
     if wl["force_amp"]:
         fr = core.forcing_draw(wl["seed"], 0, wl["force_amp"])
         frc = fr
-    p = core.Params(n=wl["n"], forcing=frc)
+    p = core.Params(n=wl["n"], forcing=frc, order=wl.get("order", 6))
     w = np.zeros_like(f)
     t0 = time.perf_counter()
     for s in range(3):
@@ -286,8 +294,9 @@ def run_ours(args, wl):
     n = wl["n"]
     ncell = n[0] * n[1] * n[2]
     stream = torch.cuda.current_stream()
+    order = wl.get("order", 6)
     sim = ac.Simulation(n, precision=prec, force_amp=wl["force_amp"], seed=wl["seed"],
-                        device="cuda:%d" % local, stream=stream.cuda_stream)
+                        device="cuda:%d" % local, stream=stream.cuda_stream, order=order)
     f0 = make_state(wl)
     host_in = torch.from_numpy(f0.reshape(-1)).pin_memory()
     host_out = torch.empty_like(host_in).pin_memory()
@@ -345,7 +354,7 @@ def run_ours(args, wl):
     avg = {s: statistics.mean(per_sub[s]) for s in range(3)}
     avg_all = statistics.mean(avg.values())
     if wl["precision"] == "fp64":
-        flops = {s: FLOPS_PER_CELL[s] * ncell for s in range(3)}
+        flops = {s: flops_per_cell(order, s) * ncell for s in range(3)}
         achieved = statistics.mean(flops[s] / avg[s] for s in range(3)) / 1e12
         dg = fp64_dgemm_tflops(torch) if (rank == 0 and args.fp64_peak) else None
         fixed = ac.ac_get_stencil_path(sim.h)
@@ -355,23 +364,27 @@ def run_ours(args, wl):
                 # ncu capture scaled by cells (profiles/substep_fx_128_full.md)
                 "traffic": FX_TRAFFIC_PER_CELL * ncell if (fixed and n == (256, 256, 256)) else None,
                 "kernel": ("substep_fx_kernel (int64 stencil sums) + fx_max + fx_quantize"
-                           if fixed else "substep_kernel<double,double,IdxPeriodic>"),
+                           if fixed else "substep_kernel<double,double,IdxPeriodicR<%d>>"
+                           % (order // 2)),
                 "peak_source": "nominal GB300 dense FP64, 2 FP64 lanes/SM/cycle x 152 SMs x "
                                "2.07 GHz (no measured FP64 peak in MEASURED_PEAKS.json)",
-                "note": ("achieved counts the method's 759 binary64 flops per cell-substep; "
+                "note": ("achieved counts the method's %d binary64 flops per cell-substep; "
+                         % flops_per_cell(order, 1) +
                          "540 of them (the stencil sums) run as exact int64 operations on the "
                          "integer pipes, so frac can exceed 1; ncu: FP64 pipe 68% busy"
                          if fixed else "all arithmetic on the FP64 pipe"),
                 "fp64_dgemm_measured_tflops": dg,
                 "avg_launch_ms": 1e3 * avg_all,
-                "alg_flops_per_cell_substep": FLOPS_PER_CELL}
+                "alg_flops_per_cell_substep": {s: flops_per_cell(order, s) for s in range(3)}}
     else:
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
         bytes_s = {s: bytes_per_cell(elem_f, elem_w, s) * ncell for s in range(3)}
         achieved = statistics.mean(bytes_s[s] / avg[s] for s in range(3)) / 1e9
         roof = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                 "frac": achieved / peaks["hbm_gbs"], "traffic": None,
-                "kernel": "substep_tiled_kernel<float,true> (shared-memory plane ring)",
+                "kernel": ("substep_tiled_kernel<float,true> (shared-memory plane ring)"
+                           if order == 6 else
+                           "substep_kernel<float,float,IdxPeriodicR<%d>>" % (order // 2)),
                 "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)",
                 "avg_launch_ms": 1e3 * avg_all}
 
@@ -403,6 +416,7 @@ def run_ours(args, wl):
                 "dtype": "f64" if wl["precision"] == "fp64" else "f32", "data": "synthetic",
                 "config": {"workload": wl["desc"], "grid": list(n), "dt": dt,
                            "precision": wl["precision"], "layout": "periodic (wrap on load)",
+                           "stencil_order": order,
                            "parallelism": "replicas" if ws > 1 else "single GPU",
                            "l2": "inputs larger than L2 (%.1f GB of state resident)"
                                  % (ncell * (16 * elem_f + 8 * elem_w) / 1e9),
@@ -938,6 +952,11 @@ def run_closure_forward_reference(args, wl):
 def main():
     args = parse()
     wl = dict(WORKLOADS[args.workload])
+    if args.stencil_order != 6:
+        wl["order"] = args.stencil_order
+        wl["desc"] = wl["desc"].replace("6th-order", "%dth-order" % args.stencil_order) + \
+            " (stencil order %d)" % args.stencil_order
+        wl.pop("vs", None)
     if args.grid and not wl.get("ensemble") and not wl.get("closure"):
         g = args.grid
         wl["n"] = (g, g, g)

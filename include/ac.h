@@ -169,9 +169,25 @@ int ac_store_w(ac_handle *h, int field, double *host_dst);
 int ac_integrate_substep(ac_handle *h, double dt, int s);
 
 /*
+ * Stencil order (Sec. 4 uses sixth order, radius 3, on the points of Eq. 13;
+ * orders 2, 4 and 8 use the same kind of point set out to radius 1, 2, 4:
+ * the axes and the face diagonals).  Central weights of order 2r: first
+ * derivative sum_m w_m (f_m - f_-m) / dx, second derivative
+ * [a_0 f_0 + sum_m a_m (f_m + f_-m)] / dx^2, mixed derivative
+ * sum_m a_m S_m / (4 dx_a dx_b) on the diagonal sums S_m.  Default 6.  Order 8
+ * needs the periodic layout (the padded layout's halo is 3 cells).  Only at a
+ * step boundary (AC_ERR_STATE otherwise); AC_ERR_ARG for other orders, or for
+ * an order other than 6 while AC_STENCIL_FIXED is set.  Binary32 handles use
+ * the shared-memory tiled kernel at order 6 and the direct-load kernel
+ * otherwise; reductions (E_M's curl) use the same order.
+ */
+int ac_set_stencil_order(ac_handle *h, int order);
+int ac_get_stencil_order(const ac_handle *h, int *order);
+
+/*
  * Arithmetic of the stencil sums for AC_FP64.  AC_STENCIL_AUTO (default): exact
  * integer sums whenever they apply (binary64 fields, periodic layout, equal
- * spacing dx = dy = dz), plain binary64 sums otherwise.  With integer sums each
+ * spacing dx = dy = dz, stencil order 6), plain binary64 sums otherwise.  With integer sums each
  * field group (ln rho; u; s; A) is first written as int64 fixed point with one
  * power-of-two scale per group (|F| <= 2^50, resolution 2^-51 of the group's
  * largest |f|, i.e. four binary64 units in the last place at that magnitude);

@@ -124,6 +124,8 @@ def load_library(path=None):
         "ac_batch_info": ([_vp, ctypes.POINTER(_c.c_longlong), ctypes.POINTER(_c.c_int),
                            ctypes.POINTER(_c.c_int), ctypes.POINTER(_c.c_int),
                            ctypes.POINTER(_c.c_ulonglong)], _c.c_int),
+        "ac_set_stencil_order": ([_vp, _c.c_int], _c.c_int),
+        "ac_get_stencil_order": ([_vp, ctypes.POINTER(_c.c_int)], _c.c_int),
         "ac_get_state": ([_vp, ctypes.POINTER(_vp), ctypes.POINTER(_c.c_int),
                           ctypes.POINTER(_c.c_int), ctypes.POINTER(_c.c_int)], _c.c_int),
         "ac_closure_init": ([ctypes.POINTER(_vp), _c.c_int, _c.c_int, _c.c_int, _vp], _c.c_int),
@@ -298,6 +300,16 @@ def ac_set_forcing(h, k, e, phi):
     kk = (ctypes.c_int * 3)(*[int(v) for v in k])
     ee = (ctypes.c_double * 3)(*[float(v) for v in e])
     _check(load_library().ac_set_forcing(h, kk, ee, float(phi)), "ac_set_forcing")
+
+
+def ac_set_stencil_order(h, order):
+    _check(load_library().ac_set_stencil_order(h, int(order)), "ac_set_stencil_order")
+
+
+def ac_get_stencil_order(h):
+    o = ctypes.c_int()
+    _check(load_library().ac_get_stencil_order(h, ctypes.byref(o)), "ac_get_stencil_order")
+    return o.value
 
 
 def ac_get_step(h):
@@ -566,7 +578,7 @@ class Simulation:
 
     def __init__(self, n, L=(2 * math.pi,) * 3, layout=AC_LAYOUT_PERIODIC, precision=AC_FP64,
                  nu=5e-3, eta=5e-3, cs0=1.0, gamma=5.0 / 3.0, cp=1.0, lnrho0=0.0,
-                 force_amp=0.0, seed=0, device="cuda", stream=None):
+                 force_amp=0.0, seed=0, device="cuda", stream=None, order=6):
         import torch
         self.n = tuple(n)
         self.precision = precision
@@ -585,6 +597,8 @@ class Simulation:
         ptrs = [self.state[b, q].data_ptr() for b in range(2) for q in range(8)]
         ptrs += [self.w[q].data_ptr() for q in range(8)]
         ac_bind_buffers(self.h, ptrs)
+        if order != 6:
+            ac_set_stencil_order(self.h, order)
         self._closed = False
 
     def load(self, f):

@@ -132,7 +132,7 @@ extern "C" int ac_init(ac_handle **out, const ac_grid *grid, const ac_params *pa
     h->params = *params;
     h->g = make_geom(grid->nx, grid->ny, grid->nz, grid->layout);
     const double dx[3] = {grid->lx / grid->nx, grid->ly / grid->ny, grid->lz / grid->nz};
-    h->coefs = make_coefs(dx);
+    h->coefs = make_coefs(dx, 3);
     h->phys = make_phys(*params);
     h->stream = static_cast<cudaStream_t>(stream);
     h->elem_f = params->precision == AC_FP64 ? 8 : 4;
@@ -441,13 +441,33 @@ static int fx_applicable(const ac_handle *h) {
     const double dx = h->grid.lx / h->grid.nx, dy = h->grid.ly / h->grid.ny,
                  dz = h->grid.lz / h->grid.nz;
     return h->params.precision == AC_FP64 && h->grid.layout == AC_LAYOUT_PERIODIC && dx == dy &&
-           dy == dz;
+           dy == dz && h->coefs.radius == 3;
 }
 
 extern "C" int ac_set_stencil_mode(ac_handle *h, int mode) {
     if (!h || mode < AC_STENCIL_AUTO || mode > AC_STENCIL_FIXED) return AC_ERR_ARG;
     if (mode == AC_STENCIL_FIXED && !fx_applicable(h)) return AC_ERR_ARG;
     h->stencil_mode = mode;
+    return AC_OK;
+}
+
+extern "C" int ac_set_stencil_order(ac_handle *h, int order) {
+    if (!h || (order != 2 && order != 4 && order != 6 && order != 8)) return AC_ERR_ARG;
+    if (h->grid.layout == AC_LAYOUT_PADDED && order > 6) return AC_ERR_ARG;  // halo is 3 wide
+    if (h->next_s != 0) return AC_ERR_STATE;  // only at a step boundary
+    const int old = h->coefs.radius;
+    const double dx[3] = {h->grid.lx / h->grid.nx, h->grid.ly / h->grid.ny, h->grid.lz / h->grid.nz};
+    h->coefs = make_coefs(dx, order / 2);
+    if (h->stencil_mode == AC_STENCIL_FIXED && !fx_applicable(h)) {
+        h->coefs = make_coefs(dx, old);
+        return AC_ERR_ARG;
+    }
+    return AC_OK;
+}
+
+extern "C" int ac_get_stencil_order(const ac_handle *h, int *order) {
+    if (!h || !order) return AC_ERR_ARG;
+    *order = 2 * h->coefs.radius;
     return AC_OK;
 }
 

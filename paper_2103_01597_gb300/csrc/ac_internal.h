@@ -43,13 +43,16 @@ inline Geom make_geom(int nx, int ny, int nz, int layout) {
     return g;
 }
 
-// Stencil coefficients with the grid spacing folded in (host side, binary64).
+// Stencil coefficients with the grid spacing folded in (host side, binary64),
+// for central differences of order 2r, radius r = 1 .. 4 (r = 3 is Sec. 4's).
+constexpr int MAX_RADIUS = 4;
 struct StencilCoefs {
-    double d1[3][3];  // first derivative: [axis][m-1] multiplies (f_m - f_-m)
-    double d2[3][4];  // second derivative: [axis][0] centre, [axis][m] (f_m + f_-m)
-    double dc[3][3];  // mixed derivative: plane 0 = xy, 1 = xz, 2 = yz; [m-1] multiplies S_m
+    double d1[3][MAX_RADIUS];      // first derivative: [axis][m-1] multiplies (f_m - f_-m)
+    double d2[3][MAX_RADIUS + 1];  // second derivative: [axis][0] centre, [axis][m] (f_m + f_-m)
+    double dc[3][MAX_RADIUS];      // mixed: plane 0 = xy, 1 = xz, 2 = yz; [m-1] multiplies S_m
+    int radius;
 };
-StencilCoefs make_coefs(const double dx[3]);
+StencilCoefs make_coefs(const double dx[3], int radius = 3);
 
 // Physical constants of Eqs. B.1-B.4 in the form the kernels use.
 struct PhysConsts {

@@ -8,24 +8,47 @@
 namespace ac {
 
 // ---------------------------------------------------------------------------
-// Coefficients (host).  Sixth-order central weights on the points of Eq. 13:
-//   d/dx:      (45, -9, 1) / 60 on (f_m - f_-m);
-//   d2/dx2:    -49/18 on f_0 and (3/2, -3/20, 1/90) on (f_m + f_-m);
-//   d2/dxdy:   (270, -27, 2) / 720 on the diagonal sums S_m.
+// Coefficients (host).  Central weights of order 2r on the points of Eq. 13
+// (axes and face diagonals out to radius r), as integer numerators over a
+// common denominator:
+//   r = 3 (Sec. 4): d/dx (45, -9, 1) / 60 on (f_m - f_-m); d2/dx2 -49/18 on f_0
+//          and (3/2, -3/20, 1/90) on (f_m + f_-m); d2/dxdy (270, -27, 2) / 720
+//          on the diagonal sums S_m;
+//   r = 1: (1) / 2;   -2, (1);                       (1) / 4;
+//   r = 2: (8, -1) / 12;   -30/12, (16, -1) / 12;    (16, -1) / 48;
+//   r = 4: (672, -168, 32, -3) / 840;   -14350/5040, (8064, -1008, 128, -9) / 5040;
+//          (8064, -1008, 128, -9) / 20160.
+// The mixed weights are the second-difference weights over 4 (S_m expands like
+// 4 m^2 dx_a dx_b d_a d_b plus the same higher moments).
 // ---------------------------------------------------------------------------
-StencilCoefs make_coefs(const double dx[3]) {
-    StencilCoefs c;
-    const double w1[3] = {45.0, -9.0, 1.0};
-    const double w2[3] = {1.5, -0.15, 1.0 / 90.0};
-    const double wc[3] = {270.0, -27.0, 2.0};
-    for (int a = 0; a < 3; ++a) {
-        for (int m = 0; m < 3; ++m) c.d1[a][m] = w1[m] / (60.0 * dx[a]);
-        c.d2[a][0] = (-49.0 / 18.0) / (dx[a] * dx[a]);
-        for (int m = 0; m < 3; ++m) c.d2[a][m + 1] = w2[m] / (dx[a] * dx[a]);
-    }
+StencilCoefs make_coefs(const double dx[3], int radius) {
+    StencilCoefs c = {};
+    c.radius = radius;
     const int pa[3] = {0, 0, 1}, pb[3] = {1, 2, 2};
+    if (radius == 3) {
+        const double w1[3] = {45.0, -9.0, 1.0};
+        const double w2[3] = {1.5, -0.15, 1.0 / 90.0};
+        const double wc[3] = {270.0, -27.0, 2.0};
+        for (int a = 0; a < 3; ++a) {
+            for (int m = 0; m < 3; ++m) c.d1[a][m] = w1[m] / (60.0 * dx[a]);
+            c.d2[a][0] = (-49.0 / 18.0) / (dx[a] * dx[a]);
+            for (int m = 0; m < 3; ++m) c.d2[a][m + 1] = w2[m] / (dx[a] * dx[a]);
+        }
+        for (int pl = 0; pl < 3; ++pl)
+            for (int m = 0; m < 3; ++m) c.dc[pl][m] = wc[m] / (720.0 * dx[pa[pl]] * dx[pb[pl]]);
+        return c;
+    }
+    static const double n1[5][4] = {{0}, {1}, {8, -1}, {0}, {672, -168, 32, -3}};
+    static const double q1[5] = {0, 2, 12, 0, 840};
+    static const double n2[5][5] = {{0}, {-2, 1}, {-30, 16, -1}, {0}, {-14350, 8064, -1008, 128, -9}};
+    static const double q2[5] = {0, 1, 12, 0, 5040};
+    for (int a = 0; a < 3; ++a) {
+        for (int m = 0; m < radius; ++m) c.d1[a][m] = n1[radius][m] / (q1[radius] * dx[a]);
+        for (int m = 0; m <= radius; ++m) c.d2[a][m] = n2[radius][m] / (q2[radius] * dx[a] * dx[a]);
+    }
     for (int pl = 0; pl < 3; ++pl)
-        for (int m = 0; m < 3; ++m) c.dc[pl][m] = wc[m] / (720.0 * dx[pa[pl]] * dx[pb[pl]]);
+        for (int m = 0; m < radius; ++m)
+            c.dc[pl][m] = n2[radius][m + 1] / (4.0 * q2[radius] * dx[pa[pl]] * dx[pb[pl]]);
     return c;
 }
 
@@ -227,7 +250,7 @@ int reduce_max_blocks() { return RED_MAX_BLOCKS; }
 
 // Rows of constant (y, z) are dealt to warps; lanes walk x.  The periodic
 // offsets of y and z are set once per row, those of x once per cell.
-template <typename R, class IX>
+template <typename R, class IX, int RAD = 3>
 __global__ void __launch_bounds__(RED_THREADS) reduce_kernel(PtrPack<const R> pk, Geom g,
                                                              DevCoefs<R> k, int op, int quantity,
                                                              double *partials,
@@ -245,7 +268,7 @@ __global__ void __launch_bounds__(RED_THREADS) reduce_kernel(PtrPack<const R> pk
         ix.set_z(kz, g);
         for (int i = lane; i < g.nx; i += 32) {
             ix.set_x(i, g);
-            const double v = cell_quantity<R>(pk.p, ix, k, quantity);
+            const double v = cell_quantity<R, IX, RAD>(pk.p, ix, k, quantity);
             if (!isfinite(v)) bad = 1;
             acc = red_combine(op, acc, op == AC_RMS ? v * v : v);
         }
@@ -310,12 +333,31 @@ static cudaError_t launch_reduce_t(const ReduceLaunch &L, cudaStream_t st, int *
     long long blocks = (rows + RED_THREADS / 32 - 1) / (RED_THREADS / 32);
     if (blocks > L.blocks) blocks = L.blocks;
     if (blocks < 1) blocks = 1;
-    if (L.g.padded)
-        reduce_kernel<R, IdxPadded><<<(unsigned)blocks, RED_THREADS, 0, st>>>(
-            pk, L.g, k, L.op, L.quantity, L.partials, L.flags);
-    else
-        reduce_kernel<R, IdxPeriodic><<<(unsigned)blocks, RED_THREADS, 0, st>>>(
-            pk, L.g, k, L.op, L.quantity, L.partials, L.flags);
+    const unsigned nb = (unsigned)blocks;
+    // B = curl A uses the handle's stencil order (padded layout: radius <= 3)
+    switch (L.c.radius) {
+        case 1:
+            if (L.g.padded)
+                reduce_kernel<R, IdxPadded, 1><<<nb, RED_THREADS, 0, st>>>(pk, L.g, k, L.op, L.quantity, L.partials, L.flags);
+            else
+                reduce_kernel<R, IdxPeriodicR<1>, 1><<<nb, RED_THREADS, 0, st>>>(pk, L.g, k, L.op, L.quantity, L.partials, L.flags);
+            break;
+        case 2:
+            if (L.g.padded)
+                reduce_kernel<R, IdxPadded, 2><<<nb, RED_THREADS, 0, st>>>(pk, L.g, k, L.op, L.quantity, L.partials, L.flags);
+            else
+                reduce_kernel<R, IdxPeriodicR<2>, 2><<<nb, RED_THREADS, 0, st>>>(pk, L.g, k, L.op, L.quantity, L.partials, L.flags);
+            break;
+        case 4:
+            reduce_kernel<R, IdxPeriodicR<4>, 4><<<nb, RED_THREADS, 0, st>>>(pk, L.g, k, L.op, L.quantity, L.partials, L.flags);
+            break;
+        default:
+            if (L.g.padded)
+                reduce_kernel<R, IdxPadded><<<nb, RED_THREADS, 0, st>>>(pk, L.g, k, L.op, L.quantity, L.partials, L.flags);
+            else
+                reduce_kernel<R, IdxPeriodic><<<nb, RED_THREADS, 0, st>>>(pk, L.g, k, L.op, L.quantity, L.partials, L.flags);
+            break;
+    }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     reduce_final_kernel<<<1, RED_THREADS, 0, st>>>(L.partials, L.flags, (int)blocks, L.op,

@@ -24,7 +24,7 @@ __device__ __forceinline__ double red_combine(int op, double a, double b) {
 
 // Per-cell quantity, evaluated in the field precision R (binary64 fields: all
 // in binary64) and widened to binary64 for the accumulation.
-template <typename R, class IX>
+template <typename R, class IX, int RAD = 3>
 __device__ double cell_quantity(const R *const *f, const IX &ix, const DevCoefs<R> &k,
                                 int quantity) {
     const long long c0 = ix(0, 0, 0);
@@ -36,9 +36,9 @@ __device__ double cell_quantity(const R *const *f, const IX &ix, const DevCoefs<
     if (quantity == AC_Q_EKIN) return (double)((R)0.5 * exp(lnrho) * u2);
     // B = curl A with the first-derivative operator.
     const GlobalView<R, IX> ax{f[5], ix}, ay{f[6], ix}, az{f[7], ix};
-    const R Bx = op_d1<1>(az, k.d1[1]) - op_d1<2>(ay, k.d1[2]);
-    const R By = op_d1<2>(ax, k.d1[2]) - op_d1<0>(az, k.d1[0]);
-    const R Bz = op_d1<0>(ay, k.d1[0]) - op_d1<1>(ax, k.d1[1]);
+    const R Bx = op_d1<1, RAD>(az, k.d1[1]) - op_d1<2, RAD>(ay, k.d1[2]);
+    const R By = op_d1<2, RAD>(ax, k.d1[2]) - op_d1<0, RAD>(az, k.d1[0]);
+    const R Bz = op_d1<0, RAD>(ay, k.d1[0]) - op_d1<1, RAD>(ax, k.d1[1]);
     const R b2 = Bx * Bx + By * By + Bz * Bz;
     if (quantity == AC_Q_EMAG) return (double)((R)0.5 * b2);
     // AC_Q_CFL

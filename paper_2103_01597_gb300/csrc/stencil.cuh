@@ -1,7 +1,7 @@
 // Device-side stencil machinery: cell indexing with the periodic map of
-// Sec. 3.3 or a radius-3 halo, the sixth-order operators on the point set of
-// Sec. 4 Eq. 13, and the fused RHS (Eqs. B.1-B.4) + Runge-Kutta update of one
-// cell.
+// Sec. 3.3 or a radius-3 halo, the central operators of order 2r on the point
+// set of Sec. 4 Eq. 13 (r = 3 there; r = 1, 2, 4 widen it), and the fused RHS
+// (Eqs. B.1-B.4) + Runge-Kutta update of one cell.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -13,9 +13,9 @@ namespace ac {
 // Coefficients and constants in the kernel's arithmetic type R.
 template <typename R>
 struct DevCoefs {
-    R d1[3][3];
-    R d2[3][4];
-    R dc[3][3];
+    R d1[3][MAX_RADIUS];
+    R d2[3][MAX_RADIUS + 1];
+    R dc[3][MAX_RADIUS];
     R nu, eta, nu3, two_nu;  // nu / 3, 2 nu
     R inv_cp, cs2_ref, gamma_cp, gm1, cp_gm1;
 };
@@ -24,11 +24,11 @@ template <typename R>
 inline DevCoefs<R> to_dev(const StencilCoefs &c, const PhysConsts &p) {
     DevCoefs<R> d;
     for (int a = 0; a < 3; ++a) {
-        for (int m = 0; m < 3; ++m) {
+        for (int m = 0; m < MAX_RADIUS; ++m) {
             d.d1[a][m] = (R)c.d1[a][m];
             d.dc[a][m] = (R)c.dc[a][m];
         }
-        for (int m = 0; m < 4; ++m) d.d2[a][m] = (R)c.d2[a][m];
+        for (int m = 0; m <= MAX_RADIUS; ++m) d.d2[a][m] = (R)c.d2[a][m];
     }
     d.nu = (R)p.nu;
     d.eta = (R)p.eta;
@@ -42,38 +42,42 @@ inline DevCoefs<R> to_dev(const StencilCoefs &c, const PhysConsts &p) {
     return d;
 }
 
-// Periodic wrap of an index that is at most 3 cells outside [0, n).
+// Periodic wrap of an index that is at most MAX_RADIUS cells outside [0, n).
 __device__ __forceinline__ int wrap_near(int v, int n) {
-    // n >= 1; v in [-3, n + 2]
+    // n >= 1; v in [-MAX_RADIUS, n + MAX_RADIUS - 1]
     while (v < 0) v += n;
     while (v >= n) v -= n;
     return v;
 }
 
-// Cell addressing without a halo: every offset is wrapped (Sec. 3.3 map).
-struct IdxPeriodic {
-    int xo[7];
-    long long yo[7];
-    long long zo[7];
+// Cell addressing without a halo: every offset is wrapped (Sec. 3.3 map);
+// offsets up to RAD cells along each axis.
+template <int RAD>
+struct IdxPeriodicR {
+    static constexpr int W = 2 * RAD + 1;
+    int xo[W];
+    long long yo[W];
+    long long zo[W];
     __device__ __forceinline__ void set_xy(int i, int j, const Geom &g) {
 #pragma unroll
-        for (int d = 0; d < 7; ++d) {
-            xo[d] = wrap_near(i + d - 3, g.nx);
-            yo[d] = (long long)wrap_near(j + d - 3, g.ny) * g.px;
+        for (int d = 0; d < W; ++d) {
+            xo[d] = wrap_near(i + d - RAD, g.nx);
+            yo[d] = (long long)wrap_near(j + d - RAD, g.ny) * g.px;
         }
     }
     __device__ __forceinline__ void set_z(int k, const Geom &g) {
 #pragma unroll
-        for (int d = 0; d < 7; ++d) zo[d] = (long long)wrap_near(k + d - 3, g.nz) * g.pxy;
+        for (int d = 0; d < W; ++d) zo[d] = (long long)wrap_near(k + d - RAD, g.nz) * g.pxy;
     }
     __device__ __forceinline__ void set_x(int i, const Geom &g) {
 #pragma unroll
-        for (int d = 0; d < 7; ++d) xo[d] = wrap_near(i + d - 3, g.nx);
+        for (int d = 0; d < W; ++d) xo[d] = wrap_near(i + d - RAD, g.nx);
     }
     __device__ __forceinline__ long long operator()(int dx, int dy, int dz) const {
-        return zo[dz + 3] + yo[dy + 3] + xo[dx + 3];
+        return zo[dz + RAD] + yo[dy + RAD] + xo[dx + RAD];
     }
 };
+using IdxPeriodic = IdxPeriodicR<3>;
 
 // Cell addressing inside a padded array whose halo holds the periodic images.
 struct IdxPadded {
@@ -129,44 +133,51 @@ struct GlobalCell {
     __device__ __forceinline__ long long center() const { return ix(0, 0, 0); }
 };
 
-// ---- sixth-order operators (r = 3) ---------------------------------------
+// ---- central operators of order 2 RAD (RAD = 3: sixth order, Sec. 4) ------
+// Sums run m = 1 .. RAD in that order, so RAD = 3 rounds exactly as the
+// sixth-order formulas written out term by term.
 
 // First derivative along axis AX: sum_m d1[m-1] (f_m - f_-m).
-template <int AX, typename R, class V>
-__device__ __forceinline__ R op_d1(const V &f, const R (&c)[3]) {
+template <int AX, int RAD = 3, typename R, class V>
+__device__ __forceinline__ R op_d1(const V &f, const R (&c)[MAX_RADIUS]) {
     constexpr int ox = AX == 0, oy = AX == 1, oz = AX == 2;
-    const R a1 = f(ox, oy, oz) - f(-ox, -oy, -oz);
-    const R a2 = f(2 * ox, 2 * oy, 2 * oz) - f(-2 * ox, -2 * oy, -2 * oz);
-    const R a3 = f(3 * ox, 3 * oy, 3 * oz) - f(-3 * ox, -3 * oy, -3 * oz);
-    return c[0] * a1 + c[1] * a2 + c[2] * a3;
+    R sum = c[0] * (f(ox, oy, oz) - f(-ox, -oy, -oz));
+#pragma unroll
+    for (int m = 2; m <= RAD; ++m)
+        sum += c[m - 1] * (f(m * ox, m * oy, m * oz) - f(-m * ox, -m * oy, -m * oz));
+    return sum;
 }
 
 // Second derivative along axis AX: d2[0] f_0 + sum_m d2[m] (f_m + f_-m).
-template <int AX, typename R, class V>
-__device__ __forceinline__ R op_d2(const V &f, R f0, const R (&c)[4]) {
+template <int AX, int RAD = 3, typename R, class V>
+__device__ __forceinline__ R op_d2(const V &f, R f0, const R (&c)[MAX_RADIUS + 1]) {
     constexpr int ox = AX == 0, oy = AX == 1, oz = AX == 2;
-    const R s1 = f(ox, oy, oz) + f(-ox, -oy, -oz);
-    const R s2 = f(2 * ox, 2 * oy, 2 * oz) + f(-2 * ox, -2 * oy, -2 * oz);
-    const R s3 = f(3 * ox, 3 * oy, 3 * oz) + f(-3 * ox, -3 * oy, -3 * oz);
-    return c[0] * f0 + c[1] * s1 + c[2] * s2 + c[3] * s3;
+    R sum = c[0] * f0;
+#pragma unroll
+    for (int m = 1; m <= RAD; ++m)
+        sum += c[m] * (f(m * ox, m * oy, m * oz) + f(-m * ox, -m * oy, -m * oz));
+    return sum;
 }
 
 // Mixed derivative in the plane of axes A < B from the face diagonals of Eq. 13:
 // sum_m dc[m-1] S_m, S_m = f(+m,+m) + f(-m,-m) - f(+m,-m) - f(-m,+m).
-template <int A, int B, typename R, class V>
-__device__ __forceinline__ R op_dab(const V &f, const R (&c)[3]) {
+template <int A, int B, int RAD = 3, typename R, class V>
+__device__ __forceinline__ R op_dab(const V &f, const R (&c)[MAX_RADIUS]) {
     constexpr int ax = A == 0, ay = A == 1, az = A == 2;
     constexpr int bx = B == 0, by = B == 1, bz = B == 2;
-    R S[3];
+    R S[RAD];
 #pragma unroll
-    for (int m = 1; m <= 3; ++m) {
+    for (int m = 1; m <= RAD; ++m) {
         const R pp = f(m * (ax + bx), m * (ay + by), m * (az + bz));
         const R mm = f(-m * (ax + bx), -m * (ay + by), -m * (az + bz));
         const R pm = f(m * (ax - bx), m * (ay - by), m * (az - bz));
         const R mp = f(-m * (ax - bx), -m * (ay - by), -m * (az - bz));
         S[m - 1] = (pp + mm) - (pm + mp);
     }
-    return c[0] * S[0] + c[1] * S[1] + c[2] * S[2];
+    R sum = c[0] * S[0];
+#pragma unroll
+    for (int m = 2; m <= RAD; ++m) sum += c[m - 1] * S[m - 1];
+    return sum;
 }
 
 // Plane index of the axis pair (a, b): xy -> 0, xz -> 1, yz -> 2.
@@ -180,18 +191,18 @@ struct Plane {
 // Second derivatives of one vector component V_C: its Laplacian, the pure
 // derivative along its own axis (d_CC V_C) and the two mixed derivatives
 // d_C d_b V_C (b != C) that enter grad(div V).
-template <int C, typename R, class V>
+template <int C, int RAD = 3, typename R, class V>
 __device__ __forceinline__ void component_second(const V &f, R f0, const DevCoefs<R> &k, R &lap,
                                                  R &dcc, R &cross_b1, R &cross_b2) {
-    const R dxx = op_d2<0>(f, f0, k.d2[0]);
-    const R dyy = op_d2<1>(f, f0, k.d2[1]);
-    const R dzz = op_d2<2>(f, f0, k.d2[2]);
+    const R dxx = op_d2<0, RAD>(f, f0, k.d2[0]);
+    const R dyy = op_d2<1, RAD>(f, f0, k.d2[1]);
+    const R dzz = op_d2<2, RAD>(f, f0, k.d2[2]);
     lap = dxx + dyy + dzz;
     constexpr int B1 = C == 0 ? 1 : 0;
     constexpr int B2 = C == 2 ? 1 : 2;
     dcc = C == 0 ? dxx : (C == 1 ? dyy : dzz);
-    cross_b1 = op_dab<(C < B1 ? C : B1), (C < B1 ? B1 : C)>(f, k.dc[Plane<C, B1>::id]);
-    cross_b2 = op_dab<(C < B2 ? C : B2), (C < B2 ? B2 : C)>(f, k.dc[Plane<C, B2>::id]);
+    cross_b1 = op_dab<(C < B1 ? C : B1), (C < B1 ? B1 : C), RAD>(f, k.dc[Plane<C, B1>::id]);
+    cross_b2 = op_dab<(C < B2 ? C : B2), (C < B2 ? B2 : C), RAD>(f, k.dc[Plane<C, B2>::id]);
 }
 
 template <typename R> __device__ __forceinline__ R dev_exp(R x);
@@ -263,7 +274,7 @@ __device__ __forceinline__ void cell_physics(R lnrho, const R (&u)[3], R ss, con
 // `f` is a cell accessor: f[q] is the view of field q around the cell.  With
 // `cfl` non-null, the fastest signal speed of the input state at the cell,
 // |u| + sqrt(c_s^2 + |B|^2 / rho) (mu0 = 1), is written there as well.
-template <typename R, class CELL>
+template <typename R, int RAD = 3, class CELL>
 __device__ __forceinline__ void cell_rhs(const CELL &f, const DevCoefs<R> &k, const R frc[3],
                                          R out[NF], R *cfl = nullptr) {
     const R lnrho = f[0](0, 0, 0);
@@ -273,50 +284,50 @@ __device__ __forceinline__ void cell_rhs(const CELL &f, const DevCoefs<R> &k, co
 
     // First derivatives.
     R gl[3], gs[3], gu[3][3], ga[3][3];
-    gl[0] = op_d1<0>(f[0], k.d1[0]);
-    gl[1] = op_d1<1>(f[0], k.d1[1]);
-    gl[2] = op_d1<2>(f[0], k.d1[2]);
-    gs[0] = op_d1<0>(f[4], k.d1[0]);
-    gs[1] = op_d1<1>(f[4], k.d1[1]);
-    gs[2] = op_d1<2>(f[4], k.d1[2]);
+    gl[0] = op_d1<0, RAD>(f[0], k.d1[0]);
+    gl[1] = op_d1<1, RAD>(f[0], k.d1[1]);
+    gl[2] = op_d1<2, RAD>(f[0], k.d1[2]);
+    gs[0] = op_d1<0, RAD>(f[4], k.d1[0]);
+    gs[1] = op_d1<1, RAD>(f[4], k.d1[1]);
+    gs[2] = op_d1<2, RAD>(f[4], k.d1[2]);
 #pragma unroll
     for (int m = 0; m < 3; ++m) {
-        gu[m][0] = op_d1<0>(f[1 + m], k.d1[0]);
-        gu[m][1] = op_d1<1>(f[1 + m], k.d1[1]);
-        gu[m][2] = op_d1<2>(f[1 + m], k.d1[2]);
-        ga[m][0] = op_d1<0>(f[5 + m], k.d1[0]);
-        ga[m][1] = op_d1<1>(f[5 + m], k.d1[1]);
-        ga[m][2] = op_d1<2>(f[5 + m], k.d1[2]);
+        gu[m][0] = op_d1<0, RAD>(f[1 + m], k.d1[0]);
+        gu[m][1] = op_d1<1, RAD>(f[1 + m], k.d1[1]);
+        gu[m][2] = op_d1<2, RAD>(f[1 + m], k.d1[2]);
+        ga[m][0] = op_d1<0, RAD>(f[5 + m], k.d1[0]);
+        ga[m][1] = op_d1<1, RAD>(f[5 + m], k.d1[1]);
+        ga[m][2] = op_d1<2, RAD>(f[5 + m], k.d1[2]);
     }
 
     // Second derivatives: Laplacians and grad(div .) of u and A.
     R lapu[3], lapa[3], gdu[3], gda[3];
     {
         R dcc, c1, c2;
-        component_second<0>(f[1], u[0], k, lapu[0], dcc, c1, c2);  // c1 = d_xy u_x, c2 = d_xz u_x
+        component_second<0, RAD>(f[1], u[0], k, lapu[0], dcc, c1, c2);  // c1 = d_xy u_x, c2 = d_xz u_x
         gdu[0] = dcc;
         gdu[1] = c1;
         gdu[2] = c2;
-        component_second<1>(f[2], u[1], k, lapu[1], dcc, c1, c2);  // c1 = d_xy u_y, c2 = d_yz u_y
+        component_second<1, RAD>(f[2], u[1], k, lapu[1], dcc, c1, c2);  // c1 = d_xy u_y, c2 = d_yz u_y
         gdu[0] += c1;
         gdu[1] += dcc;
         gdu[2] += c2;
-        component_second<2>(f[3], u[2], k, lapu[2], dcc, c1, c2);  // c1 = d_xz u_z, c2 = d_yz u_z
+        component_second<2, RAD>(f[3], u[2], k, lapu[2], dcc, c1, c2);  // c1 = d_xz u_z, c2 = d_yz u_z
         gdu[0] += c1;
         gdu[1] += c2;
         gdu[2] += dcc;
     }
     {
         R dcc, c1, c2;
-        component_second<0>(f[5], aa[0], k, lapa[0], dcc, c1, c2);
+        component_second<0, RAD>(f[5], aa[0], k, lapa[0], dcc, c1, c2);
         gda[0] = dcc;
         gda[1] = c1;
         gda[2] = c2;
-        component_second<1>(f[6], aa[1], k, lapa[1], dcc, c1, c2);
+        component_second<1, RAD>(f[6], aa[1], k, lapa[1], dcc, c1, c2);
         gda[0] += c1;
         gda[1] += dcc;
         gda[2] += c2;
-        component_second<2>(f[7], aa[2], k, lapa[2], dcc, c1, c2);
+        component_second<2, RAD>(f[7], aa[2], k, lapa[2], dcc, c1, c2);
         gda[0] += c1;
         gda[1] += c2;
         gda[2] += dcc;
