@@ -50,6 +50,9 @@ typedef struct {
     double force_e[3];     /* unit polarisation vector, perpendicular to k    */
     double force_phi;      /* phase of this step's forcing                     */
     int64_t radius;        /* stencil radius r (order 2r): 1, 2, 3 or 4       */
+    double K;              /* radiative thermal conductivity (constant)        */
+    double zeta;           /* bulk viscosity (kinematic, as in Eq. B.2)        */
+    double heat, cool;     /* explicit heating H and cooling C (uniform rates) */
 } oracle_params;
 
 /* ------------------------------------------------------------------------ */
@@ -283,9 +286,10 @@ void oracle_rhs(const double *const f[NFIELDS], const oracle_params *p,
     /* Eq. B.1: D ln rho / Dt = -div u. */
     out[LNRHO] = -ADV(LNRHO) - divu;
 
-    /* Eq. B.2 (zeta = 0):
+    /* Eq. B.2:
      * Du/Dt = -c_s^2 grad(s/c_p + ln rho) + j x B / rho
-     *         + nu [lap u + grad(div u)/3 + 2 S . grad ln rho]  (+ forcing). */
+     *         + nu [lap u + grad(div u)/3 + 2 S . grad ln rho]
+     *         + zeta grad(div u)  (+ forcing). */
     double fr[3] = {0.0, 0.0, 0.0};
     if (p->force_on)
         forcing_at(p, c, fr);
@@ -297,12 +301,29 @@ void oracle_rhs(const double *const f[NFIELDS], const oracle_params *p,
                   - cs2 * (g[SS][m] / p->cp + g[LNRHO][m])
                   + JxB[m] / rho
                   + p->nu * (lapu[m] + graddivu[m] / 3.0 + 2.0 * sgl)
+                  + p->zeta * graddivu[m]
                   + fr[m];
     }
 
-    /* Eq. B.3 (H = C = K = zeta = 0, mu0 = 1):
-     * rho T Ds/Dt = eta j^2 + 2 rho nu S:S. */
-    out[SS] = -ADV(SS) + (p->eta * J2 + 2.0 * rho * p->nu * SS2) / (rho * T);
+    /* Eq. B.3 (mu0 = 1):
+     * rho T Ds/Dt = H - C + div(K grad T) + eta j^2 + 2 rho nu S:S + zeta rho (div u)^2.
+     * Reading (the paper fixes no discretisation of the conduction term): with
+     * T = T_0 exp(xi), xi = gamma s / c_p + (gamma - 1)(ln rho - ln rho0),
+     * grad T = T grad xi and, K constant, div(K grad T) = K T (lap xi + |grad xi|^2),
+     * with grad xi and lap xi from the stencils of s and ln rho.  H and C are
+     * uniform rates (the paper gives no form). */
+    double cond = 0.0;
+    if (p->K != 0.0) {
+        double gxi2 = 0.0, lapxi = 0.0;
+        for (int a = 0; a < 3; ++a) {
+            const double gxi = p->gamma / p->cp * g[SS][a] + (p->gamma - 1.0) * g[LNRHO][a];
+            gxi2 += gxi * gxi;
+            lapxi += p->gamma / p->cp * d2(f[SS], p, c, a) + (p->gamma - 1.0) * d2(f[LNRHO], p, c, a);
+        }
+        cond = p->K * T * (lapxi + gxi2);
+    }
+    out[SS] = -ADV(SS) + (p->heat - p->cool + cond + p->eta * J2 + 2.0 * rho * p->nu * SS2
+                          + p->zeta * rho * divu * divu) / (rho * T);
 
     /* Eq. B.4: dA/dt = u x B + eta lap A. */
     for (int m = 0; m < 3; ++m)

@@ -138,6 +138,9 @@ def rhs(f, p, ops=None):
         return U[0] * g[q][0] + U[1] * g[q][1] + U[2] * g[q][2]
 
     out = np.empty((NF, v[0].size))
+    K = getattr(p, "K", 0.0)
+    zeta = getattr(p, "zeta", 0.0)
+    heat, cool = getattr(p, "heat", 0.0), getattr(p, "cool", 0.0)
     out[0] = -adv(0) - divu
     force = np.zeros((3, v[0].size))
     if p.forcing is not None:
@@ -150,8 +153,14 @@ def rhs(f, p, ops=None):
     for m in range(3):
         sgl = S[m][0] * g[0][0] + S[m][1] * g[0][1] + S[m][2] * g[0][2]
         out[1 + m] = (-adv(1 + m) - cs2 * (g[4][m] / p.cp + g[0][m]) + JxB[m] / rho
-                      + p.nu * (lapu[m] + gdu[m] / 3.0 + 2.0 * sgl) + force[m])
-    out[4] = -adv(4) + (p.eta * J2 + 2.0 * rho * p.nu * SS2) / (rho * T)
+                      + p.nu * (lapu[m] + gdu[m] / 3.0 + 2.0 * sgl) + zeta * gdu[m] + force[m])
+    # conduction div(K grad T) = K T (lap xi + |grad xi|^2), xi = gamma s / c_p + (gamma-1) ln rho
+    gxi = [p.gamma / p.cp * g[4][a] + (p.gamma - 1.0) * g[0][a] for a in range(3)]
+    lapxi = sum(p.gamma / p.cp * (ops.D2[a, a] @ s) + (p.gamma - 1.0) * (ops.D2[a, a] @ lnrho)
+                for a in range(3))
+    cond = K * T * (lapxi + sum(x * x for x in gxi))
+    out[4] = -adv(4) + (heat - cool + cond + p.eta * J2 + 2.0 * rho * p.nu * SS2
+                        + zeta * rho * divu ** 2) / (rho * T)
     for m in range(3):
         out[5 + m] = UxB[m] + p.eta * lapa[m]
     return out.reshape((NF,) + shape)

@@ -26,7 +26,8 @@ class _CParams(ctypes.Structure):
     _fields_ = [("n", _i64 * 3), ("dx", _f64 * 3), ("nu", _f64), ("eta", _f64),
                 ("cs0", _f64), ("gamma", _f64), ("cp", _f64), ("lnrho0", _f64),
                 ("force_on", _i64), ("force_amp", _f64), ("force_k", _i64 * 3),
-                ("force_e", _f64 * 3), ("force_phi", _f64), ("radius", _i64)]
+                ("force_e", _f64 * 3), ("force_phi", _f64), ("radius", _i64),
+                ("K", _f64), ("zeta", _f64), ("heat", _f64), ("cool", _f64)]
 
 
 @dataclass
@@ -51,6 +52,10 @@ class Params:
     lnrho0: float = 0.0
     forcing: Forcing = field(default=None)
     order: int = 6                 # stencil order 2r (Sec. 4 uses 6; 2, 4, 8 widen it)
+    K: float = 0.0                 # thermal conductivity (Eq. B.3)
+    zeta: float = 0.0              # bulk viscosity (Eqs. B.2, B.3)
+    heat: float = 0.0              # explicit heating H (uniform rate)
+    cool: float = 0.0              # explicit cooling C (uniform rate)
 
     @property
     def dx(self):
@@ -66,6 +71,7 @@ class Params:
         if self.order not in (2, 4, 6, 8):
             raise ValueError("stencil order must be 2, 4, 6 or 8")
         cp.radius = self.order // 2
+        cp.K, cp.zeta, cp.heat, cp.cool = self.K, self.zeta, self.heat, self.cool
         if self.forcing is not None:
             cp.force_on = 1
             cp.force_amp = self.forcing.amp
