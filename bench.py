@@ -97,6 +97,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--stencil-order", type=int, default=6, choices=[2, 4, 6, 8],
                     help="central-difference order of the substep (the paper's is 6)")
+    ap.add_argument("--full-entropy", action="store_true",
+                    help="switch on conduction, bulk viscosity, heating and cooling "
+                         "(K = zeta = 1e-3, H = 0.02, C = 0.01)")
     ap.add_argument("--closure-pairs", type=int, default=24)
     ap.add_argument("--closure-iters", type=int, default=800)
     ap.add_argument("--closure-rollout", type=int, default=20)
@@ -197,7 +200,7 @@ def oracle_sample(wl, f, planes):
     if wl["force_amp"]:
         fr = core.forcing_draw(wl["seed"], 0, wl["force_amp"])
         frc = fr
-    p = core.Params(n=wl["n"], forcing=frc, order=wl.get("order", 6))
+    p = core.Params(n=wl["n"], forcing=frc, order=wl.get("order", 6), **wl.get("entropy", {}))
     w = np.zeros_like(f)
     t0 = time.perf_counter()
     for s in range(3):
@@ -296,7 +299,8 @@ def run_ours(args, wl):
     stream = torch.cuda.current_stream()
     order = wl.get("order", 6)
     sim = ac.Simulation(n, precision=prec, force_amp=wl["force_amp"], seed=wl["seed"],
-                        device="cuda:%d" % local, stream=stream.cuda_stream, order=order)
+                        device="cuda:%d" % local, stream=stream.cuda_stream, order=order,
+                        **wl.get("entropy", {}))
     f0 = make_state(wl)
     host_in = torch.from_numpy(f0.reshape(-1)).pin_memory()
     host_out = torch.empty_like(host_in).pin_memory()
@@ -417,6 +421,7 @@ def run_ours(args, wl):
                 "config": {"workload": wl["desc"], "grid": list(n), "dt": dt,
                            "precision": wl["precision"], "layout": "periodic (wrap on load)",
                            "stencil_order": order,
+                           "entropy_terms": wl.get("entropy"),
                            "parallelism": "replicas" if ws > 1 else "single GPU",
                            "l2": "inputs larger than L2 (%.1f GB of state resident)"
                                  % (ncell * (16 * elem_f + 8 * elem_w) / 1e9),
@@ -952,6 +957,10 @@ def run_closure_forward_reference(args, wl):
 def main():
     args = parse()
     wl = dict(WORKLOADS[args.workload])
+    if args.full_entropy:
+        wl["entropy"] = dict(K=1e-3, zeta=1e-3, heat=0.02, cool=0.01)
+        wl["desc"] += " + conduction, bulk viscosity, heating, cooling"
+        wl.pop("vs", None)
     if args.stencil_order != 6:
         wl["order"] = args.stencil_order
         wl["desc"] = wl["desc"].replace("6th-order", "%dth-order" % args.stencil_order) + \

@@ -169,6 +169,20 @@ int ac_store_w(ac_handle *h, int field, double *host_dst);
 int ac_integrate_substep(ac_handle *h, double dt, int s);
 
 /*
+ * The terms of Eqs. B.2-B.3 that the base configuration sets to zero: thermal
+ * conductivity K (constant), bulk viscosity zeta (kinematic, as written in
+ * Eq. B.2: du/dt gains zeta grad(div u), rho T ds/dt gains zeta rho (div u)^2),
+ * and explicit heating H and cooling C (uniform rates: rho T ds/dt gains
+ * H - C).  Conduction: div(K grad T) = K T (lap xi + |grad xi|^2) with
+ * xi = gamma s / c_p + (gamma - 1)(ln rho - ln rho0) (grad T = T grad xi), the
+ * gradient and Laplacian of xi taken with the stencils of s and ln rho.
+ * All four must be finite and >= 0 (AC_ERR_ARG otherwise); default 0.  Any
+ * non-zero term selects kernels that evaluate them (binary64, binary32 and
+ * the integer-sum path alike); the batched ensemble keeps the base terms.
+ */
+int ac_set_entropy_terms(ac_handle *h, double K, double zeta, double heat, double cool);
+
+/*
  * Stencil order (Sec. 4 uses sixth order, radius 3, on the points of Eq. 13;
  * orders 2, 4 and 8 use the same kind of point set out to radius 1, 2, 4:
  * the axes and the face diagonals).  Central weights of order 2r: first

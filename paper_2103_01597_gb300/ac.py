@@ -125,6 +125,8 @@ def load_library(path=None):
                            ctypes.POINTER(_c.c_int), ctypes.POINTER(_c.c_int),
                            ctypes.POINTER(_c.c_ulonglong)], _c.c_int),
         "ac_set_stencil_order": ([_vp, _c.c_int], _c.c_int),
+        "ac_set_entropy_terms": ([_vp, _c.c_double, _c.c_double, _c.c_double, _c.c_double],
+                                 _c.c_int),
         "ac_get_stencil_order": ([_vp, ctypes.POINTER(_c.c_int)], _c.c_int),
         "ac_get_state": ([_vp, ctypes.POINTER(_vp), ctypes.POINTER(_c.c_int),
                           ctypes.POINTER(_c.c_int), ctypes.POINTER(_c.c_int)], _c.c_int),
@@ -300,6 +302,11 @@ def ac_set_forcing(h, k, e, phi):
     kk = (ctypes.c_int * 3)(*[int(v) for v in k])
     ee = (ctypes.c_double * 3)(*[float(v) for v in e])
     _check(load_library().ac_set_forcing(h, kk, ee, float(phi)), "ac_set_forcing")
+
+
+def ac_set_entropy_terms(h, K=0.0, zeta=0.0, heat=0.0, cool=0.0):
+    _check(load_library().ac_set_entropy_terms(h, float(K), float(zeta), float(heat), float(cool)),
+           "ac_set_entropy_terms")
 
 
 def ac_set_stencil_order(h, order):
@@ -578,7 +585,8 @@ class Simulation:
 
     def __init__(self, n, L=(2 * math.pi,) * 3, layout=AC_LAYOUT_PERIODIC, precision=AC_FP64,
                  nu=5e-3, eta=5e-3, cs0=1.0, gamma=5.0 / 3.0, cp=1.0, lnrho0=0.0,
-                 force_amp=0.0, seed=0, device="cuda", stream=None, order=6):
+                 force_amp=0.0, seed=0, device="cuda", stream=None, order=6, K=0.0, zeta=0.0,
+                 heat=0.0, cool=0.0):
         import torch
         self.n = tuple(n)
         self.precision = precision
@@ -599,6 +607,8 @@ class Simulation:
         ac_bind_buffers(self.h, ptrs)
         if order != 6:
             ac_set_stencil_order(self.h, order)
+        if K or zeta or heat or cool:
+            ac_set_entropy_terms(self.h, K, zeta, heat, cool)
         self._closed = False
 
     def load(self, f):

@@ -451,6 +451,17 @@ extern "C" int ac_set_stencil_mode(ac_handle *h, int mode) {
     return AC_OK;
 }
 
+extern "C" int ac_set_entropy_terms(ac_handle *h, double K, double zeta, double heat,
+                                    double cool) {
+    if (!h || !isfinite(K) || !isfinite(zeta) || !isfinite(heat) || !isfinite(cool) || K < 0.0 ||
+        zeta < 0.0 || heat < 0.0 || cool < 0.0)
+        return AC_ERR_ARG;
+    h->phys.K = K;
+    h->phys.zeta = zeta;
+    h->phys.hc = heat - cool;
+    return AC_OK;
+}
+
 extern "C" int ac_set_stencil_order(ac_handle *h, int order) {
     if (!h || (order != 2 && order != 4 && order != 6 && order != 8)) return AC_ERR_ARG;
     if (h->grid.layout == AC_LAYOUT_PADDED && order > 6) return AC_ERR_ARG;  // halo is 3 wide

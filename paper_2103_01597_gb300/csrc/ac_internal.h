@@ -62,6 +62,11 @@ struct PhysConsts {
     double gamma_cp;    // gamma / c_p
     double gm1;         // gamma - 1
     double cp_gm1;      // c_p (gamma - 1): 1/T = c_p (gamma - 1) / c_s^2
+    // Eq. B.2-B.3 terms beyond the base configuration (all 0 by default):
+    double K;           // thermal conductivity
+    double zeta;        // bulk viscosity
+    double hc;          // heating minus cooling, H - C
+    bool ext() const { return K != 0.0 || zeta != 0.0 || hc != 0.0; }
 };
 PhysConsts make_phys(const ac_params &p);
 

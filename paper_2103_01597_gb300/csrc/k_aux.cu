@@ -61,6 +61,9 @@ PhysConsts make_phys(const ac_params &p) {
     c.gamma_cp = p.gamma / p.cp;
     c.gm1 = p.gamma - 1.0;
     c.cp_gm1 = p.cp * (p.gamma - 1.0);
+    c.K = 0.0;
+    c.zeta = 0.0;
+    c.hc = 0.0;
     return c;
 }
 

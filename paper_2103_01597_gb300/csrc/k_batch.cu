@@ -88,7 +88,7 @@ __global__ void __launch_bounds__(TT_THREADS, 1) batch_substep_kernel(const __gr
         if (it >= b.nitems) break;
         const int4 wi = b.items[it];
         const TileBox<W> ta(b, b.box[wi.x]);
-        tiled_body<W, true, false>(ta, wi.y, wi.z, wi.w >> 16, wi.w & 0xffff, bt_smem_raw);
+        tiled_body<W, true, false, false>(ta, wi.y, wi.z, wi.w >> 16, wi.w & 0xffff, bt_smem_raw);
     }
 }
 

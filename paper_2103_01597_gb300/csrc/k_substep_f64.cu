@@ -33,7 +33,7 @@ cudaError_t launch_substep_f64(const SubstepLaunch &L, cudaStream_t st, int *lau
     FxCoefs fc;
     fc.inv60dx = 1.0 / (60.0 * L.dx);
     fc.nu180 = L.ph.nu / (180.0 * L.dx * L.dx);
-    fc.nu2160 = L.ph.nu / (2160.0 * L.dx * L.dx);
+    fc.nu2160 = (L.ph.nu + 3.0 * L.ph.zeta) / (2160.0 * L.dx * L.dx);
     fc.inv180dx2 = 1.0 / (180.0 * L.dx * L.dx);
     fc.inv720dx2 = 1.0 / (720.0 * L.dx * L.dx);
 
@@ -51,10 +51,17 @@ cudaError_t launch_substep_f64(const SubstepLaunch &L, cudaStream_t st, int *lau
     zchunk = zchunk < 1 ? 1 : (zchunk > 16 ? 16 : zchunk);
     a.zchunk = zchunk;
     const dim3 grid(gx, gy, (L.g.nz + zchunk - 1) / zchunk);
-    if (a.cfl_max)
-        substep_fx_kernel<IdxPeriodic, true><<<grid, block, 0, st>>>(a, fx, fc, L.fx_gmax);
-    else
-        substep_fx_kernel<IdxPeriodic, false><<<grid, block, 0, st>>>(a, fx, fc, L.fx_gmax);
+    if (L.ph.ext()) {
+        if (a.cfl_max)
+            substep_fx_kernel<IdxPeriodic, true, true><<<grid, block, 0, st>>>(a, fx, fc, L.fx_gmax);
+        else
+            substep_fx_kernel<IdxPeriodic, false, true><<<grid, block, 0, st>>>(a, fx, fc, L.fx_gmax);
+    } else {
+        if (a.cfl_max)
+            substep_fx_kernel<IdxPeriodic, true><<<grid, block, 0, st>>>(a, fx, fc, L.fx_gmax);
+        else
+            substep_fx_kernel<IdxPeriodic, false><<<grid, block, 0, st>>>(a, fx, fc, L.fx_gmax);
+    }
     *launches += 3;
     return cudaGetLastError();
 }

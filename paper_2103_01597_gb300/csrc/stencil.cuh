@@ -16,8 +16,9 @@ struct DevCoefs {
     R d1[3][MAX_RADIUS];
     R d2[3][MAX_RADIUS + 1];
     R dc[3][MAX_RADIUS];
-    R nu, eta, nu3, two_nu;  // nu / 3, 2 nu
+    R nu, eta, nu3, two_nu;  // nu3: coefficient of grad(div u), nu / 3 + zeta; 2 nu
     R inv_cp, cs2_ref, gamma_cp, gm1, cp_gm1;
+    R K, zeta, hc;           // conduction, bulk viscosity, H - C (Eqs. B.2-B.3)
 };
 
 template <typename R>
@@ -32,13 +33,16 @@ inline DevCoefs<R> to_dev(const StencilCoefs &c, const PhysConsts &p) {
     }
     d.nu = (R)p.nu;
     d.eta = (R)p.eta;
-    d.nu3 = (R)(p.nu / 3.0);
+    d.nu3 = (R)(p.nu / 3.0 + p.zeta);
     d.two_nu = (R)(2.0 * p.nu);
     d.inv_cp = (R)p.inv_cp;
     d.cs2_ref = (R)p.cs2_ref;
     d.gamma_cp = (R)p.gamma_cp;
     d.gm1 = (R)p.gm1;
     d.cp_gm1 = (R)p.cp_gm1;
+    d.K = (R)p.K;
+    d.zeta = (R)p.zeta;
+    d.hc = (R)p.hc;
     return d;
 }
 
@@ -209,18 +213,20 @@ template <typename R> __device__ __forceinline__ R dev_exp(R x);
 template <> __device__ __forceinline__ double dev_exp<double>(double x) { return exp(x); }
 template <> __device__ __forceinline__ float dev_exp<float>(float x) { return expf(x); }
 
-// RHS of Eqs. B.1-B.4 at one cell (mu0 = 1, zeta = H = C = K = 0), with the
-// forcing term `frc` added to du/dt.  Output order: Table B.1.
-// Eqs. B.1-B.4 at one cell given the centre values and the derivative terms:
-// gl, gs, gu[m][a] first derivatives of ln rho, s, u_m; B = curl A; viscl =
-// nu (lap u + grad(div u) / 3); lapa = lap A; J = grad(div A) - lap A (mu0 = 1).
-template <typename R>
+// Eqs. B.1-B.4 at one cell (mu0 = 1) given the centre values and the derivative
+// terms: gl, gs, gu[m][a] first derivatives of ln rho, s, u_m; B = curl A;
+// viscl = nu lap u + (nu / 3 + zeta) grad(div u) (the bulk viscosity of Eq. B.2
+// folded into the grad-div coefficient); lapa = lap A; J = grad(div A) - lap A.
+// The forcing term `frc` is added to du/dt.  EXT adds the remaining terms of
+// Eq. B.3: H - C, zeta rho (div u)^2 and div(K grad T) (from lapxi = lap xi);
+// without EXT they are zero.  Output order: Table B.1.
+template <typename R, bool EXT = false>
 __device__ __forceinline__ void cell_physics(R lnrho, const R (&u)[3], R ss, const R (&gl)[3],
                                              const R (&gs)[3], const R (&gu)[3][3],
                                              const R (&B)[3], const R (&viscl)[3],
                                              const R (&lapa)[3], const R (&J)[3],
                                              const DevCoefs<R> &k, const R frc[3], R out[NF],
-                                             R *cfl) {
+                                             R *cfl, R lapxi = (R)0) {
     // Thermodynamics: c_s^2 = c_s0^2 exp(gamma s / c_p + (gamma-1)(ln rho - ln rho0)),
     // 1/rho = exp(-ln rho), 1/T = c_p (gamma - 1) / c_s^2.
     const R rho_inv = dev_exp<R>(-lnrho);
@@ -260,6 +266,18 @@ __device__ __forceinline__ void cell_physics(R lnrho, const R (&u)[3], R ss, con
     // Eq. B.3: Ds/Dt = (eta j^2 + 2 rho nu S:S) / (rho T)
     out[4] = -(u[0] * gs[0] + u[1] * gs[1] + u[2] * gs[2])
            + (k.eta * J2 * rho_inv + k.two_nu * SS2) * inv_T;
+    if (EXT) {
+        // + (H - C + zeta rho (div u)^2) / (rho T) + div(K grad T) / (rho T), the last
+        // = K (lap xi + |grad xi|^2) / rho with xi = gamma s / c_p + (gamma-1) ln rho
+        // (grad T = T grad xi); lapxi is passed in, grad xi built from gs and gl.
+        R gxi2 = (R)0;
+#pragma unroll
+        for (int m = 0; m < 3; ++m) {
+            const R gxi = k.gamma_cp * gs[m] + k.gm1 * gl[m];
+            gxi2 += gxi * gxi;
+        }
+        out[4] += (k.hc * rho_inv + k.zeta * divu * divu) * inv_T + k.K * rho_inv * (lapxi + gxi2);
+    }
     // Eq. B.4
 #pragma unroll
     for (int m = 0; m < 3; ++m) out[5 + m] = UxB[m] + k.eta * lapa[m];
@@ -274,7 +292,7 @@ __device__ __forceinline__ void cell_physics(R lnrho, const R (&u)[3], R ss, con
 // `f` is a cell accessor: f[q] is the view of field q around the cell.  With
 // `cfl` non-null, the fastest signal speed of the input state at the cell,
 // |u| + sqrt(c_s^2 + |B|^2 / rho) (mu0 = 1), is written there as well.
-template <typename R, int RAD = 3, class CELL>
+template <typename R, int RAD = 3, bool EXT = false, class CELL>
 __device__ __forceinline__ void cell_rhs(const CELL &f, const DevCoefs<R> &k, const R frc[3],
                                          R out[NF], R *cfl = nullptr) {
     const R lnrho = f[0](0, 0, 0);
@@ -339,7 +357,15 @@ __device__ __forceinline__ void cell_rhs(const CELL &f, const DevCoefs<R> &k, co
     R viscl[3];
 #pragma unroll
     for (int m = 0; m < 3; ++m) viscl[m] = k.nu * lapu[m] + k.nu3 * gdu[m];
-    cell_physics<R>(lnrho, u, ss, gl, gs, gu, B, viscl, lapa, J, k, frc, out, cfl);
+    R lapxi = (R)0;
+    if (EXT) {  // lap xi = gamma / c_p lap s + (gamma - 1) lap ln rho
+        const R lsx = op_d2<0, RAD>(f[4], ss, k.d2[0]), lsy = op_d2<1, RAD>(f[4], ss, k.d2[1]),
+                lsz = op_d2<2, RAD>(f[4], ss, k.d2[2]);
+        const R llx = op_d2<0, RAD>(f[0], lnrho, k.d2[0]), lly = op_d2<1, RAD>(f[0], lnrho, k.d2[1]),
+                llz = op_d2<2, RAD>(f[0], lnrho, k.d2[2]);
+        lapxi = k.gamma_cp * (lsx + lsy + lsz) + k.gm1 * (llx + lly + llz);
+    }
+    cell_physics<R, EXT>(lnrho, u, ss, gl, gs, gu, B, viscl, lapa, J, k, frc, out, cfl, lapxi);
 }
 
 // Block-wide max of a non-negative value folded into a global 64-bit word that

@@ -39,7 +39,7 @@ __device__ __forceinline__ void rk_update(const SubstepArgs<R, W> &a, int q, lon
 
 // One (x, y) column of the tile: cells k0 .. k1-1 of the CTA's z range.  With
 // cfl_acc non-null the largest CFL speed of the input state is kept there.
-template <typename R, typename W, class IX, int RAD = 3>
+template <typename R, typename W, class IX, int RAD = 3, bool EXT = false>
 __device__ __forceinline__ void substep_column(const SubstepArgs<R, W> &a, int i, int j,
                                                R *cfl_acc) {
     const int k0 = blockIdx.z * a.zchunk;
@@ -68,10 +68,10 @@ __device__ __forceinline__ void substep_column(const SubstepArgs<R, W> &a, int i
         const GlobalCell<R, IX> cell{a.fin, ix};
         if (cfl_acc) {
             R c;
-            cell_rhs<R, RAD>(cell, a.k, frc, rhs, &c);
+            cell_rhs<R, RAD, EXT>(cell, a.k, frc, rhs, &c);
             *cfl_acc = (c > *cfl_acc || c != c) ? c : *cfl_acc;
         } else {
-            cell_rhs<R, RAD>(cell, a.k, frc, rhs);
+            cell_rhs<R, RAD, EXT>(cell, a.k, frc, rhs);
         }
         const long long o = ix(0, 0, 0);
 #pragma unroll
@@ -80,38 +80,48 @@ __device__ __forceinline__ void substep_column(const SubstepArgs<R, W> &a, int i
 }
 
 // CFL: also track the largest CFL speed of the input state (substep 0).
-template <typename R, typename W, class IX, bool CFL, int RAD = 3>
+// EXT: the conduction, bulk-viscosity and heating/cooling terms of Eq. B.3.
+template <typename R, typename W, class IX, bool CFL, int RAD = 3, bool EXT = false>
 __global__ void __launch_bounds__(128) substep_kernel(const SubstepArgs<R, W> a) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const int j = blockIdx.y * blockDim.y + threadIdx.y;
     const bool active = i < a.g.nx && j < a.g.ny;
     if (CFL) {
         R cfl = (R)0;
-        if (active) substep_column<R, W, IX, RAD>(a, i, j, &cfl);
+        if (active) substep_column<R, W, IX, RAD, EXT>(a, i, j, &cfl);
         block_max_to_global((double)cfl, a.cfl_max);
     } else if (active) {
-        substep_column<R, W, IX, RAD>(a, i, j, nullptr);
+        substep_column<R, W, IX, RAD, EXT>(a, i, j, nullptr);
     }
 }
 
 // Launch for radius RAD: periodic addressing with RAD-wide offsets, or the
 // padded layout (halo 3, so RAD <= 3).
-template <typename R, typename W, int RAD>
+template <typename R, typename W, int RAD, bool EXT>
 void launch_substep_r(const SubstepArgs<R, W> &a, bool padded, bool cfl, dim3 grid, dim3 block,
                       cudaStream_t st) {
     if (padded) {
         if constexpr (RAD <= 3) {
             if (cfl)
-                substep_kernel<R, W, IdxPadded, true, RAD><<<grid, block, 0, st>>>(a);
+                substep_kernel<R, W, IdxPadded, true, RAD, EXT><<<grid, block, 0, st>>>(a);
             else
-                substep_kernel<R, W, IdxPadded, false, RAD><<<grid, block, 0, st>>>(a);
+                substep_kernel<R, W, IdxPadded, false, RAD, EXT><<<grid, block, 0, st>>>(a);
         }
     } else {
         if (cfl)
-            substep_kernel<R, W, IdxPeriodicR<RAD>, true, RAD><<<grid, block, 0, st>>>(a);
+            substep_kernel<R, W, IdxPeriodicR<RAD>, true, RAD, EXT><<<grid, block, 0, st>>>(a);
         else
-            substep_kernel<R, W, IdxPeriodicR<RAD>, false, RAD><<<grid, block, 0, st>>>(a);
+            substep_kernel<R, W, IdxPeriodicR<RAD>, false, RAD, EXT><<<grid, block, 0, st>>>(a);
     }
+}
+
+template <typename R, typename W, int RAD>
+void launch_substep_re(const SubstepArgs<R, W> &a, bool padded, bool cfl, bool ext, dim3 grid,
+                       dim3 block, cudaStream_t st) {
+    if (ext)
+        launch_substep_r<R, W, RAD, true>(a, padded, cfl, grid, block, st);
+    else
+        launch_substep_r<R, W, RAD, false>(a, padded, cfl, grid, block, st);
 }
 
 template <typename R, typename W>
@@ -148,11 +158,12 @@ cudaError_t launch_substep_t(const SubstepLaunch &L, cudaStream_t st, int *launc
     a.zchunk = zchunk;
     const dim3 grid(gx, gy, (L.g.nz + zchunk - 1) / zchunk);
     const bool cfl = a.cfl_max != nullptr;
+    const bool ext = L.ph.ext();
     switch (L.c.radius) {
-        case 1: launch_substep_r<R, W, 1>(a, L.g.padded, cfl, grid, block, st); break;
-        case 2: launch_substep_r<R, W, 2>(a, L.g.padded, cfl, grid, block, st); break;
-        case 4: launch_substep_r<R, W, 4>(a, L.g.padded, cfl, grid, block, st); break;
-        default: launch_substep_r<R, W, 3>(a, L.g.padded, cfl, grid, block, st); break;
+        case 1: launch_substep_re<R, W, 1>(a, L.g.padded, cfl, ext, grid, block, st); break;
+        case 2: launch_substep_re<R, W, 2>(a, L.g.padded, cfl, ext, grid, block, st); break;
+        case 4: launch_substep_re<R, W, 4>(a, L.g.padded, cfl, ext, grid, block, st); break;
+        default: launch_substep_re<R, W, 3>(a, L.g.padded, cfl, ext, grid, block, st); break;
     }
     ++*launches;
     return cudaGetLastError();

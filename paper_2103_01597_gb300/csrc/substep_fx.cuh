@@ -138,12 +138,12 @@ __device__ __forceinline__ long long ndab(const V &F) {
 struct FxCoefs {
     double inv60dx;    // 1 / (60 dx): first derivatives
     double nu180;      // nu / (180 dx^2): nu lap u
-    double nu2160;     // nu / (2160 dx^2): nu grad(div u) / 3
+    double nu2160;     // (nu + 3 zeta) / (2160 dx^2): (nu / 3 + zeta) grad(div u)
     double inv180dx2;  // 1 / (180 dx^2): lap A
     double inv720dx2;  // 1 / (720 dx^2): grad(div A)
 };
 
-template <class IX, bool CFL>
+template <class IX, bool CFL, bool EXT = false>
 __global__ void __launch_bounds__(128) substep_fx_kernel(const SubstepArgs<double, double> a,
                                                          const FxPtrs fx, FxCoefs fc,
                                                          const unsigned long long *gmax) {
@@ -262,6 +262,15 @@ __global__ void __launch_bounds__(128) substep_fx_kernel(const SubstepArgs<doubl
                 lapa[m] = (double)LA[m] * cla;
                 J[m] = (double)GA[m] * cga - lapa[m];
             }
+            // EXT: lap xi = gamma / c_p lap s + (gamma - 1) lap ln rho (conduction)
+            double lapxi = 0.0;
+            if (EXT) {
+                const long long l0 = Fl(0, 0, 0), s0 = Fs(0, 0, 0);
+                const long long LL = nd2<0>(Fl, l0) + nd2<1>(Fl, l0) + nd2<2>(Fl, l0);
+                const long long LS = nd2<0>(Fs, s0) + nd2<1>(Fs, s0) + nd2<2>(Fs, s0);
+                lapxi = a.k.gamma_cp * ((double)LS * (sc[2] * fc.inv180dx2)) +
+                        a.k.gm1 * ((double)LL * (sc[0] * fc.inv180dx2));
+            }
             // centre values: the binary64 state
             const double lnrho = ldg(a.fin[0] + o);
             const double u[3] = {ldg(a.fin[1] + o), ldg(a.fin[2] + o), ldg(a.fin[3] + o)};
@@ -269,11 +278,12 @@ __global__ void __launch_bounds__(128) substep_fx_kernel(const SubstepArgs<doubl
             double rhs[NF];
             if (CFL) {
                 double c;
-                cell_physics<double>(lnrho, u, ss, gl, gs, gu, B, viscl, lapa, J, a.k, frc, rhs, &c);
+                cell_physics<double, EXT>(lnrho, u, ss, gl, gs, gu, B, viscl, lapa, J, a.k, frc, rhs,
+                                          &c, lapxi);
                 cfl = (c > cfl || c != c) ? c : cfl;
             } else {
-                cell_physics<double>(lnrho, u, ss, gl, gs, gu, B, viscl, lapa, J, a.k, frc, rhs,
-                                     nullptr);
+                cell_physics<double, EXT>(lnrho, u, ss, gl, gs, gu, B, viscl, lapa, J, a.k, frc, rhs,
+                                          nullptr, lapxi);
             }
 #pragma unroll
             for (int q = 0; q < NF; ++q) rk_update(a, q, o, rhs[q]);

@@ -168,7 +168,7 @@ struct TileOne {
 
 // One output tile: columns [x0, x0+32) x [y0, y0+8), planes [z0, z1).  CFL:
 // also fold the largest CFL speed of the input cells into ta.cfl_max().
-template <typename W, bool VEC, bool CFL, class TA>
+template <typename W, bool VEC, bool CFL, bool EXT, class TA>
 __device__ __forceinline__ void tiled_body(const TA &ta, int x0, int y0, int z0, int z1,
                                            unsigned char *smem_raw) {
     float *sm = reinterpret_cast<float *>(smem_raw);
@@ -239,10 +239,10 @@ __device__ __forceinline__ void tiled_body(const TA &ta, int x0, int y0, int z0,
             float rhs[NF];
             if (CFL) {
                 float c;
-                cell_rhs<float>(cell, ta.k(), frc, rhs, &c);
+                cell_rhs<float, 3, EXT>(cell, ta.k(), frc, rhs, &c);
                 cfl = (c > cfl || c != c) ? c : cfl;
             } else {
-                cell_rhs<float>(cell, ta.k(), frc, rhs);
+                cell_rhs<float, 3, EXT>(cell, ta.k(), frc, rhs);
             }
             const long long o = (long long)z * g.pxy + (long long)j * g.px + i;
             const W *wz = wring + ((z - z0) % TT_NW) * (NF * TT_THREADS) + tid;
@@ -261,24 +261,33 @@ __device__ __forceinline__ void tiled_body(const TA &ta, int x0, int y0, int z0,
     if (CFL) block_max_to_global((double)cfl, ta.cfl_max());
 }
 
-template <typename W, bool VEC, bool CFL>
+template <typename W, bool VEC, bool CFL, bool EXT>
 __global__ void __launch_bounds__(TT_THREADS, 1) substep_tiled_kernel(const SubstepArgs<float, W> a) {
     extern __shared__ __align__(128) unsigned char tt_smem_raw[];
     const int z0 = blockIdx.z * a.zchunk;
     const int z1 = min(z0 + a.zchunk, a.g.nz);
     const TileOne<W> ta{a};
-    tiled_body<W, VEC, CFL>(ta, blockIdx.x * TT_X, blockIdx.y * TT_Y, z0, z1, tt_smem_raw);
+    tiled_body<W, VEC, CFL, EXT>(ta, blockIdx.x * TT_X, blockIdx.y * TT_Y, z0, z1, tt_smem_raw);
 }
 
+template <typename W, bool VEC, bool CFL, bool EXT>
+static cudaError_t launch_tiled_variant_e(const SubstepArgs<float, W> &a, dim3 grid, dim3 block,
+                                          cudaStream_t st) {
+    const size_t smem = tt_smem_bytes<W>();
+    cudaError_t e = cudaFuncSetAttribute(substep_tiled_kernel<W, VEC, CFL, EXT>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    substep_tiled_kernel<W, VEC, CFL, EXT><<<grid, block, smem, st>>>(a);
+    return cudaGetLastError();
+}
+
+// EXT (the extra terms of Eq. B.3) is chosen from the coefficients.
 template <typename W, bool VEC, bool CFL>
 static cudaError_t launch_tiled_variant(const SubstepArgs<float, W> &a, dim3 grid, dim3 block,
                                         cudaStream_t st) {
-    const size_t smem = tt_smem_bytes<W>();
-    cudaError_t e = cudaFuncSetAttribute(substep_tiled_kernel<W, VEC, CFL>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    substep_tiled_kernel<W, VEC, CFL><<<grid, block, smem, st>>>(a);
-    return cudaGetLastError();
+    const bool ext = a.k.K != 0.f || a.k.zeta != 0.f || a.k.hc != 0.f;
+    return ext ? launch_tiled_variant_e<W, VEC, CFL, true>(a, grid, block, st)
+               : launch_tiled_variant_e<W, VEC, CFL, false>(a, grid, block, st);
 }
 
 // Launch the tiled kernel for binary32 fields in the periodic layout.
