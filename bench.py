@@ -54,6 +54,12 @@ FP64_NOMINAL_TFLOPS = 1.25
 # DRAM bytes per cell of one launch of the integer-sum FP64 substep kernel
 # (ncu, 128^3: 426.3 MB read + 239.0 MB written over 2,097,152 cells).
 FX_TRAFFIC_PER_CELL = (426.260224e6 + 238.959616e6) / 2097152
+# DRAM bytes per cell of one launch of the binary32 tiled substep (ncu, 256^3,
+# substep 1: 1126.6 MB read + 1023.2 MB written over 16,777,216 cells)
+TILED_TRAFFIC_PER_CELL = (1126.612e6 + 1023.183e6) / 16777216
+# The same for one launch of the 64-box ensemble kernel (ncu: 1834.6 MB read +
+# 1697.9 MB written over its 27,340,800 cells)
+BATCH_TRAFFIC_PER_CELL = (1834.648e6 + 1697.876e6) / 27340800
 
 WORKLOADS = {
     "forced256_fp64": dict(n=(256, 256, 256), precision="fp64", force_amp=0.05, seed=2,
@@ -384,8 +390,12 @@ def run_ours(args, wl):
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
         bytes_s = {s: bytes_per_cell(elem_f, elem_w, s) * ncell for s in range(3)}
         achieved = statistics.mean(bytes_s[s] / avg[s] for s in range(3)) / 1e9
+        tiled = order == 6 and not wl.get("entropy")
         roof = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                "frac": achieved / peaks["hbm_gbs"], "traffic": None,
+                "frac": achieved / peaks["hbm_gbs"],
+                # dram read + write per launch (ncu at 256^3 scaled by cells; the same
+                # kernel, profiles/substep_fp32_tiled_256_full.md)
+                "traffic": TILED_TRAFFIC_PER_CELL * ncell if tiled else None,
                 "kernel": ("substep_tiled_kernel<float,true> (shared-memory plane ring)"
                            if order == 6 else
                            "substep_kernel<float,float,IdxPeriodicR<%d>>" % (order // 2)),
@@ -504,7 +514,9 @@ def run_ensemble(args, wl):
     alg = statistics.mean(bytes_per_cell(4, 4, s) for s in range(3)) * ncell
     achieved = alg / launch_s / 1e9
     roof = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-            "frac": achieved / peaks["hbm_gbs"], "traffic": None,
+            "frac": achieved / peaks["hbm_gbs"],
+            # dram read + write per launch (ncu, profiles/ensemble_batch_substep_full.md)
+            "traffic": BATCH_TRAFFIC_PER_CELL * ncell,
             "kernel": "batch_substep_kernel<float> (persistent, graph-captured)",
             "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)",
             "avg_launch_ms": 1e3 * launch_s}
