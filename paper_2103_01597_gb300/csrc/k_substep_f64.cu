@@ -51,17 +51,19 @@ cudaError_t launch_substep_f64(const SubstepLaunch &L, cudaStream_t st, int *lau
     zchunk = zchunk < 1 ? 1 : (zchunk > 16 ? 16 : zchunk);
     a.zchunk = zchunk;
     const dim3 grid(gx, gy, (L.g.nz + zchunk - 1) / zchunk);
-    if (L.ph.ext()) {
-        if (a.cfl_max)
-            substep_fx_kernel<IdxPeriodic, true, true><<<grid, block, 0, st>>>(a, fx, fc, L.fx_gmax);
-        else
-            substep_fx_kernel<IdxPeriodic, false, true><<<grid, block, 0, st>>>(a, fx, fc, L.fx_gmax);
+    // 32-bit neighbour offsets whenever they fit (always, for binary64 state in
+    // 280 GB: fewer than 2^31 cells), 64-bit otherwise
+    const bool off32 = L.g.elems < (1ll << 31);
+    const bool ext = L.ph.ext(), cfl = a.cfl_max != nullptr;
+#define AC_FX(IX, C, X) substep_fx_kernel<IX, C, X><<<grid, block, 0, st>>>(a, fx, fc, L.fx_gmax)
+    if (off32) {
+        if (ext) { if (cfl) AC_FX(IdxPeriodic32, true, true); else AC_FX(IdxPeriodic32, false, true); }
+        else { if (cfl) AC_FX(IdxPeriodic32, true, false); else AC_FX(IdxPeriodic32, false, false); }
     } else {
-        if (a.cfl_max)
-            substep_fx_kernel<IdxPeriodic, true><<<grid, block, 0, st>>>(a, fx, fc, L.fx_gmax);
-        else
-            substep_fx_kernel<IdxPeriodic, false><<<grid, block, 0, st>>>(a, fx, fc, L.fx_gmax);
+        if (ext) { if (cfl) AC_FX(IdxPeriodic, true, true); else AC_FX(IdxPeriodic, false, true); }
+        else { if (cfl) AC_FX(IdxPeriodic, true, false); else AC_FX(IdxPeriodic, false, false); }
     }
+#undef AC_FX
     *launches += 3;
     return cudaGetLastError();
 }

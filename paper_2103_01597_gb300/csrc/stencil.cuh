@@ -55,33 +55,36 @@ __device__ __forceinline__ int wrap_near(int v, int n) {
 }
 
 // Cell addressing without a halo: every offset is wrapped (Sec. 3.3 map);
-// offsets up to RAD cells along each axis.
-template <int RAD>
+// offsets up to RAD cells along each axis.  OFF is the type of the stored row
+// and plane offsets: 32-bit ones (arrays of fewer than 2^31 elements) save
+// fourteen registers per thread, which the register-bound kernels feel.
+template <int RAD, typename OFF = long long>
 struct IdxPeriodicR {
     static constexpr int W = 2 * RAD + 1;
     int xo[W];
-    long long yo[W];
-    long long zo[W];
+    OFF yo[W];
+    OFF zo[W];
     __device__ __forceinline__ void set_xy(int i, int j, const Geom &g) {
 #pragma unroll
         for (int d = 0; d < W; ++d) {
             xo[d] = wrap_near(i + d - RAD, g.nx);
-            yo[d] = (long long)wrap_near(j + d - RAD, g.ny) * g.px;
+            yo[d] = (OFF)wrap_near(j + d - RAD, g.ny) * (OFF)g.px;
         }
     }
     __device__ __forceinline__ void set_z(int k, const Geom &g) {
 #pragma unroll
-        for (int d = 0; d < W; ++d) zo[d] = (long long)wrap_near(k + d - RAD, g.nz) * g.pxy;
+        for (int d = 0; d < W; ++d) zo[d] = (OFF)wrap_near(k + d - RAD, g.nz) * (OFF)g.pxy;
     }
     __device__ __forceinline__ void set_x(int i, const Geom &g) {
 #pragma unroll
         for (int d = 0; d < W; ++d) xo[d] = wrap_near(i + d - RAD, g.nx);
     }
     __device__ __forceinline__ long long operator()(int dx, int dy, int dz) const {
-        return zo[dz + RAD] + yo[dy + RAD] + xo[dx + RAD];
+        return (long long)(zo[dz + RAD] + yo[dy + RAD] + xo[dx + RAD]);
     }
 };
 using IdxPeriodic = IdxPeriodicR<3>;
+using IdxPeriodic32 = IdxPeriodicR<3, int>;  // arrays of fewer than 2^31 elements
 
 // Cell addressing inside a padded array whose halo holds the periodic images.
 struct IdxPadded {

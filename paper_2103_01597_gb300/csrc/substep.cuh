@@ -107,6 +107,11 @@ void launch_substep_r(const SubstepArgs<R, W> &a, bool padded, bool cfl, dim3 gr
             else
                 substep_kernel<R, W, IdxPadded, false, RAD, EXT><<<grid, block, 0, st>>>(a);
         }
+    } else if (a.g.elems < (1ll << 31)) {  // 32-bit neighbour offsets (fewer registers)
+        if (cfl)
+            substep_kernel<R, W, IdxPeriodicR<RAD, int>, true, RAD, EXT><<<grid, block, 0, st>>>(a);
+        else
+            substep_kernel<R, W, IdxPeriodicR<RAD, int>, false, RAD, EXT><<<grid, block, 0, st>>>(a);
     } else {
         if (cfl)
             substep_kernel<R, W, IdxPeriodicR<RAD>, true, RAD, EXT><<<grid, block, 0, st>>>(a);
