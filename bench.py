@@ -696,7 +696,8 @@ def run_closure(args, wl):
     # the same state, on both convolution paths
     xs = cl._rows(cl.current_state(sim))
     fwd_s = {}
-    for path, name in ((ac.AC_CONV_MMA_SYNC, "mma_sync"), (ac.AC_CONV_TCGEN05, "tcgen05")):
+    for path, name in ((ac.AC_CONV_MMA_SYNC, "mma_sync"), (ac.AC_CONV_TCGEN05_PAIR, "tcgen05_pair"),
+                       (ac.AC_CONV_TCGEN05, "tcgen05")):
         ac.ac_closure_set_conv_path(c.c, path)
         for it in range(args.steps):
             conv_ev[it][0].record(stream)
@@ -869,7 +870,8 @@ def run_closure_forward(args, wl):
 
     # per-launch device times (events around each launch, on the closure's stream)
     per = {}
-    for path, name in ((ac.AC_CONV_TCGEN05, "tcgen05"), (ac.AC_CONV_MMA_SYNC, "mma_sync")):
+    for path, name in ((ac.AC_CONV_TCGEN05, "tcgen05"), (ac.AC_CONV_TCGEN05_PAIR, "tcgen05_pair"),
+                       (ac.AC_CONV_MMA_SYNC, "mma_sync")):
         ac.ac_closure_set_conv_path(c.c, path)
         ac.ac_closure_forward_timings(c.c, rin, rout)
         rows = [ac.ac_closure_forward_timings(c.c, rin, rout) for _ in range(max(3, args.steps))]

@@ -380,10 +380,13 @@ int ac_closure_launch_count(const ac_closure *c, unsigned long long *count);
  * accumulator in tensor memory, on channels-last activations, persistent CTAs
  * holding one layer's weights in shared memory.  AC_CONV_MMA_SYNC: the
  * warp-level mma.sync kernels on channel-major activations that
- * ac_closure_backward always uses.  Both take the same bfloat16 operands and
- * accumulate in binary32, in a different order. */
+ * ac_closure_backward always uses.  AC_CONV_TCGEN05_PAIR: the tcgen05 kernel
+ * on clusters of two CTAs (cta_group::2, M = 256), each CTA holding half of a
+ * layer's weights.  All take the same bfloat16 operands and accumulate in
+ * binary32, in different orders.  Any other value: AC_ERR_ARG. */
 #define AC_CONV_TCGEN05 0
 #define AC_CONV_MMA_SYNC 1
+#define AC_CONV_TCGEN05_PAIR 2
 int ac_closure_set_conv_path(ac_closure *c, int path);
 int ac_closure_get_conv_path(const ac_closure *c, int *path);
 /* Reads and clears the device error word of the tcgen05 kernels

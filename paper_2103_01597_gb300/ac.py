@@ -31,7 +31,7 @@ AC_FP64, AC_FP32, AC_FP32_W64 = 0, 1, 2
 AC_LAYOUT_PERIODIC, AC_LAYOUT_PADDED = 0, 1
 AC_MAX, AC_MIN, AC_SUM, AC_RMS = 0, 1, 2, 3
 AC_STENCIL_AUTO, AC_STENCIL_FP64, AC_STENCIL_FIXED = 0, 1, 2
-AC_CONV_TCGEN05, AC_CONV_MMA_SYNC = 0, 1
+AC_CONV_TCGEN05, AC_CONV_MMA_SYNC, AC_CONV_TCGEN05_PAIR = 0, 1, 2
 AC_Q_UMAG, AC_Q_EKIN, AC_Q_EMAG, AC_Q_CFL = 8, 9, 10, 11
 
 

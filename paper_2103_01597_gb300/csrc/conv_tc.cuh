@@ -513,7 +513,7 @@ __global__ void __launch_bounds__(THREADS, 1)
         float bias[COUT];
 #pragma unroll
         for (int c = 0; c < COUT; ++c) bias[c] = a.bias[c];
-        double gm = 0.0;  // EPI_SCALED_F32: this thread's largest |output|
+        float gm = 0.f;  // EPI_SCALED_F32: this thread's largest |output| (NaN if any)
         uint32_t par = 0;  // bit k: parity of the tiles block k has held so far
         bool ok = true;
         for (long long g = blockIdx.x; g < nseg && ok; g += gridDim.x) {
@@ -557,7 +557,7 @@ __global__ void __launch_bounds__(THREADS, 1)
                     for (int c = 0; c < COUT; ++c) {
                         const float val = a.out_scale[c] * (v[c] + bias[c]);
                         a.out[c][p] = val;
-                        const double m = fabs((double)val);
+                        const float m = fabsf(val);  // exact: the max needs no wider type
                         gm = (m > gm || m != m) ? m : gm;
                     }
                 }
@@ -565,7 +565,7 @@ __global__ void __launch_bounds__(THREADS, 1)
         }
         if (!ok && lane == 0) atomicExch(a.err, 1u);
         if (EPI == EPI_SCALED_F32 && a.gmax) {
-            unsigned long long bits = (unsigned long long)__double_as_longlong(gm);
+            unsigned long long bits = (unsigned long long)__double_as_longlong((double)gm);
             for (int o = 16; o > 0; o >>= 1) {
                 const unsigned long long other = __shfl_xor_sync(0xffffffffu, bits, o);
                 bits = other > bits ? other : bits;
@@ -578,19 +578,381 @@ __global__ void __launch_bounds__(THREADS, 1)
     if (warp == 0) tmem_dealloc(tmem, TCOLS);
 }
 
+// ---- paired CTAs: tcgen05 with cta_group::2 (M = 256 over two SMs) ---------
+//
+// A cluster of two CTAs computes two neighbouring columns of one z-chunk in
+// lockstep.  Each CTA stages its own column's slices and holds one N-half of
+// the kz-stacked weights; the leader (cluster rank 0) issues every MMA with
+// cta_group::2, so one instruction covers 256 cells (128 per CTA, each CTA's
+// rows landing in its own TMEM) and the per-SM instruction count halves.
+// Synchronisation across the pair: the peer's TMA copies complete on the
+// leader's slot barrier (cp.async.bulk.tensor .cta_group::2 with the leader's
+// barrier), commits are multicast to both CTAs' barriers, and the peer's
+// epilogue warps arrive remotely on the leader's TMEM-block barrier.
+// Every MMA window spans three TMEM blocks (N = 3 NB): tile t of a segment owns
+// block t + 2 and blocks 0, 1, L + 2, L + 3 take the contributions meant for
+// tiles outside the segment, which are never read; all segments have the same
+// length L (the last z-chunk overlaps the one before it), so those spare
+// blocks never hold a real tile.
+constexpr int PZC = 12;            // tiles per column segment (L), at most
+constexpr int PBLK = PZC + 4;      // TMEM blocks per CTA
+
+__device__ __forceinline__ uint32_t cluster_rank() {
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;\n" : "=r"(r));
+    return r;
+}
+// Shared-memory address of the same variable in the leader CTA (cluster window).
+__device__ __forceinline__ uint32_t leader_addr(const void *p) {
+    uint32_t r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, 0;\n" : "=r"(r) : "r"(smem_u32(p)));
+    return r;
+}
+__device__ __forceinline__ void cluster_sync() {
+    asm volatile("barrier.cluster.arrive.release.aligned;\n"
+                 "barrier.cluster.wait.acquire.aligned;\n" ::: "memory");
+}
+__device__ __forceinline__ void tmem_alloc2(uint32_t *dst, unsigned ncols) {
+    asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(
+                     smem_u32(dst)),
+                 "r"(ncols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::2.sync.aligned;\n" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc2(uint32_t taddr, unsigned ncols) {
+    asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, %1;\n" ::"r"(taddr), "r"(ncols)
+                 : "memory");
+}
+__device__ __forceinline__ void mma2_bf16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc,
+                                          uint32_t idesc) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.u32 p, 1, 0;\n"
+        " tcgen05.mma.cta_group::2.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
+        "l"(adesc), "l"(bdesc), "r"(idesc)
+        : "memory");
+}
+// Arrive on the barrier at `bar`'s offset in both CTAs once the leader's MMAs so far are done.
+__device__ __forceinline__ void mma2_commit(uint64_t *bar) {
+    const uint16_t mask = 0x3;
+    asm volatile(
+        "tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64"
+        " [%0], %1;\n" ::"r"(smem_u32(bar)),
+        "h"(mask)
+        : "memory");
+}
+// Tiled TMA load into this CTA's shared memory, completing on a barrier given by
+// its cluster-window address (the leader's).
+__device__ __forceinline__ void tma2_load_5d(void *dst, const CUtensorMap *map, uint32_t bar_cluster,
+                                             int c0, int c1, int c2, int c3, int c4) {
+    asm volatile(
+        "cp.async.bulk.tensor.5d.cta_group::2.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%3, %4, %5, %6, %7}], [%2];\n" ::"r"(smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(bar_cluster), "r"(c0), "r"(c1), "r"(c2), "r"(c3),
+        "r"(c4)
+        : "memory");
+}
+__device__ __forceinline__ void mbar_arrive_cluster(uint32_t bar_cluster) {
+    asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];\n" ::"r"(bar_cluster)
+                 : "memory");
+}
+
+// Column pair segment h (chunk-major over column pairs): this CTA's column is
+// 2 pc + rank; when the column count is odd the last pair's second CTA repeats
+// column ncols - 1 and writes nothing.  Every segment has a.zc tiles; the last
+// chunk starts at nz - zc, and only its tiles from chunk * zc on are written
+// (those before it belong to the chunk before).
+struct PairSegment {
+    Segment s;
+    int zw;      // first z this CTA writes
+    bool write;  // false: duplicate column
+};
+
+__device__ __forceinline__ PairSegment pair_segment_of(long long h, const ConvTcArgs &a, int segs,
+                                                       uint32_t rank) {
+    const int ncols = a.ny * segs;
+    const int pcols = (ncols + 1) / 2;
+    const int chunk = (int)(h / pcols);
+    const int pc = (int)(h - (long long)chunk * pcols);
+    int col = 2 * pc + (int)rank;
+    PairSegment p;
+    p.write = col < ncols;
+    col = p.write ? col : ncols - 1;
+    p.s.y = col / segs;
+    p.s.seg = col - p.s.y * segs;
+    p.zw = chunk * a.zc;
+    p.s.z0 = p.zw + a.zc <= a.nz ? p.zw : a.nz - a.zc;
+    p.s.len = a.zc;
+    return p;
+}
+
+// Shared memory of one CTA of a pair: its half of the weight image and the ring.
+constexpr int PNBUF = 6;
+__host__ __device__ constexpr size_t pair_smem_bytes(int cin) {
+    return (size_t)w_bytes(cin, 32) / 2 + (size_t)PNBUF * 3 * row_bytes(cin);
+}
+
+// The paired kernel.  Same slice numbering, ring and weight-image order as
+// conv_tc_kernel, with these differences: the image is split by kz-stack rows,
+// rows [r 3NB/2, (r+1) 3NB/2) in CTA r; slice j of a segment always issues the
+// full window, N = 3 NB at TMEM block j (blocks j .. j+2 = tiles j-2 .. j);
+// the barriers live in both CTAs but only these phases are used:
+//   leader full[b]  : expect_tx of both CTAs' slice bytes; both CTAs' TMA land on it;
+//   empty[b], accf[k], fin : multicast commits, waited on locally in each CTA;
+//   leader acce[k]  : 8 arrivals, the four epilogue warps of each CTA;
+//   wbar            : this CTA's weight half landed (checked before the cluster
+//                     barrier that precedes the first MMA).
+template <int CIN, int COUT, int EPI>
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(THREADS, 1)
+    conv_tc_pair_kernel(const __grid_constant__ CUtensorMap xmap, const ConvTcArgs a) {
+    // N = 3 NB must be a multiple of 32 for cta_group::2, so the stack always has
+    // 32 rows per kz (zero weights past COUT); the epilogue reads NR of them
+    constexpr int NB = 32;
+    constexpr int NR = COUT < 16 ? 16 : COUT;
+    constexpr int KC = CIN / 8;
+    constexpr bool PAIR = CIN == 8;
+    constexpr int NGH = 3 * NB / 16;           // core-matrix rows of this CTA's stack half
+    constexpr int ROW = row_bytes(CIN);
+    constexpr int SLICE = 3 * ROW;
+    constexpr int WH_BYTES = w_bytes(CIN, NB) / 2;
+    constexpr uint32_t SLICE_TX = 3 * KC * PLANE;
+    constexpr uint32_t TCOLS = PBLK * NB;      // 512 or 256 TMEM columns
+    constexpr uint32_t IDESC = idesc_bf16(2 * TM, 3 * NB);
+    static_assert((CIN % 16 == 0 || CIN == 8) && COUT % 8 == 0 && COUT <= 32, "shape");
+    static_assert(NGH * 16 == 3 * NB && PBLK <= 32, "stack halves, block masks");
+    extern __shared__ __align__(1024) unsigned char smem[];
+    __shared__ uint64_t full[PNBUF], empty[PNBUF], accf[PBLK], acce[PBLK], wbar, fin;
+    __shared__ uint32_t tmem_base;
+    unsigned char *Ws = smem;
+    unsigned char *Ss = smem + WH_BYTES;
+    const uint32_t rank = cluster_rank();
+    const bool leader = rank == 0;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int segs = (a.nx + TM - 1) / TM;
+    const int ncols = a.ny * segs;
+    const long long nseg = (long long)((a.nz + a.zc - 1) / a.zc) * ((ncols + 1) / 2);
+    const long long pair0 = blockIdx.x >> 1, npairs = gridDim.x >> 1;
+    const int L = a.zc;
+
+    if (warp == 0) tmem_alloc2(&tmem_base, TCOLS);
+    if (threadIdx.x == 128) {
+        for (int b = 0; b < PNBUF; ++b) {
+            mbar_init(&full[b], 1);
+            mbar_init(&empty[b], 1);
+        }
+        for (int k = 0; k < PBLK; ++k) {
+            mbar_init(&accf[k], 1);
+            mbar_init(&acce[k], 8);
+        }
+        mbar_init(&wbar, 1);
+        mbar_init(&fin, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+        mbar_expect_tx(&wbar, WH_BYTES);
+        bulk_load(Ws, reinterpret_cast<const unsigned char *>(a.w) + rank * WH_BYTES, WH_BYTES, &wbar);
+    }
+    __syncthreads();  // TMEM address published
+    tc_fence_after_sync();
+    const uint32_t tmem = tmem_base;
+    if (warp < 4) {  // every accumulator block starts at zero
+        for (int k = 0; k < PBLK; ++k) tmem_zero<NB>(tmem + ((uint32_t)(warp * 32) << 16) + k * NB);
+        tc_fence_before_sync();
+    }
+    if (threadIdx.x == 128 && !mbar_wait(&wbar, 0)) atomicExch(a.err, 1u);
+    // both CTAs: barriers initialised, TMEM zeroed, weight halves landed
+    cluster_sync();
+    tc_fence_after_sync();
+
+    if (warp == 4) {
+        if (lane == 0) {  // ---- TMA producer (both CTAs; completions land on the leader's full[b])
+            long long s = 0;
+            bool ok = true;
+            for (long long h = pair0; h < nseg && ok; h += npairs) {
+                const Segment sg = pair_segment_of(h, a, segs, rank).s;
+                for (int j = 0; j < L + 2; ++j, ++s) {
+                    const int b = (int)(s % PNBUF);
+                    const long long k = s / PNBUF;
+                    if (k > 0 && !mbar_wait(&empty[b], (unsigned)((k - 1) & 1))) {
+                        ok = false;
+                        break;
+                    }
+                    if (leader) mbar_expect_tx(&full[b], 2 * SLICE_TX);
+                    const uint32_t fb = leader_addr(&full[b]);
+                    const int z = wrapi(sg.z0 + j - 1, a.nz);
+                    unsigned char *dst = Ss + b * SLICE;
+#pragma unroll
+                    for (int r = 0; r < 3; ++r)
+                        tma2_load_5d(dst + r * ROW, &xmap, fb, 0, sg.seg * (TM / 8), 0,
+                                     wrapi(sg.y + r - 1, a.ny), z);
+                }
+            }
+            if (!ok) atomicExch(a.err, 1u);
+            // no copy may be in flight when either CTA exits: the leader waits for
+            // each buffer's last fill (both CTAs' bytes) before the final cluster barrier
+            if (leader)
+                for (int b = 0; b < PNBUF; ++b)
+                    if (s > b) mbar_wait(&full[b], (unsigned)(((s - 1 - b) / PNBUF) & 1));
+        }
+    } else if (warp == 5) {
+        if (leader && lane == 0) {  // ---- MMA issuer (leader only; M = 256 over the pair)
+            bool ok = true;
+            long long s = 0;
+            // bit k of `used`: block k has held a tile; bit k of `par`: parity of their count
+            uint32_t used = 0, par = 0;
+            const uint64_t b0 = smem_desc(smem_u32(Ws), NGH * CORE, CORE);
+            for (long long h = pair0; h < nseg && ok; h += npairs) {
+                for (int j = 0; j < L + 2; ++j, ++s) {
+                    const int b = (int)(s % PNBUF);
+                    if (j % GROUP == 0) {
+                        uint32_t addr[2 * GROUP];
+                        unsigned want[2 * GROUP];
+                        uint32_t pending = 0;
+#pragma unroll
+                        for (int q = 0; q < GROUP; ++q) {
+                            const long long sq = s + q;
+                            const int jq = j + q;
+                            const int kq = jq < L ? jq + 2 : 0;  // block tile jq opens
+                            addr[2 * q] = smem_u32(&full[sq % PNBUF]);
+                            want[2 * q] = (unsigned)((sq / PNBUF) & 1);
+                            addr[2 * q + 1] = smem_u32(&acce[kq]);
+                            want[2 * q + 1] = ((par >> kq) & 1u) ^ 1u;
+                            if (jq < L + 2) pending |= 1u << (2 * q);
+                            if (jq < L && ((used >> kq) & 1u)) pending |= 1u << (2 * q + 1);
+                        }
+                        ok = mbar_wait_all(addr, want, pending);
+                        if (!ok) break;
+                        tc_fence_after_sync();
+                    }
+                    if (j < L) {  // tile j opens in block j + 2
+                        used |= 1u << (j + 2);
+                        par ^= 1u << (j + 2);
+                    }
+                    const uint32_t sbase = smem_u32(Ss + b * SLICE);
+                    const uint32_t dtm = tmem + (uint32_t)(j * NB);
+                    if constexpr (PAIR) {
+                        const uint64_t a0 = smem_desc(sbase, 0, CORE);
+#pragma unroll
+                        for (int p = 0; p < 5; ++p) {
+                            const int ta0 = pair_tap(p, 0), tb0 = pair_tap(p, 1);
+                            const uint32_t off = (ta0 / 3) * ROW + (ta0 % 3) * 16;
+                            const uint32_t lbo = (tb0 / 3) * ROW + (tb0 % 3) * 16 - off;
+                            const uint64_t ad = a0 + (off >> 4) + ((uint64_t)(lbo >> 4) << 16);
+                            const uint64_t bd = b0 + ((2 * p * NGH * CORE) >> 4);
+                            mma2_bf16(dtm, ad, bd, IDESC);
+                        }
+                    } else {
+                        const uint64_t a0 = smem_desc(sbase, PLANE, CORE);
+#pragma unroll
+                        for (int dy = 0; dy < 3; ++dy)
+#pragma unroll
+                            for (int dx = 0; dx < 3; ++dx)
+#pragma unroll
+                                for (int kk = 0; kk < CIN / 16; ++kk) {
+                                    const int dyx = dy * 3 + dx;
+                                    const uint64_t ad = a0 + ((dy * ROW + dx * 16 + kk * 2 * PLANE) >> 4);
+                                    const uint64_t bd = b0 + (((dyx * KC + 2 * kk) * NGH * CORE) >> 4);
+                                    mma2_bf16(dtm, ad, bd, IDESC);
+                                }
+                    }
+                    mma2_commit(&empty[b]);
+                    if (j >= 2) mma2_commit(&accf[j]);  // block j: tile j-2 has had its third slice
+                }
+            }
+            if (!ok) atomicExch(a.err, 1u);
+            // no MMA may be in flight when TMEM is freed: a final commit covers all
+            mma2_commit(&fin);
+            mbar_wait(&fin, 0);
+        } else if (lane == 0) {
+            // the peer: the final commit's arrival on its own fin is the last write
+            // the leader's MMAs make into this CTA; it must land before the CTA exits
+            if (!mbar_wait(&fin, 0)) atomicExch(a.err, 1u);
+        }
+    } else {  // ---- epilogue: warps 0-3 of each CTA, its TMEM lanes 32 warp .. 32 warp + 31
+        float bias[COUT];
+#pragma unroll
+        for (int c = 0; c < COUT; ++c) bias[c] = a.bias[c];
+        float gm = 0.f;
+        uint32_t par = 0;  // bit k: parity of the tiles block k has held so far
+        bool ok = true;
+        for (long long h = pair0; h < nseg && ok; h += npairs) {
+            const PairSegment ps = pair_segment_of(h, a, segs, rank);
+            const Segment &sg = ps.s;
+            const int x = sg.seg * TM + warp * 32 + lane;
+            for (int i = 0; i < L; ++i) {
+                const int kb = i + 2;
+                ok = __all_sync(0xffffffffu, mbar_wait(&accf[kb], (par >> kb) & 1u));
+                par ^= 1u << kb;
+                if (!ok) break;
+                tc_fence_after_sync();
+                const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(kb * NB);
+                float v[NR];
+                if constexpr (NR == 32)
+                    tmem_ld32(taddr, v);
+                else
+                    tmem_ld16(taddr, v);
+                tmem_zero<NR>(taddr);  // columns past NR only ever receive zero weights
+                tc_fence_before_sync();
+                __syncwarp();
+                if (lane == 0) mbar_arrive_cluster(leader_addr(&acce[kb]));
+                const int z = sg.z0 + i;
+                if (!ps.write || z < ps.zw || x >= a.nx) continue;
+                if (EPI == EPI_RELU_BF16) {
+                    __align__(16) bf16 o[COUT];
+#pragma unroll
+                    for (int c = 0; c < COUT; ++c) o[c] = __float2bfloat16_rn(fmaxf(v[c] + bias[c], 0.f));
+                    bf16 *Y = a.y;
+#pragma unroll
+                    for (int kc = 0; kc < COUT / 8; ++kc) {
+                        const uint4 val = reinterpret_cast<const uint4 *>(o)[kc];
+                        bf16 *plane =
+                            Y + ((((long long)z * a.ny + sg.y) * (COUT / 8) + kc) * rp_cells(a.nx)) * 8;
+                        *reinterpret_cast<uint4 *>(plane + (long long)(x + 1) * 8) = val;
+                        if (x == 0) *reinterpret_cast<uint4 *>(plane + (long long)(a.nx + 1) * 8) = val;
+                        if (x == a.nx - 1) *reinterpret_cast<uint4 *>(plane) = val;
+                    }
+                } else {
+                    const long long p = ((long long)z * a.ny + sg.y) * a.nx + x;
+#pragma unroll
+                    for (int c = 0; c < COUT; ++c) {
+                        const float val = a.out_scale[c] * (v[c] + bias[c]);
+                        a.out[c][p] = val;
+                        const float m = fabsf(val);  // exact: the max needs no wider type
+                        gm = (m > gm || m != m) ? m : gm;
+                    }
+                }
+            }
+        }
+        if (!ok && lane == 0) atomicExch(a.err, 1u);
+        if (EPI == EPI_SCALED_F32 && a.gmax) {
+            unsigned long long bits = (unsigned long long)__double_as_longlong((double)gm);
+            for (int o = 16; o > 0; o >>= 1) {
+                const unsigned long long other = __shfl_xor_sync(0xffffffffu, bits, o);
+                bits = other > bits ? other : bits;
+            }
+            if (lane == 0) atomicMax(a.gmax, bits);
+        }
+    }
+    // the leader's MMAs have finished (it waited on fin), every remote arrival
+    // and every copy into either CTA has landed: TMEM can go
+    tc_fence_before_sync();
+    cluster_sync();
+    if (warp == 0) tmem_dealloc2(tmem, TCOLS);
+}
+
 // Weight image for conv_tc_kernel from binary32 W[cout][cin_real][27] (tap =
-// 9 kz + 3 ky + kx); nb = accumulator columns per tile (COUT padded to 16);
-// cin = 8 gives the tap-pair image.
+// 9 kz + 3 ky + kx); nb = accumulator columns per tile (COUT padded to 16 or
+// 32); cin = 8 gives the tap-pair image.  Only the core-matrix rows ng_lo ..
+// ng_lo + ng_cnt - 1 of the kz stack are written, as an image of their own
+// (ng_cnt = 3 nb / 8 for the whole stack; the paired kernel takes the two
+// halves one after the other).
 __global__ void conv_tc_prep_kernel(const float *__restrict__ W, int cout, int cin_real, int cin,
-                                    int nb, bf16 *__restrict__ img) {
-    const int KC = cin / 8, NGS = 3 * nb / 8;
+                                    int nb, int ng_lo, int ng_cnt, bf16 *__restrict__ img) {
+    const int KC = cin / 8;
     const bool pair = cin == 8;
-    const int total = (pair ? 10 : 9 * KC) * NGS * 64;
+    const int total = (pair ? 10 : 9 * KC) * ng_cnt * 64;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x) {
         const int c = i & 7, r = (i >> 3) & 7;
-        const int rest = i >> 6;  // kq * NGS + ng
-        const int ng = rest % NGS;
-        const int kq = rest / NGS;
+        const int rest = i >> 6;  // kq * ng_cnt + (ng - ng_lo)
+        const int ng = ng_lo + rest % ng_cnt;
+        const int kq = rest / ng_cnt;
         int dyx, ci;
         bool live = true;
         if (pair) {

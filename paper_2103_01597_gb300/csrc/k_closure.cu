@@ -475,6 +475,11 @@ struct ac_closure {
     int tc_grid[3];
     int tc_zc;
     CUtensorMap tc_map[3];
+    // paired-CTA forward: the two halves of each layer's kz stack, grid, segment length
+    bf16 *pimg1, *pimg2, *pimg3;
+    int tp_grid[3];
+    int tp_smem[3];  // dynamic shared memory of a launch (at least half an SM's)
+    int tp_zc;
     float *part;
     double *lossp;
     double *loss_host;
@@ -515,6 +520,56 @@ static cudaError_t tc_grid_for(const ac_closure *c, int sms, int *grid) {
     return cudaSuccess;
 }
 
+// Persistent grid of the paired kernel: as many CTA pairs as can be resident at
+// once (clusters must fit within a GPC, so this can be below half the SMs),
+// at most one per pair segment.  Each CTA allocates all 512 TMEM columns, so a
+// second CTA on an SM would only wait for the first: the launch asks for more
+// than half an SM's shared memory, which keeps it to one CTA per SM.
+template <int CIN, int COUT, int EPI>
+static cudaError_t tp_grid_for(const ac_closure *c, int sms, int *grid, int *smem) {
+    auto k = tc::conv_tc_pair_kernel<CIN, COUT, EPI>;
+    int dev = 0, per_sm_bytes = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess)
+        e = cudaDeviceGetAttribute(&per_sm_bytes, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+    if (e != cudaSuccess) return e;
+    int bytes = (int)tc::pair_smem_bytes(CIN);
+    if (bytes < per_sm_bytes / 2 + 1024) bytes = per_sm_bytes / 2 + 1024;
+    *smem = bytes;
+    e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e != cudaSuccess) return e;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)(sms / 2 * 2), 1, 1);
+    cfg.blockDim = dim3(tc::THREADS, 1, 1);
+    cfg.dynamicSmemBytes = (size_t)bytes;
+    cfg.stream = c->stream;
+    int clusters = 0;
+    e = cudaOccupancyMaxActiveClusters(&clusters, (const void *)k, &cfg);
+    if (e != cudaSuccess) return e;
+    const long long cols = (long long)c->g.ny * ((c->g.nx + tc::TM - 1) / tc::TM);
+    const long long psegs = (long long)((c->g.nz + c->tp_zc - 1) / c->tp_zc) * ((cols + 1) / 2);
+    long long n = clusters < 1 ? 1 : clusters;
+    n = n < psegs ? n : psegs;
+    *grid = (int)(2 * n);
+    return cudaSuccess;
+}
+
+// Segment length of the paired kernel: every segment has the same length L <=
+// PZC (the last z-chunk overlaps the one before); L minimises the slices staged
+// per column, ceil(nz / L) (L + 2), the larger L on ties.
+static int pair_zc(int nz) {
+    int best = 1;
+    long long cost = -1;
+    for (int L = 1; L <= tc::PZC && L <= nz; ++L) {
+        const long long k = (long long)((nz + L - 1) / L) * (L + 2);
+        if (cost < 0 || k <= cost) {
+            best = L;
+            cost = k;
+        }
+    }
+    return best;
+}
+
 // Tensor map of a row-planar activation with KC groups of 8 channels: dims
 // (64 = 8 cells x 8 channels, nxp / 8, KC, ny, nz), box (64, 17, KC, 1, 1).
 static cudaError_t tc_encode(PFN_cuTensorMapEncodeTiled_v12000 enc, const ac_closure *c, void *base,
@@ -540,6 +595,13 @@ static cudaError_t tc_setup(ac_closure *c) {
     if (e == cudaSuccess) e = tc_grid_for<8, 32, tc::EPI_RELU_BF16>(c, sms, &c->tc_grid[0]);
     if (e == cudaSuccess) e = tc_grid_for<32, 32, tc::EPI_RELU_BF16>(c, sms, &c->tc_grid[1]);
     if (e == cudaSuccess) e = tc_grid_for<32, 8, tc::EPI_SCALED_F32>(c, sms, &c->tc_grid[2]);
+    c->tp_zc = pair_zc(c->g.nz);
+    if (e == cudaSuccess)
+        e = tp_grid_for<8, 32, tc::EPI_RELU_BF16>(c, sms, &c->tp_grid[0], &c->tp_smem[0]);
+    if (e == cudaSuccess)
+        e = tp_grid_for<32, 32, tc::EPI_RELU_BF16>(c, sms, &c->tp_grid[1], &c->tp_smem[1]);
+    if (e == cudaSuccess)
+        e = tp_grid_for<32, 8, tc::EPI_SCALED_F32>(c, sms, &c->tp_grid[2], &c->tp_smem[2]);
     void *fn = nullptr;
     cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
     if (e == cudaSuccess)
@@ -574,7 +636,8 @@ extern "C" int ac_closure_init(ac_closure **out, int nx, int ny, int nz, void *s
     const size_t np = AC_CLOSURE_NPARAMS;
     // params, m, v, grads, scales (24), bf16 weights (fwd and transposed layouts)
     const size_t wbytes = 2 * (32 * 27 * 16 + 32 * 27 * 32 + 8 * 27 * 32 + 32 * 27 * 16 + 32 * 27 * 32) +
-                          2 * (27 * 16 * 32 + 27 * 32 * 32 + 27 * 32 * 16);
+                          2 * (27 * 16 * 32 + 27 * 32 * 32 + 27 * 32 * 16) +
+                          (size_t)tc::w_bytes(8, 32) + 2 * (size_t)tc::w_bytes(32, 32);
     const size_t fbytes = sizeof(float) * (4 * np + 64) + wbytes + 256;
     c->lossblocks = 304;
     const size_t part_floats = (size_t)9 * CL_WG_CTAS * 32 * 96;
@@ -609,6 +672,9 @@ extern "C" int ac_closure_init(ac_closure **out, int nx, int ny, int nz, void *s
     c->img1 = c->wb2 + 32 * 27 * 32;  // byte offsets stay multiples of 16
     c->img2 = c->img1 + 27 * 16 * 32;
     c->img3 = c->img2 + 27 * 32 * 32;
+    c->pimg1 = c->img3 + 27 * 32 * 16;
+    c->pimg2 = c->pimg1 + tc::w_bytes(8, 32) / 2;
+    c->pimg3 = c->pimg2 + tc::w_bytes(32, 32) / 2;
     char *a = static_cast<char *>(c->act_block);
     c->x0 = reinterpret_cast<bf16 *>(a);
     c->a1 = c->x0 + 16 * np2;
@@ -649,10 +715,20 @@ static int prep_weights(ac_closure *c) {
     prep_weights_kernel<<<32, 256, 0, c->stream>>>(c->params + P_W1, 32, 8, 16, c->wf1, 0, nullptr);
     prep_weights_kernel<<<128, 256, 0, c->stream>>>(c->params + P_W2, 32, 32, 32, c->wf2, 32, c->wb2);
     prep_weights_kernel<<<32, 256, 0, c->stream>>>(c->params + P_W3, 8, 32, 32, c->wf3, 16, c->wb3);
-    tc::conv_tc_prep_kernel<<<16, 256, 0, c->stream>>>(c->params + P_W1, 32, 8, 8, 32, c->img1);
-    tc::conv_tc_prep_kernel<<<128, 256, 0, c->stream>>>(c->params + P_W2, 32, 32, 32, 32, c->img2);
-    tc::conv_tc_prep_kernel<<<64, 256, 0, c->stream>>>(c->params + P_W3, 8, 32, 32, 16, c->img3);
-    c->launches += 6;
+    tc::conv_tc_prep_kernel<<<16, 256, 0, c->stream>>>(c->params + P_W1, 32, 8, 8, 32, 0, 12, c->img1);
+    tc::conv_tc_prep_kernel<<<128, 256, 0, c->stream>>>(c->params + P_W2, 32, 32, 32, 32, 0, 12,
+                                                        c->img2);
+    tc::conv_tc_prep_kernel<<<64, 256, 0, c->stream>>>(c->params + P_W3, 8, 32, 32, 16, 0, 6, c->img3);
+    // paired kernel: stack rows 0..47 (core rows 0..5) then 48..95, 32 per kz
+    for (int h = 0; h < 2; ++h) {
+        tc::conv_tc_prep_kernel<<<16, 256, 0, c->stream>>>(c->params + P_W1, 32, 8, 8, 32, 6 * h, 6,
+                                                           c->pimg1 + h * tc::w_bytes(8, 32) / 4);
+        tc::conv_tc_prep_kernel<<<64, 256, 0, c->stream>>>(c->params + P_W2, 32, 32, 32, 32, 6 * h, 6,
+                                                           c->pimg2 + h * tc::w_bytes(32, 32) / 4);
+        tc::conv_tc_prep_kernel<<<64, 256, 0, c->stream>>>(c->params + P_W3, 8, 32, 32, 32, 6 * h, 6,
+                                                           c->pimg3 + h * tc::w_bytes(32, 32) / 4);
+    }
+    c->launches += 12;
     CCK(cudaGetLastError());
     return AC_OK;
 }
@@ -729,9 +805,13 @@ static int run_forward(ac_closure *c, const float *const in[8], cudaEvent_t *ev 
     return AC_OK;
 }
 
+// One layer on the tcgen05 kernels: the single-CTA kernel with the whole kz
+// stack (img), or, when pair is set, the paired kernel with the two stack halves
+// (pimg).
 template <int CIN, int COUT, int EPI>
-static void launch_tc(const ac_closure *c, int layer, const bf16 *img, const float *bias, bf16 *y,
-                      float *const out[8] = nullptr, unsigned long long *gmax = nullptr) {
+static void launch_tc(const ac_closure *c, int layer, bool pair, const bf16 *img, const bf16 *pimg,
+                      const float *bias, bf16 *y, float *const out[8] = nullptr,
+                      unsigned long long *gmax = nullptr) {
     tc::ConvTcArgs a;
     a.w = img;
     a.bias = bias;
@@ -742,8 +822,14 @@ static void launch_tc(const ac_closure *c, int layer, const bf16 *img, const flo
     a.nx = c->g.nx;
     a.ny = c->g.ny;
     a.nz = c->g.nz;
-    a.zc = c->tc_zc;
+    a.zc = pair ? c->tp_zc : c->tc_zc;
     a.err = c->tc_err;
+    if (pair) {
+        a.w = pimg;
+        tc::conv_tc_pair_kernel<CIN, COUT, EPI>
+            <<<c->tp_grid[layer], tc::THREADS, c->tp_smem[layer], c->stream>>>(c->tc_map[layer], a);
+        return;
+    }
     tc::conv_tc_kernel<CIN, COUT, EPI>
         <<<c->tc_grid[layer], tc::THREADS, tc::smem_bytes(CIN, COUT < 16 ? 16 : COUT), c->stream>>>(
             c->tc_map[layer], a);
@@ -762,12 +848,13 @@ static int run_forward_tc(ac_closure *c, const float *const in[8], float *const 
     mark(ev, 0, c->stream);
     pack_input_rp_kernel<<<cl_grid(g.n), 256, 0, c->stream>>>(f, c->scales, g.nx, g.n, c->x0);
     mark(ev, 1, c->stream);
-    launch_tc<8, 32, tc::EPI_RELU_BF16>(c, 0, c->img1, c->params + P_B1, c->a1);
+    const bool pair = c->conv_path == AC_CONV_TCGEN05_PAIR;
+    launch_tc<8, 32, tc::EPI_RELU_BF16>(c, 0, pair, c->img1, c->pimg1, c->params + P_B1, c->a1);
     mark(ev, 2, c->stream);
-    launch_tc<32, 32, tc::EPI_RELU_BF16>(c, 1, c->img2, c->params + P_B2, c->a2);
+    launch_tc<32, 32, tc::EPI_RELU_BF16>(c, 1, pair, c->img2, c->pimg2, c->params + P_B2, c->a2);
     mark(ev, 3, c->stream);
-    launch_tc<32, 8, tc::EPI_SCALED_F32>(c, 2, c->img3, c->params + P_B3, nullptr, out ? out : own,
-                                         gmax);
+    launch_tc<32, 8, tc::EPI_SCALED_F32>(c, 2, pair, c->img3, c->pimg3, c->params + P_B3, nullptr,
+                                         out ? out : own, gmax);
     mark(ev, 4, c->stream);
     c->launches += 4;
     CCK(cudaGetLastError());
@@ -779,7 +866,7 @@ static int run_forward_tc(ac_closure *c, const float *const in[8], float *const 
 // (on the tcgen05 path the fifth, the output scaling, is empty).
 static int run_inference(ac_closure *c, const float *const in[8], float *const out[8],
                          cudaEvent_t *ev = nullptr) {
-    if (c->conv_path == AC_CONV_TCGEN05) {
+    if (c->conv_path != AC_CONV_MMA_SYNC) {
         int rc = run_forward_tc(c, in, out, nullptr, ev);
         mark(ev, 5, c->stream);
         return rc;
@@ -797,7 +884,8 @@ static int run_inference(ac_closure *c, const float *const in[8], float *const o
 }
 
 extern "C" int ac_closure_set_conv_path(ac_closure *c, int path) {
-    if (!c || (path != AC_CONV_TCGEN05 && path != AC_CONV_MMA_SYNC)) return AC_ERR_ARG;
+    if (!c || (path != AC_CONV_TCGEN05 && path != AC_CONV_MMA_SYNC && path != AC_CONV_TCGEN05_PAIR))
+        return AC_ERR_ARG;
     c->conv_path = path;
     return AC_OK;
 }
@@ -927,7 +1015,7 @@ extern "C" int ac_closure_apply(ac_closure *c, ac_handle *h, double limit, int *
     }
     CCK(cudaMemsetAsync(c->guard, 0, sizeof(unsigned long long), c->stream));
     const float *yscale = nullptr;  // y already scaled (tcgen05 path)
-    if (c->conv_path == AC_CONV_TCGEN05) {
+    if (c->conv_path != AC_CONV_MMA_SYNC) {
         rc = run_forward_tc(c, in, nullptr, c->guard);
         if (rc) return rc;
     } else {

@@ -64,13 +64,15 @@ def _setup(n, seed):
     return net, params, x, in_scale, out_scale
 
 
-PATHS = [ac.AC_CONV_TCGEN05, ac.AC_CONV_MMA_SYNC]
+PATHS = [ac.AC_CONV_TCGEN05, ac.AC_CONV_MMA_SYNC, ac.AC_CONV_TCGEN05_PAIR]
 
 
-# one x-row tile, ragged tiles, several tiles per row, odd sizes, a single cell
+# one x-row tile, ragged tiles, several tiles per row, odd sizes, a single cell;
+# nz = 29 and 26 split into z-chunks whose last one overlaps the one before on
+# the paired path, (7, 5, 3) and (300, 1, 29) have an odd number of columns
 @pytest.mark.parametrize("path", PATHS)
 @pytest.mark.parametrize("n", [(16, 12, 10), (40, 8, 6), (130, 3, 4), (300, 2, 3), (7, 5, 3),
-                               (1, 1, 1)])
+                               (1, 1, 1), (24, 6, 29), (300, 1, 29), (129, 3, 26)])
 def test_forward_matches_oracle(n, path):
     net, params, x, ins, outs = _setup(n, 5)
     c = cl.Closure(n, params=params, conv_path=path)
@@ -85,10 +87,10 @@ def test_forward_matches_oracle(n, path):
 
 
 def test_forward_paths_agree_at_64_cubed():
-    """The tcgen05 and mma.sync forward passes on a 64^3 grid (32 768 tiles of
-    a row each on the persistent grid): same bfloat16 operands, different
-    accumulation order, so agreement to bfloat16 rounding of the hidden
-    activations."""
+    """The tcgen05 (one CTA and paired) and mma.sync forward passes on a 64^3
+    grid (4 096 tiles of a row each on the persistent grids): same bfloat16
+    operands, different accumulation order, so agreement to bfloat16 rounding
+    of the hidden activations."""
     n = (64, 64, 64)
     net, params, x, ins, outs = _setup(n, 9)
     xs = _dev(x)
@@ -99,7 +101,8 @@ def test_forward_paths_agree_at_64_cubed():
         outs_.append(c.correction(xs).double().cpu().numpy())
         c.status()
         c.close()
-    assert _maxrel(outs_[0], outs_[1]) <= 1e-2, _maxrel(outs_[0], outs_[1])
+    for o in outs_[1:]:
+        assert _maxrel(outs_[0], o) <= 1e-2, _maxrel(outs_[0], o)
     # every cell against the oracle
     xn = x / ins.astype(np.float64)[:, None, None, None]
     y, _ = net.forward(xn, round_bf16=True)
@@ -112,18 +115,21 @@ def test_conv_path_selection():
     assert ac.ac_closure_get_conv_path(c.c) == ac.AC_CONV_TCGEN05
     ac.ac_closure_set_conv_path(c.c, ac.AC_CONV_MMA_SYNC)
     assert ac.ac_closure_get_conv_path(c.c) == ac.AC_CONV_MMA_SYNC
+    ac.ac_closure_set_conv_path(c.c, ac.AC_CONV_TCGEN05_PAIR)
+    assert ac.ac_closure_get_conv_path(c.c) == ac.AC_CONV_TCGEN05_PAIR
     with pytest.raises(ac.AcError):
         ac.ac_closure_set_conv_path(c.c, 7)
     c.close()
 
 
-def test_gradients_and_adam_match_oracle():
+@pytest.mark.parametrize("path", PATHS)
+def test_gradients_and_adam_match_oracle(path):
     n = (16, 12, 10)
     net, params, x, ins, outs = _setup(n, 6)
     rng = np.random.default_rng(7)
     tgt = (outs.astype(np.float64)[:, None, None, None]
            * rng.standard_normal(x.shape)).astype(np.float32).astype(np.float64)
-    c = cl.Closure(n, params=params)
+    c = cl.Closure(n, params=params, conv_path=path)
     c.set_scales(ins, outs)
     loss = c.loss(_dev(x), _dev(tgt))
     g = ac.ac_closure_get_grads(c.c).astype(np.float64)
