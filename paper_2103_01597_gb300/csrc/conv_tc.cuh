@@ -72,33 +72,36 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, unsigned parity) {
     return false;
 }
 
-// Non-blocking test of one mbarrier phase.
-__device__ __forceinline__ bool mbar_test(uint32_t bar_addr, unsigned parity) {
-    uint32_t done;
+// Six mbarrier phase tests issued back to back (their shared-memory latencies
+// overlap); bit k of the result is set if phase (addr[k], par[k]) has completed.
+__device__ __forceinline__ uint32_t mbar_test6(const uint32_t (&addr)[6], const unsigned (&par)[6]) {
+    uint32_t r;
     asm volatile(
-        "{\n .reg .pred p;\n"
-        " mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-        " selp.u32 %0, 1, 0, p;\n}\n"
-        : "=r"(done)
-        : "r"(bar_addr), "r"(parity)
+        "{\n .reg .pred p0, p1, p2, p3, p4, p5;\n .reg .b32 t0, t1, t2, t3, t4, t5;\n"
+        " mbarrier.test_wait.parity.shared::cta.b64 p0, [%1], %7;\n"
+        " mbarrier.test_wait.parity.shared::cta.b64 p1, [%2], %8;\n"
+        " mbarrier.test_wait.parity.shared::cta.b64 p2, [%3], %9;\n"
+        " mbarrier.test_wait.parity.shared::cta.b64 p3, [%4], %10;\n"
+        " mbarrier.test_wait.parity.shared::cta.b64 p4, [%5], %11;\n"
+        " mbarrier.test_wait.parity.shared::cta.b64 p5, [%6], %12;\n"
+        " selp.b32 t0, 1, 0, p0;\n selp.b32 t1, 2, 0, p1;\n selp.b32 t2, 4, 0, p2;\n"
+        " selp.b32 t3, 8, 0, p3;\n selp.b32 t4, 16, 0, p4;\n selp.b32 t5, 32, 0, p5;\n"
+        " or.b32 t0, t0, t1;\n or.b32 t2, t2, t3;\n or.b32 t4, t4, t5;\n"
+        " or.b32 t0, t0, t2;\n or.b32 %0, t0, t4;\n}\n"
+        : "=r"(r)
+        : "r"(addr[0]), "r"(addr[1]), "r"(addr[2]), "r"(addr[3]), "r"(addr[4]), "r"(addr[5]),
+          "r"(par[0]), "r"(par[1]), "r"(par[2]), "r"(par[3]), "r"(par[4]), "r"(par[5])
         : "memory");
-    return done != 0;
+    return r;
 }
 
-// Wait for the mbarrier phases (addr[k], par[k]) whose bit k is set in
-// `pending`, all at once: the tests of one round are independent, so their
-// shared-memory latencies overlap.  False on timeout.
-template <int N>
-__device__ __forceinline__ bool mbar_wait_all(const uint32_t (&addr)[N], const unsigned (&par)[N],
-                                              uint32_t pending) {
-    for (unsigned it = 0; it < WAIT_LIMIT && pending; ++it) {
-        uint32_t done = 0;
-#pragma unroll
-        for (int k = 0; k < N; ++k)
-            if ((pending >> k) & 1u) done |= (uint32_t)mbar_test(addr[k], par[k]) << k;
-        pending &= ~done;
-    }
-    return pending == 0;
+// Warp-wide wait for the phases whose bit is set in `pending` (every address
+// must be a valid barrier; the others are tested and ignored).  Returns the
+// same value on every lane: false if a lane gave up after WAIT_LIMIT rounds.
+__device__ __forceinline__ bool mbar_wait6_warp(const uint32_t (&addr)[6], const unsigned (&par)[6],
+                                                uint32_t pending) {
+    for (unsigned it = 0; it < WAIT_LIMIT && pending; ++it) pending &= ~mbar_test6(addr, par);
+    return __all_sync(0xffffffffu, pending == 0);
 }
 
 __device__ __forceinline__ void fence_proxy_async_smem() {
@@ -148,23 +151,31 @@ __host__ __device__ constexpr uint32_t idesc_bf16(int m, int n) {
            | ((uint32_t)(m >> 4) << 24);   // M / 16
 }
 
-__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc,
-                                         uint32_t idesc, uint32_t accumulate) {
+// A bfloat16 MMA (accumulating), issued by one elected lane of a converged warp.  The issuing loop runs
+// on the whole warp so that its descriptors stay warp-uniform; with the loop
+// inside a one-lane branch the MMA stream measured ~10% slower.
+__device__ __forceinline__ void mma_bf16_elect(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc,
+                                               uint32_t idesc) {
     asm volatile(
-        "{\n .reg .pred p;\n"
-        " setp.ne.u32 p, %4, 0;\n"
-        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
-        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        "{\n .reg .pred p, e;\n .reg .b32 r;\n"
+        " elect.sync r|e, 0xffffffff;\n"
+        " setp.ne.u32 p, 1, 0;\n"
+        " @e tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
+        "l"(adesc), "l"(bdesc), "r"(idesc)
         : "memory");
 }
 
-// Arrive on `bar` once all previously issued MMAs of this thread have completed.
-__device__ __forceinline__ void mma_commit(uint64_t *bar) {
+// Arrive on `bar` once all MMAs issued so far by this warp have completed (one
+// elected lane).
+__device__ __forceinline__ void mma_commit_elect(uint64_t *bar) {
     asm volatile(
-        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
+        "{\n .reg .pred e;\n .reg .b32 r;\n"
+        " elect.sync r|e, 0xffffffff;\n"
+        " @e tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n}\n" ::"r"(
             smem_u32(bar))
         : "memory");
 }
+
 
 // 32 lanes x 32 columns of binary32 from TMEM: thread t of the warp gets lane
 // (warp's quadrant base + t), columns col .. col + 31.
@@ -428,8 +439,9 @@ __global__ void __launch_bounds__(THREADS, 1)
                 if (s > b) mbar_wait(&full[b], (unsigned)(((s - 1 - b) / NBUF) & 1));
         }
     } else if (warp == 5) {
-        if (lane == 0) {  // ---- MMA issuer
-            bool ok = mbar_wait(&wbar, 0);
+        {  // ---- MMA issuer: the whole warp runs the loop, one elected lane issues
+            static_assert(GROUP == 3, "the combined wait tests six barriers");
+            bool ok = __all_sync(0xffffffffu, mbar_wait(&wbar, 0));
             long long s = 0;  // slices consumed
             // per TMEM block: bit k of `used` = block k has held a tile, bit k of
             // `par` = parity of the number of tiles it has held (registers, not an
@@ -458,7 +470,7 @@ __global__ void __launch_bounds__(THREADS, 1)
                             if (jq < L + 2) pending |= 1u << (2 * q);
                             if (jq < L && ((used >> jq) & 1u)) pending |= 1u << (2 * q + 1);
                         }
-                        ok = mbar_wait_all(addr, want, pending);
+                        ok = mbar_wait6_warp(addr, want, pending);
                         if (!ok) break;
                         tc_fence_after_sync();
                     }
@@ -484,7 +496,7 @@ __global__ void __launch_bounds__(THREADS, 1)
                             const uint32_t lbo = (tb0 / 3) * ROW + (tb0 % 3) * 16 - off;
                             const uint64_t ad = a0 + (off >> 4) + ((uint64_t)(lbo >> 4) << 16);
                             const uint64_t bd = b0 + ((2 * p * NGS * CORE) >> 4);
-                            mma_bf16(dtm, ad, bd, idesc, 1u);
+                            mma_bf16_elect(dtm, ad, bd, idesc);
                         }
                     } else {
                         const uint64_t a0 = smem_desc(sbase, PLANE, CORE);
@@ -497,16 +509,16 @@ __global__ void __launch_bounds__(THREADS, 1)
                                     const int dyx = dy * 3 + dx;
                                     const uint64_t ad = a0 + ((dy * ROW + dx * 16 + kk * 2 * PLANE) >> 4);
                                     const uint64_t bd = b0 + (((dyx * KC + 2 * kk) * NGS * CORE) >> 4);
-                                    mma_bf16(dtm, ad, bd, idesc, 1u);
+                                    mma_bf16_elect(dtm, ad, bd, idesc);
                                 }
                     }
-                    mma_commit(&empty[b]);
-                    if (j >= 2) mma_commit(&accf[j - 2]);  // tile j-2 has had its third slice
+                    mma_commit_elect(&empty[b]);
+                    if (j >= 2) mma_commit_elect(&accf[j - 2]);  // tile j-2 has had its third slice
                 }
             }
-            if (!ok) atomicExch(a.err, 1u);
+            if (!ok && lane == 0) atomicExch(a.err, 1u);
             // no MMA may be in flight when TMEM is freed: a final commit covers all
-            mma_commit(&fin);
+            mma_commit_elect(&fin);
             mbar_wait(&fin, 0);
         }
     } else {  // ---- epilogue: warps 0-3, TMEM lanes 32 warp .. 32 warp + 31
@@ -623,20 +635,23 @@ __device__ __forceinline__ void tmem_dealloc2(uint32_t taddr, unsigned ncols) {
     asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, %1;\n" ::"r"(taddr), "r"(ncols)
                  : "memory");
 }
-__device__ __forceinline__ void mma2_bf16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc,
-                                          uint32_t idesc) {
+// Paired MMA (accumulating), issued by one elected lane of the leader's converged warp.
+__device__ __forceinline__ void mma2_bf16_elect(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc,
+                                                uint32_t idesc) {
     asm volatile(
-        "{\n .reg .pred p;\n setp.ne.u32 p, 1, 0;\n"
-        " tcgen05.mma.cta_group::2.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
+        "{\n .reg .pred p, e;\n .reg .b32 r;\n elect.sync r|e, 0xffffffff;\n setp.ne.u32 p, 1, 0;\n"
+        " @e tcgen05.mma.cta_group::2.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
         "l"(adesc), "l"(bdesc), "r"(idesc)
         : "memory");
 }
-// Arrive on the barrier at `bar`'s offset in both CTAs once the leader's MMAs so far are done.
-__device__ __forceinline__ void mma2_commit(uint64_t *bar) {
+// Arrive on the barrier at `bar`'s offset in both CTAs once the leader's MMAs so
+// far are done (one elected lane).
+__device__ __forceinline__ void mma2_commit_elect(uint64_t *bar) {
     const uint16_t mask = 0x3;
     asm volatile(
-        "tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64"
-        " [%0], %1;\n" ::"r"(smem_u32(bar)),
+        "{\n .reg .pred e;\n .reg .b32 r;\n elect.sync r|e, 0xffffffff;\n"
+        " @e tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64"
+        " [%0], %1;\n}\n" ::"r"(smem_u32(bar)),
         "h"(mask)
         : "memory");
 }
@@ -792,7 +807,8 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(THREADS, 1)
                     if (s > b) mbar_wait(&full[b], (unsigned)(((s - 1 - b) / PNBUF) & 1));
         }
     } else if (warp == 5) {
-        if (leader && lane == 0) {  // ---- MMA issuer (leader only; M = 256 over the pair)
+        if (leader) {  // ---- MMA issuer: the leader's whole warp, one elected lane issues
+            static_assert(GROUP == 3, "the combined wait tests six barriers");
             bool ok = true;
             long long s = 0;
             // bit k of `used`: block k has held a tile; bit k of `par`: parity of their count
@@ -817,7 +833,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(THREADS, 1)
                             if (jq < L + 2) pending |= 1u << (2 * q);
                             if (jq < L && ((used >> kq) & 1u)) pending |= 1u << (2 * q + 1);
                         }
-                        ok = mbar_wait_all(addr, want, pending);
+                        ok = mbar_wait6_warp(addr, want, pending);
                         if (!ok) break;
                         tc_fence_after_sync();
                     }
@@ -836,7 +852,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(THREADS, 1)
                             const uint32_t lbo = (tb0 / 3) * ROW + (tb0 % 3) * 16 - off;
                             const uint64_t ad = a0 + (off >> 4) + ((uint64_t)(lbo >> 4) << 16);
                             const uint64_t bd = b0 + ((2 * p * NGH * CORE) >> 4);
-                            mma2_bf16(dtm, ad, bd, IDESC);
+                            mma2_bf16_elect(dtm, ad, bd, IDESC);
                         }
                     } else {
                         const uint64_t a0 = smem_desc(sbase, PLANE, CORE);
@@ -849,16 +865,16 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(THREADS, 1)
                                     const int dyx = dy * 3 + dx;
                                     const uint64_t ad = a0 + ((dy * ROW + dx * 16 + kk * 2 * PLANE) >> 4);
                                     const uint64_t bd = b0 + (((dyx * KC + 2 * kk) * NGH * CORE) >> 4);
-                                    mma2_bf16(dtm, ad, bd, IDESC);
+                                    mma2_bf16_elect(dtm, ad, bd, IDESC);
                                 }
                     }
-                    mma2_commit(&empty[b]);
-                    if (j >= 2) mma2_commit(&accf[j]);  // block j: tile j-2 has had its third slice
+                    mma2_commit_elect(&empty[b]);
+                    if (j >= 2) mma2_commit_elect(&accf[j]);  // block j: tile j-2 has had its third slice
                 }
             }
-            if (!ok) atomicExch(a.err, 1u);
+            if (!ok && lane == 0) atomicExch(a.err, 1u);
             // no MMA may be in flight when TMEM is freed: a final commit covers all
-            mma2_commit(&fin);
+            mma2_commit_elect(&fin);
             mbar_wait(&fin, 0);
         } else if (lane == 0) {
             // the peer: the final commit's arrival on its own fin is the last write
