@@ -52,8 +52,8 @@ def bytes_per_cell(elem_f, elem_w, s):
 # Nominal dense FP64 rate of one GB300 (no measured FP64 peak is provided).
 FP64_NOMINAL_TFLOPS = 1.25
 # DRAM bytes per cell of one launch of the integer-sum FP64 substep kernel
-# (ncu, 128^3: 425.9 MB read + 236.9 MB written over 2,097,152 cells).
-FX_TRAFFIC_PER_CELL = (425.94432e6 + 236.861696e6) / 2097152
+# (ncu, 128^3: 428.1 MB read + 235.0 MB written over 2,097,152 cells).
+FX_TRAFFIC_PER_CELL = (428.075264e6 + 234.951680e6) / 2097152
 # DRAM bytes per cell of one launch of the binary32 tiled substep (ncu, 256^3,
 # substep 1: 1126.6 MB read + 1023.2 MB written over 16,777,216 cells)
 TILED_TRAFFIC_PER_CELL = (1126.612e6 + 1023.183e6) / 16777216
@@ -381,7 +381,7 @@ def run_ours(args, wl):
                 "note": ("achieved counts the method's %d binary64 flops per cell-substep; "
                          % flops_per_cell(order, 1) +
                          "540 of them (the stencil sums) run as exact int64 operations on the "
-                         "integer pipes, so frac can exceed 1; ncu: FP64 pipe 76% busy"
+                         "integer pipes, so frac can exceed 1; ncu: FP64 pipe 79% busy"
                          if fixed else "all arithmetic on the FP64 pipe"),
                 "fp64_dgemm_measured_tflops": dg,
                 "avg_launch_ms": 1e3 * avg_all,
