@@ -683,6 +683,13 @@ def run_closure(args, wl):
     ta, tb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     l0 = ac.ac_launch_count(sim.h) + ac.ac_closure_launch_count(c.c)
     lib = ac.load_library()
+    bus = None
+    try:
+        bus = torch.cuda.get_device_properties(0).pci_bus_id
+    except Exception:
+        pass
+    sampler = ClockSampler(bus)
+    time.sleep(0.3)
     ta.record(stream)
     for it in range(args.steps):
         sim.step(2 * dtf)
@@ -690,7 +697,25 @@ def run_closure(args, wl):
         assert rc == 0, ac.ac_strerror(rc)
     tb.record(stream)
     torch.cuda.synchronize()
+    clocks = sampler.stop()
     elapsed = ta.elapsed_time(tb) / 1e3
+    # end to end through the public calls with host binary64 buffers: load the
+    # coarse state, step, apply the guarded closure, store the state
+    hstate = torch.from_numpy(sim.store().reshape(-1).copy()).pin_memory()
+    hout = torch.empty_like(hstate).pin_memory()
+    ne = max(2, args.e2e_steps)
+    torch.cuda.synchronize()
+    tt0 = time.perf_counter()
+    for _ in range(ne):
+        ac.ac_load(sim.h, ac.AC_ALL, hstate)
+        sim.step(2 * dtf)
+        rc = lib.ac_closure_apply(c.c, sim.h, 1e3, None)
+        assert rc == 0, ac.ac_strerror(rc)
+        ac.ac_store(sim.h, ac.AC_ALL, hout)
+    tt = time.perf_counter() - tt0
+    e2e = {"value": cells * 3 * ne / tt / 1e9, "unit": UNIT,
+           "h2d_bytes_per_step": 8 * cells * 8, "d2h_bytes_per_step": 8 * cells * 8,
+           "steps": ne}
     launches = ac.ac_launch_count(sim.h) + ac.ac_closure_launch_count(c.c) - l0
     # the forward pass (input pack + three convolution launches), timed alone on
     # the same state, on both convolution paths
@@ -774,8 +799,8 @@ def run_closure(args, wl):
                        "dt_coarse": 2 * dtf,
                        "step": "coarse RK3 step (3 fused substeps) + closure forward "
                                "(3 conv layers) + guarded correction"},
-            "roofline": roof, "cpu_baseline": None, "e2e": None, "gpu_launches": launches,
-            "clocks": None, "closure": quality}
+            "roofline": roof, "cpu_baseline": None, "e2e": e2e, "gpu_launches": launches,
+            "clocks": clocks, "closure": quality}
     print(json.dumps(line))
     return 0
 

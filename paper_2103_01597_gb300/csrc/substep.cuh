@@ -129,7 +129,10 @@ void launch_substep_r(const SubstepArgs<R, W> &a, bool padded, bool cfl, dim3 gr
             else
                 launch_substep_one<R, W, IdxPadded, false, RAD, EXT>(a, grid, block, st);
         }
-    } else if (a.g.elems < (1ll << 31)) {  // 32-bit neighbour offsets (fewer registers)
+    } else if (a.g.elems < (1ll << 31) && !(sizeof(R) == 4 && RAD == 1)) {
+        // 32-bit neighbour offsets (fewer registers).  Measured at 256^3: binary32
+        // radius 2 and 4 gain 14% and 21% from them, radius 1 loses 17% (19.4
+        // against 16.2 Gcell-updates/s) and keeps 64-bit ones; binary64 is unchanged.
         if (cfl)
             launch_substep_one<R, W, IdxPeriodicR<RAD, int>, true, RAD, EXT>(a, grid, block, st);
         else
