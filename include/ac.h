@@ -394,6 +394,14 @@ int ac_closure_get_conv_path(const ac_closure *c, int *path);
  * mbarrier waits ran out since the last call (the outputs of that call are
  * then undefined), else AC_OK. */
 int ac_closure_status(ac_closure *c);
+/* Diagnostic of the bounded device waits that the tcgen05 kernels use: one CTA
+ * waits, through the same bounded mbarrier wait, on a phase that nothing
+ * completes, gives up after `polls` polls (1 <= polls <= 2^18, the kernels'
+ * own bound, about one second; else AC_ERR_ARG), records that in a device word
+ * and returns.  The expected
+ * result is AC_ERR_TIMEOUT, with the context still usable; AC_OK would mean
+ * the wait completed.  `stream` may be NULL; synchronises it. */
+int ac_diag_wait_timeout(unsigned polls, void *stream);
 
 /* Full-weighting restriction of eight fine fields (nx, ny, nz even; binary64
  * for AC_FP64, binary32 otherwise; periodic layout) to eight binary32 coarse

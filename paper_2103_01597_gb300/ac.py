@@ -145,6 +145,7 @@ def load_library(path=None):
         "ac_closure_apply": ([_vp, _vp, _c.c_double, ctypes.POINTER(_c.c_int)], _c.c_int),
         "ac_closure_launch_count": ([_vp, ctypes.POINTER(_c.c_ulonglong)], _c.c_int),
         "ac_closure_set_conv_path": ([_vp, _c.c_int], _c.c_int),
+        "ac_diag_wait_timeout": ([_c.c_uint, _vp], _c.c_int),
         "ac_closure_get_conv_path": ([_vp, ctypes.POINTER(_c.c_int)], _c.c_int),
         "ac_closure_status": ([_vp], _c.c_int),
         "ac_restrict": ([ctypes.POINTER(_vp), _c.c_int, _c.c_int, _c.c_int, _c.c_int,
@@ -442,6 +443,12 @@ def ac_closure_launch_count(c):
     n = ctypes.c_ulonglong()
     _check(load_library().ac_closure_launch_count(c, ctypes.byref(n)), "ac_closure_launch_count")
     return n.value
+
+
+def ac_diag_wait_timeout(polls, stream=None):
+    """Run the bounded-wait diagnostic; returns the library's status code
+    (AC_ERR_TIMEOUT is the expected outcome)."""
+    return load_library().ac_diag_wait_timeout(int(polls), stream)
 
 
 def ac_closure_set_conv_path(c, path):

@@ -25,6 +25,10 @@ static thread_local char g_cuda_msg[256] = "";
 
 static int cuda_fail(cudaError_t e) {
     snprintf(g_cuda_msg, sizeof g_cuda_msg, "%s: %s", cudaGetErrorName(e), cudaGetErrorString(e));
+    // the error is reported through the return code: clear the runtime's
+    // per-thread last error so that the caller's next, unrelated CUDA call
+    // (an allocation in the application, say) does not find it
+    (void)cudaGetLastError();
     return e == cudaErrorMemoryAllocation ? AC_ERR_OOM : AC_ERR_CUDA;
 }
 

@@ -44,7 +44,12 @@ constexpr int CORE = 128;        // bytes of one core matrix (8 rows x 16 B)
 constexpr int PCELLS = TM + 8;          // cells of a staged plane (130 used)
 constexpr int PLANE = PCELLS * 16;      // bytes of one staged 8-channel plane
 constexpr int NBUF = 6;          // z-slices in the shared-memory ring
-constexpr unsigned WAIT_LIMIT = 1u << 24;  // polls of an mbarrier before giving up
+// Bounds of every wait, set by time: a try_wait poll of a phase that does not
+// complete returns after about 3.8 us (measured on GB300), so 2^18 polls give
+// up after about one second; a round of non-blocking tests takes well under a
+// microsecond, so 2^23 rounds bound the issuer's waits to about a second too.
+constexpr unsigned WAIT_LIMIT = 1u << 18;  // try_wait polls of an mbarrier before giving up
+constexpr unsigned TEST_LIMIT = 1u << 23;  // rounds of non-blocking tests before giving up
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
     return (uint32_t)__cvta_generic_to_shared(p);
@@ -55,10 +60,11 @@ __device__ __forceinline__ void mbar_init(uint64_t *bar, unsigned count) {
                  : "memory");
 }
 
-// Wait for the phase with the given parity to complete; false on timeout.
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, unsigned parity) {
+// Wait for the phase with the given parity to complete, giving up after
+// `limit` tests; false on timeout.
+__device__ __forceinline__ bool mbar_wait_n(uint64_t *bar, unsigned parity, unsigned limit) {
     const uint32_t a = smem_u32(bar);
-    for (unsigned it = 0; it < WAIT_LIMIT; ++it) {
+    for (unsigned it = 0; it < limit; ++it) {
         uint32_t done;
         asm volatile(
             "{\n .reg .pred p;\n"
@@ -70,6 +76,23 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, unsigned parity) {
         if (done) return true;
     }
     return false;
+}
+
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, unsigned parity) {
+    return mbar_wait_n(bar, parity, WAIT_LIMIT);
+}
+
+// A CTA that waits on a phase nothing completes, through the same bounded wait
+// as the kernels above: err[0] = 1 once the wait has given up (the expected
+// outcome), 0 if it completed.  Exercises the timeout path without a fault.
+__global__ void wait_timeout_kernel(unsigned limit, unsigned *err) {
+    __shared__ uint64_t bar;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) err[0] = mbar_wait_n(&bar, 0, limit) ? 0u : 1u;
 }
 
 // Six mbarrier phase tests issued back to back (their shared-memory latencies
@@ -97,10 +120,10 @@ __device__ __forceinline__ uint32_t mbar_test6(const uint32_t (&addr)[6], const 
 
 // Warp-wide wait for the phases whose bit is set in `pending` (every address
 // must be a valid barrier; the others are tested and ignored).  Returns the
-// same value on every lane: false if a lane gave up after WAIT_LIMIT rounds.
+// same value on every lane: false if a lane gave up after TEST_LIMIT rounds.
 __device__ __forceinline__ bool mbar_wait6_warp(const uint32_t (&addr)[6], const unsigned (&par)[6],
                                                 uint32_t pending) {
-    for (unsigned it = 0; it < WAIT_LIMIT && pending; ++it) pending &= ~mbar_test6(addr, par);
+    for (unsigned it = 0; it < TEST_LIMIT && pending; ++it) pending &= ~mbar_test6(addr, par);
     return __all_sync(0xffffffffu, pending == 0);
 }
 

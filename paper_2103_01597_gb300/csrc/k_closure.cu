@@ -906,6 +906,24 @@ extern "C" int ac_closure_status(ac_closure *c) {
     return err ? AC_ERR_TIMEOUT : AC_OK;
 }
 
+extern "C" int ac_diag_wait_timeout(unsigned polls, void *stream) {
+    if (polls == 0 || polls > tc::WAIT_LIMIT) return AC_ERR_ARG;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    unsigned *d = nullptr;
+    unsigned h = 2;
+    cudaError_t e = cudaMalloc(&d, sizeof(unsigned));
+    if (e == cudaSuccess) e = cudaMemsetAsync(d, 0xff, sizeof(unsigned), st);
+    if (e == cudaSuccess) {
+        tc::wait_timeout_kernel<<<1, 32, 0, st>>>(polls, d);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&h, d, sizeof h, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (d) cudaFree(d);
+    if (e != cudaSuccess) return ac_report_cuda(e);
+    return h == 1u ? AC_ERR_TIMEOUT : (h == 0u ? AC_OK : AC_ERR_CUDA);
+}
+
 extern "C" int ac_closure_forward(ac_closure *c, const float *const in[8], float *const out[8]) {
     if (!c || !in) return AC_ERR_ARG;
     for (int i = 0; i < 8; ++i)

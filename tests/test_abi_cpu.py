@@ -55,6 +55,9 @@ def test_argument_validation_without_gpu(lib):
     assert L.ac_init(None, ctypes.byref(g), ctypes.byref(p), None) == lib.AC_ERR_ARG
     assert L.ac_integrate_substep(None, 1e-3, 0) == lib.AC_ERR_ARG
     assert L.ac_quit(None) == lib.AC_OK
+    # the bounded-wait diagnostic checks its limit before touching the device
+    assert lib.ac_diag_wait_timeout(0) == lib.AC_ERR_ARG
+    assert lib.ac_diag_wait_timeout((1 << 18) + 1) == lib.AC_ERR_ARG
 
 
 def test_strerror(lib):
