@@ -186,10 +186,29 @@ def make_state(wl):
 
 
 def dist_setup(args):
+    """(world size, rank, local rank) from the launcher's environment (torchrun
+    sets WORLD_SIZE, RANK, LOCAL_RANK; a plain launch is rank 0 of 1)."""
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     return ws, rank, local
+
+
+def timed_region_max(elapsed, dist, device):
+    """Seconds of the timed region for the whole job: the largest over the ranks
+    (the job ends with its slowest rank); unchanged without a process group."""
+    if dist is None:
+        return elapsed
+    import torch
+    t = torch.tensor([elapsed], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(units_per_rank, ws, elapsed):
+    """Whole-job throughput: the units every rank processed (the same number on
+    each replica) over the slowest rank's time."""
+    return ws * units_per_rank / elapsed
 
 
 # ---------------------------------------------------------------------------
@@ -352,13 +371,10 @@ def run_ours(args, wl):
     elapsed = t0.elapsed_time(t1) / 1e3
     launches = ac.ac_launch_count(sim.h) - launches0
     clocks = sampler.stop() if sampler else None
-    if dist:
-        tt = torch.tensor([elapsed], device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        elapsed = float(tt.item())
+    elapsed = timed_region_max(elapsed, dist, "cuda")
     per_sub = [[evs[it][s][0].elapsed_time(evs[it][s][1]) / 1e3 for it in range(args.steps)]
                for s in range(3)]
-    value = ws * ncell * 3 * args.steps / elapsed / 1e9
+    value = job_rate(ncell * 3 * args.steps, ws, elapsed) / 1e9
 
     # dominant kernel: the fused substep; its average launch duration per substep index
     avg = {s: statistics.mean(per_sub[s]) for s in range(3)}
@@ -503,11 +519,8 @@ def run_ensemble(args, wl):
     elapsed = t0.elapsed_time(t1) / 1e3
     launches = ac.ac_batch_info(b.b)["launches"] - l0
     clocks = sampler.stop() if sampler else None
-    if dist:
-        tt = torch.tensor([elapsed], device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        elapsed = float(tt.item())
-    value = ws * ncell * 3 * args.steps / elapsed / 1e9
+    elapsed = timed_region_max(elapsed, dist, "cuda")
+    value = job_rate(ncell * 3 * args.steps, ws, elapsed) / 1e9
     step_s = statistics.mean(e[0].elapsed_time(e[1]) / 1e3 for e in evs)
     launch_s = step_s / 3
     peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -887,11 +900,8 @@ def run_closure_forward(args, wl):
     clocks = sampler.stop() if sampler else None
     launches = ac.ac_closure_launch_count(c.c) - l0
     c.status()
-    if dist:
-        t = torch.tensor([elapsed], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        elapsed = float(t.item())
-    value = ws * cells * args.steps / elapsed / 1e9
+    elapsed = timed_region_max(elapsed, dist, "cuda")
+    value = job_rate(cells * args.steps, ws, elapsed) / 1e9
 
     # per-launch device times (events around each launch, on the closure's stream)
     per = {}
