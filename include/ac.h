@@ -403,6 +403,21 @@ int ac_closure_status(ac_closure *c);
  * the wait completed.  `stream` may be NULL; synchronises it. */
 int ac_diag_wait_timeout(unsigned polls, void *stream);
 
+/* Global-index checks of a library built with AC_BOUNDS_CHECK (a separate,
+ * slower build for tests): every index the stencil, substep and convolution
+ * kernels form is compared with its array's extent, and an index outside it is
+ * recorded (bit 63 set, a kind tag in bits 48-62, the index's low 48 bits) and
+ * redirected or skipped instead of performed.  Writes the first recorded word
+ * since the last call to *first (0: none) and clears them all; AC_OK.  In the
+ * normal build *first = 0 and the result is AC_ERR_STATE (nothing is checked).
+ * Synchronises the device. */
+int ac_bounds_check_take(unsigned long long *first);
+/* Self-test of those checks (checked build): one kernel computes two checked
+ * indices without using them, -5 and 3 against an extent of 10, and writes
+ * them to out: expected 0 (redirected, and recorded with tag 7 for the next
+ * ac_bounds_check_take) and 3.  AC_ERR_STATE in the normal build. */
+int ac_bounds_check_selftest(long long out[2]);
+
 /* Full-weighting restriction of eight fine fields (nx, ny, nz even; binary64
  * for AC_FP64, binary32 otherwise; periodic layout) to eight binary32 coarse
  * arrays: coarse(I) = sum over d in {-1,0,1}^3 of prod_a w(d_a) fine(2I + d),

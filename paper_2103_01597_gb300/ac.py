@@ -146,6 +146,8 @@ def load_library(path=None):
         "ac_closure_launch_count": ([_vp, ctypes.POINTER(_c.c_ulonglong)], _c.c_int),
         "ac_closure_set_conv_path": ([_vp, _c.c_int], _c.c_int),
         "ac_diag_wait_timeout": ([_c.c_uint, _vp], _c.c_int),
+        "ac_bounds_check_take": ([ctypes.POINTER(_c.c_ulonglong)], _c.c_int),
+        "ac_bounds_check_selftest": ([ctypes.POINTER(_c.c_longlong)], _c.c_int),
         "ac_closure_get_conv_path": ([_vp, ctypes.POINTER(_c.c_int)], _c.c_int),
         "ac_closure_status": ([_vp], _c.c_int),
         "ac_restrict": ([ctypes.POINTER(_vp), _c.c_int, _c.c_int, _c.c_int, _c.c_int,
@@ -449,6 +451,21 @@ def ac_diag_wait_timeout(polls, stream=None):
     """Run the bounded-wait diagnostic; returns the library's status code
     (AC_ERR_TIMEOUT is the expected outcome)."""
     return load_library().ac_diag_wait_timeout(int(polls), stream)
+
+
+def ac_bounds_check_take():
+    """(status, first recorded word) of the global-index checks; status is
+    AC_ERR_STATE for a library built without them."""
+    w = _c.c_ulonglong(0)
+    rc = load_library().ac_bounds_check_take(ctypes.byref(w))
+    return rc, w.value
+
+
+def ac_bounds_check_selftest():
+    """(status, [index -5 checked, index 3 checked]) of the checked build."""
+    out = (_c.c_longlong * 2)()
+    rc = load_library().ac_bounds_check_selftest(out)
+    return rc, [out[0], out[1]]
 
 
 def ac_closure_set_conv_path(c, path):

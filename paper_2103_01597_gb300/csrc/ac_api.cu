@@ -531,6 +531,36 @@ extern "C" int ac_launch_count(const ac_handle *h, unsigned long long *count) {
 
 // ---- integration ------------------------------------------------------------
 
+#ifdef AC_BOUNDS_CHECK
+namespace ac {
+unsigned long long bc_take_aux();
+unsigned long long bc_take_batch();
+unsigned long long bc_take_closure();
+unsigned long long bc_take_noalloc();
+unsigned long long bc_take_f32();
+unsigned long long bc_take_f32g();
+unsigned long long bc_take_f64();
+}  // namespace ac
+#endif
+
+extern "C" int ac_bounds_check_take(unsigned long long *first) {
+    if (!first) return AC_ERR_ARG;
+    *first = 0;
+#ifdef AC_BOUNDS_CHECK
+    unsigned long long (*const readers[])() = {bc_take_aux, bc_take_batch, bc_take_closure,
+                                               bc_take_noalloc, bc_take_f32, bc_take_f32g,
+                                               bc_take_f64};
+    for (auto r : readers) {
+        const unsigned long long w = r();
+        if (w == ~0ull) return AC_ERR_CUDA;
+        if (!*first) *first = w;
+    }
+    return AC_OK;
+#else
+    return AC_ERR_STATE;  // this build does not check
+#endif
+}
+
 extern "C" int ac_integrate_substep(ac_handle *h, double dt, int s) {
     if (!h || s < 0 || s > 2 || !isfinite(dt)) return AC_ERR_ARG;
     if (s != h->next_s) return AC_ERR_STATE;

@@ -33,6 +33,8 @@
 #include <cuda_bf16.h>
 #include <stdint.h>
 
+#include "bounds.cuh"
+
 namespace ac {
 namespace tc {
 
@@ -317,6 +319,18 @@ __host__ __device__ constexpr int pair_tap(int p, int h) {
     return h == 0 ? (p < 4 ? 2 * p : 7) : (p < 4 ? 2 * p + 1 : 8);
 }
 
+// One 16-byte store of eight channels into a row-planar activation (element
+// offset e); the checked build skips it if [e, e + 8) leaves the array.
+#ifdef AC_BOUNDS_CHECK
+__device__ __forceinline__ void store_rp(bf16 *Y, long long e, long long lim, uint4 v) {
+    if (AC_BC_RANGE(e, 8, lim, AC_BC_CONV_ACT)) *reinterpret_cast<uint4 *>(Y + e) = v;
+}
+#else
+__device__ __forceinline__ void store_rp(bf16 *Y, long long e, uint4 v) {
+    *reinterpret_cast<uint4 *>(Y + e) = v;
+}
+#endif
+
 struct ConvTcArgs {
     const bf16 *w;        // weights in the shared-memory image order (see prep)
     const float *bias;    // [COUT]
@@ -576,18 +590,20 @@ __global__ void __launch_bounds__(THREADS, 1)
                     __align__(16) bf16 o[COUT];
 #pragma unroll
                     for (int c = 0; c < COUT; ++c) o[c] = __float2bfloat16_rn(fmaxf(v[c] + bias[c], 0.f));
-                    bf16 *Y = a.y;
+                    AC_BC_ONLY(const long long lim =
+                                   (long long)rp_cells(a.nx) * a.ny * a.nz * COUT;)
 #pragma unroll
                     for (int kc = 0; kc < COUT / 8; ++kc) {
                         const uint4 val = reinterpret_cast<const uint4 *>(o)[kc];
-                        bf16 *plane =
-                            Y + ((((long long)z * a.ny + sg.y) * (COUT / 8) + kc) * rp_cells(a.nx)) * 8;
-                        *reinterpret_cast<uint4 *>(plane + (long long)(x + 1) * 8) = val;
-                        if (x == 0) *reinterpret_cast<uint4 *>(plane + (long long)(a.nx + 1) * 8) = val;
-                        if (x == a.nx - 1) *reinterpret_cast<uint4 *>(plane) = val;
+                        const long long plane =
+                            ((((long long)z * a.ny + sg.y) * (COUT / 8) + kc) * rp_cells(a.nx)) * 8;
+                        store_rp(a.y, plane + (long long)(x + 1) * 8, AC_BC_ONLY(lim, ) val);
+                        if (x == 0) store_rp(a.y, plane + (long long)(a.nx + 1) * 8, AC_BC_ONLY(lim, ) val);
+                        if (x == a.nx - 1) store_rp(a.y, plane, AC_BC_ONLY(lim, ) val);
                     }
                 } else {
-                    const long long p = ((long long)z * a.ny + sg.y) * a.nx + x;
+                    const long long p = AC_BC(((long long)z * a.ny + sg.y) * a.nx + x,
+                                              (long long)a.nx * a.ny * a.nz, AC_BC_CONV_OUT);
 #pragma unroll
                     for (int c = 0; c < COUT; ++c) {
                         const float val = a.out_scale[c] * (v[c] + bias[c]);
@@ -937,18 +953,20 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(THREADS, 1)
                     __align__(16) bf16 o[COUT];
 #pragma unroll
                     for (int c = 0; c < COUT; ++c) o[c] = __float2bfloat16_rn(fmaxf(v[c] + bias[c], 0.f));
-                    bf16 *Y = a.y;
+                    AC_BC_ONLY(const long long lim =
+                                   (long long)rp_cells(a.nx) * a.ny * a.nz * COUT;)
 #pragma unroll
                     for (int kc = 0; kc < COUT / 8; ++kc) {
                         const uint4 val = reinterpret_cast<const uint4 *>(o)[kc];
-                        bf16 *plane =
-                            Y + ((((long long)z * a.ny + sg.y) * (COUT / 8) + kc) * rp_cells(a.nx)) * 8;
-                        *reinterpret_cast<uint4 *>(plane + (long long)(x + 1) * 8) = val;
-                        if (x == 0) *reinterpret_cast<uint4 *>(plane + (long long)(a.nx + 1) * 8) = val;
-                        if (x == a.nx - 1) *reinterpret_cast<uint4 *>(plane) = val;
+                        const long long plane =
+                            ((((long long)z * a.ny + sg.y) * (COUT / 8) + kc) * rp_cells(a.nx)) * 8;
+                        store_rp(a.y, plane + (long long)(x + 1) * 8, AC_BC_ONLY(lim, ) val);
+                        if (x == 0) store_rp(a.y, plane + (long long)(a.nx + 1) * 8, AC_BC_ONLY(lim, ) val);
+                        if (x == a.nx - 1) store_rp(a.y, plane, AC_BC_ONLY(lim, ) val);
                     }
                 } else {
-                    const long long p = ((long long)z * a.ny + sg.y) * a.nx + x;
+                    const long long p = AC_BC(((long long)z * a.ny + sg.y) * a.nx + x,
+                                              (long long)a.nx * a.ny * a.nz, AC_BC_CONV_OUT);
 #pragma unroll
                     for (int c = 0; c < COUT; ++c) {
                         const float val = a.out_scale[c] * (v[c] + bias[c]);

@@ -375,3 +375,35 @@ cudaError_t launch_reduce(const ReduceLaunch &L, cudaStream_t st, int *launches)
 }
 
 }  // namespace ac
+
+#ifdef AC_BOUNDS_CHECK
+namespace ac {
+// Self-test of the checks: two indices are only computed, never used to
+// address memory: -5 against an extent of 10 must be recorded (tag 7) and
+// redirected to 0, 3 must pass unchanged.
+__global__ void bc_selftest_kernel(long long *out) {
+    out[0] = AC_BC(-5ll, 10ll, 7u);
+    out[1] = AC_BC(3ll, 10ll, 7u);
+}
+}  // namespace ac
+#endif
+
+extern "C" int ac_bounds_check_selftest(long long out[2]) {
+    if (!out) return AC_ERR_ARG;
+#ifdef AC_BOUNDS_CHECK
+    long long *d = nullptr;
+    cudaError_t e = cudaMalloc(&d, 2 * sizeof(long long));
+    if (e == cudaSuccess) {
+        ac::bc_selftest_kernel<<<1, 1>>>(d);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpy(out, d, 2 * sizeof(long long), cudaMemcpyDeviceToHost);
+    if (d) cudaFree(d);
+    return e == cudaSuccess ? AC_OK : ac::ac_report_cuda(e);
+#else
+    out[0] = out[1] = 0;
+    return AC_ERR_STATE;
+#endif
+}
+
+AC_BC_READER(bc_take_aux)

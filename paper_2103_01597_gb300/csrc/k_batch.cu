@@ -573,3 +573,5 @@ extern "C" int ac_batch_info(const ac_batch *b, long long *cells, int *items, in
     if (launches) *launches = b->launches;
     return AC_OK;
 }
+
+AC_BC_READER(bc_take_batch)

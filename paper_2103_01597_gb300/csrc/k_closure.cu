@@ -1085,3 +1085,5 @@ extern "C" int ac_restrict(const void *const fine[8], int fine_precision, int nx
     CCK(cudaGetLastError());
     return AC_OK;
 }
+
+AC_BC_READER(bc_take_closure)

@@ -191,3 +191,5 @@ extern "C" int ac_reduce_noalloc(const void *const fields[8], const ac_grid *gri
     memcpy(&flag, &res[1], sizeof flag);
     return flag ? AC_ERR_NONFINITE : AC_OK;
 }
+
+AC_BC_READER(bc_take_noalloc)

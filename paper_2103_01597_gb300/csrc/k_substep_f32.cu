@@ -16,3 +16,5 @@ cudaError_t launch_substep_f32w64(const SubstepLaunch &L, cudaStream_t st, int *
     return launch_substep_f32_direct(L, st, launches, true);
 }
 }  // namespace ac
+
+AC_BC_READER(bc_take_f32)

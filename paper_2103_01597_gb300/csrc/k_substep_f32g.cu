@@ -9,3 +9,5 @@ cudaError_t launch_substep_f32_direct(const SubstepLaunch &L, cudaStream_t st, i
                : launch_substep_t<float, float>(L, st, launches);
 }
 }  // namespace ac
+
+AC_BC_READER(bc_take_f32g)

@@ -69,3 +69,5 @@ cudaError_t launch_substep_f64(const SubstepLaunch &L, cudaStream_t st, int *lau
 }
 
 }  // namespace ac
+
+AC_BC_READER(bc_take_f64)

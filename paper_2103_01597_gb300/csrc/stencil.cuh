@@ -7,6 +7,7 @@
 #include <cuda_runtime.h>
 
 #include "ac_internal.h"
+#include "bounds.cuh"
 
 namespace ac {
 
@@ -64,7 +65,9 @@ struct IdxPeriodicR {
     int xo[W];
     OFF yo[W];
     OFF zo[W];
+    AC_BC_ONLY(long long bc_lim;)
     __device__ __forceinline__ void set_xy(int i, int j, const Geom &g) {
+        AC_BC_ONLY(bc_lim = g.elems;)
 #pragma unroll
         for (int d = 0; d < W; ++d) {
             xo[d] = wrap_near(i + d - RAD, g.nx);
@@ -80,7 +83,7 @@ struct IdxPeriodicR {
         for (int d = 0; d < W; ++d) xo[d] = wrap_near(i + d - RAD, g.nx);
     }
     __device__ __forceinline__ long long operator()(int dx, int dy, int dz) const {
-        return (long long)(zo[dz + RAD] + yo[dy + RAD] + xo[dx + RAD]);
+        return AC_BC((long long)(zo[dz + RAD] + yo[dy + RAD] + xo[dx + RAD]), bc_lim, AC_BC_STENCIL);
     }
 };
 using IdxPeriodic = IdxPeriodicR<3>;
@@ -93,7 +96,9 @@ struct IdxPadded {
     long long row;   // jrow + k * pxy
     int i, px;
     long long pxy;
+    AC_BC_ONLY(long long bc_lim;)
     __device__ __forceinline__ void set_xy(int i_, int j, const Geom &g) {
+        AC_BC_ONLY(bc_lim = g.elems;)
         px = g.px;
         pxy = g.pxy;
         i = i_;
@@ -110,7 +115,7 @@ struct IdxPadded {
         c = row + i;
     }
     __device__ __forceinline__ long long operator()(int dx, int dy, int dz) const {
-        return c + dz * pxy + (long long)dy * px + dx;
+        return AC_BC(c + dz * pxy + (long long)dy * px + dx, bc_lim, AC_BC_STENCIL);
     }
 };
 

@@ -93,6 +93,7 @@ struct TileCopies {
     int soff[N];
     const float *src[N];
     int n;
+    AC_BC_ONLY(long long bc_idx[N]; long long bc_lim;)
     template <class TA>
     __device__ __forceinline__ void init(const TA &ta, const Geom &g, int x0, int y0) {
         const int tid = threadIdx.y * TT_X + threadIdx.x;
@@ -112,6 +113,7 @@ struct TileCopies {
                 const int gx = wrap_mod(x0 - 4 + CW * c, g.nx);
                 soff[u] = q * TT_FIELD + r * TT_ROW + CW * c;
                 src[u] = ta.fin(q) + (long long)gy * g.px + gx;
+                AC_BC_ONLY(bc_idx[u] = (long long)gy * g.px + gx; bc_lim = g.elems;)
                 n = u + 1;
             }
         }
@@ -121,7 +123,7 @@ struct TileCopies {
         const long long zoff = (long long)wrap_mod(p, g.nz) * g.pxy;
 #pragma unroll
         for (int u = 0; u < N; ++u)
-            if (u < n) {
+            if (u < n && AC_BC_RANGE(bc_idx[u] + zoff, VEC ? 4 : 1, bc_lim, AC_BC_TILE_IN)) {
                 if (VEC)
                     cp_async16(slot + soff[u], src[u] + zoff);
                 else
@@ -136,7 +138,7 @@ __device__ __forceinline__ void tile_load_w(W *wslot, const TA &ta, const Geom &
                                             int z, bool active) {
     if (!active) return;
     const int tid = threadIdx.y * TT_X + threadIdx.x;
-    const long long o = (long long)z * g.pxy + (long long)j * g.px + i;
+    const long long o = AC_BC((long long)z * g.pxy + (long long)j * g.px + i, g.elems, AC_BC_TILE_W);
 #pragma unroll
     for (int q = 0; q < NF; ++q) {
         if (sizeof(W) == 8) {
@@ -244,7 +246,8 @@ __device__ __forceinline__ void tiled_body(const TA &ta, int x0, int y0, int z0,
             } else {
                 cell_rhs<float, 3, EXT>(cell, ta.k(), frc, rhs);
             }
-            const long long o = (long long)z * g.pxy + (long long)j * g.px + i;
+            const long long o =
+                AC_BC((long long)z * g.pxy + (long long)j * g.px + i, g.elems, AC_BC_TILE_OUT);
             const W *wz = wring + ((z - z0) % TT_NW) * (NF * TT_THREADS) + tid;
 #pragma unroll
             for (int q = 0; q < NF; ++q) {

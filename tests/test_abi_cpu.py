@@ -58,6 +58,10 @@ def test_argument_validation_without_gpu(lib):
     # the bounded-wait diagnostic checks its limit before touching the device
     assert lib.ac_diag_wait_timeout(0) == lib.AC_ERR_ARG
     assert lib.ac_diag_wait_timeout((1 << 18) + 1) == lib.AC_ERR_ARG
+    # the normal build does not check global indices and says so
+    assert lib.ac_bounds_check_take() == (lib.AC_ERR_STATE, 0)
+    assert lib.ac_bounds_check_selftest() == (lib.AC_ERR_STATE, [0, 0])
+    assert L.ac_bounds_check_take(None) == lib.AC_ERR_ARG
 
 
 def test_strerror(lib):
