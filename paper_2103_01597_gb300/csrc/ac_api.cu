@@ -324,9 +324,11 @@ static int store_common(ac_handle *h, int field, double *dst, int from_w) {
 }
 
 extern "C" int ac_load(ac_handle *h, int field, const double *src) {
+    AC_RANGE("ac_load");
     return load_common(h, field, src, 0);
 }
 extern "C" int ac_store(ac_handle *h, int field, double *dst) {
+    AC_RANGE("ac_store");
     return store_common(h, field, dst, 0);
 }
 extern "C" int ac_load_w(ac_handle *h, int field, const double *src) {
@@ -562,6 +564,7 @@ extern "C" int ac_bounds_check_take(unsigned long long *first) {
 }
 
 extern "C" int ac_integrate_substep(ac_handle *h, double dt, int s) {
+    AC_RANGE("ac_integrate_substep");
     if (!h || s < 0 || s > 2 || !isfinite(dt)) return AC_ERR_ARG;
     if (s != h->next_s) return AC_ERR_STATE;
     int rc = ensure_state(h);
@@ -636,6 +639,7 @@ extern "C" int ac_integrate_substep(ac_handle *h, double dt, int s) {
 }
 
 extern "C" int ac_integrate_step(ac_handle *h, double dt) {
+    AC_RANGE("ac_integrate_step");
     if (!h || !isfinite(dt)) return AC_ERR_ARG;
     if (h->next_s != 0) return AC_ERR_STATE;
     for (int s = 0; s < 3; ++s) {
@@ -657,6 +661,7 @@ extern "C" int ac_last_cfl(ac_handle *h, double *out) {
 // ---- reductions -------------------------------------------------------------
 
 extern "C" int ac_reduce(ac_handle *h, int op, int quantity, double *out) {
+    AC_RANGE("ac_reduce");
     if (!h || !out || op < AC_MAX || op > AC_RMS || quantity < 0 || quantity > AC_Q_CFL)
         return AC_ERR_ARG;
     int rc = ensure_state(h);

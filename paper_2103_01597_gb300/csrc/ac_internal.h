@@ -2,11 +2,23 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 #include <stdint.h>
 
 #include "ac.h"
 
 namespace ac {
+
+// An NVTX range named after the C call for its whole extent (shows in profiler
+// timelines; costs a call into the NVTX stub when no tool is attached).
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
+};
+#define AC_RANGE(name) ::ac::NvtxRange ac_nvtx_range_(name)
+
 
 constexpr int NF = 8;
 constexpr int R = 3;  // stencil radius (sixth order, Sec. 4)

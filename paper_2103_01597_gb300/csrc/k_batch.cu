@@ -381,6 +381,7 @@ extern "C" int ac_batch_store_w(ac_batch *b, int box, int field, double *host) {
 }
 
 extern "C" int ac_batch_integrate_substep(ac_batch *b, double dt, int s) {
+    AC_RANGE("ac_batch_integrate_substep");
     if (!b || s < 0 || s > 2 || !isfinite(dt)) return AC_ERR_ARG;
     if (s != b->next_s) return AC_ERR_STATE;
     BCK(launch_batch(b, dt, s, b->cur, b->stream));
@@ -422,6 +423,7 @@ extern "C" int ac_batch_set_graph(ac_batch *b, int enable) {
 }
 
 extern "C" int ac_batch_integrate_step(ac_batch *b, double dt) {
+    AC_RANGE("ac_batch_integrate_step");
     if (!b || !isfinite(dt)) return AC_ERR_ARG;
     if (b->next_s != 0) return AC_ERR_STATE;
     if (!b->graph_on) {

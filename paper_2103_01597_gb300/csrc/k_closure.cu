@@ -925,6 +925,7 @@ extern "C" int ac_diag_wait_timeout(unsigned polls, void *stream) {
 }
 
 extern "C" int ac_closure_forward(ac_closure *c, const float *const in[8], float *const out[8]) {
+    AC_RANGE("ac_closure_forward");
     if (!c || !in) return AC_ERR_ARG;
     for (int i = 0; i < 8; ++i)
         if (!in[i] || (out && !out[i])) return AC_ERR_ARG;
@@ -955,6 +956,7 @@ extern "C" int ac_closure_forward_timings(ac_closure *c, const float *const in[8
 
 extern "C" int ac_closure_backward(ac_closure *c, const float *const in[8],
                                    const float *const target[8], double *loss) {
+    AC_RANGE("ac_closure_backward");
     if (!c || !in || !target) return AC_ERR_ARG;
     for (int i = 0; i < 8; ++i)
         if (!in[i] || !target[i]) return AC_ERR_ARG;
@@ -1004,6 +1006,7 @@ extern "C" int ac_closure_backward(ac_closure *c, const float *const in[8],
 }
 
 extern "C" int ac_closure_adam_step(ac_closure *c, float lr, float beta1, float beta2, float eps) {
+    AC_RANGE("ac_closure_adam_step");
     if (!c || !(lr > 0) || !(beta1 >= 0 && beta1 < 1) || !(beta2 >= 0 && beta2 < 1) || !(eps > 0))
         return AC_ERR_ARG;
     c->adam_t++;
@@ -1017,6 +1020,7 @@ extern "C" int ac_closure_adam_step(ac_closure *c, float lr, float beta1, float 
 }
 
 extern "C" int ac_closure_apply(ac_closure *c, ac_handle *h, double limit, int *applied) {
+    AC_RANGE("ac_closure_apply");
     if (!c || !h || !(limit > 0)) return AC_ERR_ARG;
     void *ptrs[8];
     int precision = 0, layout = 0, n[3];
