@@ -398,9 +398,9 @@ int ac_closure_status(ac_closure *c);
  * waits, through the same bounded mbarrier wait, on a phase that nothing
  * completes, gives up after `polls` polls (1 <= polls <= 2^18, the kernels'
  * own bound, about one second; else AC_ERR_ARG), records that in a device word
- * and returns.  The expected
- * result is AC_ERR_TIMEOUT, with the context still usable; AC_OK would mean
- * the wait completed.  `stream` may be NULL; synchronises it. */
+ * and returns.  The expected result is AC_ERR_TIMEOUT, with the context still
+ * usable; AC_OK would mean the wait completed.  `stream` may be NULL;
+ * synchronises it. */
 int ac_diag_wait_timeout(unsigned polls, void *stream);
 
 /* Global-index checks of a library built with AC_BOUNDS_CHECK (a separate,
