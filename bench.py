@@ -303,6 +303,30 @@ def fp64_dgemm_tflops(torch):
     return 2 * n ** 3 / best / 1e12
 
 
+def host_link_gbs(host):
+    """Rate of one copy of the pinned host buffer `host` to the device and back (GB/s,
+    best of three each way, CUDA events on the current stream): the bound that the
+    machine's host link puts on the end-to-end figures.  `host` is overwritten with
+    its own contents."""
+    import torch
+    flat = host.view(-1)
+    dev = torch.empty_like(flat, device="cuda")
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    nb = flat.numel() * flat.element_size()
+    best = [0.0, 0.0]
+    for _ in range(3):
+        ev[0].record()
+        dev.copy_(flat, non_blocking=True)
+        ev[1].record()
+        flat.copy_(dev, non_blocking=True)
+        ev[2].record()
+        ev[2].synchronize()
+        best[0] = max(best[0], nb / ev[0].elapsed_time(ev[1]) / 1e6)
+        best[1] = max(best[1], nb / ev[1].elapsed_time(ev[2]) / 1e6)
+    del dev
+    return {"h2d_gbs": round(best[0], 1), "d2h_gbs": round(best[1], 1), "bytes": nb}
+
+
 def run_ours(args, wl):
     import torch
     ws, rank, local = dist_setup(args)
@@ -423,6 +447,7 @@ def run_ours(args, wl):
     e2e = None
     if args.e2e_steps > 0:
         ne = max(8, args.e2e_steps)  # the first load and the last store are not overlapped
+        link = host_link_gbs(host_out)
         torch.cuda.synchronize()
         h2d = 8 * ncell * 8
         d2h = 8 * ncell * 8 + 16
@@ -463,7 +488,8 @@ def run_ours(args, wl):
                       "other's compute",
                "serial_one_handle": {"value": serial, "d2h_bytes_per_step": d2h,
                                      "how": "ac_load, ac_integrate_step, CFL read, ac_store "
-                                            "in sequence"}}
+                                            "in sequence"},
+               "host_link": link}
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
@@ -627,6 +653,8 @@ def run_ensemble(args, wl):
         torch.cuda.synchronize()
         ins = [torch.from_numpy(f.reshape(-1)).pin_memory() for f in states]
         outs = [torch.empty_like(t).pin_memory() for t in ins]
+        link = host_link_gbs(outs[int(np.argmax([t.numel() for t in outs]))])
+        torch.cuda.synchronize()
         tt0 = time.perf_counter()
         for _ in range(args.e2e_steps):
             for i, t in enumerate(ins):
@@ -637,7 +665,7 @@ def run_ensemble(args, wl):
         tt = time.perf_counter() - tt0
         e2e = {"value": ncell * 3 * args.e2e_steps * ws / tt / 1e9, "unit": UNIT,
                "h2d_bytes_per_step": 8 * ncell * 8, "d2h_bytes_per_step": 8 * ncell * 8,
-               "steps": args.e2e_steps}
+               "steps": args.e2e_steps, "host_link": link}
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         n0 = boxes[0][0]
@@ -748,6 +776,7 @@ def run_closure(args, wl):
     hstate = torch.from_numpy(sim.store().reshape(-1).copy()).pin_memory()
     hout = torch.empty_like(hstate).pin_memory()
     ne = max(2, args.e2e_steps)
+    link = host_link_gbs(hout)
     torch.cuda.synchronize()
     tt0 = time.perf_counter()
     for _ in range(ne):
@@ -759,7 +788,7 @@ def run_closure(args, wl):
     tt = time.perf_counter() - tt0
     e2e = {"value": cells * 3 * ne / tt / 1e9, "unit": UNIT,
            "h2d_bytes_per_step": 8 * cells * 8, "d2h_bytes_per_step": 8 * cells * 8,
-           "steps": ne}
+           "steps": ne, "host_link": link}
     launches = ac.ac_launch_count(sim.h) + ac.ac_closure_launch_count(c.c) - l0
     # the forward pass (input pack + three convolution launches), timed alone on
     # the same state, on both convolution paths
@@ -966,6 +995,7 @@ def run_closure_forward(args, wl):
     hout = torch.empty_like(hin).pin_memory()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     ne = max(8, args.e2e_steps)
+    link = host_link_gbs(hout)
     torch.cuda.synchronize()
     # (a) one closure on one stream: copy in, forward, copy out in sequence
     e0.record(stream)
@@ -1003,7 +1033,7 @@ def run_closure_forward(args, wl):
            "steps": ne,
            "how": "two closures on two streams take alternate forwards (copy in, "
                   "ac_closure_forward, copy out each), one's copies overlapping the other's compute",
-           "serial_one_stream": {"value": serial}}
+           "serial_one_stream": {"value": serial}, "host_link": link}
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         params = ac.ac_closure_get_params(c.c)
