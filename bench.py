@@ -52,8 +52,9 @@ def bytes_per_cell(elem_f, elem_w, s):
 # Nominal dense FP64 rate of one GB300 (no measured FP64 peak is provided).
 FP64_NOMINAL_TFLOPS = 1.25
 # DRAM bytes per cell of one launch of the integer-sum FP64 substep kernel
-# (ncu, 128^3: 428.1 MB read + 235.0 MB written over 2,097,152 cells).
-FX_TRAFFIC_PER_CELL = (428.075264e6 + 234.951680e6) / 2097152
+# (ncu, 128^3, substeps 1-2 variant: 430.7 MB read + 234.9 MB written over
+# 2,097,152 cells).
+FX_TRAFFIC_PER_CELL = (430.685440e6 + 234.900224e6) / 2097152
 # DRAM bytes per cell of one launch of the binary32 tiled substep (ncu, 256^3,
 # substep 1: 1126.6 MB read + 1023.2 MB written over 16,777,216 cells)
 TILED_TRAFFIC_PER_CELL = (1126.612e6 + 1023.183e6) / 16777216
@@ -411,7 +412,7 @@ def run_ours(args, wl):
         roof = {"bound": "alu", "achieved": achieved, "peak": FP64_NOMINAL_TFLOPS,
                 "unit": "TFLOP/s", "frac": achieved / FP64_NOMINAL_TFLOPS,
                 # dram read + write per 256^3 launch of the unchanged kernel, from the 128^3
-                # ncu capture scaled by cells (profiles/substep_fx_128_full.md)
+                # ncu capture scaled by cells (profiles/substep_fx_128_metrics.md)
                 "traffic": FX_TRAFFIC_PER_CELL * ncell if (fixed and n == (256, 256, 256)) else None,
                 "kernel": ("substep_fx_kernel (int64 stencil sums) + fx_max + fx_quantize"
                            if fixed else "substep_kernel<double,double,IdxPeriodicR<%d>>"
@@ -421,7 +422,7 @@ def run_ours(args, wl):
                 "note": ("achieved counts the method's %d binary64 flops per cell-substep; "
                          % flops_per_cell(order, 1) +
                          "540 of them (the stencil sums) run as exact int64 operations on the "
-                         "integer pipes, so frac can exceed 1; ncu: FP64 pipe 79% busy"
+                         "integer pipes, so frac can exceed 1; ncu: FP64 pipe 75-80% busy"
                          if fixed else "all arithmetic on the FP64 pipe"),
                 "fp64_dgemm_measured_tflops": dg,
                 "avg_launch_ms": 1e3 * avg_all,

@@ -8,6 +8,7 @@
 
 #include "ac_internal.h"
 #include "bounds.cuh"
+#include "exp_table.cuh"
 
 namespace ac {
 
@@ -19,6 +20,7 @@ struct DevCoefs {
     R dc[3][MAX_RADIUS];
     R nu, eta, nu3, two_nu;  // nu3: coefficient of grad(div u), nu / 3 + zeta; 2 nu
     R inv_cp, cs2_ref, gamma_cp, gm1, cp_gm1;
+    R inv_T_ref;             // c_p (gamma - 1) / c_s0^2
     R K, zeta, hc;           // conduction, bulk viscosity, H - C (Eqs. B.2-B.3)
 };
 
@@ -41,6 +43,7 @@ inline DevCoefs<R> to_dev(const StencilCoefs &c, const PhysConsts &p) {
     d.gamma_cp = (R)p.gamma_cp;
     d.gm1 = (R)p.gm1;
     d.cp_gm1 = (R)p.cp_gm1;
+    d.inv_T_ref = (R)(p.cp_gm1 / p.cs2_ref);
     d.K = (R)p.K;
     d.zeta = (R)p.zeta;
     d.hc = (R)p.hc;
@@ -221,25 +224,129 @@ template <typename R> __device__ __forceinline__ R dev_exp(R x);
 template <> __device__ __forceinline__ double dev_exp<double>(double x) { return exp(x); }
 template <> __device__ __forceinline__ float dev_exp<float>(float x) { return expf(x); }
 
+// ---- binary64 exp by Tang's table-driven method (ACM TOMS 15(2), 1989) ------
+// x = N ln2/256 + r with N = rint(256 x / ln 2) and |r| <= ln2/512; with
+// N = 256 m + j, exp(x) = 2^m 2^(j/256) exp(r), exp(r) - 1 from its degree-4
+// Taylor polynomial (truncation below 4e-17 relative).  The same reduction gives
+// exp(-x) from 2^(-j/256) and exp(-r).  Measured on GB300 in FP64-pipe DFMA
+// equivalents: 8.7 for exp alone and 13.4 for the pair, against 15.0 for CUDA's
+// exp and 7.5 for a division; within 1 ulp of CUDA's exp for |x| < 700.  `tab` is
+// EXP_TAB (exp_table.cuh) staged in shared memory.
+
+// |x| < 700 (finite, and every result below stays normal), tested on the bits.
+__device__ __forceinline__ bool exp_tab_ok(double x) {
+    return (__double_as_longlong(x) & 0x7fffffffffffffffll) < 0x4085e00000000000ll;  // 700.0
+}
+
+struct ExpReduced {
+    double r;
+    int n;
+};
+
+__device__ __forceinline__ ExpReduced exp_reduce(double x) {
+    constexpr double SH = 6755399441055744.0;  // 1.5 * 2^52: adding it rounds to an integer
+    const double t = fma(x, EXP_INV, SH);
+    const double nd = t - SH;
+    ExpReduced e;
+    e.n = (int)(__double_as_longlong(t) & 0xffffffffll);  // low word of t = N (two's complement)
+    e.r = fma(-nd, EXP_L2, fma(-nd, EXP_L1, x));          // nd * EXP_L1 is exact
+    return e;
+}
+
+// 2^m y for normal y and a normal result: m added to the exponent field.
+__device__ __forceinline__ double exp_scale(double y, int m) {
+    return __longlong_as_double(__double_as_longlong(y) + ((long long)m << 52));
+}
+
+__device__ __forceinline__ double exp_tab(double x, const double *tab) {
+    const ExpReduced e = exp_reduce(x);
+    double p = fma(e.r, 1.0 / 24.0, 1.0 / 6.0);
+    p = fma(p, e.r, 0.5);
+    p = fma(p * e.r, e.r, e.r);  // exp(r) - 1
+    const double tj = tab[e.n & 255];
+    return exp_scale(fma(tj, p, tj), e.n >> 8);
+}
+
+__device__ __forceinline__ void exp_tab_pm(double x, const double *tab, double &ep, double &em) {
+    const ExpReduced e = exp_reduce(x);
+    double p = fma(e.r, 1.0 / 24.0, 1.0 / 6.0);
+    p = fma(p, e.r, 0.5);
+    p = fma(p * e.r, e.r, e.r);  // exp(r) - 1
+    double q = fma(e.r, 1.0 / 24.0, -1.0 / 6.0);
+    q = fma(q, e.r, 0.5);
+    q = fma(q * e.r, e.r, -e.r);  // exp(-r) - 1
+    const int j = e.n & 255, m = e.n >> 8;
+    const double tp = tab[j], tm = tab[256 + j];
+    ep = exp_scale(fma(tp, p, tp), m);
+    em = exp_scale(fma(tm, q, tm), -m);
+}
+
+// Copy EXP_TAB into the shared array `tab` (every thread of the CTA calls this;
+// it ends with a barrier).
+__device__ __forceinline__ void exp_tab_stage(double *tab) {
+    const int nt = blockDim.x * blockDim.y * blockDim.z;
+    for (int t = (threadIdx.z * blockDim.y + threadIdx.y) * blockDim.x + threadIdx.x; t < 512;
+         t += nt)
+        tab[t] = EXP_TAB[t];
+    __syncthreads();
+}
+
+// The thermodynamic factors with CUDA's exp and a division.  (Kept inline: out
+// of line, the call made the binary64 substep-0 kernel 13% slower through
+// register allocation, although it is never taken on physical states.)
+template <typename R>
+__device__ __forceinline__ void thermo_lib(R lnrho, R xi, R cs2_ref, R cp_gm1, R &rho_inv, R &cs2,
+                                        R &inv_T) {
+    rho_inv = dev_exp<R>(-lnrho);
+    cs2 = cs2_ref * dev_exp<R>(xi);
+    inv_T = cp_gm1 / cs2;
+}
+
+// Thermodynamic factors of one cell: c_s^2 = c_s0^2 exp(xi) with
+// xi = gamma s / c_p + (gamma-1)(ln rho - ln rho0), 1/rho = exp(-ln rho) and
+// 1/T = c_p (gamma - 1) / c_s^2 = c_p (gamma - 1) exp(-xi) / c_s0^2.  With `etab`
+// (binary64 only) the exponentials come from the table-driven exp above and 1/T
+// from exp(-xi) instead of a division.
+template <typename R>
+struct Thermo {
+    R rho_inv, cs2, inv_T;
+};
+
+template <typename R>
+__device__ __forceinline__ Thermo<R> thermo_factors(R lnrho, R ss, const DevCoefs<R> &k,
+                                                    const double *etab) {
+    const R xi = k.gamma_cp * ss + k.gm1 * lnrho;
+    Thermo<R> t;
+    if (sizeof(R) != 8 || etab == nullptr) {
+        thermo_lib<R>(lnrho, xi, k.cs2_ref, k.cp_gm1, t.rho_inv, t.cs2, t.inv_T);
+    } else if (exp_tab_ok((double)lnrho) && exp_tab_ok((double)xi)) {
+        t.rho_inv = (R)exp_tab(-(double)lnrho, etab);
+        double ep, em;
+        exp_tab_pm((double)xi, etab, ep, em);
+        t.cs2 = k.cs2_ref * (R)ep;
+        t.inv_T = k.inv_T_ref * (R)em;
+    } else {
+        thermo_lib<R>(lnrho, xi, k.cs2_ref, k.cp_gm1, t.rho_inv, t.cs2, t.inv_T);
+    }
+    return t;
+}
+
 // Eqs. B.1-B.4 at one cell (mu0 = 1) given the centre values and the derivative
 // terms: gl, gs, gu[m][a] first derivatives of ln rho, s, u_m; B = curl A;
 // viscl = nu lap u + (nu / 3 + zeta) grad(div u) (the bulk viscosity of Eq. B.2
 // folded into the grad-div coefficient); lapa = lap A; J = grad(div A) - lap A.
 // The forcing term `frc` is added to du/dt.  EXT adds the remaining terms of
 // Eq. B.3: H - C, zeta rho (div u)^2 and div(K grad T) (from lapxi = lap xi);
-// without EXT they are zero.  Output order: Table B.1.
+// without EXT they are zero.  `th` holds the cell's thermodynamic factors.
+// Output order: Table B.1.
 template <typename R, bool EXT = false>
 __device__ __forceinline__ void cell_physics(R lnrho, const R (&u)[3], R ss, const R (&gl)[3],
                                              const R (&gs)[3], const R (&gu)[3][3],
                                              const R (&B)[3], const R (&viscl)[3],
                                              const R (&lapa)[3], const R (&J)[3],
                                              const DevCoefs<R> &k, const R frc[3], R out[NF],
-                                             R *cfl, R lapxi = (R)0) {
-    // Thermodynamics: c_s^2 = c_s0^2 exp(gamma s / c_p + (gamma-1)(ln rho - ln rho0)),
-    // 1/rho = exp(-ln rho), 1/T = c_p (gamma - 1) / c_s^2.
-    const R rho_inv = dev_exp<R>(-lnrho);
-    const R cs2 = k.cs2_ref * dev_exp<R>(k.gamma_cp * ss + k.gm1 * lnrho);
-    const R inv_T = k.cp_gm1 / cs2;
+                                             R *cfl, R lapxi, const Thermo<R> &th) {
+    const R rho_inv = th.rho_inv, cs2 = th.cs2, inv_T = th.inv_T;
 
     const R divu = gu[0][0] + gu[1][1] + gu[2][2];
     const R third_div = divu * (R)(1.0 / 3.0);
@@ -373,7 +480,8 @@ __device__ __forceinline__ void cell_rhs(const CELL &f, const DevCoefs<R> &k, co
                 llz = op_d2<2, RAD>(f[0], lnrho, k.d2[2]);
         lapxi = k.gamma_cp * (lsx + lsy + lsz) + k.gm1 * (llx + lly + llz);
     }
-    cell_physics<R, EXT>(lnrho, u, ss, gl, gs, gu, B, viscl, lapa, J, k, frc, out, cfl, lapxi);
+    cell_physics<R, EXT>(lnrho, u, ss, gl, gs, gu, B, viscl, lapa, J, k, frc, out, cfl, lapxi,
+                         thermo_factors<R>(lnrho, ss, k, nullptr));
 }
 
 // Block-wide max of a non-negative value folded into a global 64-bit word that
