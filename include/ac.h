@@ -402,6 +402,15 @@ int ac_closure_status(ac_closure *c);
  * usable; AC_OK would mean the wait completed.  `stream` may be NULL;
  * synchronises it. */
 int ac_diag_wait_timeout(unsigned polls, void *stream);
+/* Diagnostic of the table-driven binary64 exp that the binary64 substep
+ * kernels use for exp(-ln rho), exp(xi) and exp(-xi) (Tang's method with a
+ * 256-entry table; the library exp where |x| >= 700 or x is not finite).
+ * `x`: n device binary64 values; `y`: 4n device binary64 values, written as
+ * y[i] = the table exp of x[i], y[n + i] = CUDA's exp(x[i]), y[2n + i] and
+ * y[3n + i] = exp(x[i]) and exp(-x[i]) from the paired evaluation.  Both
+ * buffers belong to the caller.  n < 0, or a NULL pointer with n > 0, is
+ * AC_ERR_ARG; n == 0 does nothing.  `stream` may be NULL; synchronises it. */
+int ac_diag_exp_table(const double *x, long long n, double *y, void *stream);
 
 /* Global-index checks of a library built with AC_BOUNDS_CHECK (a separate,
  * slower build for tests): every index the stencil, substep and convolution

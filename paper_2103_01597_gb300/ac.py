@@ -146,6 +146,7 @@ def load_library(path=None):
         "ac_closure_launch_count": ([_vp, ctypes.POINTER(_c.c_ulonglong)], _c.c_int),
         "ac_closure_set_conv_path": ([_vp, _c.c_int], _c.c_int),
         "ac_diag_wait_timeout": ([_c.c_uint, _vp], _c.c_int),
+        "ac_diag_exp_table": ([_vp, _c.c_longlong, _vp, _vp], _c.c_int),
         "ac_bounds_check_take": ([ctypes.POINTER(_c.c_ulonglong)], _c.c_int),
         "ac_bounds_check_selftest": ([ctypes.POINTER(_c.c_longlong)], _c.c_int),
         "ac_closure_get_conv_path": ([_vp, ctypes.POINTER(_c.c_int)], _c.c_int),
@@ -451,6 +452,13 @@ def ac_diag_wait_timeout(polls, stream=None):
     """Run the bounded-wait diagnostic; returns the library's status code
     (AC_ERR_TIMEOUT is the expected outcome)."""
     return load_library().ac_diag_wait_timeout(int(polls), stream)
+
+
+def ac_diag_exp_table(x, y, stream=None):
+    """Table-driven exp diagnostic on device tensors: `x` (n binary64 values),
+    `y` (4 n binary64 values, written); returns the library's status code."""
+    return load_library().ac_diag_exp_table(_vp(x.data_ptr()), int(x.numel()),
+                                            _vp(y.data_ptr()), stream)
 
 
 def ac_bounds_check_take():

@@ -68,6 +68,44 @@ cudaError_t launch_substep_f64(const SubstepLaunch &L, cudaStream_t st, int *lau
     return cudaGetLastError();
 }
 
+// The table-driven exp of the binary64 kernels beside CUDA's exp, for tests:
+// y[i] = exp_tab(x[i]), y[n + i] = exp(x[i]), y[2n + i] and y[3n + i] = the pair
+// exp(x[i]), exp(-x[i]) from exp_tab_pm; where exp_tab_ok(x[i]) fails, the three
+// table values are CUDA's (the kernels' fallback).
+__global__ void diag_exp_kernel(const double *x, long long n, double *y) {
+    __shared__ double tab[512];
+    exp_tab_stage(tab);
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        const double v = x[i];
+        double a, b, c;
+        if (exp_tab_ok(v)) {
+            a = exp_tab(v, tab);
+            exp_tab_pm(v, tab, b, c);
+        } else {
+            a = exp(v);
+            b = exp(v);
+            c = exp(-v);
+        }
+        y[i] = a;
+        y[n + i] = exp(v);
+        y[2 * n + i] = b;
+        y[3 * n + i] = c;
+    }
+}
+
 }  // namespace ac
+
+extern "C" int ac_diag_exp_table(const double *x, long long n, double *y, void *stream) {
+    if (n < 0 || (n > 0 && (!x || !y))) return AC_ERR_ARG;
+    if (n == 0) return AC_OK;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const long long want = (n + 255) / 256;
+    const unsigned blocks = (unsigned)(want < 152 * 8 ? want : 152 * 8);
+    ac::diag_exp_kernel<<<blocks, 256, 0, st>>>(x, n, y);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    return e == cudaSuccess ? AC_OK : ac::ac_report_cuda(e);
+}
 
 AC_BC_READER(bc_take_f64)

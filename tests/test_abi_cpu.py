@@ -58,6 +58,10 @@ def test_argument_validation_without_gpu(lib):
     # the bounded-wait diagnostic checks its limit before touching the device
     assert lib.ac_diag_wait_timeout(0) == lib.AC_ERR_ARG
     assert lib.ac_diag_wait_timeout((1 << 18) + 1) == lib.AC_ERR_ARG
+    # the exp diagnostic checks its arguments before touching the device
+    assert L.ac_diag_exp_table(None, -1, None, None) == lib.AC_ERR_ARG
+    assert L.ac_diag_exp_table(None, 5, None, None) == lib.AC_ERR_ARG
+    assert L.ac_diag_exp_table(None, 0, None, None) == lib.AC_OK
     # the normal build does not check global indices and says so
     assert lib.ac_bounds_check_take() == (lib.AC_ERR_STATE, 0)
     assert lib.ac_bounds_check_selftest() == (lib.AC_ERR_STATE, [0, 0])
