@@ -404,6 +404,24 @@ __device__ __forceinline__ void cell_physics(R lnrho, const R (&u)[3], R ss, con
 }
 
 
+// The same with the thermodynamic factors computed at its top by CUDA's exp and
+// a division, in the statement order the binary64 direct-load kernels were
+// measured with (their register allocation depends on it).
+template <typename R, bool EXT = false>
+__device__ __forceinline__ void cell_physics(R lnrho, const R (&u)[3], R ss, const R (&gl)[3],
+                                             const R (&gs)[3], const R (&gu)[3][3],
+                                             const R (&B)[3], const R (&viscl)[3],
+                                             const R (&lapa)[3], const R (&J)[3],
+                                             const DevCoefs<R> &k, const R frc[3], R out[NF],
+                                             R *cfl, R lapxi) {
+    const R rho_inv = dev_exp<R>(-lnrho);
+    const R cs2 = k.cs2_ref * dev_exp<R>(k.gamma_cp * ss + k.gm1 * lnrho);
+    const R inv_T = k.cp_gm1 / cs2;
+    cell_physics<R, EXT>(lnrho, u, ss, gl, gs, gu, B, viscl, lapa, J, k, frc, out, cfl, lapxi,
+                         Thermo<R>{rho_inv, cs2, inv_T});
+}
+
+
 // `f` is a cell accessor: f[q] is the view of field q around the cell.  With
 // `cfl` non-null, the fastest signal speed of the input state at the cell,
 // |u| + sqrt(c_s^2 + |B|^2 / rho) (mu0 = 1), is written there as well.
@@ -480,8 +498,15 @@ __device__ __forceinline__ void cell_rhs(const CELL &f, const DevCoefs<R> &k, co
                 llz = op_d2<2, RAD>(f[0], lnrho, k.d2[2]);
         lapxi = k.gamma_cp * (lsx + lsy + lsz) + k.gm1 * (llx + lly + llz);
     }
-    cell_physics<R, EXT>(lnrho, u, ss, gl, gs, gu, B, viscl, lapa, J, k, frc, out, cfl, lapxi,
-                         thermo_factors<R>(lnrho, ss, k, nullptr));
+    // binary32: factors computed before the call (ptxas then gives the r = 1
+    // substep-0 kernel 96 instead of 114 registers, measured 19.5 -> 20.2
+    // Gcell-updates/s at 512^3); binary64: at the top of the physics, the order
+    // its direct-load kernels were measured with
+    if constexpr (sizeof(R) == 4)
+        cell_physics<R, EXT>(lnrho, u, ss, gl, gs, gu, B, viscl, lapa, J, k, frc, out, cfl, lapxi,
+                             thermo_factors<R>(lnrho, ss, k, nullptr));
+    else
+        cell_physics<R, EXT>(lnrho, u, ss, gl, gs, gu, B, viscl, lapa, J, k, frc, out, cfl, lapxi);
 }
 
 // Block-wide max of a non-negative value folded into a global 64-bit word that
