@@ -20,7 +20,7 @@ struct DevCoefs {
     R dc[3][MAX_RADIUS];
     R nu, eta, nu3, two_nu;  // nu3: coefficient of grad(div u), nu / 3 + zeta; 2 nu
     R inv_cp, cs2_ref, gamma_cp, gm1, cp_gm1;
-    R inv_T_ref;             // c_p (gamma - 1) / c_s0^2
+    R inv_T_ref;             // c_p (gamma - 1) / cs2_ref
     R K, zeta, hc;           // conduction, bulk viscosity, H - C (Eqs. B.2-B.3)
 };
 
@@ -296,17 +296,18 @@ __device__ __forceinline__ void exp_tab_stage(double *tab) {
 // register allocation, although it is never taken on physical states.)
 template <typename R>
 __device__ __forceinline__ void thermo_lib(R lnrho, R xi, R cs2_ref, R cp_gm1, R &rho_inv, R &cs2,
-                                        R &inv_T) {
+                                           R &inv_T) {
     rho_inv = dev_exp<R>(-lnrho);
     cs2 = cs2_ref * dev_exp<R>(xi);
     inv_T = cp_gm1 / cs2;
 }
 
-// Thermodynamic factors of one cell: c_s^2 = c_s0^2 exp(xi) with
-// xi = gamma s / c_p + (gamma-1)(ln rho - ln rho0), 1/rho = exp(-ln rho) and
-// 1/T = c_p (gamma - 1) / c_s^2 = c_p (gamma - 1) exp(-xi) / c_s0^2.  With `etab`
-// (binary64 only) the exponentials come from the table-driven exp above and 1/T
-// from exp(-xi) instead of a division.
+// Thermodynamic factors of one cell: c_s^2 = c_s0^2 exp(gamma s / c_p + (gamma-1)
+// (ln rho - ln rho0)) = cs2_ref exp(xi) with xi = gamma s / c_p + (gamma-1) ln rho
+// and cs2_ref = c_s0^2 exp(-(gamma-1) ln rho0); 1/rho = exp(-ln rho); 1/T =
+// c_p (gamma - 1) / c_s^2 = inv_T_ref exp(-xi).  With `etab` (binary64 only) the
+// exponentials come from the table-driven exp above and 1/T from exp(-xi) instead
+// of a division.
 template <typename R>
 struct Thermo {
     R rho_inv, cs2, inv_T;
