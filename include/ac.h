@@ -296,6 +296,11 @@ typedef struct {
 
 typedef struct ac_batch ac_batch; /* opaque; owned by the library */
 
+/* Create a batch of `nbox` boxes (`boxes`: host array, copied) sharing the
+ * constants and precision of `common` (its force_amp must be 0); *b receives
+ * the handle, freed by ac_batch_quit (NULL is accepted there).  `stream`
+ * (cudaStream_t, may be NULL) orders every later call of the batch.
+ * AC_ERR_ARG outside the limits above, AC_ERR_OOM if device memory runs out. */
 int ac_batch_init(ac_batch **b, int nbox, const ac_box *boxes, const ac_params *common,
                   void *stream);
 int ac_batch_quit(ac_batch *b);
@@ -312,6 +317,7 @@ int ac_batch_integrate_substep(ac_batch *b, double dt, int s);
  * (and the counter resets) are captured once per (dt, state buffer) into a
  * CUDA graph and replayed. */
 int ac_batch_integrate_step(ac_batch *b, double dt);
+/* Enable (non-zero) or disable (0, the default) the graph of ac_batch_integrate_step. */
 int ac_batch_set_graph(ac_batch *b, int enable);
 /* Autotuner: times substep 0 (which leaves the state unchanged) for work items
  * of z extent 8, 16, 32, 64 and 128 and keeps the fastest (*zc_out).  With a
@@ -346,6 +352,11 @@ int ac_get_state(const ac_handle *h, void *dev_ptrs[8], int *precision, int *lay
 #define AC_CLOSURE_NPARAMS 41544
 typedef struct ac_closure ac_closure; /* opaque; owned by the library */
 
+/* Create a closure for a coarse periodic grid of nx x ny x nz cells with zero
+ * parameters and unit scales; *c receives the handle, freed by ac_closure_quit
+ * (NULL is accepted there).  `stream` (cudaStream_t, may be NULL) orders every
+ * later call.  AC_ERR_ARG for sizes outside 1..2^20, AC_ERR_OOM if device
+ * memory runs out. */
 int ac_closure_init(ac_closure **c, int nx, int ny, int nz, void *stream);
 int ac_closure_quit(ac_closure *c);
 /* Host binary32 parameters in/out (set also clears the Adam moments). */
@@ -374,6 +385,7 @@ int ac_closure_adam_step(ac_closure *c, float lr, float beta1, float beta2, floa
  * only if every correction value is finite and at most `limit` in magnitude
  * (the guard runs on the device; *applied, if non-NULL, synchronises). */
 int ac_closure_apply(ac_closure *c, ac_handle *h, double limit, int *applied);
+/* Number of kernels the closure has launched so far. */
 int ac_closure_launch_count(const ac_closure *c, unsigned long long *count);
 /* Convolution kernels of the forward pass run by ac_closure_forward and
  * ac_closure_apply.  AC_CONV_TCGEN05 (the default): tcgen05.mma with the
