@@ -52,9 +52,13 @@ def bytes_per_cell(elem_f, elem_w, s):
 # Nominal dense FP64 rate of one GB300 (no measured FP64 peak is provided).
 FP64_NOMINAL_TFLOPS = 1.25
 # DRAM bytes per cell of one launch of the integer-sum FP64 substep kernel
-# (ncu, 128^3, substeps 1-2 variant: 430.7 MB read + 234.9 MB written over
-# 2,097,152 cells).
-FX_TRAFFIC_PER_CELL = (430.685440e6 + 234.900224e6) / 2097152
+# (ncu, 128^3, substeps 1-2 variant, group-scale mode; None until the kernel
+# as it stands has been captured).
+FX_TRAFFIC_PER_CELL = None
+# FP64-pipe thread instructions per cell of that kernel (ncu
+# sm__inst_executed_pipe_fp64 x 32 / cells, 128^3), substep-0 (CFL) and
+# substep-1/2 variants; None until captured.
+FX_FP64_PIPE_INST_PER_CELL = None
 # DRAM bytes per cell of one launch of the binary32 tiled substep (ncu, 256^3,
 # substep 1: 1126.6 MB read + 1023.2 MB written over 16,777,216 cells)
 TILED_TRAFFIC_PER_CELL = (1126.612e6 + 1023.183e6) / 16777216
@@ -117,6 +121,11 @@ def parse():
                     help="also time a cuBLAS FP64 GEMM as a measured FP64 reference rate")
     ap.add_argument("--grid", type=int, default=0,
                     help="override the cube edge (small cases for profiling)")
+    ap.add_argument("--no-workloads", action="store_true",
+                    help="default workload only: skip the other workloads of the table")
+    ap.add_argument("--fp64-compare-steps", type=int, default=0,
+                    help="binary32 workloads: steps of a binary64 run from the same state "
+                         "for the per-field error")
     return ap.parse_args()
 
 
@@ -215,7 +224,7 @@ def job_rate(units_per_rank, ws, elapsed):
 # ---------------------------------------------------------------------------
 # the oracle arm / CPU baseline: a bounded sample of the same workload
 # ---------------------------------------------------------------------------
-def oracle_sample(wl, f, planes):
+def oracle_sample(wl, f, planes, nthreads=None):
     """One RK3 step (3 substeps) of the oracle at the cells of `planes` z-planes
     of the full-size state (the substeps read the full arrays)."""
     from oracle import core
@@ -230,22 +239,99 @@ def oracle_sample(wl, f, planes):
     w = np.zeros_like(f)
     t0 = time.perf_counter()
     for s in range(3):
-        core.substep_cells(f, w, p, wl["dt"], s, cells, nthreads=os.cpu_count())
+        core.substep_cells(f, w, p, wl["dt"], s, cells, nthreads=nthreads or os.cpu_count())
     return time.perf_counter() - t0, 3 * cells.shape[0]
 
 
 def cpu_baseline(wl, f, seconds):
+    """The oracle on the host cores, all threads (OpenMP) and one thread, each on
+    a slab of z-planes of the workload's state sized for about `seconds`."""
     import oracle
     oracle.build_oracle()
-    planes = 1
-    dt, cu = oracle_sample(wl, f, planes)
-    planes = max(1, min(wl["n"][2], int(planes * seconds / max(dt, 1e-3))))
-    dt, cu = oracle_sample(wl, f, planes)
-    return {"value": cu / dt / 1e9, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
-            "sample": "one RK3 step (3 substeps) at the %d cells of %d z-planes of the %s "
-                      "state, FP64 C oracle, OpenMP over %d threads"
-                      % (cu // 3, planes, "x".join(map(str, wl["n"])), os.cpu_count()),
-            "seconds": dt}
+    out = {}
+    for nth in (os.cpu_count(), 1):
+        planes = 1
+        dt, cu = oracle_sample(wl, f, planes, nth)
+        planes = max(1, min(wl["n"][2], int(planes * seconds / max(dt, 1e-3))))
+        dt, cu = oracle_sample(wl, f, planes, nth)
+        out[nth] = {"value": cu / dt / 1e9, "unit": UNIT, "cores": nth, "kind": "oracle",
+                    "sample": "one RK3 step (3 substeps) at the %d cells of %d z-planes of the "
+                              "%s state, FP64 C oracle, OpenMP over %d thread%s"
+                              % (cu // 3, planes, "x".join(map(str, wl["n"])), nth,
+                                 "s" if nth > 1 else ""),
+                    "seconds": dt}
+    line = dict(out[os.cpu_count()])
+    line["single_thread"] = out[1]
+    return line
+
+
+def _sample_cells(n, count, seed):
+    g = np.random.default_rng(seed)
+    return np.stack([g.integers(0, n[0], count), g.integers(0, n[1], count),
+                     g.integers(0, n[2], count)], axis=1).astype(np.int64)
+
+
+def _rel_per_field(g, o):
+    return [float(np.max(np.abs(g[q] - o[q])) / np.max(np.abs(o[q])))
+            if np.max(np.abs(o[q])) > 0 else float(np.max(np.abs(g[q] - o[q])))
+            for q in range(g.shape[0])]
+
+
+def sampled_parity(sim, wl, order, count=2000):
+    """One more RK3 step of the GPU state after the timed region, each substep
+    checked against the FP64 oracle at `count` sampled cells (computed from the
+    GPU's own input state of that substep): per-field max-norm relative error of
+    f and w, and the paper's ulp metric on f."""
+    from oracle import core
+    from paper_2103_01597_gb300 import ac
+    n = wl["n"]
+    cells = _sample_cells(n, count, 11)
+    idx = (cells[:, 2], cells[:, 1], cells[:, 0])
+    step, _ = ac.ac_get_step(sim.h)
+    forcing = core.forcing_draw(wl["seed"], step, wl["force_amp"]) if wl["force_amp"] else None
+    p = core.Params(n=n, forcing=forcing, order=order, **wl.get("entropy", {}))
+    f, w = sim.store(), sim.store_w()
+    ef, ew, ulp = np.zeros(8), np.zeros(8), 0.0
+    for s in range(3):
+        fo, wo = core.substep_cells(f, w if s else None, p, wl["dt"], s, cells,
+                                    nthreads=os.cpu_count())
+        sim.substep(wl["dt"], s)
+        f, w = sim.store(), sim.store_w()
+        gs = np.stack([f[q][idx] for q in range(8)])
+        gw = np.stack([w[q][idx] for q in range(8)])
+        ef = np.maximum(ef, _rel_per_field(gs, fo))
+        ew = np.maximum(ew, _rel_per_field(gw, wo))
+        nz = fo != 0
+        e = np.ldexp(1.0, (np.floor(np.log2(np.abs(fo[nz]))) - 52).astype(int))
+        ulp = max(ulp, float(np.max(np.abs(gs[nz] - fo[nz]) / e)))
+    return {"cells": count, "substeps": 3, "rel_err_f": ef.tolist(), "rel_err_w": ew.tolist(),
+            "max_ulp_f": ulp, "bound": 1e-12,
+            "how": "substeps 0-2 of the step after the timed region, oracle from the GPU's "
+                   "own input state of each substep"}
+
+
+def fp32_against_fp64(sim, wl, f0, steps, stream):
+    """Per-field error of the binary32 state against a binary64 run of the same
+    workload from the same initial state after `steps` steps (forcing draws
+    identical: both handles restart at step 0)."""
+    from paper_2103_01597_gb300 import ac
+    ref = ac.Simulation(wl["n"], precision=ac.AC_FP64, force_amp=wl["force_amp"],
+                        seed=wl["seed"], stream=stream.cuda_stream)
+    ref.load(f0)
+    sim.load(f0)
+    ac.ac_set_step(sim.h, 0, 0)
+    for _ in range(steps):
+        ref.step(wl["dt"])
+        sim.step(wl["dt"])
+    r = ref.store()
+    modes = ac.ac_get_stencil_modes(ref.h)
+    ref.close()
+    g = sim.store()
+    return {"steps": steps, "rel_err_per_field": _rel_per_field(g, r),
+            "fields": ["lnrho", "ux", "uy", "uz", "ss", "ax", "ay", "az"],
+            "fp64_stencil_modes": list(modes),
+            "how": "max|f32 - f64| / max|f64| per field after the same steps from the same "
+                   "state (binary64 run: the default integer-sum path)"}
 
 
 def run_reference(args, wl):
@@ -380,6 +466,7 @@ def run_ours(args, wl):
     evs = [[[torch.cuda.Event(enable_timing=True) for _ in range(2)] for _ in range(3)]
            for _ in range(args.steps)]
     launches0 = ac.ac_launch_count(sim.h)
+    modes0 = ac.ac_get_stencil_modes(sim.h)
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
@@ -404,29 +491,52 @@ def run_ours(args, wl):
     # dominant kernel: the fused substep; its average launch duration per substep index
     avg = {s: statistics.mean(per_sub[s]) for s in range(3)}
     avg_all = statistics.mean(avg.values())
+    modes = [m1 - m0 for m0, m1 in zip(modes0, ac.ac_get_stencil_modes(sim.h))]
     if wl["precision"] == "fp64":
         flops = {s: flops_per_cell(order, s) * ncell for s in range(3)}
-        achieved = statistics.mean(flops[s] / avg[s] for s in range(3)) / 1e12
+        equiv = statistics.mean(flops[s] / avg[s] for s in range(3)) / 1e12
         dg = fp64_dgemm_tflops(torch) if (rank == 0 and args.fp64_peak) else None
         fixed = ac.ac_get_stencil_path(sim.h)
-        roof = {"bound": "alu", "achieved": achieved, "peak": FP64_NOMINAL_TFLOPS,
-                "unit": "TFLOP/s", "frac": achieved / FP64_NOMINAL_TFLOPS,
-                # dram read + write per 256^3 launch of the unchanged kernel, from the 128^3
-                # ncu capture scaled by cells (profiles/substep_fx_128_metrics.md)
-                "traffic": FX_TRAFFIC_PER_CELL * ncell if (fixed and n == (256, 256, 256)) else None,
-                "kernel": ("substep_fx_kernel (int64 stencil sums) + fx_max + fx_quantize"
-                           if fixed else "substep_kernel<double,double,IdxPeriodicR<%d>>"
-                           % (order // 2)),
-                "peak_source": "nominal GB300 dense FP64, 2 FP64 lanes/SM/cycle x 152 SMs x "
-                               "2.07 GHz (no measured FP64 peak in MEASURED_PEAKS.json)",
-                "note": ("achieved counts the method's %d binary64 flops per cell-substep; "
-                         % flops_per_cell(order, 1) +
-                         "540 of them (the stencil sums) run as exact int64 operations on the "
-                         "integer pipes, so frac can exceed 1; ncu: FP64 pipe 75-80% busy"
-                         if fixed else "all arithmetic on the FP64 pipe"),
+        # measured denominator: the library's DFMA-chain probe (2 flops per FMA)
+        dfma = ac.ac_diag_fma_rate(ac.AC_FP64, stream.cuda_stream)
+        peak = 2 * dfma / 1e12
+        group = fixed and modes[0] == sum(modes)
+        inst = FX_FP64_PIPE_INST_PER_CELL if (group and order == 6) else None
+        achieved = None
+        if inst is not None:
+            # FP64-pipe thread instructions of each launch, as DFMA-equivalent flops
+            achieved = statistics.mean(2 * inst[min(s, 1)] * ncell / avg[s]
+                                       for s in range(3)) / 1e12
+        roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak if achieved is not None else None,
+                "what": "FP64 pipe: FP64-pipe thread instructions per launch (ncu count per "
+                        "cell x cells) x 2 flops / CUDA-event launch time, against the "
+                        "measured DFMA rate",
+                "fp64_pipe_inst_per_cell": inst,
+                "peak_source": "measured: ac_diag_fma_rate(AC_FP64), the library's own DFMA "
+                               "chains, x 2 flops (nominal: %.2f TFLOP/s)" % FP64_NOMINAL_TFLOPS,
+                # dram read + write per 256^3 launch, from the 128^3 ncu capture of the
+                # same kernel scaled by cells (profiles/substep_fx_128_metrics.md)
+                "traffic": (FX_TRAFFIC_PER_CELL * ncell
+                            if (group and FX_TRAFFIC_PER_CELL and n == (256, 256, 256))
+                            else None),
+                "kernel": ("fx_stats + fx_plan + fx_quantize + substep_fx_kernel (int64 "
+                           "stencil sums)" if fixed else
+                           "substep_kernel<double,double,IdxPeriodicR<%d>>" % (order // 2)),
+                "method_flops_equiv": {
+                    "achieved": equiv, "frac_of_peak": equiv / peak,
+                    "alg_flops_per_cell_substep": {s: flops_per_cell(order, s)
+                                                   for s in range(3)},
+                    "note": ("the method's binary64 flops per cell-substep over the launch "
+                             "time; on the integer-sum path the 540 stencil flops run as "
+                             "exact int64 operations on the integer pipes, so this rate can "
+                             "exceed the FP64 peak" if fixed else
+                             "all arithmetic on the FP64 pipe")},
                 "fp64_dgemm_measured_tflops": dg,
-                "avg_launch_ms": 1e3 * avg_all,
-                "alg_flops_per_cell_substep": {s: flops_per_cell(order, s) for s in range(3)}}
+                "fma_peaks_tflops": {"fp64": peak,
+                                     "fp32": 2 * ac.ac_diag_fma_rate(ac.AC_FP32,
+                                                                     stream.cuda_stream) / 1e12},
+                "avg_launch_ms": 1e3 * avg_all}
     else:
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
         bytes_s = {s: bytes_per_cell(elem_f, elem_w, s) * ncell for s in range(3)}
@@ -492,6 +602,13 @@ def run_ours(args, wl):
                                             "in sequence"},
                "host_link": link}
 
+    parity = None
+    fp32_err = None
+    if rank == 0 and ws == 1:
+        if wl["precision"] == "fp64":
+            parity = sampled_parity(sim, wl, order)
+        elif args.fp64_compare_steps > 0:
+            fp32_err = fp32_against_fp64(sim, wl, f0, args.fp64_compare_steps, stream)
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(wl, f0, args.cpu_seconds)
@@ -513,12 +630,14 @@ def run_ours(args, wl):
                                    "max CFL speed) + 8-byte read of that max"},
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": launches, "clocks": clocks,
+                "stencil_modes": ({"group_scales": modes[0], "field_scales": modes[1],
+                                   "plain_binary64": modes[2]} if sum(modes) else None),
+                "parity_sampled": parity, "fp32_vs_fp64": fp32_err,
                 "last_cfl_speed": cfl,
                 "substep_ms": {str(s): 1e3 * avg[s] for s in range(3)}}
-        print(json.dumps(line))
     if dist:
         dist.destroy_process_group()
-    return 0
+    return line if rank == 0 else None
 
 
 def run_ensemble(args, wl):
@@ -687,10 +806,9 @@ def run_ensemble(args, wl):
                            "step": "3 persistent substep launches (graph replay)"},
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
                 "clocks": clocks, "compare": compare, "fp32_vs_fp64": err}
-        print(json.dumps(line))
     if dist:
         dist.destroy_process_group()
-    return 0
+    return line if rank == 0 else None
 
 
 def _spectra(f, n):
@@ -875,8 +993,7 @@ def run_closure(args, wl):
                                "(3 conv layers) + guarded correction"},
             "roofline": roof, "cpu_baseline": None, "e2e": e2e, "gpu_launches": launches,
             "clocks": clocks, "closure": quality}
-    print(json.dumps(line))
-    return 0
+    return line
 
 
 # ---------------------------------------------------------------------------
@@ -1057,10 +1174,9 @@ def run_closure_forward(args, wl):
                            "step": "one ac_closure_forward (pack + 3 conv + scale)"},
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
                 "clocks": clocks}
-        print(json.dumps(line))
     if dist:
         dist.destroy_process_group()
-    return 0
+    return line if rank == 0 else None
 
 
 def run_closure_forward_reference(args, wl):
@@ -1118,6 +1234,18 @@ def main():
         if wl.get("closure_forward"):
             return run_closure_forward_reference(args, wl)
         return run_reference(args, wl)
+    line = run_workload(args, wl)
+    if line is None:
+        return 0
+    ws, _, _ = dist_setup(args)
+    if args.workload == "forced256_fp64" and ws == 1 and not args.no_workloads and \
+            not args.grid and args.stencil_order == 6 and not args.full_entropy:
+        line["workloads"] = run_other_workloads(args)
+    print(json.dumps(line))
+    return 0
+
+
+def run_workload(args, wl):
     if wl.get("closure_forward"):
         return run_closure_forward(args, wl)
     if wl.get("ensemble"):
@@ -1125,6 +1253,40 @@ def main():
     if wl.get("closure"):
         return run_closure(args, wl)
     return run_ours(args, wl)
+
+
+# The other workloads of the measurement table, run after the headline in the
+# same process with fewer steps; each keeps its own roofline, clocks and error
+# against binary64.
+OTHER_WORKLOADS = {
+    "paper256_fp64": dict(steps=10, warmup=3),
+    "forced512_fp32": dict(steps=10, warmup=3, fp64_compare_steps=50),
+    "ensemble64_fp32": dict(steps=10, warmup=3),
+    "closure_forward256": dict(steps=10, warmup=3),
+}
+SUMMARY_KEYS = ("metric", "value", "unit", "ms_per_step", "steps", "warmup", "dtype",
+                "roofline", "clocks", "gpu_launches", "substep_ms", "fp32_vs_fp64",
+                "parity_sampled", "compare", "stencil_modes", "config", "closure")
+
+
+def run_other_workloads(args):
+    import torch
+    out = {}
+    for name, over in OTHER_WORKLOADS.items():
+        sub = argparse.Namespace(**vars(args))
+        sub.workload = name
+        sub.e2e_steps = 0
+        sub.no_cpu_baseline = True
+        sub.fp64_compare_steps = 0
+        for k, v in over.items():
+            setattr(sub, k, v)
+        t0 = time.perf_counter()
+        line = run_workload(sub, dict(WORKLOADS[name]))
+        torch.cuda.synchronize()
+        torch.cuda.empty_cache()
+        out[name] = {k: line[k] for k in SUMMARY_KEYS if k in line and line[k] is not None}
+        out[name]["wall_s"] = round(time.perf_counter() - t0, 1)
+    return out
 
 
 if __name__ == "__main__":

@@ -201,14 +201,24 @@ int ac_get_stencil_order(const ac_handle *h, int *order);
 /*
  * Arithmetic of the stencil sums for AC_FP64.  AC_STENCIL_AUTO (default): exact
  * integer sums whenever they apply (binary64 fields, periodic layout, equal
- * spacing dx = dy = dz, stencil order 6), plain binary64 sums otherwise.  With integer sums each
- * field group (ln rho; u; s; A) is first written as int64 fixed point with one
- * power-of-two scale per group (|F| <= 2^50, resolution 2^-51 of the group's
- * largest |f|, i.e. four binary64 units in the last place at that magnitude);
- * every stencil numerator and every sum of numerators with a common
- * coefficient is then exact and only one int64 -> binary64 conversion
- * and one multiplication per derivative term run on the FP64 pipe.  The result
- * stays within the same 1e-12 relative bound of the exact-rounding definition.
+ * spacing dx = dy = dz, stencil order 6), plain binary64 sums otherwise.  With
+ * integer sums every field is first written, on the device before each
+ * substep, as int64 fixed point about its own offset: F = round((f - c)
+ * 2^(50 - E)), c the midpoint of the field's range and 2^E above its
+ * half-range, so |F| <= 2^50 + 2 and each input is resolved to 2^-51 of the
+ * field's own range (the weights of every Eq. 13 stencil sum to zero, so the
+ * offset changes no derivative).  Every stencil numerator and every sum of
+ * numerators with a common coefficient is then exact and only one int64 ->
+ * binary64 conversion and one multiplication per derivative term run on the
+ * FP64 pipe.  The device picks, per substep, one of three modes (counted by
+ * ac_get_stencil_modes): AC_STENCIL_MODE_GROUP when the components of u and of
+ * A each share one E (their cross-component sums stay single integers);
+ * AC_STENCIL_MODE_FIELD otherwise (each field keeps its own scale; the sums
+ * across components are added in binary64); AC_STENCIL_MODE_PLAIN when the
+ * state holds a NaN or an infinity or a range outside [2^-960, 2^960) (plain
+ * binary64 stencils, the AC_STENCIL_FP64 arithmetic, so non-finite values
+ * propagate as the definition does and show in ac_last_cfl).  The result stays
+ * within the 1e-12 relative bound of the exact-rounding definition.
  * AC_STENCIL_FP64: binary64 arithmetic throughout.  AC_STENCIL_FIXED: integer
  * sums, AC_ERR_ARG where they do not apply.  Extra device memory for integer
  * sums: one int64 copy of the eight fields, allocated on first use.
@@ -219,6 +229,15 @@ int ac_get_stencil_order(const ac_handle *h, int *order);
 int ac_set_stencil_mode(ac_handle *h, int mode);
 /* *fixed = 1 if the next substeps use integer stencil sums. */
 int ac_get_stencil_path(const ac_handle *h, int *fixed);
+/*
+ * counts[m] = substeps the integer-sum path has run in mode m since the
+ * handle's first integer-sum substep (all 0 before it).  Synchronises the
+ * handle's stream.
+ */
+#define AC_STENCIL_MODE_GROUP 0
+#define AC_STENCIL_MODE_FIELD 1
+#define AC_STENCIL_MODE_PLAIN 2
+int ac_get_stencil_modes(ac_handle *h, unsigned long long counts[3]);
 
 /* Substeps 0, 1, 2 with the same dt (one full Runge-Kutta step). */
 int ac_integrate_step(ac_handle *h, double dt);
@@ -439,6 +458,68 @@ int ac_bounds_check_take(unsigned long long *first);
  * ac_bounds_check_take) and 3.  AC_ERR_STATE in the normal build. */
 int ac_bounds_check_selftest(long long out[2]);
 
+/*
+ * Domain decomposition with halo exchange (Sec. 3.2-3.3, Fig. "concurrency"):
+ * the periodic grid (AC_LAYOUT_PERIODIC; n_a divisible by p_a, n_a / p_a >= 6)
+ * is split into p[0] x p[1] x p[2] subdomains of n' = n / p cells, each held
+ * with a radius-3 halo.  Subdomains are ordered in Z-order (their coordinates
+ * sorted by Morton code, bits of x, y, z interleaved with x lowest:
+ * ac_decomp_coord), the order in which they would be assigned to devices.
+ * Every substep (ac_decomp_integrate_substep) runs the iteration of Sec. 3.3:
+ * pack the outbound halo segments (6 sides and 12 edges per subdomain; the 8
+ * corners are never read by the Eq. 13 stencil and are not sent) into
+ * contiguous message buffers, deliver the messages, unpack them into the
+ * receivers' halos, and update the outer segments; the inner segment
+ * (interior cells at least 3 from the subdomain's faces, whose stencils read
+ * no halo cell) is updated on the caller's `stream` while the exchange runs on
+ * a second, higher-priority stream.  ac_decomp_set_overlap(d, 0) runs pack,
+ * exchange, unpack and one whole-subdomain update in sequence instead.  All
+ * subdomains live on the current device, so a message is a device-local copy.
+ * Arithmetic: plain binary64 (AC_FP64) or binary32 stencils of order 6, the
+ * same per-cell code as the undecomposed padded-layout substep, so the result
+ * equals ac_integrate_substep on an AC_LAYOUT_PADDED handle (or, in binary64,
+ * an AC_STENCIL_FP64 periodic one) bitwise.  Forcing is drawn per step from
+ * (seed, step) as ac_integrate_substep draws it.  ac_decomp_load/_store take
+ * the whole unpadded host array (x fastest) and are synchronous; substeps are
+ * stream-ordered and checked in order (AC_ERR_STATE).
+ */
+typedef struct ac_decomp ac_decomp;
+int ac_decomp_init(ac_decomp **d, const ac_grid *grid, const ac_params *params, const int p[3],
+                   void *stream);
+int ac_decomp_quit(ac_decomp *d);
+int ac_decomp_load(ac_decomp *d, int field, const double *host_src);
+int ac_decomp_store(ac_decomp *d, int field, double *host_dst);
+int ac_decomp_load_w(ac_decomp *d, int field, const double *host_src);
+int ac_decomp_store_w(ac_decomp *d, int field, double *host_dst);
+int ac_decomp_integrate_substep(ac_decomp *d, double dt, int s);
+int ac_decomp_integrate_step(ac_decomp *d, double dt);
+int ac_decomp_set_overlap(ac_decomp *d, int on);
+/* Partition, local size, message count (18 per subdomain) and kernel launches. */
+int ac_decomp_info(const ac_decomp *d, int p[3], int nloc[3], int *messages,
+                   unsigned long long *launches);
+/* Host-only schedule (no device call).  ac_decomp_partition: the paper's
+ * partition of a power-of-two device count, P = morton^-1(count - 1) +
+ * (1, 1, 1).  ac_decomp_coord: coordinates of the subdomain with Z-order
+ * position `rank` in a p grid.  ac_decomp_segment: halo segment `seg` (0..17:
+ * sides x-, x+, y-, y+, z-, z+, then the edges in lexicographic order of the
+ * direction) of a subdomain of nloc cells: its direction d, the origin of the
+ * receiver's halo box (dst_b0) and of the cells of the neighbour at +d that
+ * fill it (src_b0), both in padded coordinates (interior from 3 to 3 + n' - 1),
+ * and the box's extent; src = ((dst - 3) mod n') + 3 per axis (Sec. 3.3). */
+int ac_decomp_partition(int count, int p[3]);
+int ac_decomp_coord(const int p[3], int rank, int coord[3]);
+int ac_decomp_segment(const int nloc[3], int seg, int dir[3], int src_b0[3], int dst_b0[3],
+                      int ext[3]);
+
+/* Arithmetic-rate probe (no counterpart in the paper; the denominator of the
+ * binary64 substep's roofline): *fma_per_s = thread-level fused multiply-adds
+ * per second of the library's own FMA-chain kernel (8 independent chains per
+ * thread, 8 CTAs of 256 threads per SM, each timed launch about 50 ms, best of
+ * several) in binary64 (AC_FP64: the FP64 pipe) or binary32 (AC_FP32: the
+ * FP32 pipes) on the current device.  Synchronises `stream`.  AC_ERR_ARG for
+ * another precision. */
+int ac_diag_fma_rate(int precision, double *fma_per_s, void *stream);
+
 /* Full-weighting restriction of eight fine fields (nx, ny, nz even; binary64
  * for AC_FP64, binary32 otherwise; periodic layout) to eight binary32 coarse
  * arrays: coarse(I) = sum over d in {-1,0,1}^3 of prod_a w(d_a) fine(2I + d),
@@ -454,21 +535,26 @@ int ac_restrict(const void *const fine[8], int fine_precision, int nx, int ny, i
  * allocated with cudaMalloc).
  *
  * Same result as ac_reduce (op, quantity, binary64 accumulation, per-cell
- * quantities evaluated the same way) for the state held in `fields`: eight
- * device arrays in the order of Table B.1, each laid out for `grid` (padded
- * layout: the halo must already hold the periodic images) with elements of
- * `params->precision` (double for AC_FP64, float otherwise).  The partial sums
- * go to a fixed device array inside the library (one slot per z-plane, at most
- * AC_NOALLOC_MAX_NZ planes: larger nz is rejected with AC_ERR_ARG); nothing is
- * allocated.  The result is written to host memory *out and `stream`
- * (cudaStream_t, NULL: legacy default stream) is synchronised; AC_ERR_NONFINITE
- * if a NaN or infinity was met.  Only the summation order differs from
- * ac_reduce, so sums and rms agree to rounding and max/min exactly.
+ * quantities evaluated the same way at stencil order 6) for the state held in
+ * `fields`: eight device arrays in the field order of the AC_LNRHO..AC_AZ
+ * constants above, each laid out for `grid` (padded layout: the halo must
+ * already hold the periodic images) with elements of `params->precision`
+ * (double for AC_FP64, float otherwise).  The curl of A in AC_Q_EMAG and
+ * AC_Q_CFL always uses the sixth-order first derivative, so those two match
+ * ac_reduce only on handles at stencil order 6.  `grid` and `params` are
+ * checked as ac_init checks them.  The partial sums go to a fixed device array
+ * inside the library (one slot per z-plane, at most AC_NOALLOC_MAX_NZ planes:
+ * larger nz is rejected with AC_ERR_ARG); nothing is allocated.  The result is
+ * written to host memory *out and `stream` (cudaStream_t, NULL: legacy default
+ * stream) is synchronised; AC_ERR_NONFINITE if a NaN or infinity was met.
+ * Only the summation order differs from ac_reduce, so sums and rms agree to
+ * rounding and max/min exactly.
  *
- * The first call on a device looks up that device's copy of the fixed array
- * (with the device current); make that first call before any stream capture.
- * Every call shares the array: calls whose work overlaps on the GPU (other
- * streams or host threads) race on it and must be serialised by the caller.
+ * The fixed array has one copy per device; each call uses the copy of the
+ * device current on the calling thread (looked up on every call), so `stream`
+ * and the field arrays must belong to that device.  Every call shares the
+ * array: calls whose work overlaps on the GPU (other streams or host threads)
+ * race on it and must be serialised by the caller.
  */
 #define AC_NOALLOC_MAX_NZ 8192
 int ac_reduce_noalloc(const void *const fields[8], const ac_grid *grid, const ac_params *params,

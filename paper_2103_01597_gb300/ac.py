@@ -31,6 +31,7 @@ AC_FP64, AC_FP32, AC_FP32_W64 = 0, 1, 2
 AC_LAYOUT_PERIODIC, AC_LAYOUT_PADDED = 0, 1
 AC_MAX, AC_MIN, AC_SUM, AC_RMS = 0, 1, 2, 3
 AC_STENCIL_AUTO, AC_STENCIL_FP64, AC_STENCIL_FIXED = 0, 1, 2
+AC_STENCIL_MODE_GROUP, AC_STENCIL_MODE_FIELD, AC_STENCIL_MODE_PLAIN = 0, 1, 2
 AC_CONV_TCGEN05, AC_CONV_MMA_SYNC, AC_CONV_TCGEN05_PAIR = 0, 1, 2
 AC_Q_UMAG, AC_Q_EKIN, AC_Q_EMAG, AC_Q_CFL = 8, 9, 10, 11
 
@@ -100,6 +101,26 @@ def load_library(path=None):
         "ac_last_cfl": ([_vp, _pd], _c.c_int),
         "ac_set_stencil_mode": ([_vp, _c.c_int], _c.c_int),
         "ac_get_stencil_path": ([_vp, ctypes.POINTER(_c.c_int)], _c.c_int),
+        "ac_get_stencil_modes": ([_vp, ctypes.POINTER(_c.c_ulonglong)], _c.c_int),
+        "ac_diag_fma_rate": ([_c.c_int, _pd, _vp], _c.c_int),
+        "ac_decomp_init": ([ctypes.POINTER(_vp), ctypes.POINTER(ac_grid),
+                            ctypes.POINTER(ac_params), ctypes.POINTER(_c.c_int), _vp], _c.c_int),
+        "ac_decomp_quit": ([_vp], _c.c_int),
+        "ac_decomp_load": ([_vp, _c.c_int, _vp], _c.c_int),
+        "ac_decomp_store": ([_vp, _c.c_int, _vp], _c.c_int),
+        "ac_decomp_load_w": ([_vp, _c.c_int, _vp], _c.c_int),
+        "ac_decomp_store_w": ([_vp, _c.c_int, _vp], _c.c_int),
+        "ac_decomp_integrate_substep": ([_vp, _c.c_double, _c.c_int], _c.c_int),
+        "ac_decomp_integrate_step": ([_vp, _c.c_double], _c.c_int),
+        "ac_decomp_set_overlap": ([_vp, _c.c_int], _c.c_int),
+        "ac_decomp_info": ([_vp, ctypes.POINTER(_c.c_int), ctypes.POINTER(_c.c_int),
+                            ctypes.POINTER(_c.c_int), ctypes.POINTER(_c.c_ulonglong)], _c.c_int),
+        "ac_decomp_partition": ([_c.c_int, ctypes.POINTER(_c.c_int)], _c.c_int),
+        "ac_decomp_coord": ([ctypes.POINTER(_c.c_int), _c.c_int, ctypes.POINTER(_c.c_int)],
+                            _c.c_int),
+        "ac_decomp_segment": ([ctypes.POINTER(_c.c_int), _c.c_int, ctypes.POINTER(_c.c_int),
+                               ctypes.POINTER(_c.c_int), ctypes.POINTER(_c.c_int),
+                               ctypes.POINTER(_c.c_int)], _c.c_int),
         "ac_reduce": ([_vp, _c.c_int, _c.c_int, _pd], _c.c_int),
         "ac_forcing_draw": ([_c.c_ulonglong, _c.c_ulonglong, ctypes.POINTER(_c.c_int), _pd, _pd],
                             _c.c_int),
@@ -257,6 +278,22 @@ def ac_get_stencil_path(h):
     fixed = ctypes.c_int()
     _check(load_library().ac_get_stencil_path(h, ctypes.byref(fixed)), "ac_get_stencil_path")
     return bool(fixed.value)
+
+
+def ac_get_stencil_modes(h):
+    """Substeps the integer-sum path ran with group scales, per-field scales and
+    plain binary64 stencils (AC_STENCIL_MODE_GROUP/FIELD/PLAIN), as a 3-tuple."""
+    out = (ctypes.c_ulonglong * 3)()
+    _check(_lib.ac_get_stencil_modes(h, out), "ac_get_stencil_modes")
+    return tuple(int(v) for v in out)
+
+
+def ac_diag_fma_rate(precision, stream=None):
+    """Fused multiply-adds per second of the library's FMA-chain probe kernel
+    (AC_FP64: FP64 pipe, AC_FP32: FP32 pipes) on the current device."""
+    out = ctypes.c_double()
+    _check(_lib.ac_diag_fma_rate(precision, ctypes.byref(out), stream), "ac_diag_fma_rate")
+    return out.value
 
 
 def ac_last_cfl(h):
@@ -558,6 +595,109 @@ def ac_batch_info(b):
                                         ctypes.byref(launches)), "ac_batch_info")
     return dict(cells=cells.value, items=items.value, zc=zc.value, ctas=ctas.value,
                 launches=launches.value)
+
+
+def _int3(v):
+    return (ctypes.c_int * 3)(*[int(x) for x in v])
+
+
+def ac_decomp_partition(count):
+    p = (ctypes.c_int * 3)()
+    _check(load_library().ac_decomp_partition(int(count), p), "ac_decomp_partition")
+    return tuple(p)
+
+
+def ac_decomp_coord(p, rank):
+    c = (ctypes.c_int * 3)()
+    _check(load_library().ac_decomp_coord(_int3(p), int(rank), c), "ac_decomp_coord")
+    return tuple(c)
+
+
+def ac_decomp_segment(nloc, seg):
+    """(dir, src_b0, dst_b0, ext) of halo segment `seg` (0..17), padded coordinates."""
+    out = [(ctypes.c_int * 3)() for _ in range(4)]
+    _check(load_library().ac_decomp_segment(_int3(nloc), int(seg), *out), "ac_decomp_segment")
+    return tuple(tuple(v) for v in out)
+
+
+def ac_decomp_init(grid, params, p, stream=None):
+    d = _vp()
+    _check(load_library().ac_decomp_init(ctypes.byref(d), ctypes.byref(grid),
+                                         ctypes.byref(params), _int3(p), stream),
+           "ac_decomp_init")
+    return d
+
+
+def ac_decomp_info(d):
+    p, nl = (ctypes.c_int * 3)(), (ctypes.c_int * 3)()
+    m, la = ctypes.c_int(), ctypes.c_ulonglong()
+    _check(load_library().ac_decomp_info(d, p, nl, ctypes.byref(m), ctypes.byref(la)),
+           "ac_decomp_info")
+    return dict(p=tuple(p), nloc=tuple(nl), messages=m.value, launches=la.value)
+
+
+class Decomp:
+    """A periodic grid split into p = (px, py, pz) subdomains with halo exchange
+    (all subdomains on the current device)."""
+
+    def __init__(self, n, p, L=(2 * math.pi,) * 3, precision=AC_FP64, nu=5e-3, eta=5e-3,
+                 cs0=1.0, gamma=5.0 / 3.0, cp=1.0, lnrho0=0.0, force_amp=0.0, seed=0,
+                 stream=None, overlap=True):
+        if stream is None:
+            import torch
+            stream = torch.cuda.current_stream().cuda_stream
+        self.n = tuple(n)
+        self.d = ac_decomp_init(make_grid(n, L),
+                                make_params(nu, eta, cs0, gamma, cp, lnrho0, force_amp, seed,
+                                            precision), p, stream)
+        _check(_lib.ac_decomp_set_overlap(self.d, 1 if overlap else 0), "ac_decomp_set_overlap")
+        self._closed = False
+
+    def set_overlap(self, on):
+        _check(_lib.ac_decomp_set_overlap(self.d, 1 if on else 0), "ac_decomp_set_overlap")
+
+    def _io(self, fn, arr, where):
+        _check(fn(self.d, AC_ALL, arr.ctypes.data_as(_vp)), where)
+
+    def load(self, f):
+        self._io(_lib.ac_decomp_load, np.ascontiguousarray(f, dtype=np.float64), "ac_decomp_load")
+
+    def load_w(self, w):
+        self._io(_lib.ac_decomp_load_w, np.ascontiguousarray(w, dtype=np.float64),
+                 "ac_decomp_load_w")
+
+    def store(self):
+        nx, ny, nz = self.n
+        out = np.empty((8, nz, ny, nx))
+        self._io(_lib.ac_decomp_store, out, "ac_decomp_store")
+        return out
+
+    def store_w(self):
+        nx, ny, nz = self.n
+        out = np.empty((8, nz, ny, nx))
+        self._io(_lib.ac_decomp_store_w, out, "ac_decomp_store_w")
+        return out
+
+    def substep(self, dt, s):
+        _check(_lib.ac_decomp_integrate_substep(self.d, float(dt), int(s)),
+               "ac_decomp_integrate_substep")
+
+    def step(self, dt):
+        _check(_lib.ac_decomp_integrate_step(self.d, float(dt)), "ac_decomp_integrate_step")
+
+    def info(self):
+        return ac_decomp_info(self.d)
+
+    def close(self):
+        if not self._closed:
+            _lib.ac_decomp_quit(self.d)
+            self._closed = True
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class Batch:

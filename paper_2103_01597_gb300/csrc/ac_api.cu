@@ -61,7 +61,8 @@ struct ac_handle {
     unsigned long long *cfl_dev;  // max CFL speed of the last substep-0 input (bits of a double)
     int stencil_mode;             // AC_STENCIL_*
     long long *fx_block;          // int64 copies of the fields (integer stencil sums)
-    unsigned long long *fx_gmax;  // group maxima of |f| (bits of doubles)
+    unsigned long long *fx_stats; // per-field extremes (16 words) of the substep's input
+    void *fx_plan;                // device plan of the integer-sum path (mode, scales)
     double *stage;       // float64 staging for load/store
     size_t stage_elems;
     int next_s;
@@ -91,7 +92,7 @@ extern "C" const char *ac_strerror(int code) {
 
 extern "C" const char *ac_last_cuda_error(void) { return g_cuda_msg; }
 
-static int valid_grid(const ac_grid *g) {
+int ac::valid_grid(const ac_grid *g) {
     if (!g) return 0;
     if (g->nx < 1 || g->ny < 1 || g->nz < 1) return 0;
     if (!(g->lx > 0) || !(g->ly > 0) || !(g->lz > 0)) return 0;
@@ -102,7 +103,7 @@ static int valid_grid(const ac_grid *g) {
     return 1;
 }
 
-static int valid_params(const ac_params *p) {
+int ac::valid_params(const ac_params *p) {
     if (!p) return 0;
     const double v[7] = {p->nu, p->eta, p->cs0, p->gamma, p->cp, p->lnrho0, p->force_amp};
     for (int i = 0; i < 7; ++i)
@@ -123,7 +124,8 @@ static void free_handle_memory(ac_handle *h) {
     if (h->stage) cudaFree(h->stage);
     if (h->cfl_dev) cudaFree(h->cfl_dev);
     if (h->fx_block) cudaFree(h->fx_block);
-    if (h->fx_gmax) cudaFree(h->fx_gmax);
+    if (h->fx_stats) cudaFree(h->fx_stats);
+    if (h->fx_plan) cudaFree(h->fx_plan);
 }
 
 extern "C" int ac_init(ac_handle **out, const ac_grid *grid, const ac_params *params,
@@ -494,6 +496,37 @@ extern "C" int ac_get_stencil_path(const ac_handle *h, int *fixed) {
     return AC_OK;
 }
 
+// Work areas of the integer-sum path, on first use: the int64 copies of the
+// fields, the extremes words and the plan (zeroed, so its mode counts start at 0).
+static int ensure_fx(ac_handle *h) {
+    if (h->fx_block) return AC_OK;
+    long long *blk = nullptr;
+    unsigned long long *stats = nullptr;
+    void *plan = nullptr;
+    cudaError_t e = cudaMalloc(&blk, (size_t)NF * h->g.elems * sizeof(long long));
+    if (e == cudaSuccess) e = cudaMalloc(&stats, 2 * NF * sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaMalloc(&plan, fx_plan_bytes());
+    if (e == cudaSuccess) e = cudaMemsetAsync(plan, 0, fx_plan_bytes(), h->stream);
+    if (e != cudaSuccess) {
+        if (blk) cudaFree(blk);
+        if (stats) cudaFree(stats);
+        if (plan) cudaFree(plan);
+        return cuda_fail(e);
+    }
+    h->fx_block = blk;
+    h->fx_stats = stats;
+    h->fx_plan = plan;
+    return AC_OK;
+}
+
+extern "C" int ac_get_stencil_modes(ac_handle *h, unsigned long long counts[3]) {
+    if (!h || !counts) return AC_ERR_ARG;
+    counts[0] = counts[1] = counts[2] = 0;
+    if (!h->fx_plan) return AC_OK;
+    CK(fx_plan_taken(h->fx_plan, counts, h->stream));
+    return AC_OK;
+}
+
 extern "C" int ac_get_step(const ac_handle *h, unsigned long long *step, int *next_substep) {
     if (!h) return AC_ERR_ARG;
     if (step) *step = h->step;
@@ -538,6 +571,7 @@ namespace ac {
 unsigned long long bc_take_aux();
 unsigned long long bc_take_batch();
 unsigned long long bc_take_closure();
+unsigned long long bc_take_decomp();
 unsigned long long bc_take_noalloc();
 unsigned long long bc_take_f32();
 unsigned long long bc_take_f32g();
@@ -549,9 +583,9 @@ extern "C" int ac_bounds_check_take(unsigned long long *first) {
     if (!first) return AC_ERR_ARG;
     *first = 0;
 #ifdef AC_BOUNDS_CHECK
-    unsigned long long (*const readers[])() = {bc_take_aux, bc_take_batch, bc_take_closure,
-                                               bc_take_noalloc, bc_take_f32, bc_take_f32g,
-                                               bc_take_f64};
+    unsigned long long (*const readers[])() = {bc_take_aux,     bc_take_batch, bc_take_closure,
+                                               bc_take_decomp,  bc_take_noalloc, bc_take_f32,
+                                               bc_take_f32g,    bc_take_f64};
     for (auto r : readers) {
         const unsigned long long w = r();
         if (w == ~0ull) return AC_ERR_CUDA;
@@ -607,15 +641,15 @@ extern "C" int ac_integrate_substep(ac_handle *h, double dt, int s) {
     L.s = s;
     L.use_fx = h->stencil_mode != AC_STENCIL_FP64 && fx_applicable(h);
     L.dx = h->grid.lx / h->grid.nx;
-    L.fx_gmax = nullptr;
+    L.fx_stats = nullptr;
+    L.fx_plan = nullptr;
     for (int q = 0; q < NF; ++q) L.fxF[q] = nullptr;
     if (L.use_fx) {
-        if (!h->fx_block) {
-            CK(cudaMalloc(&h->fx_block, (size_t)NF * h->g.elems * sizeof(long long)));
-            CK(cudaMalloc(&h->fx_gmax, 4 * sizeof(unsigned long long)));
-        }
+        rc = ensure_fx(h);
+        if (rc) return rc;
         for (int q = 0; q < NF; ++q) L.fxF[q] = h->fx_block + (size_t)q * h->g.elems;
-        L.fx_gmax = h->fx_gmax;
+        L.fx_stats = h->fx_stats;
+        L.fx_plan = h->fx_plan;
     }
     L.cfl_max = nullptr;
     if (s == 0) {  // the step's input state: record its max CFL speed on the way

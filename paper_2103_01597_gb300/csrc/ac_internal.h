@@ -102,12 +102,18 @@ struct SubstepLaunch {
     int s;
     unsigned long long *cfl_max;  // substep 0: device word for the max CFL speed (or NULL)
     // binary64 with integer stencil sums (cubic periodic grids): int64 copies of
-    // the fields and four group-max words; use_fx = 0 selects plain binary64 sums.
+    // the fields, 16 words of per-field extremes and the device plan of the
+    // substep (fx_plan_bytes()); use_fx = 0 selects plain binary64 sums.
     int use_fx;
     long long *fxF[NF];
-    unsigned long long *fx_gmax;
+    unsigned long long *fx_stats;
+    void *fx_plan;
     double dx;
 };
+size_t fx_plan_bytes();
+// Substeps run in each mode (group scales, per-field scales, plain binary64)
+// since the plan was zeroed; synchronises `st`.
+cudaError_t fx_plan_taken(const void *plan, unsigned long long taken[3], cudaStream_t st);
 
 cudaError_t launch_substep(const SubstepLaunch &L, cudaStream_t st, int *launches);
 cudaError_t launch_halo(int precision, const Geom &g, void *const f[NF], cudaStream_t st);
@@ -137,5 +143,11 @@ cudaError_t launch_reduce(const ReduceLaunch &L, cudaStream_t st, int *launches)
 
 // Record a CUDA error for ac_last_cuda_error() and map it to an AC_ERR_* code.
 int ac_report_cuda(cudaError_t e);
+
+// Argument checks of ac_init: 1 if the grid (positive finite box lengths, a
+// known layout, every axis at most 2^24 cells) or the parameters (finite,
+// nu, eta >= 0, c_s0, c_p > 0, gamma > 1, a known precision) are valid.
+int valid_grid(const ac_grid *g);
+int valid_params(const ac_params *p);
 
 }  // namespace ac

@@ -18,8 +18,6 @@
 #include <stddef.h>
 #include <string.h>
 
-#include <mutex>
-
 #include "reduce.cuh"
 
 namespace ac {
@@ -33,7 +31,6 @@ struct NoallocScratch {
 static __device__ __align__(256) NoallocScratch g_noalloc_scratch;
 
 constexpr int NOALLOC_THREADS = 256;
-constexpr int NOALLOC_MAX_DEVICES = 64;
 
 // Pass 1: block z reduces z-plane z into partial[z] and flag[z].
 template <typename R, class IX>
@@ -105,25 +102,16 @@ __global__ void reduce_planes_final_kernel(int nz, int op, double count, Noalloc
     }
 }
 
-// Device address of the scratch array, looked up once per device.
-static std::mutex g_noalloc_mu;
-static void *g_noalloc_addr[NOALLOC_MAX_DEVICES];
-
+// Device address of the current device's copy of the scratch array.  The
+// symbol's host-side name is not a device address, so the runtime is asked,
+// with the device current, on every call: the lookup allocates nothing, and an
+// address kept from an earlier call could outlive a reset of the device's
+// context.
 static cudaError_t noalloc_scratch(NoallocScratch **out) {
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
+    void *p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
     if (e != cudaSuccess) return e;
-    if (dev < 0 || dev >= NOALLOC_MAX_DEVICES) return cudaErrorInvalidDevice;
-    std::lock_guard<std::mutex> lock(g_noalloc_mu);
-    if (!g_noalloc_addr[dev]) {
-        void *p = nullptr;
-        // The symbol's host-side name is not a device address: ask the runtime
-        // for this device's copy (with the device current).
-        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-        if (e != cudaSuccess) return e;
-        g_noalloc_addr[dev] = p;
-    }
-    *out = static_cast<NoallocScratch *>(g_noalloc_addr[dev]);
+    *out = static_cast<NoallocScratch *>(p);
     return cudaSuccess;
 }
 
@@ -153,18 +141,9 @@ using namespace ac;
 extern "C" int ac_reduce_noalloc(const void *const fields[8], const ac_grid *grid,
                                  const ac_params *params, int op, int quantity, double *out,
                                  void *stream) {
-    if (!fields || !grid || !params || !out) return AC_ERR_ARG;
+    if (!fields || !out || !valid_grid(grid) || !valid_params(params)) return AC_ERR_ARG;
     if (op < AC_MAX || op > AC_RMS || quantity < 0 || quantity > AC_Q_CFL) return AC_ERR_ARG;
-    if (grid->nx < 1 || grid->ny < 1 || grid->nz < 1 || grid->nx > (1 << 24) ||
-        grid->ny > (1 << 24))
-        return AC_ERR_ARG;
     if (grid->nz > AC_NOALLOC_MAX_NZ) return AC_ERR_ARG;  // one scratch slot per z-plane
-    if (!(grid->lx > 0) || !(grid->ly > 0) || !(grid->lz > 0)) return AC_ERR_ARG;
-    if (grid->layout != AC_LAYOUT_PERIODIC && grid->layout != AC_LAYOUT_PADDED) return AC_ERR_ARG;
-    if (params->precision != AC_FP64 && params->precision != AC_FP32 &&
-        params->precision != AC_FP32_W64)
-        return AC_ERR_ARG;
-    if (!(params->cp > 0) || !(params->gamma > 1.0) || !(params->cs0 > 0)) return AC_ERR_ARG;
     for (int q = 0; q < NF; ++q)
         if (!fields[q]) return AC_ERR_ARG;
 

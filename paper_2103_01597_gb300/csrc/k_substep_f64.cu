@@ -10,7 +10,9 @@ static unsigned fx_grid(long long n) {
 }
 
 cudaError_t launch_substep_f64(const SubstepLaunch &L, cudaStream_t st, int *launches) {
-    if (!L.use_fx) return launch_substep_t<double, double>(L, st, launches);
+    // Integer sums need 32-bit neighbour offsets (always true for a binary64
+    // state in HBM: fewer than 2^31 cells per array).
+    if (!L.use_fx || L.g.elems >= (1ll << 31)) return launch_substep_t<double, double>(L, st, launches);
     SubstepArgs<double, double> a;
     a.g = L.g;
     FxPtrs fx;
@@ -38,10 +40,12 @@ cudaError_t launch_substep_f64(const SubstepLaunch &L, cudaStream_t st, int *lau
     fc.inv720dx2 = 1.0 / (720.0 * L.dx * L.dx);
 
     const long long n = L.g.elems;
-    cudaError_t e = cudaMemsetAsync(L.fx_gmax, 0, 4 * sizeof(unsigned long long), st);
+    FxPlan *plan = static_cast<FxPlan *>(L.fx_plan);
+    cudaError_t e = cudaMemsetAsync(L.fx_stats, 0, 2 * NF * sizeof(unsigned long long), st);
     if (e != cudaSuccess) return e;
-    fx_max_kernel<<<fx_grid(n), 256, 0, st>>>(fx, n, L.fx_gmax);
-    fx_quantize_kernel<<<fx_grid(n), 256, 0, st>>>(fx, n, L.fx_gmax);
+    fx_stats_kernel<<<fx_grid(n), 256, 0, st>>>(fx, n, L.fx_stats);
+    fx_plan_kernel<<<1, 32, 0, st>>>(L.fx_stats, plan);
+    fx_quantize_kernel<<<fx_grid(n), 256, 0, st>>>(fx, n, plan);
 
     const dim3 block(32, 4, 1);
     const unsigned gx = (L.g.nx + block.x - 1) / block.x;
@@ -51,21 +55,25 @@ cudaError_t launch_substep_f64(const SubstepLaunch &L, cudaStream_t st, int *lau
     zchunk = zchunk < 1 ? 1 : (zchunk > 16 ? 16 : zchunk);
     a.zchunk = zchunk;
     const dim3 grid(gx, gy, (L.g.nz + zchunk - 1) / zchunk);
-    // 32-bit neighbour offsets whenever they fit (always, for binary64 state in
-    // 280 GB: fewer than 2^31 cells), 64-bit otherwise
-    const bool off32 = L.g.elems < (1ll << 31);
     const bool ext = L.ph.ext(), cfl = a.cfl_max != nullptr;
-#define AC_FX(IX, C, X) substep_fx_kernel<IX, C, X><<<grid, block, 0, st>>>(a, fx, fc, L.fx_gmax)
-    if (off32) {
-        if (ext) { if (cfl) AC_FX(IdxPeriodic32, true, true); else AC_FX(IdxPeriodic32, false, true); }
-        else { if (cfl) AC_FX(IdxPeriodic32, true, false); else AC_FX(IdxPeriodic32, false, false); }
-    } else {
-        if (ext) { if (cfl) AC_FX(IdxPeriodic, true, true); else AC_FX(IdxPeriodic, false, true); }
-        else { if (cfl) AC_FX(IdxPeriodic, true, false); else AC_FX(IdxPeriodic, false, false); }
-    }
+#define AC_FX(C, X) substep_fx_kernel<C, X><<<grid, block, 0, st>>>(a, fx, fc, plan)
+    if (ext) { if (cfl) AC_FX(true, true); else AC_FX(false, true); }
+    else { if (cfl) AC_FX(true, false); else AC_FX(false, false); }
 #undef AC_FX
-    *launches += 3;
+    *launches += 4;
     return cudaGetLastError();
+}
+
+// Size of the device plan of the integer-sum path (allocated by the handle).
+size_t fx_plan_bytes() { return sizeof(FxPlan); }
+
+// Substeps run in each mode of the integer-sum path, read from a plan.
+cudaError_t fx_plan_taken(const void *plan, unsigned long long taken[3], cudaStream_t st) {
+    const FxPlan *p = static_cast<const FxPlan *>(plan);
+    cudaError_t e = cudaMemcpyAsync(taken, p->taken, 3 * sizeof(unsigned long long),
+                                    cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    return e;
 }
 
 // The table-driven exp of the binary64 kernels beside CUDA's exp, for tests:

@@ -37,20 +37,21 @@ __device__ __forceinline__ void rk_update(const SubstepArgs<R, W> &a, int q, lon
     a.fout[q][o] = (R)((W)ldg(a.fin[q] + o) + a.beta * wn);
 }
 
-// One (x, y) column of the tile: cells k0 .. k1-1 of the CTA's z range.  With
-// cfl_acc non-null the largest CFL speed of the input state is kept there.
+// One (x, y) column: cells k0 .. k1-1.  With cfl_acc non-null the largest CFL
+// speed of the input state is kept there.  `tx`, `ty`, `tz` are the forcing
+// phase tables of the x, y and z axes (entries indexed by i, j, k).
 template <typename R, typename W, class IX, int RAD = 3, bool EXT = false>
-__device__ __forceinline__ void substep_column(const SubstepArgs<R, W> &a, int i, int j,
-                                               R *cfl_acc) {
-    const int k0 = blockIdx.z * a.zchunk;
-    const int k1 = min(k0 + a.zchunk, a.g.nz);
+__device__ __forceinline__ void substep_column(const SubstepArgs<R, W> &a, int i, int j, int k0,
+                                               int k1, const typename Vec2<R>::type *tx,
+                                               const typename Vec2<R>::type *ty,
+                                               const typename Vec2<R>::type *tz, R *cfl_acc) {
     using V2 = typename Vec2<R>::type;
     IX ix;
     ix.set_xy(i, j, a.g);
     // Forcing phase factor of this (x, y) column: e^{i (theta_x + theta_y)}.
     V2 exy = {(R)0, (R)0};
     if (a.force_on) {
-        const V2 ex = a.ftab[i], ey = a.ftab[a.g.nx + j];
+        const V2 ex = tx[i], ey = ty[j];
         exy.x = ex.x * ey.x - ex.y * ey.y;
         exy.y = ex.x * ey.y + ex.y * ey.x;
     }
@@ -58,7 +59,7 @@ __device__ __forceinline__ void substep_column(const SubstepArgs<R, W> &a, int i
         ix.set_z(kk, a.g);
         R frc[3] = {(R)0, (R)0, (R)0};
         if (a.force_on) {
-            const V2 ez = a.ftab[a.g.nx + a.g.ny + kk];
+            const V2 ez = tz[kk];
             const R cph = exy.x * ez.x - exy.y * ez.y;  // cos(k . x + phi)
             frc[0] = a.amp_e[0] * cph;
             frc[1] = a.amp_e[1] * cph;
@@ -86,13 +87,34 @@ __device__ __forceinline__ void substep_body(const SubstepArgs<R, W> &a) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const int j = blockIdx.y * blockDim.y + threadIdx.y;
     const bool active = i < a.g.nx && j < a.g.ny;
+    const int k0 = blockIdx.z * a.zchunk;
+    const int k1 = min(k0 + a.zchunk, a.g.nz);
+    const auto *tx = a.ftab, *ty = a.ftab + a.g.nx, *tz = a.ftab + a.g.nx + a.g.ny;
     if (CFL) {
         R cfl = (R)0;
-        if (active) substep_column<R, W, IX, RAD, EXT>(a, i, j, &cfl);
+        if (active) substep_column<R, W, IX, RAD, EXT>(a, i, j, k0, k1, tx, ty, tz, &cfl);
         block_max_to_global((double)cfl, a.cfl_max);
     } else if (active) {
-        substep_column<R, W, IX, RAD, EXT>(a, i, j, nullptr);
+        substep_column<R, W, IX, RAD, EXT>(a, i, j, k0, k1, tx, ty, tz, nullptr);
     }
+}
+
+// A box [b0, b1) of the interior (x, y, z), for updates of one segment of a
+// subdomain: blocks cover the box's x-y extent, blockIdx.z its z range in
+// chunks of a.zchunk.  `ftab` holds the subdomain's own tables [nx | ny | nz].
+struct Box {
+    int b0[3], b1[3];
+};
+
+template <typename R, typename W, int RAD, bool EXT>
+__global__ void __launch_bounds__(128) substep_box_kernel(const SubstepArgs<R, W> a, Box box) {
+    const int i = box.b0[0] + blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = box.b0[1] + blockIdx.y * blockDim.y + threadIdx.y;
+    if (i >= box.b1[0] || j >= box.b1[1]) return;
+    const int k0 = box.b0[2] + blockIdx.z * a.zchunk;
+    const int k1 = min(k0 + a.zchunk, box.b1[2]);
+    const auto *tx = a.ftab, *ty = a.ftab + a.g.nx, *tz = a.ftab + a.g.nx + a.g.ny;
+    substep_column<R, W, IdxPadded, RAD, EXT>(a, i, j, k0, k1, tx, ty, tz, nullptr);
 }
 
 template <typename R, typename W, class IX, bool CFL, int RAD = 3, bool EXT = false>

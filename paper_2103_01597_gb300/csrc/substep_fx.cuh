@@ -3,17 +3,34 @@
 // GB300 executes two FP64 lanes per SM per cycle, so the binary64 substep is
 // bound by its FP64 instruction count, most of which (about 400 of 600 per
 // cell) are the additions and multiplications of the 54 stencils of Eq. 13.
-// Here each field group (ln rho; u; s; A) is first written as int64 fixed
-// point with one power-of-two scale per group, F = round(f 2^(50 - e)) with
-// max |f| < 2^e, so |F| <= 2^50.  Every stencil numerator -- and every sum of
-// numerators that share a coefficient (curl A, lap u, grad(div u), lap A,
-// grad(div A)) -- is then an exact integer on the integer pipes (largest:
-// 6744 |F| < 2^63), and only one int64 -> binary64 conversion and one
-// multiplication per derivative term remain on the FP64 pipe.  The
-// quantisation step, 2^-50 of the group's largest magnitude, is four binary64
-// units in the last place at that magnitude; the centre values used by the
-// physics and the Runge-Kutta update are the binary64 state itself.  The physics of Eqs. B.1-B.4 is unchanged
-// binary64 code (cell_physics).
+// Here each field is first written as int64 fixed point about an offset of its
+// own, F = round((f - c) 2^(50 - E)), with c the midpoint of the field's range
+// and 2^E above its half-range, so |F| <= 2^50 + 2.  Every weight set of Eq. 13
+// sums to zero, so the offset changes no derivative.  Every stencil numerator
+// -- and every sum of numerators that share a coefficient (curl A, lap u,
+// grad(div u), lap A, grad(div A)) -- is then an exact integer on the integer
+// pipes (largest: 6744 |F| < 2^63), and only one int64 -> binary64 conversion
+// and one multiplication per derivative term remain on the FP64 pipe.  The
+// centre values used by the physics and the Runge-Kutta update are the
+// binary64 state itself; the physics of Eqs. B.1-B.4 is unchanged binary64
+// code (cell_physics).
+//
+// A plan kernel picks one of three modes per substep from the fields' ranges,
+// on the device (no host round trip):
+//  * FX_GROUP: the three components of u (and of A) have the same E, so they
+//    share one scale and the cross-component sums stay single integers;
+//  * FX_FIELD: some component's E is below its group's largest, so every field
+//    keeps its own scale and the cross-component sums (curl A, grad(div u),
+//    grad(div A)) add per-field binary64 terms instead -- a component far
+//    smaller than the others (a near-2-D flow, a weak field component) is
+//    resolved to 2^-50 of its own range either way;
+//  * FX_PLAIN: a NaN or infinity in the state, or a range outside
+//    [2^-960, 2^960): the substep runs plain binary64 stencils, exactly what
+//    AC_STENCIL_FP64 computes (so a non-finite value propagates as in the
+//    definition and shows in the step's CFL word).
+// The quantisation error of every stencil input is then at most half a unit
+// of 2^(E - 50), E the field's own exponent: within a factor of about three of
+// the worst-case binary64 rounding of the same stencil.
 #pragma once
 
 #include "substep.cuh"
@@ -21,18 +38,20 @@
 namespace ac {
 
 constexpr int FX_BITS = 50;
+enum { FX_GROUP = 0, FX_FIELD = 1, FX_PLAIN = 2 };
 
 // Field -> group: 0 = ln rho, 1 = u, 2 = s, 3 = A.
 __host__ __device__ __forceinline__ int fx_group(int q) {
     return q == 0 ? 0 : (q < 4 ? 1 : (q == 4 ? 2 : 3));
 }
 
-// Smallest e with m < 2^e for the binary64 m >= 0 held in `bits` (0 for m == 0,
-// non-finite or subnormal m).
-__device__ __forceinline__ int fx_exponent(unsigned long long bits) {
-    const int eb = (int)((bits >> 52) & 0x7ff);
-    if (eb == 0 || eb == 0x7ff) return 0;
-    return eb - 1022;
+// Order-preserving map of binary64 bits to unsigned keys (NaNs sort beyond the
+// infinities of their sign) and back.
+__device__ __forceinline__ unsigned long long fx_key(unsigned long long b) {
+    return (b >> 63) ? ~b : (b | 0x8000000000000000ull);
+}
+__device__ __forceinline__ double fx_unkey(unsigned long long k) {
+    return __longlong_as_double((long long)((k >> 63) ? (k & 0x7fffffffffffffffull) : ~k));
 }
 
 // 2^k as a binary64 built from its bits (|k| < 1000).
@@ -40,56 +59,151 @@ __device__ __forceinline__ double fx_pow2(int k) {
     return __longlong_as_double((long long)(k + 1023) << 52);
 }
 
-// Largest |f| of each group over the current state (bits of binary64 values).
+// round(v 2^(FX_BITS - E)) modulo 2^64 for the binary64 v held in `b` (round
+// half away from zero), by integer operations on the bits.  Two such values
+// within 2^63 of each other subtract exactly in wrapping 64-bit arithmetic,
+// however large each is.
+__device__ __forceinline__ unsigned long long fx_round_grid(unsigned long long b, int E) {
+    const int eb = (int)((b >> 52) & 0x7ff);
+    unsigned long long m = b & 0xfffffffffffffull;
+    int ex = -1074;
+    if (eb != 0) {
+        m |= 1ull << 52;
+        ex = eb - 1075;
+    }
+    const int sh = ex + FX_BITS - E;  // |v| 2^(FX_BITS - E) = m 2^sh
+    unsigned long long a;
+    if (sh >= 0) {
+        a = sh < 64 ? m << sh : 0ull;
+    } else {
+        const int k = -sh;
+        a = k < 64 ? (m + (1ull << (k - 1))) >> k : 0ull;
+    }
+    return (b >> 63) ? 0ull - a : a;
+}
+
 struct FxPtrs {
     const double *f[NF];
     long long *F[NF];
 };
 
-__global__ void fx_max_kernel(FxPtrs p, long long n, unsigned long long *gmax) {
-    unsigned long long m[4] = {0ull, 0ull, 0ull, 0ull};
+// The quantisation plan of one substep (device memory, written by
+// fx_plan_kernel, read by the quantisation and substep kernels).
+struct FxPlan {
+    int mode;                  // FX_GROUP, FX_FIELD or FX_PLAIN
+    int zero[NF];              // constant field: F = 0
+    int E[NF];                 // F = round((f - c) 2^(FX_BITS - E)) - the offset
+    unsigned long long C[NF];  // round(c 2^(FX_BITS - E)) modulo 2^64
+    double scale[NF];          // 2^(E - FX_BITS); in FX_GROUP equal within a group
+    unsigned long long taken[3];  // substeps run in each mode (cumulative)
+};
+
+// Per-field extremes of the current state: stats[q] = largest key of field q,
+// stats[NF + q] = complement of its smallest key (so that both are maxima and a
+// zero fill initialises them).  One CTA-wide reduction, then 16 atomics per CTA.
+__global__ void __launch_bounds__(256) fx_stats_kernel(FxPtrs p, long long n,
+                                                       unsigned long long *stats) {
+    unsigned long long hi[NF], nlo[NF];
+#pragma unroll
+    for (int q = 0; q < NF; ++q) hi[q] = nlo[q] = 0ull;
     for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n;
          t += (long long)gridDim.x * blockDim.x) {
 #pragma unroll
         for (int q = 0; q < NF; ++q) {
-            const unsigned long long b =
-                (unsigned long long)__double_as_longlong(p.f[q][t]) & 0x7fffffffffffffffull;
-            const int gq = fx_group(q);
-            m[gq] = b > m[gq] ? b : m[gq];
+            const unsigned long long k = fx_key((unsigned long long)__double_as_longlong(p.f[q][t]));
+            hi[q] = k > hi[q] ? k : hi[q];
+            nlo[q] = ~k > nlo[q] ? ~k : nlo[q];
         }
     }
+    __shared__ unsigned long long red[2 * NF];
+    if (threadIdx.x < 2 * NF) red[threadIdx.x] = 0ull;
+    __syncthreads();
 #pragma unroll
-    for (int gq = 0; gq < 4; ++gq) {
-        unsigned long long v = m[gq];
+    for (int q = 0; q < NF; ++q) {
+        unsigned long long a = hi[q], b = nlo[q];
         for (int o = 16; o > 0; o >>= 1) {
-            const unsigned long long w = __shfl_xor_sync(0xffffffffu, v, o);
-            v = w > v ? w : v;
+            const unsigned long long x = __shfl_xor_sync(0xffffffffu, a, o);
+            const unsigned long long y = __shfl_xor_sync(0xffffffffu, b, o);
+            a = x > a ? x : a;
+            b = y > b ? y : b;
         }
-        if ((threadIdx.x & 31) == 0) atomicMax(&gmax[gq], v);
+        if ((threadIdx.x & 31) == 0) {
+            atomicMax(&red[q], a);
+            atomicMax(&red[NF + q], b);
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x < 2 * NF) atomicMax(&stats[threadIdx.x], red[threadIdx.x]);
+}
+
+// One warp: lane q < NF plans field q (offset, exponent), then the lanes agree
+// on the mode.  Thread 0 also counts the substep under its mode.
+__global__ void fx_plan_kernel(const unsigned long long *stats, FxPlan *plan) {
+    const int q = threadIdx.x;
+    int bad = 0, zero = 1, e = -100000;
+    double c = 0.0;
+    if (q < NF) {
+        const double hi = fx_unkey(stats[q]), lo = fx_unkey(~stats[NF + q]);
+        if (!isfinite(hi) || !isfinite(lo)) {
+            bad = 1;
+        } else {
+            c = 0.5 * lo + 0.5 * hi;
+            const double r = fmax(hi - c, c - lo);
+            if (r > 0.0) {
+                zero = 0;
+                if (!(r >= 0x1p-960 && r < 0x1p960))
+                    bad = 1;
+                else  // smallest E with r < 2^E
+                    e = (int)((__double_as_longlong(r) >> 52) & 0x7ff) - 1022;
+            }
+        }
+    }
+    // largest exponent of the field's group over its non-constant members
+    const int g = q < NF ? fx_group(q) : -1;
+    int eg = -100000;
+#pragma unroll
+    for (int r = 0; r < NF; ++r) {
+        const int er = __shfl_sync(0xffffffffu, e, r);
+        if (fx_group(r) == g && er > eg) eg = er;
+    }
+    const int disparity = q < NF && !zero && e < eg;
+    const int any_bad = __any_sync(0xffffffffu, bad);
+    const int any_disp = __any_sync(0xffffffffu, disparity);
+    const int mode = any_bad ? FX_PLAIN : (any_disp ? FX_FIELD : FX_GROUP);
+    if (q < NF) {
+        int E = mode == FX_GROUP ? eg : e;
+        const int valid = E > -100000;
+        if (!valid) E = 0;
+        plan->zero[q] = zero;
+        plan->E[q] = E;
+        plan->C[q] = fx_round_grid((unsigned long long)__double_as_longlong(c), E);
+        plan->scale[q] = valid && mode != FX_PLAIN ? fx_pow2(E - FX_BITS) : 0.0;
+    }
+    if (q == 0) {
+        plan->mode = mode;
+        plan->taken[mode] += 1ull;
     }
 }
 
-// F = round(f 2^(50 - e)) by integer operations on the binary64 bits (round
-// half up in magnitude); values below the resolution become 0.
-__global__ void fx_quantize_kernel(FxPtrs p, long long n, const unsigned long long *gmax) {
-    int e[4];
+// F = round(f 2^(50 - E)) - round(c 2^(50 - E)) by integer operations on the
+// binary64 bits; nothing to do in FX_PLAIN.
+__global__ void __launch_bounds__(256) fx_quantize_kernel(FxPtrs p, long long n,
+                                                          const FxPlan *plan) {
+    if (plan->mode == FX_PLAIN) return;
+    int E[NF], zero[NF];
+    unsigned long long C[NF];
 #pragma unroll
-    for (int gq = 0; gq < 4; ++gq) e[gq] = fx_exponent(gmax[gq]);
+    for (int q = 0; q < NF; ++q) {
+        E[q] = plan->E[q];
+        zero[q] = plan->zero[q];
+        C[q] = plan->C[q];
+    }
     for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n;
          t += (long long)gridDim.x * blockDim.x) {
 #pragma unroll
         for (int q = 0; q < NF; ++q) {
-            const long long b = __double_as_longlong(p.f[q][t]);
-            const int eb = (int)((b >> 52) & 0x7ff);
-            long long v = 0;
-            if (eb != 0 && eb != 0x7ff) {
-                const int sh = 1075 - FX_BITS + e[fx_group(q)] - eb;  // right shift of the significand
-                if (sh > 0 && sh < 62) {
-                    const long long mant = (b & 0xfffffffffffffll) | 0x10000000000000ll;
-                    v = (mant + (1ll << (sh - 1))) >> sh;
-                }
-            }
-            p.F[q][t] = b < 0 ? -v : v;
+            const unsigned long long b = (unsigned long long)__double_as_longlong(p.f[q][t]);
+            p.F[q][t] = zero[q] ? 0ll : (long long)(fx_round_grid(b, E[q]) - C[q]);
         }
     }
 }
@@ -133,8 +247,17 @@ __device__ __forceinline__ long long ndab(const V &F) {
     return 270 * S[0] - 27 * S[1] + 2 * S[2];
 }
 
-// Coefficients of the converted numerators; the group scales 2^(e - FX_BITS) are
-// read from the max words on the device.
+// (double)N 2^k exactly for the integer numerator N, by adding k to the
+// exponent field of the converted value (k_hi = k << 20, the exponent's place in
+// the high word); 0 stays 0.  Every product stays normal: 1 <= |N| < 2^63 and
+// the plan keeps 2^(E - FX_BITS) within [2^-1010, 2^910].
+__device__ __forceinline__ double fx_scaled(long long N, int k_hi) {
+    const double v = (double)N;
+    return N == 0 ? 0.0 : __hiloint2double(__double2hiint(v) + k_hi, __double2loint(v));
+}
+
+// Coefficients of the converted numerators (host side); the field scales
+// 2^(E - FX_BITS) come from the device plan.
 struct FxCoefs {
     double inv60dx;    // 1 / (60 dx): first derivatives
     double nu180;      // nu / (180 dx^2): nu lap u
@@ -143,85 +266,155 @@ struct FxCoefs {
     double inv720dx2;  // 1 / (720 dx^2): grad(div A)
 };
 
-// Two CTAs of 128 threads per SM (8 warps, as many as 255 registers allow): with
-// the minimum stated, ptxas fits the kernel in 254 registers without the spills
-// it otherwise makes (+4% at 256^3; a cap of 168 registers for 12 warps spills
-// and is slower).
-template <class IX, bool CFL, bool EXT = false>
-__global__ void __launch_bounds__(128, 2) substep_fx_kernel(const SubstepArgs<double, double> a,
-                                                         const FxPtrs fx, FxCoefs fc,
-                                                         const unsigned long long *gmax) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    const int j = blockIdx.y * blockDim.y + threadIdx.y;
-    const bool active = i < a.g.nx && j < a.g.ny;
-    __shared__ double etab[512];
-    exp_tab_stage(etab);
-    double cfl = 0.0;
-    if (active) {
-        double sc[4];
+// One (x, y) column of the integer-sum substep.  PF: per-field scales (FX_FIELD),
+// so sums across the components of u or A are formed in binary64 from per-field
+// integer numerators; otherwise one scale per group (FX_GROUP).
+template <bool PF, bool CFL, bool EXT>
+__device__ __forceinline__ void fx_column(const SubstepArgs<double, double> &a, const FxPtrs &fx,
+                                          const FxCoefs &fc, const FxPlan *plan,
+                                          const double *etab, int i, int j, double &cfl) {
+    // FX_GROUP: four group scales folded into the coefficients (registers).
+    // FX_FIELD: each field's scale 2^(E - FX_BITS) is applied to its converted
+    // numerators by an exponent add (fx_scaled), so only the grid coefficients
+    // (kernel parameters) multiply, and per-field scales cost no FP64 work.
+    double sc[NF];
+    int kh[NF];
 #pragma unroll
-        for (int gq = 0; gq < 4; ++gq) sc[gq] = fx_pow2(fx_exponent(gmax[gq]) - FX_BITS);
-        const double c1[4] = {sc[0] * fc.inv60dx, sc[1] * fc.inv60dx, sc[2] * fc.inv60dx,
-                              sc[3] * fc.inv60dx};
-        const double clu = sc[1] * fc.nu180;
-        const double cgu = sc[1] * fc.nu2160;
-        const double cla = sc[3] * fc.inv180dx2;
-        const double cga = sc[3] * fc.inv720dx2;
-        const int k0 = blockIdx.z * a.zchunk;
-        const int k1 = min(k0 + a.zchunk, a.g.nz);
-        IX ix;
-        ix.set_xy(i, j, a.g);
-        double2 exy = make_double2(0.0, 0.0);
-        if (a.force_on) {
-            const double2 ex = a.ftab[i], ey = a.ftab[a.g.nx + j];
-            exy.x = ex.x * ey.x - ex.y * ey.y;
-            exy.y = ex.x * ey.y + ex.y * ey.x;
+    for (int q = 0; q < NF; ++q) {
+        sc[q] = plan->scale[q];
+        kh[q] = (plan->E[q] - FX_BITS) << 20;
+    }
+    double c1[NF];
+#pragma unroll
+    for (int q = 0; q < NF; ++q) c1[q] = sc[q] * fc.inv60dx;
+    const double clu = sc[1] * fc.nu180, cgu = sc[1] * fc.nu2160;
+    const double cla = sc[5] * fc.inv180dx2, cga = sc[5] * fc.inv720dx2;
+    // first derivative of field q from its numerator
+    auto d1 = [&](long long N, int q) -> double {
+        if constexpr (PF)
+            return fx_scaled(N, kh[q]) * fc.inv60dx;
+        else
+            return (double)N * c1[q];
+    };
+    const int k0 = blockIdx.z * a.zchunk;
+    const int k1 = min(k0 + a.zchunk, a.g.nz);
+    IdxPeriodic32 ix;
+    ix.set_xy(i, j, a.g);
+    double2 exy = make_double2(0.0, 0.0);
+    if (a.force_on) {
+        const double2 ex = a.ftab[i], ey = a.ftab[a.g.nx + j];
+        exy.x = ex.x * ey.x - ex.y * ey.y;
+        exy.y = ex.x * ey.y + ex.y * ey.x;
+    }
+    for (int kk = k0; kk < k1; ++kk) {
+        ix.set_z(kk, a.g);
+        const long long o = ix(0, 0, 0);
+        // Centre values (the binary64 state) and the thermodynamic factors: at the
+        // top of the cell in the CFL variant (substep 0), after the stencil sums in
+        // the other; each placement measured fastest for its variant at 256^3
+        // (8.30 against 8.78 ms, 7.89 against 8.64 ms), a matter of register
+        // allocation at 255 registers.
+        double lnrho = 0.0, ss = 0.0;
+        Thermo<double> th;
+        if constexpr (CFL) {
+            lnrho = ldg(a.fin[0] + o);
+            ss = ldg(a.fin[4] + o);
+            th = thermo_factors<double>(lnrho, ss, a.k, etab);
         }
-        for (int kk = k0; kk < k1; ++kk) {
-            ix.set_z(kk, a.g);
-            const long long o = ix(0, 0, 0);
-            // Centre values (the binary64 state) and the thermodynamic factors: at the
-            // top of the cell in the CFL variant (substep 0), after the stencil sums in
-            // the other; each placement measured fastest for its variant at 256^3
-            // (8.30 against 8.78 ms, 7.89 against 8.64 ms), a matter of register
-            // allocation at 255 registers.
-            double lnrho = 0.0, ss = 0.0;
-            Thermo<double> th;
-            if constexpr (CFL) {
-                lnrho = ldg(a.fin[0] + o);
-                ss = ldg(a.fin[4] + o);
-                th = thermo_factors<double>(lnrho, ss, a.k, etab);
+        double frc[3] = {0.0, 0.0, 0.0};
+        if (a.force_on) {
+            const double2 ez = a.ftab[a.g.nx + a.g.ny + kk];
+            const double cph = exy.x * ez.x - exy.y * ez.y;
+            frc[0] = a.amp_e[0] * cph;
+            frc[1] = a.amp_e[1] * cph;
+            frc[2] = a.amp_e[2] * cph;
+        }
+        const GlobalView<long long, IdxPeriodic32> Fl{fx.F[0], ix}, Fs{fx.F[4], ix};
+        const GlobalView<long long, IdxPeriodic32> Fu[3] = {{fx.F[1], ix}, {fx.F[2], ix},
+                                                             {fx.F[3], ix}};
+        const GlobalView<long long, IdxPeriodic32> Fa[3] = {{fx.F[5], ix}, {fx.F[6], ix},
+                                                             {fx.F[7], ix}};
+        // first derivatives
+        double gl[3], gs[3], gu[3][3], B[3];
+        gl[0] = d1(nd1<0>(Fl), 0);
+        gl[1] = d1(nd1<1>(Fl), 0);
+        gl[2] = d1(nd1<2>(Fl), 0);
+        gs[0] = d1(nd1<0>(Fs), 4);
+        gs[1] = d1(nd1<1>(Fs), 4);
+        gs[2] = d1(nd1<2>(Fs), 4);
+#pragma unroll
+        for (int m = 0; m < 3; ++m) {
+            const int qu = PF ? 1 + m : 1;  // one live coefficient in FX_GROUP
+            gu[m][0] = d1(nd1<0>(Fu[m]), qu);
+            gu[m][1] = d1(nd1<1>(Fu[m]), qu);
+            gu[m][2] = d1(nd1<2>(Fu[m]), qu);
+        }
+        if constexpr (PF) {
+            B[0] = (fx_scaled(nd1<1>(Fa[2]), kh[7]) - fx_scaled(nd1<2>(Fa[1]), kh[6])) * fc.inv60dx;
+            B[1] = (fx_scaled(nd1<2>(Fa[0]), kh[5]) - fx_scaled(nd1<0>(Fa[2]), kh[7])) * fc.inv60dx;
+            B[2] = (fx_scaled(nd1<0>(Fa[1]), kh[6]) - fx_scaled(nd1<1>(Fa[0]), kh[5])) * fc.inv60dx;
+        } else {
+            B[0] = (double)(nd1<1>(Fa[2]) - nd1<2>(Fa[1])) * c1[5];
+            B[1] = (double)(nd1<2>(Fa[0]) - nd1<0>(Fa[2])) * c1[5];
+            B[2] = (double)(nd1<0>(Fa[1]) - nd1<1>(Fa[0])) * c1[5];
+        }
+        // lap V_i = sum_a N2_aa(V_i) / (180 dx^2);
+        // grad(div V)_i = [4 N2_ii(V_i) + NX_ij(V_j) + NX_ik(V_k)] / (720 dx^2);
+        // component C of V contributes 4 N2_CC to entry C and its two mixed
+        // numerators to the other two entries.
+        double viscl[3], lapa[3], J[3];
+        if constexpr (PF) {
+            // per-field scaled numerators, summed across components in binary64
+            double LU[3], GU[3], LA[3], GA[3];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                const int b1 = c == 0 ? 1 : 0, b2 = c == 2 ? 1 : 2;
+                {
+                    const long long c0 = Fu[c](0, 0, 0);
+                    const long long xx = nd2<0>(Fu[c], c0), yy = nd2<1>(Fu[c], c0),
+                                    zz = nd2<2>(Fu[c], c0);
+                    const int k = kh[1 + c];
+                    LU[c] = fx_scaled(xx + yy + zz, k);
+                    const double own = fx_scaled(4 * (c == 0 ? xx : (c == 1 ? yy : zz)), k);
+                    const double x1 = fx_scaled(c == 2 ? ndab<0, 2>(Fu[c]) : ndab<0, 1>(Fu[c]), k);
+                    const double x2 = fx_scaled(c == 0 ? ndab<0, 2>(Fu[c]) : ndab<1, 2>(Fu[c]), k);
+                    if (c == 0) {
+                        GU[0] = own;
+                        GU[1] = x1;
+                        GU[2] = x2;
+                    } else {
+                        GU[c] += own;
+                        GU[b1] += x1;
+                        GU[b2] += x2;
+                    }
+                }
+                {
+                    const long long c0 = Fa[c](0, 0, 0);
+                    const long long xx = nd2<0>(Fa[c], c0), yy = nd2<1>(Fa[c], c0),
+                                    zz = nd2<2>(Fa[c], c0);
+                    const int k = kh[5 + c];
+                    LA[c] = fx_scaled(xx + yy + zz, k);
+                    const double own = fx_scaled(4 * (c == 0 ? xx : (c == 1 ? yy : zz)), k);
+                    const double x1 = fx_scaled(c == 2 ? ndab<0, 2>(Fa[c]) : ndab<0, 1>(Fa[c]), k);
+                    const double x2 = fx_scaled(c == 0 ? ndab<0, 2>(Fa[c]) : ndab<1, 2>(Fa[c]), k);
+                    if (c == 0) {
+                        GA[0] = own;
+                        GA[1] = x1;
+                        GA[2] = x2;
+                    } else {
+                        GA[c] += own;
+                        GA[b1] += x1;
+                        GA[b2] += x2;
+                    }
+                }
             }
-            double frc[3] = {0.0, 0.0, 0.0};
-            if (a.force_on) {
-                const double2 ez = a.ftab[a.g.nx + a.g.ny + kk];
-                const double cph = exy.x * ez.x - exy.y * ez.y;
-                frc[0] = a.amp_e[0] * cph;
-                frc[1] = a.amp_e[1] * cph;
-                frc[2] = a.amp_e[2] * cph;
-            }
-            const GlobalView<long long, IX> Fl{fx.F[0], ix}, Fs{fx.F[4], ix};
-            const GlobalView<long long, IX> Fu[3] = {{fx.F[1], ix}, {fx.F[2], ix}, {fx.F[3], ix}};
-            const GlobalView<long long, IX> Fa[3] = {{fx.F[5], ix}, {fx.F[6], ix}, {fx.F[7], ix}};
-            // first derivatives
-            double gl[3], gs[3], gu[3][3], B[3];
-            gl[0] = (double)nd1<0>(Fl) * c1[0];
-            gl[1] = (double)nd1<1>(Fl) * c1[0];
-            gl[2] = (double)nd1<2>(Fl) * c1[0];
-            gs[0] = (double)nd1<0>(Fs) * c1[2];
-            gs[1] = (double)nd1<1>(Fs) * c1[2];
-            gs[2] = (double)nd1<2>(Fs) * c1[2];
 #pragma unroll
             for (int m = 0; m < 3; ++m) {
-                gu[m][0] = (double)nd1<0>(Fu[m]) * c1[1];
-                gu[m][1] = (double)nd1<1>(Fu[m]) * c1[1];
-                gu[m][2] = (double)nd1<2>(Fu[m]) * c1[1];
+                viscl[m] = fma(LU[m], fc.nu180, GU[m] * fc.nu2160);
+                lapa[m] = LA[m] * fc.inv180dx2;
+                J[m] = fma(GA[m], fc.inv720dx2, -lapa[m]);
             }
-            B[0] = (double)(nd1<1>(Fa[2]) - nd1<2>(Fa[1])) * c1[3];
-            B[1] = (double)(nd1<2>(Fa[0]) - nd1<0>(Fa[2])) * c1[3];
-            B[2] = (double)(nd1<0>(Fa[1]) - nd1<1>(Fa[0])) * c1[3];
-            // lap u_i = sum_a N2_aa(u_i) / (180 dx^2);
-            // grad(div u)_i = [4 N2_ii(u_i) + NX_ij(u_j) + NX_ik(u_k)] / (720 dx^2)
+        } else {
             long long LU[3], GU[3];
             {
                 const long long c0 = Fu[0](0, 0, 0);
@@ -273,41 +466,72 @@ __global__ void __launch_bounds__(128, 2) substep_fx_kernel(const SubstepArgs<do
                 GA[0] += ndab<0, 2>(Fa[2]);
                 GA[1] += ndab<1, 2>(Fa[2]);
             }
-            double viscl[3], lapa[3], J[3];
 #pragma unroll
             for (int m = 0; m < 3; ++m) {
                 viscl[m] = (double)LU[m] * clu + (double)GU[m] * cgu;
                 lapa[m] = (double)LA[m] * cla;
                 J[m] = (double)GA[m] * cga - lapa[m];
             }
-            // EXT: lap xi = gamma / c_p lap s + (gamma - 1) lap ln rho (conduction)
-            double lapxi = 0.0;
-            if (EXT) {
-                const long long l0 = Fl(0, 0, 0), s0 = Fs(0, 0, 0);
-                const long long LL = nd2<0>(Fl, l0) + nd2<1>(Fl, l0) + nd2<2>(Fl, l0);
-                const long long LS = nd2<0>(Fs, s0) + nd2<1>(Fs, s0) + nd2<2>(Fs, s0);
-                lapxi = a.k.gamma_cp * ((double)LS * (sc[2] * fc.inv180dx2)) +
-                        a.k.gm1 * ((double)LL * (sc[0] * fc.inv180dx2));
-            }
-            if constexpr (!CFL) {
-                lnrho = ldg(a.fin[0] + o);
-                ss = ldg(a.fin[4] + o);
-                th = thermo_factors<double>(lnrho, ss, a.k, etab);
-            }
-            const double u[3] = {ldg(a.fin[1] + o), ldg(a.fin[2] + o), ldg(a.fin[3] + o)};
-            double rhs[NF];
-            if (CFL) {
-                double c;
-                cell_physics<double, EXT>(lnrho, u, ss, gl, gs, gu, B, viscl, lapa, J, a.k, frc, rhs,
-                                          &c, lapxi, th);
-                cfl = (c > cfl || c != c) ? c : cfl;
-            } else {
-                cell_physics<double, EXT>(lnrho, u, ss, gl, gs, gu, B, viscl, lapa, J, a.k, frc, rhs,
-                                          nullptr, lapxi, th);
-            }
-#pragma unroll
-            for (int q = 0; q < NF; ++q) rk_update(a, q, o, rhs[q]);
         }
+        // EXT: lap xi = gamma / c_p lap s + (gamma - 1) lap ln rho (conduction)
+        double lapxi = 0.0;
+        if (EXT) {
+            const long long l0 = Fl(0, 0, 0), s0 = Fs(0, 0, 0);
+            const long long LL = nd2<0>(Fl, l0) + nd2<1>(Fl, l0) + nd2<2>(Fl, l0);
+            const long long LS = nd2<0>(Fs, s0) + nd2<1>(Fs, s0) + nd2<2>(Fs, s0);
+            const double ls = PF ? fx_scaled(LS, kh[4]) * fc.inv180dx2
+                                 : (double)LS * (sc[4] * fc.inv180dx2);
+            const double ll = PF ? fx_scaled(LL, kh[0]) * fc.inv180dx2
+                                 : (double)LL * (sc[0] * fc.inv180dx2);
+            lapxi = a.k.gamma_cp * ls + a.k.gm1 * ll;
+        }
+        if constexpr (!CFL) {
+            lnrho = ldg(a.fin[0] + o);
+            ss = ldg(a.fin[4] + o);
+            th = thermo_factors<double>(lnrho, ss, a.k, etab);
+        }
+        const double u[3] = {ldg(a.fin[1] + o), ldg(a.fin[2] + o), ldg(a.fin[3] + o)};
+        double rhs[NF];
+        if (CFL) {
+            double c;
+            cell_physics<double, EXT>(lnrho, u, ss, gl, gs, gu, B, viscl, lapa, J, a.k, frc, rhs,
+                                      &c, lapxi, th);
+            cfl = (c > cfl || c != c) ? c : cfl;
+        } else {
+            cell_physics<double, EXT>(lnrho, u, ss, gl, gs, gu, B, viscl, lapa, J, a.k, frc, rhs,
+                                      nullptr, lapxi, th);
+        }
+#pragma unroll
+        for (int q = 0; q < NF; ++q) rk_update(a, q, o, rhs[q]);
+    }
+}
+
+// The substep on the mode the plan chose (uniform over the grid): integer sums
+// with group or per-field scales, or plain binary64 stencils (FX_PLAIN).  Two
+// CTAs of 128 threads per SM (8 warps, as many as 255 registers allow): with
+// the minimum stated, ptxas fits the group-scale body in 254 registers without
+// the spills it otherwise makes (+4% at 256^3; a cap of 168 registers for 12
+// warps spills and is slower).
+template <bool CFL, bool EXT = false>
+__global__ void __launch_bounds__(128, 2) substep_fx_kernel(const SubstepArgs<double, double> a,
+                                                         const FxPtrs fx, FxCoefs fc,
+                                                         const FxPlan *plan) {
+    const int mode = plan->mode;
+    if (mode == FX_PLAIN) {
+        substep_body<double, double, IdxPeriodic32, CFL, 3, EXT>(a);
+        return;
+    }
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y * blockDim.y + threadIdx.y;
+    const bool active = i < a.g.nx && j < a.g.ny;
+    __shared__ double etab[512];
+    exp_tab_stage(etab);
+    double cfl = 0.0;
+    if (active) {
+        if (mode == FX_FIELD)
+            fx_column<true, CFL, EXT>(a, fx, fc, plan, etab, i, j, cfl);
+        else
+            fx_column<false, CFL, EXT>(a, fx, fc, plan, etab, i, j, cfl);
     }
     if (CFL) block_max_to_global(cfl, a.cfl_max);
 }

@@ -55,6 +55,17 @@ def test_argument_validation_without_gpu(lib):
     assert L.ac_init(None, ctypes.byref(g), ctypes.byref(p), None) == lib.AC_ERR_ARG
     assert L.ac_integrate_substep(None, 1e-3, 0) == lib.AC_ERR_ARG
     assert L.ac_quit(None) == lib.AC_OK
+    # the allocation-free reduction checks grid and parameters as ac_init does,
+    # before any CUDA call (an infinite box length would make every derivative 0)
+    fake = [8 * (q + 1) for q in range(8)]
+    for bad in [lib.make_grid((4, 4, 4), L=(float("inf"), 1, 1)), lib.make_grid((0, 4, 4)),
+                lib.make_grid((4, 4, 8193))]:
+        with pytest.raises(lib.AcError) as ei:
+            lib.ac_reduce_noalloc(fake, bad, p, lib.AC_MAX, lib.AC_UX)
+        assert ei.value.code == lib.AC_ERR_ARG
+    with pytest.raises(lib.AcError) as ei:
+        lib.ac_reduce_noalloc(fake, g, lib.make_params(eta=float("inf")), lib.AC_MAX, lib.AC_UX)
+    assert ei.value.code == lib.AC_ERR_ARG
     # the bounded-wait diagnostic checks its limit before touching the device
     assert lib.ac_diag_wait_timeout(0) == lib.AC_ERR_ARG
     assert lib.ac_diag_wait_timeout((1 << 18) + 1) == lib.AC_ERR_ARG

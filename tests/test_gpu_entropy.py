@@ -49,8 +49,7 @@ def _run(n, L, layout, precision, phys, order=6, mode=None, seed=4):
     w = None
     errs = []
     for s in range(3):
-        k, e, phi = ac.ac_forcing_draw(seed, 0)
-        p = core.Params(n=n, L=L, forcing=core.Forcing(k, e, phi, 0.05), order=order, **phys,
+        p = core.Params(n=n, L=L, forcing=core.forcing_draw(seed, 0, 0.05), order=order, **phys,
                         **TERMS)
         fo, wo = core.substep(fcur, w, p, 1e-3, s)
         sim.substep(1e-3, s)

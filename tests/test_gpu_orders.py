@@ -49,8 +49,7 @@ def _run(n, order, layout, precision, L, phys, seed, steps=3):
     dt = 1e-3
     errs = []
     for s in range(steps):
-        k, e, phi = ac.ac_forcing_draw(seed, 0)
-        p = core.Params(n=n, L=L, forcing=core.Forcing(k, e, phi, 0.05), order=order, **phys)
+        p = core.Params(n=n, L=L, forcing=core.forcing_draw(seed, 0, 0.05), order=order, **phys)
         fo, wo = core.substep(fcur, w, p, dt, s)
         sim.substep(dt, s)
         fg, wg = sim.store(), sim.store_w()

@@ -67,8 +67,7 @@ def test_fp64_substeps_match_oracle(n, layout):
     dt = 1e-3
     w = None
     for s in range(3):
-        k, e, phi = ac.ac_forcing_draw(2, 0)
-        p = _oracle_params(n, L=L, forcing=core.Forcing(k, e, phi, 0.05), **phys)
+        p = _oracle_params(n, L=L, forcing=core.forcing_draw(2, 0, 0.05), **phys)
         fo, wo = core.substep(f, w, p, dt, s)
         sim.substep(dt, s)
         fg, wg = sim.store(), sim.store_w()
@@ -99,8 +98,7 @@ def test_fp64_equal_spacing_substeps_match_oracle(n, mode):
     dt = 1e-3
     w = None
     for s in range(3):
-        k, e, phi = ac.ac_forcing_draw(2, 0)
-        p = _oracle_params(n, L=L, forcing=core.Forcing(k, e, phi, 0.05), **phys)
+        p = _oracle_params(n, L=L, forcing=core.forcing_draw(2, 0, 0.05), **phys)
         fo, wo = core.substep(f, w, p, dt, s)
         sim.substep(dt, s)
         fg, wg = sim.store(), sim.store_w()
@@ -237,8 +235,7 @@ def test_fp32_within_bound(precision, ftol, wtol, n, layout):
     w = None
     fcur = f32
     for s in range(3):
-        k, e, phi = ac.ac_forcing_draw(3, 0)
-        p = _oracle_params(n, forcing=core.Forcing(k, e, phi, 0.05))
+        p = _oracle_params(n, forcing=core.forcing_draw(3, 0, 0.05))
         fo, wo = core.substep(fcur, w, p, dt, s)
         sim.substep(dt, s)
         fg, wg = sim.store(), sim.store_w()
@@ -377,8 +374,7 @@ def test_full_size_256_sampled(precision):
     sim.load(f)
     cells = sample_cells(n, 3000, seed=7)
     w = None
-    k, e, phi = ac.ac_forcing_draw(2, 0)
-    p = _oracle_params(n, forcing=core.Forcing(k, e, phi, 0.05))
+    p = _oracle_params(n, forcing=core.forcing_draw(2, 0, 0.05))
     for s in range(3):
         fo, wo = core.substep_cells(f, w, p, 1e-3, s, cells)
         sim.substep(1e-3, s)
@@ -402,8 +398,7 @@ def test_full_size_512_fp32_sampled():
     f = sim.store()  # the binary32 state the device holds, widened
     cells = sample_cells(n, 2000, seed=8)
     idx = (cells[:, 2], cells[:, 1], cells[:, 0])
-    k, e, phi = ac.ac_forcing_draw(3, 0)
-    p = _oracle_params(n, forcing=core.Forcing(k, e, phi, 0.05))
+    p = _oracle_params(n, forcing=core.forcing_draw(3, 0, 0.05))
     w = None
     for s in range(2):
         fo, wo = core.substep_cells(f, w, p, 1e-3, s, cells)
