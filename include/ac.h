@@ -211,10 +211,12 @@ int ac_get_stencil_order(const ac_handle *h, int *order);
  * numerators with a common coefficient is then exact and only one int64 ->
  * binary64 conversion and one multiplication per derivative term run on the
  * FP64 pipe.  The device picks, per substep, one of three modes (counted by
- * ac_get_stencil_modes): AC_STENCIL_MODE_GROUP when the components of u and of
- * A each share one E (their cross-component sums stay single integers);
- * AC_STENCIL_MODE_FIELD otherwise (each field keeps its own scale; the sums
- * across components are added in binary64); AC_STENCIL_MODE_PLAIN when the
+ * ac_get_stencil_modes): AC_STENCIL_MODE_GROUP when the exponents E of the
+ * components of u (and of A) lie within one binade of each other (they share
+ * the largest, so a component keeps at least 49 bits of its own range, and the
+ * cross-component sums stay single integers); AC_STENCIL_MODE_FIELD otherwise
+ * (each field keeps its own scale; the sums across components are added in
+ * binary64); AC_STENCIL_MODE_PLAIN when the
  * state holds a NaN or an infinity or a range outside [2^-960, 2^960) (plain
  * binary64 stencils, the AC_STENCIL_FP64 arithmetic, so non-finite values
  * propagate as the definition does and show in ac_last_cfl).  The result stays
@@ -241,6 +243,21 @@ int ac_get_stencil_modes(ac_handle *h, unsigned long long counts[3]);
 
 /* Substeps 0, 1, 2 with the same dt (one full Runge-Kutta step). */
 int ac_integrate_step(ac_handle *h, double dt);
+
+/*
+ * Kernel timing (no counterpart in the paper; for the roofline of the substep
+ * kernel).  While on, every ac_integrate_substep records CUDA events on the
+ * handle's stream around its preparation kernels (on the integer-sum path: the
+ * field extremes, the plan and the quantisation) and around the substep kernel
+ * itself, for up to AC_TIMING_MAX substeps after the call that switched it on.
+ * ac_kernel_timings waits for the last recorded substep and returns, per
+ * substep index s, the average preparation and kernel times in milliseconds and
+ * how many substeps were recorded; it then clears the records.  Turning timing
+ * on creates 3 * AC_TIMING_MAX events (freed by ac_quit).
+ */
+#define AC_TIMING_MAX 1024
+int ac_set_kernel_timing(ac_handle *h, int on);
+int ac_kernel_timings(ac_handle *h, double prep_ms[3], double kernel_ms[3], int count[3]);
 
 /*
  * Largest CFL speed |u| + sqrt(c_s^2 + |B|^2 / rho) over the cells of the state

@@ -84,31 +84,40 @@ class Net:
             params.append((W, b))
         return Net(params)
 
-    def forward(self, x, round_bf16=False):
-        """Returns (y, cache).  With round_bf16, weights and the inputs of every
-        layer are rounded to bfloat16 first (the arithmetic of the GPU kernels:
-        bfloat16 operands, wider accumulation)."""
-        r = bf16_round if round_bf16 else (lambda a: a)
+    # Precision of an evaluation (the `bf16` argument):
+    #   None      -- binary64 throughout;
+    #   "config"  -- what the configuration fixes: bfloat16 weights (and the
+    #                bfloat16 network input, the first layer's operand); every
+    #                other value, forward and backward, in binary64;
+    #   "kernel"  -- a diagnostic: also bfloat16 wherever the GPU kernels store
+    #                an operand in bfloat16 (hidden activations, and in the
+    #                backward pass the output gradient and the masked input
+    #                gradients), binary64 accumulation.
+    # `perturb` (with bf16="config") replaces the rounding at those kernel
+    # points by a given function, for the spread estimate below.
+    def forward(self, x, bf16=None, perturb=None):
+        """Returns (y, activations): the input of every layer."""
+        r = bf16_round if bf16 else (lambda a: a)
+        rk = perturb or (bf16_round if bf16 == "kernel" else (lambda a: a))
         acts = [r(x)]
         h = acts[0]
         for li, (W, b) in enumerate(self.params):
             z = conv3d(h, r(W), b)
             if li < len(self.params) - 1:
-                h = r(np.maximum(z, 0.0))
+                h = rk(np.maximum(z, 0.0))
                 acts.append(h)
             else:
                 h = z
         return h, acts
 
-    def loss_and_grads(self, x, target, round_bf16=False):
-        """Mean squared error and its gradients.  With round_bf16, the output
-        gradient and the gradients passed back through each ReLU are rounded to
-        bfloat16 as well (they are the operands of the backward convolutions)."""
-        r = bf16_round if round_bf16 else (lambda a: a)
-        y, acts = self.forward(x, round_bf16)
+    def loss_and_grads(self, x, target, bf16=None, perturb=None):
+        """Mean squared error and its gradients (precision as in forward)."""
+        r = bf16_round if bf16 else (lambda a: a)
+        rk = perturb or (bf16_round if bf16 == "kernel" else (lambda a: a))
+        y, acts = self.forward(x, bf16, perturb)
         n = y.size
         loss = float(np.mean((y - target) ** 2))
-        dy = r(2.0 * (y - target) / n)
+        dy = rk(2.0 * (y - target) / n)
         grads = [None] * len(self.params)
         for li in reversed(range(len(self.params))):
             W, b = self.params[li]
@@ -116,8 +125,37 @@ class Net:
             grads[li] = (dW, db)
             if li > 0:
                 da = conv3d_input_grad(dy, r(W))
-                dy = r(da * (acts[li] > 0))
+                dy = rk(da * (acts[li] > 0))
         return loss, grads
+
+    def rounding_spread(self, x, target=None, samples=16, seed=0):
+        """Elementwise standard deviation of the output (target None) or of the
+        gradients that bfloat16 rounding at the GPU kernels' rounding points
+        produces around the bf16="config" evaluation, under the probabilistic
+        model of rounding error (Higham and Mary, SIAM J. Sci. Comput. 41(5),
+        2019: each rounding an independent error, here uniform within half a
+        bfloat16 unit in the last place of the value, 2^(floor(log2|a|) - 8)),
+        estimated from `samples` evaluations with such random errors at those
+        points.  Returns sigma of y, or a list of (sigma dW, sigma db) per
+        layer."""
+        g = np.random.Generator(np.random.PCG64(seed))
+
+        def pert(a):
+            a = np.asarray(a, dtype=np.float64)
+            half_ulp = np.where(a != 0.0, np.ldexp(1.0, (np.floor(np.log2(np.abs(np.where(
+                a != 0.0, a, 1.0)))) - 8).astype(int)), 0.0)
+            return a + half_ulp * g.uniform(-1.0, 1.0, size=a.shape)
+
+        runs = []
+        for _ in range(samples):
+            if target is None:
+                runs.append(self.forward(x, "config", pert)[0])
+            else:
+                runs.append(self.loss_and_grads(x, target, "config", pert)[1])
+        if target is None:
+            return np.std(np.stack(runs), axis=0, ddof=1)
+        return [tuple(np.std(np.stack([rr[li][a] for rr in runs]), axis=0, ddof=1)
+                      for a in range(2)) for li in range(len(self.params))]
 
     def flat(self):
         """Parameters as one vector: W1, b1, W2, b2, W3, b3 (row-major)."""

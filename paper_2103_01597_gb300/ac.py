@@ -103,6 +103,8 @@ def load_library(path=None):
         "ac_get_stencil_path": ([_vp, ctypes.POINTER(_c.c_int)], _c.c_int),
         "ac_get_stencil_modes": ([_vp, ctypes.POINTER(_c.c_ulonglong)], _c.c_int),
         "ac_diag_fma_rate": ([_c.c_int, _pd, _vp], _c.c_int),
+        "ac_set_kernel_timing": ([_vp, _c.c_int], _c.c_int),
+        "ac_kernel_timings": ([_vp, _pd, _pd, ctypes.POINTER(_c.c_int)], _c.c_int),
         "ac_decomp_init": ([ctypes.POINTER(_vp), ctypes.POINTER(ac_grid),
                             ctypes.POINTER(ac_params), ctypes.POINTER(_c.c_int), _vp], _c.c_int),
         "ac_decomp_quit": ([_vp], _c.c_int),
@@ -294,6 +296,18 @@ def ac_diag_fma_rate(precision, stream=None):
     out = ctypes.c_double()
     _check(_lib.ac_diag_fma_rate(precision, ctypes.byref(out), stream), "ac_diag_fma_rate")
     return out.value
+
+
+def ac_set_kernel_timing(h, on):
+    _check(_lib.ac_set_kernel_timing(h, 1 if on else 0), "ac_set_kernel_timing")
+
+
+def ac_kernel_timings(h):
+    """(prep_ms[3], kernel_ms[3], count[3]) per substep index since timing was
+    switched on or last read."""
+    a, b, c = (ctypes.c_double * 3)(), (ctypes.c_double * 3)(), (ctypes.c_int * 3)()
+    _check(_lib.ac_kernel_timings(h, a, b, c), "ac_kernel_timings")
+    return list(a), list(b), list(c)
 
 
 def ac_last_cfl(h):

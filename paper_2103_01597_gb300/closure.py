@@ -1,8 +1,12 @@
 """Learned-closure driver: training pairs from the solver, training, rollout.
 
-This module only sequences calls into libac.so (restriction, solver steps,
-closure forward/backward/Adam/apply kernels) and holds torch-owned device
-buffers; every arithmetic step runs in the library's CUDA kernels.
+This module sequences calls into libac.so (restriction, solver steps, closure
+forward/backward/Adam/apply kernels) and holds torch-owned device buffers.
+Every step of the solver and of the network runs in the library's CUDA
+kernels.  Two pieces of training-data preparation, outside any timed step, are
+torch tensor operations: the target defect (restricted fine state minus the
+coarse step, one subtraction on the device) and the per-channel rms of the
+training set used as the network's input and output scales (channel_rms).
 
 Data (a reading; the paper only mentions learned reconstruction, Sec. 6): a
 fine binary64 run on a grid 2x finer per axis, restricted by full weighting.
@@ -122,7 +126,8 @@ def make_pairs(f0, n_fine, npairs, dt_fine, seed=0, force_amp=0.0, warm_steps=0,
 
 
 def channel_rms(tensors):
-    """Per-channel rms over a list of (8, cells) tensors (host floats)."""
+    """Per-channel rms over a list of (8, cells) tensors (host floats; torch
+    reductions on the device, data preparation only)."""
     acc = np.zeros(8)
     count = 0
     for t in tensors:

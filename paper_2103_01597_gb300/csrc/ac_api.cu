@@ -75,6 +75,11 @@ struct ac_handle {
     int ftab_valid;
     unsigned long long ftab_step;  // step whose draw the tables hold (per-step draw mode)
     unsigned long long launches;
+    // kernel timing (ac_set_kernel_timing): three events per recorded substep
+    int timing;
+    int nrec;
+    cudaEvent_t *tev;  // [AC_TIMING_MAX][3]: start, after preparation, after the substep
+    int trec_s[AC_TIMING_MAX];
 };
 
 extern "C" const char *ac_strerror(int code) {
@@ -114,7 +119,16 @@ int ac::valid_params(const ac_params *p) {
     return 1;
 }
 
+static void free_timing(ac_handle *h) {
+    if (!h->tev) return;
+    for (int i = 0; i < 3 * AC_TIMING_MAX; ++i)
+        if (h->tev[i]) cudaEventDestroy(h->tev[i]);
+    free(h->tev);
+    h->tev = nullptr;
+}
+
 static void free_handle_memory(ac_handle *h) {
+    free_timing(h);
     if (h->owned_block) cudaFree(h->owned_block);
     if (h->ftab) cudaFree(h->ftab);
     if (h->partials) cudaFree(h->partials);
@@ -639,7 +653,9 @@ extern "C" int ac_integrate_substep(ac_handle *h, double dt, int s) {
     L.beta = RK_BETA[s];
     L.dt = dt;
     L.s = s;
-    L.use_fx = h->stencil_mode != AC_STENCIL_FP64 && fx_applicable(h);
+    // (integer sums need 32-bit neighbour offsets: fewer than 2^31 cells per array)
+    L.use_fx = h->stencil_mode != AC_STENCIL_FP64 && fx_applicable(h) &&
+               h->g.elems < (1ll << 31);
     L.dx = h->grid.lx / h->grid.nx;
     L.fx_stats = nullptr;
     L.fx_plan = nullptr;
@@ -650,6 +666,17 @@ extern "C" int ac_integrate_substep(ac_handle *h, double dt, int s) {
         for (int q = 0; q < NF; ++q) L.fxF[q] = h->fx_block + (size_t)q * h->g.elems;
         L.fx_stats = h->fx_stats;
         L.fx_plan = h->fx_plan;
+    }
+    L.ev_mid = nullptr;
+    cudaEvent_t *tev = nullptr;
+    if (h->timing && h->nrec < AC_TIMING_MAX) {
+        tev = h->tev + 3 * h->nrec;
+        h->trec_s[h->nrec++] = s;
+        CK(cudaEventRecord(tev[0], h->stream));
+        if (L.use_fx)
+            L.ev_mid = tev[1];  // recorded by the launcher after its preparation kernels
+        else
+            CK(cudaEventRecord(tev[1], h->stream));  // no preparation kernels
     }
     L.cfl_max = nullptr;
     if (s == 0) {  // the step's input state: record its max CFL speed on the way
@@ -666,9 +693,54 @@ extern "C" int ac_integrate_substep(ac_handle *h, double dt, int s) {
         e = launch_substep_f32w64(L, h->stream, &nl);
     h->launches += nl;
     if (e != cudaSuccess) return cuda_fail(e);
+    if (tev) CK(cudaEventRecord(tev[2], h->stream));
     h->cur = 1 - h->cur;
     h->next_s = (s + 1) % 3;
     if (s == 2) h->step++;
+    return AC_OK;
+}
+
+extern "C" int ac_set_kernel_timing(ac_handle *h, int on) {
+    if (!h) return AC_ERR_ARG;
+    if (on && !h->tev) {
+        h->tev = static_cast<cudaEvent_t *>(calloc(3 * AC_TIMING_MAX, sizeof(cudaEvent_t)));
+        if (!h->tev) return AC_ERR_OOM;
+        for (int i = 0; i < 3 * AC_TIMING_MAX; ++i) {
+            cudaError_t e = cudaEventCreate(&h->tev[i]);
+            if (e != cudaSuccess) {
+                free_timing(h);
+                return cuda_fail(e);
+            }
+        }
+    }
+    h->timing = on != 0;
+    h->nrec = 0;
+    return AC_OK;
+}
+
+extern "C" int ac_kernel_timings(ac_handle *h, double prep_ms[3], double kernel_ms[3],
+                                 int count[3]) {
+    if (!h || !prep_ms || !kernel_ms || !count) return AC_ERR_ARG;
+    for (int s = 0; s < 3; ++s) {
+        prep_ms[s] = kernel_ms[s] = 0.0;
+        count[s] = 0;
+    }
+    if (h->nrec) CK(cudaEventSynchronize(h->tev[3 * (h->nrec - 1) + 2]));
+    for (int r = 0; r < h->nrec; ++r) {
+        float a = 0.f, b = 0.f;
+        CK(cudaEventElapsedTime(&a, h->tev[3 * r], h->tev[3 * r + 1]));
+        CK(cudaEventElapsedTime(&b, h->tev[3 * r + 1], h->tev[3 * r + 2]));
+        const int s = h->trec_s[r];
+        prep_ms[s] += a;
+        kernel_ms[s] += b;
+        count[s]++;
+    }
+    for (int s = 0; s < 3; ++s)
+        if (count[s]) {
+            prep_ms[s] /= count[s];
+            kernel_ms[s] /= count[s];
+        }
+    h->nrec = 0;
     return AC_OK;
 }
 

@@ -109,6 +109,9 @@ struct SubstepLaunch {
     unsigned long long *fx_stats;
     void *fx_plan;
     double dx;
+    // optional: recorded after the preparation kernels (integer-sum path:
+    // extremes, plan, quantisation), before the substep kernel itself
+    cudaEvent_t ev_mid;
 };
 size_t fx_plan_bytes();
 // Substeps run in each mode (group scales, per-field scales, plain binary64)

@@ -46,6 +46,10 @@ cudaError_t launch_substep_f64(const SubstepLaunch &L, cudaStream_t st, int *lau
     fx_stats_kernel<<<fx_grid(n), 256, 0, st>>>(fx, n, L.fx_stats);
     fx_plan_kernel<<<1, 32, 0, st>>>(L.fx_stats, plan);
     fx_quantize_kernel<<<fx_grid(n), 256, 0, st>>>(fx, n, plan);
+    if (L.ev_mid) {
+        e = cudaEventRecord(L.ev_mid, st);
+        if (e != cudaSuccess) return e;
+    }
 
     const dim3 block(32, 4, 1);
     const unsigned gx = (L.g.nx + block.x - 1) / block.x;
@@ -56,11 +60,17 @@ cudaError_t launch_substep_f64(const SubstepLaunch &L, cudaStream_t st, int *lau
     a.zchunk = zchunk;
     const dim3 grid(gx, gy, (L.g.nz + zchunk - 1) / zchunk);
     const bool ext = L.ph.ext(), cfl = a.cfl_max != nullptr;
-#define AC_FX(C, X) substep_fx_kernel<C, X><<<grid, block, 0, st>>>(a, fx, fc, plan)
+    // one kernel per mode; the two the plan did not choose return at once
+#define AC_FX(C, X)                                                            \
+    do {                                                                       \
+        substep_fx_kernel<false, C, X><<<grid, block, 0, st>>>(a, fx, fc, plan); \
+        substep_fx_kernel<true, C, X><<<grid, block, 0, st>>>(a, fx, fc, plan);  \
+        substep_fx_plain_kernel<C, X><<<grid, block, 0, st>>>(a, plan);          \
+    } while (0)
     if (ext) { if (cfl) AC_FX(true, true); else AC_FX(false, true); }
     else { if (cfl) AC_FX(true, false); else AC_FX(false, false); }
 #undef AC_FX
-    *launches += 4;
+    *launches += 6;
     return cudaGetLastError();
 }
 

@@ -17,19 +17,21 @@
 //
 // A plan kernel picks one of three modes per substep from the fields' ranges,
 // on the device (no host round trip):
-//  * FX_GROUP: the three components of u (and of A) have the same E, so they
-//    share one scale and the cross-component sums stay single integers;
-//  * FX_FIELD: some component's E is below its group's largest, so every field
-//    keeps its own scale and the cross-component sums (curl A, grad(div u),
-//    grad(div A)) add per-field binary64 terms instead -- a component far
-//    smaller than the others (a near-2-D flow, a weak field component) is
-//    resolved to 2^-50 of its own range either way;
+//  * FX_GROUP: the exponents E of the three components of u (and of A) lie
+//    within one binade of each other, so they share the largest as one scale
+//    (a component keeps at least 49 bits of its own range) and the
+//    cross-component sums stay single integers;
+//  * FX_FIELD: some component lies further below its group's largest, so every
+//    field keeps its own scale and the cross-component sums (curl A,
+//    grad(div u), grad(div A)) add per-field binary64 terms instead -- a
+//    component far smaller than the others (a near-2-D flow, a weak field
+//    component) is resolved to 2^-50 of its own range;
 //  * FX_PLAIN: a NaN or infinity in the state, or a range outside
 //    [2^-960, 2^960): the substep runs plain binary64 stencils, exactly what
 //    AC_STENCIL_FP64 computes (so a non-finite value propagates as in the
 //    definition and shows in the step's CFL word).
 // The quantisation error of every stencil input is then at most half a unit
-// of 2^(E - 50), E the field's own exponent: within a factor of about three of
+// of 2^(E - 49), E the field's own exponent: within a factor of about six of
 // the worst-case binary64 rounding of the same stencil.
 #pragma once
 
@@ -38,6 +40,7 @@
 namespace ac {
 
 constexpr int FX_BITS = 50;
+constexpr int FX_GROUP_SLACK = 1;  // binades a component may lie below its group's largest
 enum { FX_GROUP = 0, FX_FIELD = 1, FX_PLAIN = 2 };
 
 // Field -> group: 0 = ln rho, 1 = u, 2 = s, 3 = A.
@@ -52,11 +55,6 @@ __device__ __forceinline__ unsigned long long fx_key(unsigned long long b) {
 }
 __device__ __forceinline__ double fx_unkey(unsigned long long k) {
     return __longlong_as_double((long long)((k >> 63) ? (k & 0x7fffffffffffffffull) : ~k));
-}
-
-// 2^k as a binary64 built from its bits (|k| < 1000).
-__device__ __forceinline__ double fx_pow2(int k) {
-    return __longlong_as_double((long long)(k + 1023) << 52);
 }
 
 // round(v 2^(FX_BITS - E)) modulo 2^64 for the binary64 v held in `b` (round
@@ -92,9 +90,8 @@ struct FxPtrs {
 struct FxPlan {
     int mode;                  // FX_GROUP, FX_FIELD or FX_PLAIN
     int zero[NF];              // constant field: F = 0
-    int E[NF];                 // F = round((f - c) 2^(FX_BITS - E)) - the offset
+    int E[NF];                 // F = round((f - c) 2^(FX_BITS - E)); the scale is 2^(E - FX_BITS)
     unsigned long long C[NF];  // round(c 2^(FX_BITS - E)) modulo 2^64
-    double scale[NF];          // 2^(E - FX_BITS); in FX_GROUP equal within a group
     unsigned long long taken[3];  // substeps run in each mode (cumulative)
 };
 
@@ -166,7 +163,10 @@ __global__ void fx_plan_kernel(const unsigned long long *stats, FxPlan *plan) {
         const int er = __shfl_sync(0xffffffffu, e, r);
         if (fx_group(r) == g && er > eg) eg = er;
     }
-    const int disparity = q < NF && !zero && e < eg;
+    // group scales while every component's exponent is within one binade of its
+    // group's largest (a component then keeps at least 49 bits of its own
+    // range); a larger disparity takes per-field scales
+    const int disparity = q < NF && !zero && e < eg - FX_GROUP_SLACK;
     const int any_bad = __any_sync(0xffffffffu, bad);
     const int any_disp = __any_sync(0xffffffffu, disparity);
     const int mode = any_bad ? FX_PLAIN : (any_disp ? FX_FIELD : FX_GROUP);
@@ -177,7 +177,6 @@ __global__ void fx_plan_kernel(const unsigned long long *stats, FxPlan *plan) {
         plan->zero[q] = zero;
         plan->E[q] = E;
         plan->C[q] = fx_round_grid((unsigned long long)__double_as_longlong(c), E);
-        plan->scale[q] = valid && mode != FX_PLAIN ? fx_pow2(E - FX_BITS) : 0.0;
     }
     if (q == 0) {
         plan->mode = mode;
@@ -273,29 +272,17 @@ template <bool PF, bool CFL, bool EXT>
 __device__ __forceinline__ void fx_column(const SubstepArgs<double, double> &a, const FxPtrs &fx,
                                           const FxCoefs &fc, const FxPlan *plan,
                                           const double *etab, int i, int j, double &cfl) {
-    // FX_GROUP: four group scales folded into the coefficients (registers).
-    // FX_FIELD: each field's scale 2^(E - FX_BITS) is applied to its converted
-    // numerators by an exponent add (fx_scaled), so only the grid coefficients
-    // (kernel parameters) multiply, and per-field scales cost no FP64 work.
-    double sc[NF];
+    // Each field's scale 2^(E - FX_BITS) is applied to its converted numerators
+    // by an exponent add on the integer pipe (fx_scaled), so only the grid
+    // coefficients -- kernel parameters, read from the constant bank -- multiply
+    // on the FP64 pipe, and no scaled coefficient occupies registers (the
+    // kernels sit at 255 registers).  In FX_GROUP the components of u and of A
+    // share their exponent.
     int kh[NF];
 #pragma unroll
-    for (int q = 0; q < NF; ++q) {
-        sc[q] = plan->scale[q];
-        kh[q] = (plan->E[q] - FX_BITS) << 20;
-    }
-    double c1[NF];
-#pragma unroll
-    for (int q = 0; q < NF; ++q) c1[q] = sc[q] * fc.inv60dx;
-    const double clu = sc[1] * fc.nu180, cgu = sc[1] * fc.nu2160;
-    const double cla = sc[5] * fc.inv180dx2, cga = sc[5] * fc.inv720dx2;
+    for (int q = 0; q < NF; ++q) kh[q] = (plan->E[q] - FX_BITS) << 20;
     // first derivative of field q from its numerator
-    auto d1 = [&](long long N, int q) -> double {
-        if constexpr (PF)
-            return fx_scaled(N, kh[q]) * fc.inv60dx;
-        else
-            return (double)N * c1[q];
-    };
+    auto d1 = [&](long long N, int q) -> double { return fx_scaled(N, kh[q]) * fc.inv60dx; };
     const int k0 = blockIdx.z * a.zchunk;
     const int k1 = min(k0 + a.zchunk, a.g.nz);
     IdxPeriodic32 ix;
@@ -354,9 +341,9 @@ __device__ __forceinline__ void fx_column(const SubstepArgs<double, double> &a, 
             B[1] = (fx_scaled(nd1<2>(Fa[0]), kh[5]) - fx_scaled(nd1<0>(Fa[2]), kh[7])) * fc.inv60dx;
             B[2] = (fx_scaled(nd1<0>(Fa[1]), kh[6]) - fx_scaled(nd1<1>(Fa[0]), kh[5])) * fc.inv60dx;
         } else {
-            B[0] = (double)(nd1<1>(Fa[2]) - nd1<2>(Fa[1])) * c1[5];
-            B[1] = (double)(nd1<2>(Fa[0]) - nd1<0>(Fa[2])) * c1[5];
-            B[2] = (double)(nd1<0>(Fa[1]) - nd1<1>(Fa[0])) * c1[5];
+            B[0] = d1(nd1<1>(Fa[2]) - nd1<2>(Fa[1]), 5);
+            B[1] = d1(nd1<2>(Fa[0]) - nd1<0>(Fa[2]), 5);
+            B[2] = d1(nd1<0>(Fa[1]) - nd1<1>(Fa[0]), 5);
         }
         // lap V_i = sum_a N2_aa(V_i) / (180 dx^2);
         // grad(div V)_i = [4 N2_ii(V_i) + NX_ij(V_j) + NX_ik(V_k)] / (720 dx^2);
@@ -468,9 +455,9 @@ __device__ __forceinline__ void fx_column(const SubstepArgs<double, double> &a, 
             }
 #pragma unroll
             for (int m = 0; m < 3; ++m) {
-                viscl[m] = (double)LU[m] * clu + (double)GU[m] * cgu;
-                lapa[m] = (double)LA[m] * cla;
-                J[m] = (double)GA[m] * cga - lapa[m];
+                viscl[m] = fma(fx_scaled(LU[m], kh[1]), fc.nu180, fx_scaled(GU[m], kh[1]) * fc.nu2160);
+                lapa[m] = fx_scaled(LA[m], kh[5]) * fc.inv180dx2;
+                J[m] = fma(fx_scaled(GA[m], kh[5]), fc.inv720dx2, -lapa[m]);
             }
         }
         // EXT: lap xi = gamma / c_p lap s + (gamma - 1) lap ln rho (conduction)
@@ -479,11 +466,8 @@ __device__ __forceinline__ void fx_column(const SubstepArgs<double, double> &a, 
             const long long l0 = Fl(0, 0, 0), s0 = Fs(0, 0, 0);
             const long long LL = nd2<0>(Fl, l0) + nd2<1>(Fl, l0) + nd2<2>(Fl, l0);
             const long long LS = nd2<0>(Fs, s0) + nd2<1>(Fs, s0) + nd2<2>(Fs, s0);
-            const double ls = PF ? fx_scaled(LS, kh[4]) * fc.inv180dx2
-                                 : (double)LS * (sc[4] * fc.inv180dx2);
-            const double ll = PF ? fx_scaled(LL, kh[0]) * fc.inv180dx2
-                                 : (double)LL * (sc[0] * fc.inv180dx2);
-            lapxi = a.k.gamma_cp * ls + a.k.gm1 * ll;
+            lapxi = a.k.gamma_cp * (fx_scaled(LS, kh[4]) * fc.inv180dx2) +
+                    a.k.gm1 * (fx_scaled(LL, kh[0]) * fc.inv180dx2);
         }
         if constexpr (!CFL) {
             lnrho = ldg(a.fin[0] + o);
@@ -506,34 +490,34 @@ __device__ __forceinline__ void fx_column(const SubstepArgs<double, double> &a, 
     }
 }
 
-// The substep on the mode the plan chose (uniform over the grid): integer sums
-// with group or per-field scales, or plain binary64 stencils (FX_PLAIN).  Two
-// CTAs of 128 threads per SM (8 warps, as many as 255 registers allow): with
-// the minimum stated, ptxas fits the group-scale body in 254 registers without
-// the spills it otherwise makes (+4% at 256^3; a cap of 168 registers for 12
-// warps spills and is slower).
-template <bool CFL, bool EXT = false>
+// The substep in one mode of the plan: each mode is its own kernel (its own
+// register allocation: in one kernel with all three bodies ptxas spilled the
+// group-scale body, 16 B per cell at 128^3, and it ran 3-10% slower), launched
+// every substep; the two kernels whose mode the plan did not choose return at
+// once.  Two CTAs of 128 threads per SM (8 warps, as many as 255 registers
+// allow): with the minimum stated, ptxas keeps the body within 255 registers
+// (a cap of 168 registers for 12 warps spills and is slower).
+template <bool PF, bool CFL, bool EXT = false>
 __global__ void __launch_bounds__(128, 2) substep_fx_kernel(const SubstepArgs<double, double> a,
                                                          const FxPtrs fx, FxCoefs fc,
                                                          const FxPlan *plan) {
-    const int mode = plan->mode;
-    if (mode == FX_PLAIN) {
-        substep_body<double, double, IdxPeriodic32, CFL, 3, EXT>(a);
-        return;
-    }
+    if (plan->mode != (PF ? FX_FIELD : FX_GROUP)) return;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const int j = blockIdx.y * blockDim.y + threadIdx.y;
     const bool active = i < a.g.nx && j < a.g.ny;
     __shared__ double etab[512];
     exp_tab_stage(etab);
     double cfl = 0.0;
-    if (active) {
-        if (mode == FX_FIELD)
-            fx_column<true, CFL, EXT>(a, fx, fc, plan, etab, i, j, cfl);
-        else
-            fx_column<false, CFL, EXT>(a, fx, fc, plan, etab, i, j, cfl);
-    }
+    if (active) fx_column<PF, CFL, EXT>(a, fx, fc, plan, etab, i, j, cfl);
     if (CFL) block_max_to_global(cfl, a.cfl_max);
+}
+
+// FX_PLAIN: plain binary64 stencils, the arithmetic of AC_STENCIL_FP64.
+template <bool CFL, bool EXT = false>
+__global__ void __launch_bounds__(128) substep_fx_plain_kernel(const SubstepArgs<double, double> a,
+                                                              const FxPlan *plan) {
+    if (plan->mode != FX_PLAIN) return;
+    substep_body<double, double, IdxPeriodic32, CFL, 3, EXT>(a);
 }
 
 }  // namespace ac

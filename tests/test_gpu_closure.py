@@ -1,10 +1,19 @@
 """GPU tests of the learned closure (restriction, conv net forward, backward,
 Adam, guarded application) against the FP64 oracle, and of what training buys.
 
-Tolerances: restriction 1e-6 relative (binary32 output of a binary64 sum);
-forward and gradients 2e-2 relative per tensor in the max norm (bfloat16
-operands on both sides, binary32 vs binary64 accumulation and the occasional
-different bfloat16 rounding of an intermediate); Adam 1e-5.
+The oracle evaluates the net at the precision the configuration fixes
+(bfloat16 weights and network input, everything else binary64).  The kernels
+also store the hidden activations, the output gradient and the masked input
+gradients as bfloat16 MMA operands; the difference that makes is bfloat16
+rounding noise, whose spread sigma per element the oracle estimates (Monte
+Carlo over random rounding errors at those points, the probabilistic model of
+Higham and Mary).  Each tensor must lie within 4 sigma in the L2 norm and 6
+sigma in the max norm of the configuration-precision oracle (the oracle's own
+kernel-point rounding, a deterministic instance, measures at most 1.7 and 2.8:
+test_oracle_closure.py).  As a diagnostic, each tensor is also compared with
+the oracle evaluated with bfloat16 at the kernel's rounding points, 2e-2
+relative in the max norm (binary32 vs binary64 accumulation).  Restriction:
+1e-6 relative (binary32 output of a binary64 sum); Adam 1e-4 of the update.
 """
 import math
 
@@ -36,6 +45,16 @@ def _rows(t):
 
 def _maxrel(g, o):
     return float(np.max(np.abs(g - o)) / np.max(np.abs(o)))
+
+
+def _within_spread(g, o, sigma, what):
+    """g against the configuration-precision oracle o, in units of the bfloat16
+    rounding spread sigma: L2 ratio <= 4 and max-norm ratio <= 6."""
+    d = np.asarray(g, dtype=np.float64) - o
+    l2 = float(np.linalg.norm(d) / np.linalg.norm(sigma))
+    mx = float(np.max(np.abs(d)) / np.max(sigma))
+    print("%s: deviation / rounding spread: L2 %.2f, max %.2f" % (what, l2, mx))
+    assert l2 <= 4.0 and mx <= 6.0, (what, l2, mx)
 
 
 def test_restriction_matches_oracle():
@@ -80,9 +99,11 @@ def test_forward_matches_oracle(n, path):
     got = c.correction(_dev(x)).double().cpu().numpy().reshape((8,) + x.shape[1:])
     c.status()
     xn = x / ins.astype(np.float64)[:, None, None, None]
-    y, _ = net.forward(xn, round_bf16=True)
-    ref = y * outs.astype(np.float64)[:, None, None, None]
-    assert _maxrel(got, ref) <= 2e-2, _maxrel(got, ref)
+    sc = outs.astype(np.float64)[:, None, None, None]
+    y, _ = net.forward(xn, bf16="config")
+    _within_spread(got, y * sc, net.rounding_spread(xn) * sc, "forward %s" % (n,))
+    yk, _ = net.forward(xn, bf16="kernel")  # diagnostic: the kernel's rounding points
+    assert _maxrel(got, yk * sc) <= 2e-2, _maxrel(got, yk * sc)
     c.close()
 
 
@@ -105,7 +126,7 @@ def test_forward_paths_agree_at_64_cubed():
         assert _maxrel(outs_[0], o) <= 1e-2, _maxrel(outs_[0], o)
     # every cell against the oracle
     xn = x / ins.astype(np.float64)[:, None, None, None]
-    y, _ = net.forward(xn, round_bf16=True)
+    y, _ = net.forward(xn, bf16="kernel")  # diagnostic: the kernel's rounding points
     ref = (y * outs.astype(np.float64)[:, None, None, None]).reshape(8, -1)
     assert _maxrel(outs_[0], ref) <= 2e-2, _maxrel(outs_[0], ref)
 
@@ -135,15 +156,19 @@ def test_gradients_and_adam_match_oracle(path):
     g = ac.ac_closure_get_grads(c.c).astype(np.float64)
     xn = x / ins.astype(np.float64)[:, None, None, None]
     tn = tgt / outs.astype(np.float64)[:, None, None, None]
-    lo, go = net.loss_and_grads(xn, tn, round_bf16=True)
+    lo, go = net.loss_and_grads(xn, tn, bf16="config")
     assert abs(loss - lo) <= 1e-3 * lo, (loss, lo)
-    go_flat = oc.Net(go).flat()
+    spread = net.rounding_spread(xn, tn)
+    _, gk = net.loss_and_grads(xn, tn, bf16="kernel")  # diagnostic
     off = 0
-    for li, (W, b) in enumerate(go):
-        for arr in (W, b):
-            sz = arr.size
-            err = _maxrel(g[off:off + sz], go_flat[off:off + sz])
-            assert err <= 2e-2, (li, arr.shape, err)
+    for li in range(3):
+        for a in range(2):
+            sz = go[li][a].size
+            gg = g[off:off + sz]
+            _within_spread(gg, go[li][a].ravel(), spread[li][a].ravel(),
+                           "gradient layer %d %s" % (li + 1, "Wb"[a]))
+            err = _maxrel(gg, gk[li][a].ravel())
+            assert err <= 2e-2, (li, a, err)
             off += sz
     # one Adam step on the GPU's own gradients
     ac.ac_closure_adam_step(c.c, 1e-3)

@@ -50,7 +50,7 @@ def expected_mode(f):
         e[q] = math.frexp(r)[1]  # smallest E with r < 2^E
     for g in GROUPS:
         es = [e[q] for q in g if q in e]
-        if es and min(es) != max(es):
+        if es and min(es) < max(es) - 1:  # more than one binade apart
             return ac.AC_STENCIL_MODE_FIELD
     return ac.AC_STENCIL_MODE_GROUP
 
@@ -160,6 +160,21 @@ def test_range_at_binade_edge(at_power):
     errs, counts, want = run_substeps(f)
     assert counts == want, (counts, want)
     assert counts[ac.AC_STENCIL_MODE_GROUP] >= 1, counts
+    assert_parity(errs)
+
+
+@pytest.mark.parametrize("mz,mode", [(0.04, 0), (0.02, 1)])
+def test_one_binade_of_slack(mz, mode):
+    """u_x spans +-0.1 (E = -3), u_y +-0.05 (E = -4): one binade apart, so the
+    components share u_x's scale.  u_z at +-0.04 (E = -4) keeps group scales;
+    at +-0.02 (E = -5, two binades below u_x) it takes per-field scales."""
+    f = synthetic.smooth_state(N, seed=91, amp=0.005)
+    for q, m in ((1, 0.1), (2, 0.05), (3, mz), (5, 0.1), (6, 0.1), (7, 0.1)):
+        f[q] = pin_range(f[q], m)
+    assert expected_mode(f) == (ac.AC_STENCIL_MODE_GROUP if mode == 0 else
+                                ac.AC_STENCIL_MODE_FIELD)
+    errs, counts, want = run_substeps(f, steps=1)
+    assert counts == want, (counts, want)
     assert_parity(errs)
 
 

@@ -99,3 +99,37 @@ def test_spectrum_of_single_mode():
     E = closure.energy_spectrum(v)
     assert abs(E[3] - 0.5 * 0.7 ** 2 / 2) < 1e-14
     assert abs(E.sum() - E[3]) < 1e-14
+
+
+def _spread_case(n, seed):
+    from paper_2103_01597_gb300 import synthetic
+    net = closure.Net.init(seed)
+    net = closure.Net.unflat(net.flat().astype(np.float32).astype(np.float64))
+    rng = np.random.default_rng(seed)
+    x = synthetic.turbulent_state(n, seed, kmax=3, amp=0.5)
+    x = (x / (0.5 + rng.random(8))[:, None, None, None]).astype(np.float32).astype(np.float64)
+    t = rng.standard_normal(x.shape)
+    return net, x, t
+
+
+@pytest.mark.parametrize("n,seed", [((16, 12, 10), 6), ((12, 8, 6), 3), ((10, 10, 10), 11)])
+def test_bf16_rounding_spread_calibrates_the_gpu_tolerance(n, seed):
+    """The GPU closure tests accept a tensor within 4 (L2) and 6 (max norm)
+    rounding spreads of the configuration-precision oracle.  The oracle's own
+    evaluation with bfloat16 at the kernels' rounding points -- one
+    deterministic instance of that rounding -- must sit well inside (measured:
+    L2 <= 1.7, max <= 2.8), and the spread must be a small but non-zero part
+    of each tensor, so the criterion still catches a wrong term."""
+    net, x, t = _spread_case(n, seed)
+    _, gk = net.loss_and_grads(x, t, bf16="kernel")
+    _, gc = net.loss_and_grads(x, t, bf16="config")
+    sg = net.rounding_spread(x, t, samples=16)
+    yk, _ = net.forward(x, bf16="kernel")
+    yc, _ = net.forward(x, bf16="config")
+    sy = net.rounding_spread(x, samples=16)
+    pairs = [(yk, yc, sy)] + [(gk[li][a], gc[li][a], sg[li][a]) for li in range(3) for a in range(2)]
+    for g, o, s in pairs:
+        d = g - o
+        assert np.linalg.norm(d) <= 2.5 * np.linalg.norm(s)
+        assert np.max(np.abs(d)) <= 4.0 * np.max(s)
+        assert 1e-5 < np.max(s) / np.max(np.abs(o)) < 0.1
