@@ -52,13 +52,13 @@ def bytes_per_cell(elem_f, elem_w, s):
 # Nominal dense FP64 rate of one GB300 (no measured FP64 peak is provided).
 FP64_NOMINAL_TFLOPS = 1.25
 # DRAM bytes per cell of one launch of the integer-sum FP64 substep kernel
-# (ncu, 128^3, substeps 1-2 variant, group-scale mode; None until the kernel
-# as it stands has been captured).
-FX_TRAFFIC_PER_CELL = None
+# (ncu, 128^3 forced, substep-1/2 variant, group scales: 423.1 MB read +
+# 236.3 MB written over 2,097,152 cells; profiles/substep_fx_128_metrics.md).
+FX_TRAFFIC_PER_CELL = (423132416 + 236319232) / 2097152
 # FP64-pipe thread instructions per cell of that kernel (ncu
-# sm__inst_executed_pipe_fp64 x 32 / cells, 128^3), substep-0 (CFL) and
-# substep-1/2 variants; None until captured.
-FX_FP64_PIPE_INST_PER_CELL = None
+# sm__inst_executed_pipe_fp64 x 32 / cells, 128^3 forced; the instruction stream
+# does not depend on the grid), per mode: substep-0 (CFL) and substep-1/2 variants.
+FX_FP64_PIPE_INST_PER_CELL = {"group": (225.3125, 199.3125), "field": (255.3125, 229.3125)}
 # DRAM bytes per cell of one launch of the binary32 tiled substep (ncu, 256^3,
 # substep 1: 1126.6 MB read + 1023.2 MB written over 16,777,216 cells)
 TILED_TRAFFIC_PER_CELL = (1126.612e6 + 1023.183e6) / 16777216
@@ -127,6 +127,9 @@ def parse():
                     help="also time a cuBLAS FP64 GEMM as a measured FP64 reference rate")
     ap.add_argument("--grid", type=int, default=0,
                     help="override the cube edge (small cases for profiling)")
+    ap.add_argument("--init", default=None, choices=["noise", "uniform", "weak_uz"],
+                    help="initial state (default: the workload's); weak_uz: noise with u_z "
+                         "scaled by 1e-3 (the integer-sum path then takes per-field scales)")
     ap.add_argument("--no-workloads", action="store_true",
                     help="default workload only: skip the other workloads of the table")
     ap.add_argument("--fp64-compare-steps", type=int, default=0,
@@ -198,7 +201,10 @@ def make_state(wl):
     from paper_2103_01597_gb300 import synthetic
     if wl["init"] == "uniform":
         return synthetic.uniform_state(wl["n"], wl["seed"])
-    return synthetic.noise_state(wl["n"], wl["seed"])
+    f = synthetic.noise_state(wl["n"], wl["seed"])
+    if wl["init"] == "weak_uz":
+        f[3] *= 1e-3
+    return f
 
 
 def dist_setup(args):
@@ -513,8 +519,13 @@ def run_ours(args, wl):
         # measured denominator: the library's DFMA-chain probe (2 flops per FMA)
         dfma = ac.ac_diag_fma_rate(ac.AC_FP64, stream.cuda_stream)
         peak = 2 * dfma / 1e12
-        group = fixed and modes[0] == sum(modes)
-        inst = FX_FP64_PIPE_INST_PER_CELL if (group and order == 6) else None
+        # the count per cell weighted by the modes the timed substeps ran (none
+        # for plain binary64 stencils, which this table does not cover)
+        inst = None
+        if fixed and order == 6 and sum(modes) and not modes[2] and not wl.get("entropy"):
+            fg = modes[0] / sum(modes)
+            G, F = FX_FP64_PIPE_INST_PER_CELL["group"], FX_FP64_PIPE_INST_PER_CELL["field"]
+            inst = [fg * G[v] + (1 - fg) * F[v] for v in range(2)]
         achieved = None
         if inst is not None:
             # FP64-pipe thread instructions of each launch, as DFMA-equivalent flops
@@ -531,8 +542,7 @@ def run_ours(args, wl):
                 # dram read + write per 256^3 launch, from the 128^3 ncu capture of the
                 # same kernel scaled by cells (profiles/substep_fx_128_metrics.md)
                 "traffic": (FX_TRAFFIC_PER_CELL * ncell
-                            if (group and FX_TRAFFIC_PER_CELL and n == (256, 256, 256))
-                            else None),
+                            if (inst is not None and modes[1] == 0) else None),
                 "kernel": ("fx_stats + fx_plan + fx_quantize + substep_fx_kernel (int64 "
                            "stencil sums)" if fixed else
                            "substep_kernel<double,double,IdxPeriodicR<%d>>" % (order // 2)),
@@ -1237,6 +1247,10 @@ def main():
         wl["desc"] = wl["desc"].replace("6th-order", "%dth-order" % args.stencil_order) + \
             " (stencil order %d)" % args.stencil_order
         wl.pop("vs", None)
+    if args.init:
+        wl["init"] = args.init
+        wl["desc"] += " (initial state: %s)" % args.init
+        wl.pop("vs", None)
     if args.grid and not wl.get("ensemble") and not wl.get("closure"):
         g = args.grid
         wl["n"] = (g, g, g)
@@ -1255,7 +1269,8 @@ def main():
         return 0
     ws, _, _ = dist_setup(args)
     if args.workload == "forced256_fp64" and ws == 1 and not args.no_workloads and \
-            not args.grid and args.stencil_order == 6 and not args.full_entropy:
+            not args.grid and args.stencil_order == 6 and not args.full_entropy and \
+            not args.init:
         line["workloads"] = run_other_workloads(args)
     print(json.dumps(line))
     return 0

@@ -510,6 +510,10 @@ extern "C" int ac_get_stencil_path(const ac_handle *h, int *fixed) {
     return AC_OK;
 }
 
+// Elements between the int64 copies of consecutive fields: even, so that every
+// copy starts on a 16-byte boundary (the quantisation stores two at a time).
+static size_t fx_stride(const ac_handle *h) { return ((size_t)h->g.elems + 1) & ~(size_t)1; }
+
 // Work areas of the integer-sum path, on first use: the int64 copies of the
 // fields, the extremes words and the plan (zeroed, so its mode counts start at 0).
 static int ensure_fx(ac_handle *h) {
@@ -517,10 +521,15 @@ static int ensure_fx(ac_handle *h) {
     long long *blk = nullptr;
     unsigned long long *stats = nullptr;
     void *plan = nullptr;
-    cudaError_t e = cudaMalloc(&blk, (size_t)NF * h->g.elems * sizeof(long long));
+    cudaError_t e = cudaMalloc(&blk, (size_t)NF * fx_stride(h) * sizeof(long long));
     if (e == cudaSuccess) e = cudaMalloc(&stats, 2 * NF * sizeof(unsigned long long));
     if (e == cudaSuccess) e = cudaMalloc(&plan, fx_plan_bytes());
     if (e == cudaSuccess) e = cudaMemsetAsync(plan, 0, fx_plan_bytes(), h->stream);
+    // extremes: largest keys start at 0, smallest at all ones (the plan kernel
+    // restores this after every read)
+    if (e == cudaSuccess) e = cudaMemsetAsync(stats, 0, NF * sizeof(unsigned long long), h->stream);
+    if (e == cudaSuccess)
+        e = cudaMemsetAsync(stats + NF, 0xff, NF * sizeof(unsigned long long), h->stream);
     if (e != cudaSuccess) {
         if (blk) cudaFree(blk);
         if (stats) cudaFree(stats);
@@ -663,7 +672,7 @@ extern "C" int ac_integrate_substep(ac_handle *h, double dt, int s) {
     if (L.use_fx) {
         rc = ensure_fx(h);
         if (rc) return rc;
-        for (int q = 0; q < NF; ++q) L.fxF[q] = h->fx_block + (size_t)q * h->g.elems;
+        for (int q = 0; q < NF; ++q) L.fxF[q] = h->fx_block + (size_t)q * fx_stride(h);
         L.fx_stats = h->fx_stats;
         L.fx_plan = h->fx_plan;
     }

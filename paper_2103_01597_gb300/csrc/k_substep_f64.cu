@@ -4,7 +4,7 @@
 
 namespace ac {
 
-static unsigned fx_grid(long long n) {
+static unsigned fx_grid(long long n) {  // n work items of one thread each
     long long b = (n + 255) / 256;
     return (unsigned)(b > 152 * 8 ? 152 * 8 : (b < 1 ? 1 : b));
 }
@@ -41,11 +41,10 @@ cudaError_t launch_substep_f64(const SubstepLaunch &L, cudaStream_t st, int *lau
 
     const long long n = L.g.elems;
     FxPlan *plan = static_cast<FxPlan *>(L.fx_plan);
-    cudaError_t e = cudaMemsetAsync(L.fx_stats, 0, 2 * NF * sizeof(unsigned long long), st);
-    if (e != cudaSuccess) return e;
-    fx_stats_kernel<<<fx_grid(n), 256, 0, st>>>(fx, n, L.fx_stats);
+    cudaError_t e;
+    fx_stats_kernel<<<fx_grid(n / 2), 256, 0, st>>>(fx, n, L.fx_stats);
     fx_plan_kernel<<<1, 32, 0, st>>>(L.fx_stats, plan);
-    fx_quantize_kernel<<<fx_grid(n), 256, 0, st>>>(fx, n, plan);
+    fx_quantize_kernel<<<fx_grid(n / 2), 256, 0, st>>>(fx, n, plan);
     if (L.ev_mid) {
         e = cudaEventRecord(L.ev_mid, st);
         if (e != cudaSuccess) return e;

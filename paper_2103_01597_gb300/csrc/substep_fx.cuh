@@ -51,7 +51,8 @@ __host__ __device__ __forceinline__ int fx_group(int q) {
 // Order-preserving map of binary64 bits to unsigned keys (NaNs sort beyond the
 // infinities of their sign) and back.
 __device__ __forceinline__ unsigned long long fx_key(unsigned long long b) {
-    return (b >> 63) ? ~b : (b | 0x8000000000000000ull);
+    // negatives: every bit flipped; positives: the sign bit set
+    return b ^ ((unsigned long long)((long long)b >> 63) | 0x8000000000000000ull);
 }
 __device__ __forceinline__ double fx_unkey(unsigned long long k) {
     return __longlong_as_double((long long)((k >> 63) ? (k & 0x7fffffffffffffffull) : ~k));
@@ -96,51 +97,76 @@ struct FxPlan {
 };
 
 // Per-field extremes of the current state: stats[q] = largest key of field q,
-// stats[NF + q] = complement of its smallest key (so that both are maxima and a
-// zero fill initialises them).  One CTA-wide reduction, then 16 atomics per CTA.
+// stats[NF + q] = its smallest key (the plan kernel resets both for the next
+// substep).  Two cells per thread and iteration (16-byte loads; the arrays are
+// 16-byte aligned), one CTA-wide reduction, then 16 atomics per CTA.
 __global__ void __launch_bounds__(256) fx_stats_kernel(FxPtrs p, long long n,
                                                        unsigned long long *stats) {
-    unsigned long long hi[NF], nlo[NF];
+    unsigned long long hi[NF], lo[NF];
 #pragma unroll
-    for (int q = 0; q < NF; ++q) hi[q] = nlo[q] = 0ull;
-    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n;
+    for (int q = 0; q < NF; ++q) {
+        hi[q] = 0ull;
+        lo[q] = ~0ull;
+    }
+    const long long n2 = n >> 1;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n2;
          t += (long long)gridDim.x * blockDim.x) {
 #pragma unroll
         for (int q = 0; q < NF; ++q) {
-            const unsigned long long k = fx_key((unsigned long long)__double_as_longlong(p.f[q][t]));
+            const double2 v = __ldg(reinterpret_cast<const double2 *>(p.f[q]) + t);
+            const unsigned long long k0 = fx_key((unsigned long long)__double_as_longlong(v.x));
+            const unsigned long long k1 = fx_key((unsigned long long)__double_as_longlong(v.y));
+            const unsigned long long kh = k0 > k1 ? k0 : k1, kl = k0 > k1 ? k1 : k0;
+            hi[q] = kh > hi[q] ? kh : hi[q];
+            lo[q] = kl < lo[q] ? kl : lo[q];
+        }
+    }
+    if ((n & 1) && blockIdx.x == 0 && threadIdx.x == 0) {
+#pragma unroll
+        for (int q = 0; q < NF; ++q) {
+            const unsigned long long k =
+                fx_key((unsigned long long)__double_as_longlong(p.f[q][n - 1]));
             hi[q] = k > hi[q] ? k : hi[q];
-            nlo[q] = ~k > nlo[q] ? ~k : nlo[q];
+            lo[q] = k < lo[q] ? k : lo[q];
         }
     }
     __shared__ unsigned long long red[2 * NF];
-    if (threadIdx.x < 2 * NF) red[threadIdx.x] = 0ull;
+    if (threadIdx.x < NF) {
+        red[threadIdx.x] = 0ull;
+        red[NF + threadIdx.x] = ~0ull;
+    }
     __syncthreads();
 #pragma unroll
     for (int q = 0; q < NF; ++q) {
-        unsigned long long a = hi[q], b = nlo[q];
+        unsigned long long a = hi[q], b = lo[q];
         for (int o = 16; o > 0; o >>= 1) {
             const unsigned long long x = __shfl_xor_sync(0xffffffffu, a, o);
             const unsigned long long y = __shfl_xor_sync(0xffffffffu, b, o);
             a = x > a ? x : a;
-            b = y > b ? y : b;
+            b = y < b ? y : b;
         }
         if ((threadIdx.x & 31) == 0) {
             atomicMax(&red[q], a);
-            atomicMax(&red[NF + q], b);
+            atomicMin(&red[NF + q], b);
         }
     }
     __syncthreads();
-    if (threadIdx.x < 2 * NF) atomicMax(&stats[threadIdx.x], red[threadIdx.x]);
+    if (threadIdx.x < NF)
+        atomicMax(&stats[threadIdx.x], red[threadIdx.x]);
+    else if (threadIdx.x < 2 * NF)
+        atomicMin(&stats[threadIdx.x], red[threadIdx.x]);
 }
 
 // One warp: lane q < NF plans field q (offset, exponent), then the lanes agree
 // on the mode.  Thread 0 also counts the substep under its mode.
-__global__ void fx_plan_kernel(const unsigned long long *stats, FxPlan *plan) {
+__global__ void fx_plan_kernel(unsigned long long *stats, FxPlan *plan) {
     const int q = threadIdx.x;
     int bad = 0, zero = 1, e = -100000;
     double c = 0.0;
     if (q < NF) {
-        const double hi = fx_unkey(stats[q]), lo = fx_unkey(~stats[NF + q]);
+        const double hi = fx_unkey(stats[q]), lo = fx_unkey(stats[NF + q]);
+        stats[q] = 0ull;        // ready for the next substep's extremes
+        stats[NF + q] = ~0ull;
         if (!isfinite(hi) || !isfinite(lo)) {
             bad = 1;
         } else {
@@ -185,7 +211,8 @@ __global__ void fx_plan_kernel(const unsigned long long *stats, FxPlan *plan) {
 }
 
 // F = round(f 2^(50 - E)) - round(c 2^(50 - E)) by integer operations on the
-// binary64 bits; nothing to do in FX_PLAIN.
+// binary64 bits; nothing to do in FX_PLAIN.  Two cells per thread and
+// iteration (16-byte loads and stores: the int64 arrays have an even stride).
 __global__ void __launch_bounds__(256) fx_quantize_kernel(FxPtrs p, long long n,
                                                           const FxPlan *plan) {
     if (plan->mode == FX_PLAIN) return;
@@ -197,12 +224,27 @@ __global__ void __launch_bounds__(256) fx_quantize_kernel(FxPtrs p, long long n,
         zero[q] = plan->zero[q];
         C[q] = plan->C[q];
     }
-    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n;
+    const long long n2 = n >> 1;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n2;
          t += (long long)gridDim.x * blockDim.x) {
 #pragma unroll
         for (int q = 0; q < NF; ++q) {
-            const unsigned long long b = (unsigned long long)__double_as_longlong(p.f[q][t]);
-            p.F[q][t] = zero[q] ? 0ll : (long long)(fx_round_grid(b, E[q]) - C[q]);
+            const double2 v = __ldg(reinterpret_cast<const double2 *>(p.f[q]) + t);
+            longlong2 o;
+            o.x = zero[q] ? 0ll
+                          : (long long)(fx_round_grid((unsigned long long)__double_as_longlong(v.x),
+                                                      E[q]) - C[q]);
+            o.y = zero[q] ? 0ll
+                          : (long long)(fx_round_grid((unsigned long long)__double_as_longlong(v.y),
+                                                      E[q]) - C[q]);
+            reinterpret_cast<longlong2 *>(p.F[q])[t] = o;
+        }
+    }
+    if ((n & 1) && blockIdx.x == 0 && threadIdx.x == 0) {
+#pragma unroll
+        for (int q = 0; q < NF; ++q) {
+            const unsigned long long b = (unsigned long long)__double_as_longlong(p.f[q][n - 1]);
+            p.F[q][n - 1] = zero[q] ? 0ll : (long long)(fx_round_grid(b, E[q]) - C[q]);
         }
     }
 }
