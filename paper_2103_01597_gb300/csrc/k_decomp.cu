@@ -256,16 +256,22 @@ static cudaError_t dc_update_box(ac_decomp *d, int si, const Box &box, double al
     for (int m = 0; m < 3; ++m) a.amp_e[m] = (R)(d->params.force_amp * d->force_e[m]);
     a.cfl_max = nullptr;
     const int ex = box.b1[0] - box.b0[0], ey = box.b1[1] - box.b0[1], ez = box.b1[2] - box.b0[2];
-    const dim3 block(128, 1, 1);
-    const unsigned gx = (unsigned)(((long long)ex * ey + 127) / 128);
-    int zc = (int)(((long long)gx * ez) / (8 * 152));
+    const bool flat = ex < 32;  // a slab a few cells thin in x
+    const dim3 block = flat ? dim3(128, 1, 1) : dim3(32, 4, 1);
+    const unsigned gx = flat ? (unsigned)(((long long)ex * ey + 127) / 128) : (unsigned)((ex + 31) / 32);
+    const unsigned gy = flat ? 1u : (unsigned)((ey + 3) / 4);
+    int zc = (int)(((long long)gx * gy * ez) / (8 * 152));
     zc = zc < 1 ? 1 : (zc > 16 ? 16 : zc);
     a.zchunk = zc;
-    const dim3 grid(gx, 1, (ez + zc - 1) / zc);
-    if (d->phys.ext())
-        substep_box_kernel<R, W, 3, true><<<grid, block, 0, st>>>(a, box);
-    else
-        substep_box_kernel<R, W, 3, false><<<grid, block, 0, st>>>(a, box);
+    const dim3 grid(gx, gy, (ez + zc - 1) / zc);
+    const bool ext = d->phys.ext();
+    if (flat) {
+        if (ext) substep_box_kernel<R, W, 3, true, true><<<grid, block, 0, st>>>(a, box);
+        else substep_box_kernel<R, W, 3, false, true><<<grid, block, 0, st>>>(a, box);
+    } else {
+        if (ext) substep_box_kernel<R, W, 3, true, false><<<grid, block, 0, st>>>(a, box);
+        else substep_box_kernel<R, W, 3, false, false><<<grid, block, 0, st>>>(a, box);
+    }
     d->launches++;
     return cudaGetLastError();
 }

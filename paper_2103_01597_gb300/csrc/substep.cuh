@@ -100,21 +100,29 @@ __device__ __forceinline__ void substep_body(const SubstepArgs<R, W> &a) {
 }
 
 // A box [b0, b1) of the interior (x, y, z), for updates of one segment of a
-// subdomain: the threads of 1-D blocks cover the box's x-y extent row by row
-// (so a slab three cells thin still keeps every lane busy), blockIdx.z its z
-// range in chunks of a.zchunk.  `ftab` holds the subdomain's own tables
-// [nx | ny | nz].
+// subdomain; blockIdx.z covers its z range in chunks of a.zchunk.  FLAT: the
+// threads of 1-D blocks cover the box's x-y extent row by row, so a slab three
+// cells thin still keeps every lane busy; otherwise 32 x 4 blocks tile it (whole
+// warps on one row: the wider boxes' loads stay coalesced).  `ftab` holds the
+// subdomain's own tables [nx | ny | nz].
 struct Box {
     int b0[3], b1[3];
 };
 
-template <typename R, typename W, int RAD, bool EXT>
+template <typename R, typename W, int RAD, bool EXT, bool FLAT>
 __global__ void __launch_bounds__(128) substep_box_kernel(const SubstepArgs<R, W> a, Box box) {
-    const int ex = box.b1[0] - box.b0[0];
-    const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (t >= (long long)ex * (box.b1[1] - box.b0[1])) return;
-    const int i = box.b0[0] + (int)(t % ex);
-    const int j = box.b0[1] + (int)(t / ex);
+    int i, j;
+    if constexpr (FLAT) {
+        const int ex = box.b1[0] - box.b0[0];
+        const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+        if (t >= (long long)ex * (box.b1[1] - box.b0[1])) return;
+        i = box.b0[0] + (int)(t % ex);
+        j = box.b0[1] + (int)(t / ex);
+    } else {
+        i = box.b0[0] + blockIdx.x * blockDim.x + threadIdx.x;
+        j = box.b0[1] + blockIdx.y * blockDim.y + threadIdx.y;
+        if (i >= box.b1[0] || j >= box.b1[1]) return;
+    }
     const int k0 = box.b0[2] + blockIdx.z * a.zchunk;
     const int k1 = min(k0 + a.zchunk, box.b1[2]);
     const auto *tx = a.ftab, *ty = a.ftab + a.g.nx, *tz = a.ftab + a.g.nx + a.g.ny;

@@ -10,6 +10,7 @@
 // periodic map of Sec. 3.3 is applied once per copied chunk.
 #pragma once
 
+#include "stencil_pair.cuh"
 #include "substep.cuh"
 
 namespace ac {
@@ -48,6 +49,21 @@ struct SmemView {
     }
 };
 
+// Two fields with the same stencil points read together as a float2 (x: q1,
+// y: q2) for the paired stencils of stencil_pair.cuh.
+template <typename R>
+struct SmemPairView {
+    const R *c1, *c2;
+    const int (&slot)[7];
+    const R (&z1)[7];
+    const R (&z2)[7];
+    __device__ __forceinline__ float2 operator()(int dx, int dy, int dz) const {
+        if (dx == 0 && dy == 0) return make_float2(z1[dz + 3], z2[dz + 3]);
+        const int o = slot[dz + 3] + dy * TT_ROW + dx;
+        return make_float2(c1[o], c2[o]);
+    }
+};
+
 template <typename R>
 struct SmemCell {
     const R *cell;  // smem + (ty + 3) * TT_ROW + tx + 4
@@ -55,6 +71,9 @@ struct SmemCell {
     const R (&zq)[NF][7];
     __device__ __forceinline__ SmemView<R> operator[](int q) const {
         return {cell + q * TT_FIELD, slot, zq[q]};
+    }
+    __device__ __forceinline__ SmemPairView<R> pair(int q1, int q2) const {
+        return {cell + q1 * TT_FIELD, cell + q2 * TT_FIELD, slot, zq[q1], zq[q2]};
     }
 };
 
@@ -239,12 +258,13 @@ __device__ __forceinline__ void tiled_body(const TA &ta, int x0, int y0, int z0,
                 frc[2] = ta.amp_e(2) * cph;
             }
             float rhs[NF];
+            // u_m with A_m and ln rho with s share every stencil: packed pairs
             if (CFL) {
                 float c;
-                cell_rhs<float, 3, EXT>(cell, ta.k(), frc, rhs, &c);
+                cell_rhs_paired<EXT>(cell, ta.k(), frc, rhs, &c);
                 cfl = (c > cfl || c != c) ? c : cfl;
             } else {
-                cell_rhs<float, 3, EXT>(cell, ta.k(), frc, rhs);
+                cell_rhs_paired<EXT>(cell, ta.k(), frc, rhs, nullptr);
             }
             const long long o =
                 AC_BC((long long)z * g.pxy + (long long)j * g.px + i, g.elems, AC_BC_TILE_OUT);
