@@ -888,6 +888,24 @@ def run_closure(args, wl):
     for x, t in held:
         corr = c.correction(x)
         defect.append(float(torch.linalg.vector_norm(t - corr) / torch.linalg.vector_norm(t)))
+    # the backward pass alone (forward, loss, input and weight gradients; no host
+    # sync, parameters unchanged) on each convolution path
+    lib = ac.load_library()
+    bx, bt = ac._ptr8(cl._rows(held[0][0])), ac._ptr8(cl._rows(held[0][1]))
+    bwd_ms = {}
+    for path, name in ((ac.AC_CONV_MMA_SYNC, "mma_sync"), (ac.AC_CONV_TCGEN05_PAIR, "tcgen05_pair"),
+                       (ac.AC_CONV_TCGEN05, "tcgen05")):
+        ac.ac_closure_set_conv_path(c.c, path)
+        for _ in range(2):
+            assert lib.ac_closure_backward(c.c, bx, bt, None) == 0
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(10):
+            lib.ac_closure_backward(c.c, bx, bt, None)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        bwd_ms[name] = e0.elapsed_time(e1) / 10
+    c.status()
 
     # timed region: coarse steps with the closure applied after each step
     sim = ac.Simulation(nc, precision=ac.AC_FP32, force_amp=wl["force_amp"], seed=wl["seed"])
@@ -1005,6 +1023,7 @@ def run_closure(args, wl):
                "heldout_loss_before_after": [base, after],
                "heldout_relative_defect_after": float(np.mean(defect)),
                "train_ms_per_iter": train_ms, "train_iters": args.closure_iters,
+               "backward_ms_per_path": bwd_ms,
                "pairs": npairs, "data_gen_s": t_data}
     for sm in (fine, plain, corr, sim):
         sm.close()

@@ -291,8 +291,13 @@ __device__ __forceinline__ void bulk_load(void *dst, const void *src, uint32_t b
 
 // Epilogues: ReLU to row-planar bfloat16 (hidden layers), or the network output
 // scaled per channel to eight binary32 channel-major arrays (optionally with the
-// largest |value|, NaN counting as largest, folded into a guard word).
-enum { EPI_RELU_BF16 = 0, EPI_SCALED_F32 = 1 };
+// largest |value|, NaN counting as largest, folded into a guard word), or (the
+// input gradient through a ReLU, training) the value where the forward
+// activation at the same cell and channel (row-planar `mask`) is positive, else
+// 0, as row-planar bfloat16.  The bfloat16 epilogues can also write a second
+// row-planar copy without the periodic halo cells (`yn`: those slots, and the
+// padding, stay zero), the gradient operand of the weight-gradient kernel.
+enum { EPI_RELU_BF16 = 0, EPI_SCALED_F32 = 1, EPI_MASK_BF16 = 2 };
 
 // Bytes of one staged row (KC planes, rounded up so rows stay 128-byte aligned).
 __host__ __device__ constexpr int row_bytes(int cin) { return (cin / 8) * PLANE; }
@@ -333,8 +338,10 @@ __device__ __forceinline__ void store_rp(bf16 *Y, long long e, uint4 v) {
 
 struct ConvTcArgs {
     const bf16 *w;        // weights in the shared-memory image order (see prep)
-    const float *bias;    // [COUT]
-    bf16 *y;              // EPI_RELU_BF16: row-planar output
+    const float *bias;    // [COUT] (not read by EPI_MASK_BF16)
+    bf16 *y;              // EPI_RELU_BF16, EPI_MASK_BF16: row-planar output (or null)
+    bf16 *yn;             // the bfloat16 epilogues: row-planar copy without halo, or null
+    const bf16 *mask;     // EPI_MASK_BF16: row-planar forward activation (COUT channels)
     float *out[8];        // EPI_SCALED_F32: channel c to out[c][cell]
     const float *out_scale;        // EPI_SCALED_F32: [8]
     unsigned long long *gmax;      // EPI_SCALED_F32: guard word (binary64 bits), or null
@@ -561,7 +568,7 @@ __global__ void __launch_bounds__(THREADS, 1)
     } else {  // ---- epilogue: warps 0-3, TMEM lanes 32 warp .. 32 warp + 31
         float bias[COUT];
 #pragma unroll
-        for (int c = 0; c < COUT; ++c) bias[c] = a.bias[c];
+        for (int c = 0; c < COUT; ++c) bias[c] = EPI == EPI_MASK_BF16 ? 0.f : a.bias[c];
         float gm = 0.f;  // EPI_SCALED_F32: this thread's largest |output| (NaN if any)
         uint32_t par = 0;  // bit k: parity of the tiles block k has held so far
         bool ok = true;
@@ -586,20 +593,37 @@ __global__ void __launch_bounds__(THREADS, 1)
                 if (lane == 0) mbar_arrive(&acce[kb]);
                 if (x >= a.nx) continue;
                 const int z = sg.z0 + i;
-                if (EPI == EPI_RELU_BF16) {
+                if (EPI == EPI_RELU_BF16 || EPI == EPI_MASK_BF16) {
                     __align__(16) bf16 o[COUT];
-#pragma unroll
-                    for (int c = 0; c < COUT; ++c) o[c] = __float2bfloat16_rn(fmaxf(v[c] + bias[c], 0.f));
                     AC_BC_ONLY(const long long lim =
                                    (long long)rp_cells(a.nx) * a.ny * a.nz * COUT;)
 #pragma unroll
                     for (int kc = 0; kc < COUT / 8; ++kc) {
-                        const uint4 val = reinterpret_cast<const uint4 *>(o)[kc];
                         const long long plane =
                             ((((long long)z * a.ny + sg.y) * (COUT / 8) + kc) * rp_cells(a.nx)) * 8;
-                        store_rp(a.y, plane + (long long)(x + 1) * 8, AC_BC_ONLY(lim, ) val);
-                        if (x == 0) store_rp(a.y, plane + (long long)(a.nx + 1) * 8, AC_BC_ONLY(lim, ) val);
-                        if (x == a.nx - 1) store_rp(a.y, plane, AC_BC_ONLY(lim, ) val);
+                        if constexpr (EPI == EPI_MASK_BF16) {
+                            __align__(16) bf16 m[8];
+                            *reinterpret_cast<uint4 *>(m) = *reinterpret_cast<const uint4 *>(
+                                a.mask + AC_BC(plane + (long long)(x + 1) * 8, lim, AC_BC_CONV_ACT));
+#pragma unroll
+                            for (int c = 0; c < 8; ++c)
+                                o[8 * kc + c] = __bfloat162float(m[c]) > 0.f
+                                                    ? __float2bfloat16_rn(v[8 * kc + c])
+                                                    : __float2bfloat16_rn(0.f);
+                        } else {
+#pragma unroll
+                            for (int c = 0; c < 8; ++c)
+                                o[8 * kc + c] =
+                                    __float2bfloat16_rn(fmaxf(v[8 * kc + c] + bias[8 * kc + c], 0.f));
+                        }
+                        const uint4 val = reinterpret_cast<const uint4 *>(o)[kc];
+                        if (a.y) {
+                            store_rp(a.y, plane + (long long)(x + 1) * 8, AC_BC_ONLY(lim, ) val);
+                            if (x == 0)
+                                store_rp(a.y, plane + (long long)(a.nx + 1) * 8, AC_BC_ONLY(lim, ) val);
+                            if (x == a.nx - 1) store_rp(a.y, plane, AC_BC_ONLY(lim, ) val);
+                        }
+                        if (a.yn) store_rp(a.yn, plane + (long long)(x + 1) * 8, AC_BC_ONLY(lim, ) val);
                     }
                 } else {
                     const long long p = AC_BC(((long long)z * a.ny + sg.y) * a.nx + x,
@@ -923,7 +947,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(THREADS, 1)
     } else {  // ---- epilogue: warps 0-3 of each CTA, its TMEM lanes 32 warp .. 32 warp + 31
         float bias[COUT];
 #pragma unroll
-        for (int c = 0; c < COUT; ++c) bias[c] = a.bias[c];
+        for (int c = 0; c < COUT; ++c) bias[c] = EPI == EPI_MASK_BF16 ? 0.f : a.bias[c];
         float gm = 0.f;
         uint32_t par = 0;  // bit k: parity of the tiles block k has held so far
         bool ok = true;
@@ -949,20 +973,37 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(THREADS, 1)
                 if (lane == 0) mbar_arrive_cluster(leader_addr(&acce[kb]));
                 const int z = sg.z0 + i;
                 if (!ps.write || z < ps.zw || x >= a.nx) continue;
-                if (EPI == EPI_RELU_BF16) {
+                if (EPI == EPI_RELU_BF16 || EPI == EPI_MASK_BF16) {
                     __align__(16) bf16 o[COUT];
-#pragma unroll
-                    for (int c = 0; c < COUT; ++c) o[c] = __float2bfloat16_rn(fmaxf(v[c] + bias[c], 0.f));
                     AC_BC_ONLY(const long long lim =
                                    (long long)rp_cells(a.nx) * a.ny * a.nz * COUT;)
 #pragma unroll
                     for (int kc = 0; kc < COUT / 8; ++kc) {
-                        const uint4 val = reinterpret_cast<const uint4 *>(o)[kc];
                         const long long plane =
                             ((((long long)z * a.ny + sg.y) * (COUT / 8) + kc) * rp_cells(a.nx)) * 8;
-                        store_rp(a.y, plane + (long long)(x + 1) * 8, AC_BC_ONLY(lim, ) val);
-                        if (x == 0) store_rp(a.y, plane + (long long)(a.nx + 1) * 8, AC_BC_ONLY(lim, ) val);
-                        if (x == a.nx - 1) store_rp(a.y, plane, AC_BC_ONLY(lim, ) val);
+                        if constexpr (EPI == EPI_MASK_BF16) {
+                            __align__(16) bf16 m[8];
+                            *reinterpret_cast<uint4 *>(m) = *reinterpret_cast<const uint4 *>(
+                                a.mask + AC_BC(plane + (long long)(x + 1) * 8, lim, AC_BC_CONV_ACT));
+#pragma unroll
+                            for (int c = 0; c < 8; ++c)
+                                o[8 * kc + c] = __bfloat162float(m[c]) > 0.f
+                                                    ? __float2bfloat16_rn(v[8 * kc + c])
+                                                    : __float2bfloat16_rn(0.f);
+                        } else {
+#pragma unroll
+                            for (int c = 0; c < 8; ++c)
+                                o[8 * kc + c] =
+                                    __float2bfloat16_rn(fmaxf(v[8 * kc + c] + bias[8 * kc + c], 0.f));
+                        }
+                        const uint4 val = reinterpret_cast<const uint4 *>(o)[kc];
+                        if (a.y) {
+                            store_rp(a.y, plane + (long long)(x + 1) * 8, AC_BC_ONLY(lim, ) val);
+                            if (x == 0)
+                                store_rp(a.y, plane + (long long)(a.nx + 1) * 8, AC_BC_ONLY(lim, ) val);
+                            if (x == a.nx - 1) store_rp(a.y, plane, AC_BC_ONLY(lim, ) val);
+                        }
+                        if (a.yn) store_rp(a.yn, plane + (long long)(x + 1) * 8, AC_BC_ONLY(lim, ) val);
                     }
                 } else {
                     const long long p = AC_BC(((long long)z * a.ny + sg.y) * a.nx + x,

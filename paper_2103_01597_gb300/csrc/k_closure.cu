@@ -23,6 +23,7 @@
 
 #include "ac_internal.h"
 #include "conv_tc.cuh"
+#include "wgrad_tc.cuh"
 
 namespace ac {
 
@@ -449,6 +450,101 @@ __global__ void restrict_kernel(const T *__restrict__ fine, int nxf, int nyf, in
     }
 }
 
+// Loss and output gradient for the tcgen05 backward pass: as loss_grad_kernel,
+// with dY (8 channels) written row-planar twice: with the periodic halo (dyh,
+// one plane, the input of the next convolution) and without it (dyn, two planes,
+// the second zero: the weight-gradient operand, N padded to 16).  Block partials
+// of the loss in partials[blockIdx.x].
+__global__ void loss_grad_rp_kernel(const float *__restrict__ y, F8 tgt,
+                                    const float *__restrict__ inv_out, int nx, long long n,
+                                    bf16 *__restrict__ dyh, bf16 *__restrict__ dyn,
+                                    double *__restrict__ partials) {
+    double acc = 0.0;
+    const float gsc = (float)(2.0 / (8.0 * (double)n));
+    const long long nxp = tc::rp_cells(nx);
+    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < n;
+         p += (long long)gridDim.x * blockDim.x) {
+        const long long row = p / nx;  // z * ny + y
+        const int xi = (int)(p - row * nx);
+        __align__(16) bf16 v[8];
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+            const float d = y[c * n + p] - tgt.p[c][p] * inv_out[c];
+            acc += (double)d * (double)d;
+            v[c] = __float2bfloat16_rn(gsc * d);
+        }
+        const uint4 val = *reinterpret_cast<const uint4 *>(v);
+        uint4 *h = reinterpret_cast<uint4 *>(dyh + row * nxp * 8);
+        h[xi + 1] = val;
+        if (xi == 0) h[nx + 1] = val;
+        if (xi == nx - 1) h[0] = val;
+        reinterpret_cast<uint4 *>(dyn + row * 2 * nxp * 8)[xi + 1] = val;
+    }
+    __shared__ double sh[256];
+    sh[threadIdx.x] = acc;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if ((int)threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) partials[blockIdx.x] = sh[0];
+}
+
+// Bias-gradient partials from a row-planar gradient without halo (every slot but
+// the cells' is zero): block (b, kc) sums plane kc of rows b, b + G, ... into
+// bpart[(kc * G + b) * 8 + c], channel 8 kc + c, in binary64 (fixed order).
+__global__ void bias_grad_rp_kernel(const bf16 *__restrict__ zn, int kcs, int nxp, long long rows,
+                                    double *__restrict__ bpart) {
+    const int kc = blockIdx.y, G = gridDim.x;
+    const long long nr = rows > blockIdx.x ? (rows - 1 - blockIdx.x) / G + 1 : 0;
+    double s[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    for (long long e = threadIdx.x; e < nr * nxp; e += blockDim.x) {
+        const long long r = blockIdx.x + (e / nxp) * G;
+        const long long j = e % nxp;
+        __align__(16) bf16 v[8];
+        *reinterpret_cast<uint4 *>(v) =
+            *reinterpret_cast<const uint4 *>(zn + ((r * kcs + kc) * nxp + j) * 8);
+#pragma unroll
+        for (int c = 0; c < 8; ++c) s[c] += (double)__bfloat162float(v[c]);
+    }
+    __shared__ double sh[8][256];
+#pragma unroll
+    for (int c = 0; c < 8; ++c) sh[c][threadIdx.x] = s[c];
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if ((int)threadIdx.x < o)
+#pragma unroll
+            for (int c = 0; c < 8; ++c) sh[c][threadIdx.x] += sh[c][threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x < 8) bpart[((long long)kc * G + blockIdx.x) * 8 + threadIdx.x] = sh[threadIdx.x][0];
+}
+
+// gb[co] = sum over blocks of the partials above (co < cout).
+__global__ void bias_reduce_kernel(const double *__restrict__ bpart, int G, int cout,
+                                   float *__restrict__ gb) {
+    const int co = threadIdx.x;
+    if (co >= cout) return;
+    double s = 0.0;
+    for (int b = 0; b < G; ++b) s += bpart[((long long)(co / 8) * G + b) * 8 + co % 8];
+    gb[co] = (float)s;
+}
+
+// Weights of the input-gradient convolution: Wt[ci][co][26 - tap] = W[co][ci][tap]
+// (the adjoint of a cross-correlation correlates with the flipped kernel, input
+// and output channels exchanged).
+__global__ void flip_transpose_kernel(const float *__restrict__ W, int cout, int cin,
+                                      float *__restrict__ Wt) {
+    const int total = cout * cin * 27;
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < total; t += gridDim.x * blockDim.x) {
+        const int co = t / (cin * 27);
+        const int rem = t - co * cin * 27;
+        const int ci = rem / 27;
+        const int tap = rem - ci * 27;
+        Wt[((long long)ci * cout + co) * 27 + 26 - tap] = W[t];
+    }
+}
+
 }  // namespace ac
 
 using namespace ac;
@@ -480,6 +576,18 @@ struct ac_closure {
     int tp_grid[3];
     int tp_smem[3];  // dynamic shared memory of a launch (at least half an SM's)
     int tp_zc;
+    // tcgen05 training (allocated by the first backward pass on that path):
+    // input-gradient weight images, gradients row-planar with halo (h, inputs of
+    // the input-gradient convolutions) and without (n, weight-gradient operands),
+    // tensor maps, per-CTA weight-gradient and bias partials
+    void *train_block;
+    bf16 *img3b, *img2b, *dyh, *dyn, *dz2h, *dz2n, *dz1n;
+    float *wt;      // flipped, transposed master weights of layers 3 and 2
+    float *wpart;
+    double *bpart;
+    CUtensorMap tr_map[5];  // dyh, dz2h, dyn, dz2n, dz1n
+    int tr_grid[5];         // conv<8,32,mask>, conv<32,32,mask>, wgrad<32,8>, <32,32>, <8,32>
+    int tr_bias_blocks;
     float *part;
     double *lossp;
     double *loss_host;
@@ -618,6 +726,7 @@ static cudaError_t tc_setup(ac_closure *c) {
 static void free_closure(ac_closure *c) {
     if (c->block) cudaFree(c->block);
     if (c->act_block) cudaFree(c->act_block);
+    if (c->train_block) cudaFree(c->train_block);
     if (c->loss_host) cudaFreeHost(c->loss_host);
 }
 
@@ -688,8 +797,8 @@ extern "C" int ac_closure_init(ac_closure **out, int nx, int ny, int nz, void *s
     c->guard = reinterpret_cast<unsigned long long *>(c->lossp + c->lossblocks);
     c->tc_err = reinterpret_cast<unsigned *>(c->guard + 1);
     for (int i = 0; i < 8; ++i) c->in_scale[i] = c->out_scale[i] = 1.f;
-    float sc[24];
-    for (int i = 0; i < 24; ++i) sc[i] = 1.f;
+    float sc[32];  // [24..31]: ones, the output scale of the training forward pass
+    for (int i = 0; i < 32; ++i) sc[i] = 1.f;
     e = cudaMemcpyAsync(c->scales, sc, sizeof sc, cudaMemcpyHostToDevice, c->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     if (e == cudaSuccess) e = tc_setup(c);
@@ -711,7 +820,19 @@ extern "C" int ac_closure_quit(ac_closure *c) {
     return AC_OK;
 }
 
+// Input-gradient weight images of layers 3 and 2 (the tcgen05 training path):
+// the flipped, transposed weights in the image order of conv_tc_kernel.
+static void prep_train_images(ac_closure *c) {
+    float *wt3 = c->wt, *wt2 = c->wt + 8 * 32 * 27;
+    flip_transpose_kernel<<<32, 256, 0, c->stream>>>(c->params + P_W3, 8, 32, wt3);
+    flip_transpose_kernel<<<128, 256, 0, c->stream>>>(c->params + P_W2, 32, 32, wt2);
+    tc::conv_tc_prep_kernel<<<16, 256, 0, c->stream>>>(wt3, 32, 8, 8, 32, 0, 12, c->img3b);
+    tc::conv_tc_prep_kernel<<<128, 256, 0, c->stream>>>(wt2, 32, 32, 32, 32, 0, 12, c->img2b);
+    c->launches += 4;
+}
+
 static int prep_weights(ac_closure *c) {
+    if (c->train_block) prep_train_images(c);
     prep_weights_kernel<<<32, 256, 0, c->stream>>>(c->params + P_W1, 32, 8, 16, c->wf1, 0, nullptr);
     prep_weights_kernel<<<128, 256, 0, c->stream>>>(c->params + P_W2, 32, 32, 32, c->wf2, 32, c->wb2);
     prep_weights_kernel<<<32, 256, 0, c->stream>>>(c->params + P_W3, 8, 32, 32, c->wf3, 16, c->wb3);
@@ -811,13 +932,15 @@ static int run_forward(ac_closure *c, const float *const in[8], cudaEvent_t *ev 
 template <int CIN, int COUT, int EPI>
 static void launch_tc(const ac_closure *c, int layer, bool pair, const bf16 *img, const bf16 *pimg,
                       const float *bias, bf16 *y, float *const out[8] = nullptr,
-                      unsigned long long *gmax = nullptr) {
+                      unsigned long long *gmax = nullptr, const float *oscale = nullptr) {
     tc::ConvTcArgs a;
     a.w = img;
     a.bias = bias;
     a.y = y;
+    a.yn = nullptr;
+    a.mask = nullptr;
     for (int i = 0; i < 8; ++i) a.out[i] = out ? out[i] : nullptr;
-    a.out_scale = c->scales + 8;
+    a.out_scale = oscale ? oscale : c->scales + 8;
     a.gmax = gmax;
     a.nx = c->g.nx;
     a.ny = c->g.ny;
@@ -838,8 +961,10 @@ static void launch_tc(const ac_closure *c, int layer, bool pair, const bf16 *img
 // Forward pass on the tcgen05 kernels (row-planar activations in x0, a1, a2);
 // layer 3 writes out_scale * net(...) channel-major to out[0..7] (the closure's
 // own y when out is null) and, if gmax is given, folds the largest |value| into it.
+// With unscaled set, layer 3 writes net(...) itself (training).
 static int run_forward_tc(ac_closure *c, const float *const in[8], float *const out[8],
-                          unsigned long long *gmax, cudaEvent_t *ev = nullptr) {
+                          unsigned long long *gmax, cudaEvent_t *ev = nullptr,
+                          bool unscaled = false) {
     const ConvGeom g = c->g;
     F8 f;
     for (int i = 0; i < 8; ++i) f.p[i] = in[i];
@@ -854,7 +979,7 @@ static int run_forward_tc(ac_closure *c, const float *const in[8], float *const 
     launch_tc<32, 32, tc::EPI_RELU_BF16>(c, 1, pair, c->img2, c->pimg2, c->params + P_B2, c->a2);
     mark(ev, 3, c->stream);
     launch_tc<32, 8, tc::EPI_SCALED_F32>(c, 2, pair, c->img3, c->pimg3, c->params + P_B3, nullptr,
-                                         out ? out : own, gmax);
+                                         out ? out : own, gmax, unscaled ? c->scales + 24 : nullptr);
     mark(ev, 4, c->stream);
     c->launches += 4;
     CCK(cudaGetLastError());
@@ -954,15 +1079,201 @@ extern "C" int ac_closure_forward_timings(ac_closure *c, const float *const in[8
     return rc;
 }
 
+// Mean squared error from the loss kernel's block partials (waits for the stream).
+static int read_loss(ac_closure *c, double *loss) {
+    double *hp = static_cast<double *>(malloc(sizeof(double) * c->lossblocks));
+    if (!hp) return AC_ERR_OOM;
+    cudaError_t e = cudaMemcpyAsync(hp, c->lossp, sizeof(double) * c->lossblocks,
+                                    cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) {
+        free(hp);
+        return ac_report_cuda(e);
+    }
+    double s = 0.0;
+    for (int i = 0; i < c->lossblocks; ++i) s += hp[i];
+    free(hp);
+    *loss = s / (8.0 * (double)c->g.n);
+    return isfinite(*loss) ? AC_OK : AC_ERR_NONFINITE;
+}
+
+// Persistent grid of a weight-gradient kernel: resident CTAs (shared memory and
+// an SM's 512 TMEM columns bound them) times SMs, at most one per segment.
+template <int CIN, int COUT>
+static cudaError_t wgrad_grid_for(const ac_closure *c, int sms, int *grid) {
+    using S = tc::WgradShape<CIN, COUT>;
+    auto k = tc::wgrad_tc_kernel<CIN, COUT>;
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::SMEM);
+    int per_sm = 0;
+    if (e == cudaSuccess)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, tc::THREADS, S::SMEM);
+    if (e != cudaSuccess) return e;
+    if (per_sm > 512 / S::TCOLS) per_sm = 512 / S::TCOLS;
+    const long long segs = (long long)((c->g.nz + c->tc_zc - 1) / c->tc_zc) * c->g.ny *
+                           ((c->g.nx + tc::TM - 1) / tc::TM);
+    long long g = (long long)(per_sm < 1 ? 1 : per_sm) * sms;
+    *grid = (int)(g < segs ? g : segs);
+    return cudaSuccess;
+}
+
+static size_t align256(size_t b) { return (b + 255) / 256 * 256; }
+
+// Buffers, tensor maps, grids and weight images of the tcgen05 training path,
+// made by its first backward pass.
+static int ensure_train(ac_closure *c) {
+    if (c->train_block) return AC_OK;
+    int dev = 0, sms = 0;
+    CCK(cudaGetDevice(&dev));
+    CCK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    CCK((tc_grid_for<8, 32, tc::EPI_MASK_BF16>(c, sms, &c->tr_grid[0])));
+    CCK((tc_grid_for<32, 32, tc::EPI_MASK_BF16>(c, sms, &c->tr_grid[1])));
+    CCK((wgrad_grid_for<32, 8>(c, sms, &c->tr_grid[2])));
+    CCK((wgrad_grid_for<32, 32>(c, sms, &c->tr_grid[3])));
+    CCK((wgrad_grid_for<8, 32>(c, sms, &c->tr_grid[4])));
+    int wmax = 0;  // largest per-CTA partial block (floats) times grid
+    {
+        const int per[3] = {tc::WgradShape<32, 8>::NACC * tc::WgradShape<32, 8>::NB,
+                            tc::WgradShape<32, 32>::NACC * tc::WgradShape<32, 32>::NB,
+                            tc::WgradShape<8, 32>::NACC * tc::WgradShape<8, 32>::NB};
+        for (int l = 0; l < 3; ++l)
+            if (per[l] * c->tr_grid[2 + l] > wmax) wmax = per[l] * c->tr_grid[2 + l];
+    }
+    const long long rows = (long long)c->g.ny * c->g.nz;
+    c->tr_bias_blocks = (int)(rows < 256 ? rows : 256);
+    const long long np2 = (long long)tc::rp_cells(c->g.nx) * rows;
+    const size_t b_wpart = align256(sizeof(float) * (size_t)wmax * tc::TM);
+    const size_t b_bpart = align256(sizeof(double) * 4 * (size_t)c->tr_bias_blocks * 8);
+    const size_t b_wt = align256(sizeof(float) * (8 * 32 * 27 + 32 * 32 * 27));
+    const size_t b_img3 = align256((size_t)tc::w_bytes(8, 32));
+    const size_t b_img2 = align256((size_t)tc::w_bytes(32, 32));
+    const size_t b_act[5] = {align256(2 * 8 * (size_t)np2), align256(2 * 16 * (size_t)np2),
+                             align256(2 * 32 * (size_t)np2), align256(2 * 32 * (size_t)np2),
+                             align256(2 * 32 * (size_t)np2)};
+    size_t total = b_wpart + b_bpart + b_wt + b_img3 + b_img2;
+    for (int i = 0; i < 5; ++i) total += b_act[i];
+    void *blk = nullptr;
+    cudaError_t e = cudaMalloc(&blk, total);
+    if (e == cudaSuccess) e = cudaMemsetAsync(blk, 0, total, c->stream);  // zero halos and padding
+    if (e != cudaSuccess) {
+        if (blk) cudaFree(blk);
+        return ac_report_cuda(e);
+    }
+    char *p = static_cast<char *>(blk);
+    c->wpart = reinterpret_cast<float *>(p);
+    p += b_wpart;
+    c->bpart = reinterpret_cast<double *>(p);
+    p += b_bpart;
+    c->wt = reinterpret_cast<float *>(p);
+    p += b_wt;
+    c->img3b = reinterpret_cast<bf16 *>(p);
+    p += b_img3;
+    c->img2b = reinterpret_cast<bf16 *>(p);
+    p += b_img2;
+    bf16 **acts[5] = {&c->dyh, &c->dyn, &c->dz2h, &c->dz2n, &c->dz1n};
+    for (int i = 0; i < 5; ++i) {
+        *acts[i] = reinterpret_cast<bf16 *>(p);
+        p += b_act[i];
+    }
+    void *fn = nullptr;
+    cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+    e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q);
+    if (e == cudaSuccess && (q != cudaDriverEntryPointSuccess || !fn)) e = cudaErrorNotSupported;
+    auto enc = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+    const int kcs[5] = {1, 4, 2, 4, 4};
+    bf16 *bases[5] = {c->dyh, c->dz2h, c->dyn, c->dz2n, c->dz1n};
+    for (int i = 0; i < 5 && e == cudaSuccess; ++i) e = tc_encode(enc, c, bases[i], kcs[i], &c->tr_map[i]);
+    if (e != cudaSuccess) {
+        cudaFree(blk);
+        return ac_report_cuda(e);
+    }
+    c->train_block = blk;
+    prep_train_images(c);
+    CCK(cudaGetLastError());
+    return AC_OK;
+}
+
+// One input-gradient convolution through a ReLU on the tcgen05 kernel: from the
+// row-planar gradient behind xmap, with image img, mask = the forward activation;
+// writes y (with halo, or null) and yn (without).
+template <int CIN>
+static void launch_mask(const ac_closure *c, const CUtensorMap &xmap, int grid, const bf16 *img,
+                        const bf16 *mask, bf16 *y, bf16 *yn) {
+    tc::ConvTcArgs a = {};
+    a.w = img;
+    a.y = y;
+    a.yn = yn;
+    a.mask = mask;
+    a.nx = c->g.nx;
+    a.ny = c->g.ny;
+    a.nz = c->g.nz;
+    a.zc = c->tc_zc;
+    a.err = c->tc_err;
+    tc::conv_tc_kernel<CIN, 32, tc::EPI_MASK_BF16>
+        <<<grid, tc::THREADS, tc::smem_bytes(CIN, 32), c->stream>>>(xmap, a);
+}
+
+template <int CIN, int COUT>
+static void launch_wgrad(const ac_closure *c, const CUtensorMap &xmap, const CUtensorMap &dmap,
+                         int grid, int cin_real, float *gW) {
+    tc::WgradTcArgs a;
+    a.part = c->wpart;
+    a.nx = c->g.nx;
+    a.ny = c->g.ny;
+    a.nz = c->g.nz;
+    a.zc = c->tc_zc;
+    a.err = c->tc_err;
+    tc::wgrad_tc_kernel<CIN, COUT>
+        <<<grid, tc::THREADS, tc::WgradShape<CIN, COUT>::SMEM, c->stream>>>(xmap, dmap, a);
+    tc::wgrad_tc_reduce_kernel<CIN, COUT><<<64, 256, 0, c->stream>>>(c->wpart, grid, cin_real, gW);
+}
+
+static void launch_bias(const ac_closure *c, const bf16 *zn, int kcs, int cout, float *gb) {
+    const long long rows = (long long)c->g.ny * c->g.nz;
+    bias_grad_rp_kernel<<<dim3((unsigned)c->tr_bias_blocks, (unsigned)(cout / 8)), 256, 0, c->stream>>>(
+        zn, kcs, tc::rp_cells(c->g.nx), rows, c->bpart);
+    bias_reduce_kernel<<<1, 32, 0, c->stream>>>(c->bpart, c->tr_bias_blocks, cout, gb);
+}
+
+// Backward pass on the tcgen05 kernels: forward (row-planar activations kept),
+// loss and dY, the two input gradients through the ReLUs (flipped, transposed
+// weights), the three weight gradients and the three bias gradients.
+static int run_backward_tc(ac_closure *c, const float *const in[8], const float *const target[8]) {
+    int rc = ensure_train(c);
+    if (rc) return rc;
+    rc = run_forward_tc(c, in, nullptr, nullptr, nullptr, true);
+    if (rc) return rc;
+    const ConvGeom g = c->g;
+    F8 t;
+    for (int i = 0; i < 8; ++i) t.p[i] = target[i];
+    loss_grad_rp_kernel<<<c->lossblocks, 256, 0, c->stream>>>(c->y, t, c->scales + 16, g.nx, g.n,
+                                                              c->dyh, c->dyn, c->lossp);
+    launch_mask<8>(c, c->tr_map[0], c->tr_grid[0], c->img3b, c->a2, c->dz2h, c->dz2n);
+    launch_mask<32>(c, c->tr_map[1], c->tr_grid[1], c->img2b, c->a1, nullptr, c->dz1n);
+    launch_wgrad<32, 8>(c, c->tc_map[2], c->tr_map[2], c->tr_grid[2], 32, c->grads + P_W3);
+    launch_wgrad<32, 32>(c, c->tc_map[1], c->tr_map[3], c->tr_grid[3], 32, c->grads + P_W2);
+    launch_wgrad<8, 32>(c, c->tc_map[0], c->tr_map[4], c->tr_grid[4], 8, c->grads + P_W1);
+    launch_bias(c, c->dyn, 2, 8, c->grads + P_B3);
+    launch_bias(c, c->dz2n, 4, 32, c->grads + P_B2);
+    launch_bias(c, c->dz1n, 4, 32, c->grads + P_B1);
+    c->launches += 15;
+    CCK(cudaGetLastError());
+    return AC_OK;
+}
+
 extern "C" int ac_closure_backward(ac_closure *c, const float *const in[8],
                                    const float *const target[8], double *loss) {
     AC_RANGE("ac_closure_backward");
     if (!c || !in || !target) return AC_ERR_ARG;
     for (int i = 0; i < 8; ++i)
         if (!in[i] || !target[i]) return AC_ERR_ARG;
+    const ConvGeom g = c->g;
+    if (c->conv_path != AC_CONV_MMA_SYNC) {
+        int rc = run_backward_tc(c, in, target);
+        if (rc) return rc;
+        return loss ? read_loss(c, loss) : AC_OK;
+    }
     int rc = run_forward(c, in);
     if (rc) return rc;
-    const ConvGeom g = c->g;
     F8 t;
     for (int i = 0; i < 8; ++i) t.p[i] = target[i];
     loss_grad_kernel<<<c->lossblocks, 256, 0, c->stream>>>(c->y, t, c->scales + 16, g.n, c->dy,
@@ -986,23 +1297,7 @@ extern "C" int ac_closure_backward(ac_closure *c, const float *const in[8],
     bias_grad_kernel<<<32, 256, 0, c->stream>>>(c->dz1, g.n, c->grads + P_B1);
     c->launches += 12;
     CCK(cudaGetLastError());
-    if (loss) {
-        double *hp = static_cast<double *>(malloc(sizeof(double) * c->lossblocks));
-        if (!hp) return AC_ERR_OOM;
-        cudaError_t e = cudaMemcpyAsync(hp, c->lossp, sizeof(double) * c->lossblocks,
-                                        cudaMemcpyDeviceToHost, c->stream);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
-        if (e != cudaSuccess) {
-            free(hp);
-            return ac_report_cuda(e);
-        }
-        double s = 0.0;
-        for (int i = 0; i < c->lossblocks; ++i) s += hp[i];
-        free(hp);
-        *loss = s / (8.0 * (double)g.n);
-        if (!isfinite(*loss)) return AC_ERR_NONFINITE;
-    }
-    return AC_OK;
+    return loss ? read_loss(c, loss) : AC_OK;
 }
 
 extern "C" int ac_closure_adam_step(ac_closure *c, float lr, float beta1, float beta2, float eps) {

@@ -143,9 +143,19 @@ def test_conv_path_selection():
     c.close()
 
 
-@pytest.mark.parametrize("path", PATHS)
-def test_gradients_and_adam_match_oracle(path):
-    n = (16, 12, 10)
+# all paths on one ragged x-tile (16 cells: one K-step of the weight gradient);
+# the tcgen05 backward also on two x-segments (the second 8 cells), several rows
+# and two z-chunks, and on a partial K-step (nx = 20) with three z-chunks, the
+# last of one tile
+GRAD_CASES = [(p, (16, 12, 10)) for p in PATHS] + [
+    (ac.AC_CONV_TCGEN05, (136, 9, 18)),
+    (ac.AC_CONV_TCGEN05_PAIR, (136, 9, 18)),
+    (ac.AC_CONV_TCGEN05, (20, 7, 33)),
+]
+
+
+@pytest.mark.parametrize("path,n", GRAD_CASES)
+def test_gradients_and_adam_match_oracle(path, n):
     net, params, x, ins, outs = _setup(n, 6)
     rng = np.random.default_rng(7)
     tgt = (outs.astype(np.float64)[:, None, None, None]
