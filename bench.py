@@ -692,6 +692,16 @@ def run_ensemble(args, wl):
         b.load(i, f)
     dt = wl["dt"]
     zc = ac.ac_batch_tune(b.b, dt)
+    _, shapes, tune_ms = ac.ac_batch_get_tiling(b.b, len(boxes))
+    cls16 = sorted({tuple(n[:2]) for (n, _, _, _), sh in zip(boxes, shapes) if sh == ac.AC_TILE_16X16})
+    tuning = {"item_z_extent": zc,
+              "boxes_per_tile_shape": {"32x8": shapes.count(ac.AC_TILE_32X8),
+                                       "16x16": shapes.count(ac.AC_TILE_16X16)},
+              "classes_on_16x16_(nx,ny)": [list(c) for c in cls16],
+              "step_ms_default_split": tune_ms[0], "step_ms_tuned": tune_ms[1],
+              "gain": tune_ms[0] / tune_ms[1] if tune_ms[1] > 0 else None,
+              "note": "whole steps (3 substeps) timed by ac_batch_tune from the same state; "
+                      "default split = z extent 64, every box on 32x8 tiles"}
     ac.ac_batch_set_graph(b.b, True)
     for _ in range(args.warmup):
         b.step(dt)
@@ -825,7 +835,7 @@ def run_ensemble(args, wl):
                 "ms_per_step": 1e3 * elapsed / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
                 "config": {"workload": wl["desc"], "boxes": len(boxes), "cells": ncell,
-                           "dt": dt, "tuned_item_z_extent": zc,
+                           "dt": dt, "tuned_item_z_extent": zc, "tuning": tuning,
                            "parallelism": "replicas" if ws > 1 else "single GPU",
                            "l2": "inputs larger than L2 (%.1f GB of state resident)"
                                  % (ncell * 24 * 4 / 1e9),
@@ -1387,6 +1397,8 @@ OTHER_WORKLOADS = {
     "forced512_fp32": dict(steps=10, warmup=3, fp64_compare_steps=50),
     "ensemble64_fp32": dict(steps=10, warmup=3),
     "closure_forward256": dict(steps=10, warmup=3),
+    "closure128": dict(steps=10, warmup=3, closure_pairs=12, closure_iters=400,
+                       closure_rollout=20),
     "decomp256_fp64": dict(steps=5, warmup=3),
 }
 SUMMARY_KEYS = ("metric", "value", "unit", "ms_per_step", "steps", "warmup", "dtype",

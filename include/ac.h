@@ -315,9 +315,10 @@ int ac_launch_count(const ac_handle *h, unsigned long long *count);
  * notes that parameter scans inflate problem sizes, Sec. 4).  Each box carries
  * its own grid and nu, eta; the other constants come from `common`.  One
  * persistent kernel launch per substep covers every box: work items are
- * (box, 32 x 8 column tile, z range), taken largest first from a device
+ * (box, column tile, z range), taken largest first from a device
  * counter; each item computes exactly what the single-box binary32 kernel
- * computes for those cells (same substep as ac_integrate_substep, no forcing).
+ * computes for those cells (same substep as ac_integrate_substep, no forcing),
+ * whatever its tile shape: 32 x 8 or 16 x 16 cells per tile, chosen per box.
  * State: binary32 fields (AC_FP32, or AC_FP32_W64 with a binary64 accumulator);
  * device memory is owned by the batch.  Limits: 1..AC_BATCH_MAX_BOXES boxes,
  * 1..4096 cells per axis, nx a multiple of 4; force_amp must be 0.
@@ -355,11 +356,32 @@ int ac_batch_integrate_substep(ac_batch *b, double dt, int s);
 int ac_batch_integrate_step(ac_batch *b, double dt);
 /* Enable (non-zero) or disable (0, the default) the graph of ac_batch_integrate_step. */
 int ac_batch_set_graph(ac_batch *b, int enable);
-/* Autotuner: times substep 0 (which leaves the state unchanged) for work items
- * of z extent 8, 16, 32, 64 and 128 and keeps the fastest (*zc_out).  With a
- * cache path, a line "<device|boxes signature> <z extent>" is reused or
- * appended.  Must be called at a step boundary (AC_ERR_STATE otherwise). */
+/* Tile shapes of the work items (one per box). */
+#define AC_TILE_32X8 0
+#define AC_TILE_16X16 1
+
+/* Autotuner of the work split: times whole steps (substeps 0, 1, 2, each
+ * candidate from the same state: the state is saved on the device first and
+ * restored afterwards, so the call leaves it unchanged and w is rewritten by
+ * the next substep 0) for work items of z extent 8, 16, 32, 64 and 128 with
+ * every box on one tile shape, for both shapes; then, for each class of boxes
+ * of equal nx and ny (largest total cells first), tries the other shape and
+ * keeps it if the step gets faster by more than 0.3%.  *zc_out receives the
+ * chosen z extent (ac_batch_get_tiling gives the shapes and the step times).
+ * With a cache path, the choice for this device, precision and set of box
+ * sizes is read from, or added to, a JSON object file written by this call:
+ * one line per entry, "<signature>": {"zc": Z, "tiles": "<one digit per box>",
+ * "ms_default": T0, "ms_tuned": T1}; a file holding anything else is read but
+ * never rewritten.  Temporarily allocates one state pool.  Must be called at a
+ * step boundary (AC_ERR_STATE otherwise). */
 int ac_batch_tune(ac_batch *b, double dt, const char *cache_path, int *zc_out);
+/* Set the work split by hand: z extent 1..4096 and `shapes` (nbox entries of
+ * AC_TILE_*, or NULL for all AC_TILE_32X8).  Results do not depend on it. */
+int ac_batch_set_tiling(ac_batch *b, int zc, const int *shapes);
+/* The current split (z extent, nbox shapes) and, after a tuning, the step time
+ * (ms) of the default split (z extent 64, all 32 x 8) and of the tuned one
+ * (0 where unknown).  Any output may be NULL. */
+int ac_batch_get_tiling(const ac_batch *b, int *zc, int *shapes, float tune_ms[2]);
 /* Reduction of one box's state, as ac_reduce. */
 int ac_batch_reduce(ac_batch *b, int box, int op, int quantity, double *out);
 /* Total cells, work items, z extent of an item, persistent CTAs, launches so far. */

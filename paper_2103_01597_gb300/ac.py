@@ -33,6 +33,7 @@ AC_MAX, AC_MIN, AC_SUM, AC_RMS = 0, 1, 2, 3
 AC_STENCIL_AUTO, AC_STENCIL_FP64, AC_STENCIL_FIXED = 0, 1, 2
 AC_STENCIL_MODE_GROUP, AC_STENCIL_MODE_FIELD, AC_STENCIL_MODE_PLAIN = 0, 1, 2
 AC_CONV_TCGEN05, AC_CONV_MMA_SYNC, AC_CONV_TCGEN05_PAIR = 0, 1, 2
+AC_TILE_32X8, AC_TILE_16X16 = 0, 1
 AC_Q_UMAG, AC_Q_EKIN, AC_Q_EMAG, AC_Q_CFL = 8, 9, 10, 11
 
 
@@ -143,6 +144,9 @@ def load_library(path=None):
         "ac_batch_integrate_step": ([_vp, _c.c_double], _c.c_int),
         "ac_batch_set_graph": ([_vp, _c.c_int], _c.c_int),
         "ac_batch_tune": ([_vp, _c.c_double, _c.c_char_p, ctypes.POINTER(_c.c_int)], _c.c_int),
+        "ac_batch_set_tiling": ([_vp, _c.c_int, ctypes.POINTER(_c.c_int)], _c.c_int),
+        "ac_batch_get_tiling": ([_vp, ctypes.POINTER(_c.c_int), ctypes.POINTER(_c.c_int),
+                                 ctypes.POINTER(_c.c_float)], _c.c_int),
         "ac_batch_reduce": ([_vp, _c.c_int, _c.c_int, _c.c_int, _pd], _c.c_int),
         "ac_batch_info": ([_vp, ctypes.POINTER(_c.c_longlong), ctypes.POINTER(_c.c_int),
                            ctypes.POINTER(_c.c_int), ctypes.POINTER(_c.c_int),
@@ -591,6 +595,22 @@ def ac_batch_tune(b, dt, cache_path=None):
     cp = cache_path.encode() if cache_path else None
     _check(load_library().ac_batch_tune(b, float(dt), cp, ctypes.byref(zc)), "ac_batch_tune")
     return zc.value
+
+
+def ac_batch_set_tiling(b, zc, shapes=None):
+    arr = None
+    if shapes is not None:
+        arr = (ctypes.c_int * len(shapes))(*[int(v) for v in shapes])
+    _check(load_library().ac_batch_set_tiling(b, int(zc), arr), "ac_batch_set_tiling")
+
+
+def ac_batch_get_tiling(b, nbox):
+    """(z extent, list of nbox tile shapes, [ms of the default split, ms tuned])."""
+    zc = ctypes.c_int()
+    arr = (ctypes.c_int * nbox)()
+    ms = (ctypes.c_float * 2)()
+    _check(load_library().ac_batch_get_tiling(b, ctypes.byref(zc), arr, ms), "ac_batch_get_tiling")
+    return zc.value, list(arr), [ms[0], ms[1]]
 
 
 def ac_batch_reduce(b, box, op, quantity):

@@ -3,13 +3,15 @@
 //
 // The paper notes that parameter scans inflate problem sizes (Sec. 4); here a
 // scan is a set of small boxes integrated together.  Work items are
-// (box, 32 x 8 column tile, z range); they are sorted by cost (largest first)
-// and taken by persistent CTAs from a device counter that a memset node resets
-// before every launch, so the kernel boundary is the only cross-CTA
-// synchronisation.  Each item runs the same tile body as the single-box
-// binary32 kernel, so every box's result is bitwise the single-box result.
-// The three substeps of a step can be captured into a CUDA graph, and the z
-// extent of the items is chosen by a measuring autotuner.
+// (box, column tile of the box's shape -- 32 x 8 or 16 x 16 --, z range); they
+// are sorted by cost (largest first) and taken by persistent CTAs from a device
+// counter that a memset node resets before every launch, so the kernel
+// boundary is the only cross-CTA synchronisation.  Each item runs the same
+// per-cell arithmetic as the single-box binary32 kernel, so every box's result
+// is bitwise the single-box result whatever its tile shape.  The three
+// substeps of a step can be captured into a CUDA graph; the z extent of the
+// items and the tile shape of each box-size class are chosen by a measuring
+// autotuner.
 #include <stdint.h>
 #include <stdio.h>
 #include <stdlib.h>
@@ -37,7 +39,7 @@ struct BatchArgs {
     const float *fin;  // state pool read this substep
     float *fout;       // state pool written this substep
     W *w;              // accumulator pool
-    const int4 *items; // (box, x0, y0, z0 << 16 | z1)
+    const int4 *items; // (box | shape << 16, x0, y0, z0 << 16 | z1)
     unsigned int *counter;
     int nitems;
     int s0;
@@ -87,9 +89,21 @@ __global__ void __launch_bounds__(TT_THREADS, 1) batch_substep_kernel(const __gr
         __syncthreads();  // every thread has read item_sh before it is overwritten
         if (it >= b.nitems) break;
         const int4 wi = b.items[it];
-        const TileBox<W> ta(b, b.box[wi.x]);
-        tiled_body<W, true, false, false>(ta, wi.y, wi.z, wi.w >> 16, wi.w & 0xffff, bt_smem_raw);
+        const TileBox<W> ta(b, b.box[wi.x & 0xffff]);
+        if (wi.x >> 16)
+            tiled_body<Tile16x16, W, true, false, false>(ta, wi.y, wi.z, wi.w >> 16, wi.w & 0xffff,
+                                                         bt_smem_raw);
+        else
+            tiled_body<Tile32x8, W, true, false, false>(ta, wi.y, wi.z, wi.w >> 16, wi.w & 0xffff,
+                                                        bt_smem_raw);
     }
+}
+
+// Dynamic shared memory of the batch kernel: the larger of the two shapes' rings.
+template <typename W>
+constexpr size_t batch_smem_bytes() {
+    return tt_smem_bytes<W, Tile32x8>() > tt_smem_bytes<W, Tile16x16>() ? tt_smem_bytes<W, Tile32x8>()
+                                                                        : tt_smem_bytes<W, Tile16x16>();
 }
 
 }  // namespace ac
@@ -117,6 +131,8 @@ struct ac_batch {
     int nitems;
     unsigned int *counter;
     int zc;           // z extent of a work item (tuned)
+    std::vector<int> shape;  // tile shape of each box (AC_TILE_32X8 / AC_TILE_16X16, tuned)
+    float tune_ms[2];        // last tuning: full step with the default split, and tuned
     int ctas;         // persistent CTAs
     int next_s;
     unsigned long long step;
@@ -137,18 +153,23 @@ struct ac_batch {
         if (e_ != cudaSuccess) return ac_report_cuda(e_); \
     } while (0)
 
+// Work items for z extent zc and the boxes' tile shapes; cost = planes staged
+// (z extent + 6), the same for every full tile of either shape.
 static int build_items(ac_batch *b, int zc) {
     std::vector<int4> items;
-    std::vector<int> cost;
+    std::vector<long long> cost;
     for (int bx = 0; bx < b->nbox; ++bx) {
         const ac_box &x = b->boxes[bx];
+        const int sh = b->shape[bx];
+        const int TX = sh ? Tile16x16::TX : Tile32x8::TX, TY = sh ? Tile16x16::TY : Tile32x8::TY;
         const int z = std::min(zc, x.nz);
         for (int z0 = 0; z0 < x.nz; z0 += z)
-            for (int y0 = 0; y0 < x.ny; y0 += TT_Y)
-                for (int x0 = 0; x0 < x.nx; x0 += TT_X) {
+            for (int y0 = 0; y0 < x.ny; y0 += TY)
+                for (int x0 = 0; x0 < x.nx; x0 += TX) {
                     const int z1 = std::min(z0 + z, x.nz);
-                    items.push_back(make_int4(bx, x0, y0, (z0 << 16) | z1));
-                    cost.push_back((z1 - z0 + 6) * std::min(TT_Y, x.ny - y0));
+                    items.push_back(make_int4(bx | (sh << 16), x0, y0, (z0 << 16) | z1));
+                    cost.push_back((long long)(z1 - z0 + 6) * std::min(TY, x.ny - y0) *
+                                   std::min(TX, x.nx - x0));
                 }
     }
     std::vector<int> order(items.size());
@@ -198,11 +219,11 @@ static cudaError_t launch_batch_t(ac_batch *b, double dt, int s, int cur, cudaSt
     }
     cudaError_t e = cudaMemsetAsync(b->counter, 0, sizeof(unsigned int), st);
     if (e != cudaSuccess) return e;
-    const size_t smem = tt_smem_bytes<W>();
+    const size_t smem = batch_smem_bytes<W>();
     e = cudaFuncSetAttribute(batch_substep_kernel<W>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)smem);
     if (e != cudaSuccess) return e;
-    batch_substep_kernel<W><<<b->ctas, dim3(TT_X, TT_Y, 1), smem, st>>>(a);
+    batch_substep_kernel<W><<<b->ctas, dim3(32, 8, 1), smem, st>>>(a);
     return cudaGetLastError();
 }
 
@@ -277,7 +298,7 @@ extern "C" int ac_batch_init(ac_batch **out, int nbox, const ac_box *boxes, cons
     if (e == cudaSuccess) e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e == cudaSuccess) {
-        const size_t smem = b->precision == AC_FP32 ? tt_smem_bytes<float>() : tt_smem_bytes<double>();
+        const size_t smem = b->precision == AC_FP32 ? batch_smem_bytes<float>() : batch_smem_bytes<double>();
         if (b->precision == AC_FP32) {
             e = cudaFuncSetAttribute(batch_substep_kernel<float>,
                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -302,6 +323,7 @@ extern "C" int ac_batch_init(ac_batch **out, int nbox, const ac_box *boxes, cons
     b->pool[1] = reinterpret_cast<float *>(static_cast<char *>(b->block) + fbytes);
     b->wpool = static_cast<char *>(b->block) + 2 * fbytes;
     b->ctas = sms * (occ < 1 ? 1 : occ);
+    b->shape.assign(nbox, AC_TILE_32X8);
     int rc = build_items(b, 64);
     if (rc) {
         free_batch(b);
@@ -444,9 +466,17 @@ extern "C" int ac_batch_integrate_step(ac_batch *b, double dt) {
     return AC_OK;
 }
 
-// Autotuner: time substep 0 (which reads only the current state, so the state
-// is unchanged) for each candidate z extent of the work items and keep the
-// fastest.  With a cache path, a line "<signature> <zc>" is read or appended.
+// Autotuner.  A candidate split (z extent, tile shape per box) is timed over a
+// whole step (substeps 0, 1, 2: substeps 1 and 2 also read the accumulator),
+// from the same state each time: the current state pool is copied aside once
+// and put back before every timed step and at the end (a step at a step
+// boundary rewrites w before reading it, so w needs no copy).  Search: every z
+// extent with all boxes on one shape, for both shapes; then, for each box-size
+// class (boxes of equal nx, ny; largest total first), the other shape, kept if
+// the step gets faster by more than the noise margin.
+static const int TUNE_ZC[5] = {8, 16, 32, 64, 128};
+static const float TUNE_MARGIN = 0.003f;  // relative gain a class change must beat
+
 static std::string batch_signature(const ac_batch *b) {
     int dev = 0;
     cudaGetDevice(&dev);
@@ -466,69 +496,217 @@ static std::string batch_signature(const ac_batch *b) {
              b->precision, b->nbox, (unsigned long long)h);
     std::string s(buf);
     for (char &c : s)
-        if (c == ' ') c = '_';
+        if (c == ' ' || c == '"' || c == '\\') c = '_';
     return s;
+}
+
+// Shortest of `reps` steps (after one untimed) from the saved state `save`.
+static int time_step(ac_batch *b, double dt, const float *save, size_t bytes, int reps, cudaEvent_t e0,
+                     cudaEvent_t e1, float *ms_out) {
+    float tmin = 1e30f;
+    for (int r = 0; r <= reps; ++r) {
+        BCK(cudaMemcpyAsync(b->pool[b->cur], save, bytes, cudaMemcpyDeviceToDevice, b->stream));
+        BCK(cudaEventRecord(e0, b->stream));
+        int c = b->cur;
+        for (int s = 0; s < 3; ++s, c = 1 - c) BCK(launch_batch(b, dt, s, c, b->stream));
+        BCK(cudaEventRecord(e1, b->stream));
+        BCK(cudaEventSynchronize(e1));
+        b->launches += 3;
+        float ms = 0.f;
+        BCK(cudaEventElapsedTime(&ms, e0, e1));
+        if (r > 0 && ms < tmin) tmin = ms;
+    }
+    *ms_out = tmin;
+    return AC_OK;
+}
+
+// One entry per line of the cache file, the file a JSON object:
+//   {
+//     "<signature>": {"zc": 64, "tiles": "0110...", "ms_default": 3.6, "ms_tuned": 3.4},
+//     ...
+//   }
+// ("tiles": one digit per box, AC_TILE_32X8 = 0, AC_TILE_16X16 = 1).
+struct CacheEntry {
+    std::string key, tiles;
+    int zc;
+    float ms[2];
+};
+
+static bool parse_entry(const char *line, CacheEntry *e) {
+    char key[512], tiles[AC_BATCH_MAX_BOXES + 1];
+    int zc = 0;
+    float m0 = 0.f, m1 = 0.f;
+    const int got = sscanf(line, " \"%511[^\"]\": {\"zc\": %d, \"tiles\": \"%128[01]\", \"ms_default\": %f, "
+                           "\"ms_tuned\": %f", key, &zc, tiles, &m0, &m1);
+    if (got < 3 || zc <= 0) return false;
+    e->key = key;
+    e->tiles = tiles;
+    e->zc = zc;
+    e->ms[0] = got >= 4 ? m0 : 0.f;
+    e->ms[1] = got >= 5 ? m1 : 0.f;
+    return true;
+}
+
+// Read the entries; false if the file holds anything this format does not
+// (then it is never rewritten).
+static bool read_cache(const char *path, std::vector<CacheEntry> *out) {
+    FILE *f = fopen(path, "r");
+    if (!f) return true;  // no file yet
+    char line[1024];
+    bool ok = true;
+    while (fgets(line, sizeof line, f)) {
+        CacheEntry e;
+        if (parse_entry(line, &e)) {
+            out->push_back(e);
+            continue;
+        }
+        // besides entries, only blank lines and the object's own braces
+        std::string t;
+        for (const char *p = line; *p; ++p)
+            if (*p != ' ' && *p != '\t' && *p != '\n' && *p != '\r') t.push_back(*p);
+        if (!t.empty() && t != "{" && t != "}") ok = false;
+    }
+    fclose(f);
+    return ok;
+}
+
+static void write_cache(const char *path, const std::vector<CacheEntry> &es) {
+    const std::string tmp = std::string(path) + ".tmp";
+    FILE *f = fopen(tmp.c_str(), "w");
+    if (!f) return;
+    fprintf(f, "{\n");
+    for (size_t i = 0; i < es.size(); ++i)
+        fprintf(f, "  \"%s\": {\"zc\": %d, \"tiles\": \"%s\", \"ms_default\": %.4f, \"ms_tuned\": %.4f}%s\n",
+                es[i].key.c_str(), es[i].zc, es[i].tiles.c_str(), es[i].ms[0], es[i].ms[1],
+                i + 1 < es.size() ? "," : "");
+    fprintf(f, "}\n");
+    const bool good = fclose(f) == 0;
+    if (good) rename(tmp.c_str(), path);
+    else remove(tmp.c_str());
+}
+
+static int set_tiling(ac_batch *b, int zc, const std::vector<int> &shape) {
+    b->shape = shape;
+    return build_items(b, zc);
+}
+
+static int tune_measure(ac_batch *b, double dt) {
+    const size_t bytes = (size_t)8 * b->total * sizeof(float);
+    float *save = nullptr;
+    BCK(cudaMalloc(&save, bytes));
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaError_t ce = cudaMemcpyAsync(save, b->pool[b->cur], bytes, cudaMemcpyDeviceToDevice, b->stream);
+    if (ce == cudaSuccess) ce = cudaEventCreate(&e0);
+    if (ce == cudaSuccess) ce = cudaEventCreate(&e1);
+    int rc = ce == cudaSuccess ? AC_OK : ac_report_cuda(ce);
+    const int reps = 3;
+    std::vector<int> best_shape(b->nbox, AC_TILE_32X8);
+    int best_zc = 64;
+    float best = 1e30f, t = 0.f;
+    if (rc == AC_OK) rc = set_tiling(b, 64, best_shape);
+    if (rc == AC_OK) rc = time_step(b, dt, save, bytes, reps, e0, e1, &t);
+    if (rc == AC_OK) b->tune_ms[0] = t;
+    for (int sh = 0; sh < 2 && rc == AC_OK; ++sh)
+        for (int c = 0; c < 5 && rc == AC_OK; ++c) {
+            const std::vector<int> all(b->nbox, sh);
+            rc = set_tiling(b, TUNE_ZC[c], all);
+            if (rc == AC_OK) rc = time_step(b, dt, save, bytes, reps, e0, e1, &t);
+            if (rc == AC_OK && t < best) {
+                best = t;
+                best_zc = TUNE_ZC[c];
+                best_shape = all;
+            }
+        }
+    // box-size classes, largest total first
+    std::vector<std::pair<long long, std::pair<int, int>>> classes;
+    for (const ac_box &x : b->boxes) {
+        bool seen = false;
+        for (auto &c : classes)
+            if (c.second.first == x.nx && c.second.second == x.ny) {
+                c.first += (long long)x.nx * x.ny * x.nz;
+                seen = true;
+            }
+        if (!seen) classes.push_back({(long long)x.nx * x.ny * x.nz, {x.nx, x.ny}});
+    }
+    std::stable_sort(classes.begin(), classes.end(),
+                     [](const auto &p, const auto &q) { return p.first > q.first; });
+    for (size_t k = 0; k < classes.size() && classes.size() > 1 && rc == AC_OK; ++k) {
+        std::vector<int> trial = best_shape;
+        for (int i = 0; i < b->nbox; ++i)
+            if (b->boxes[i].nx == classes[k].second.first && b->boxes[i].ny == classes[k].second.second)
+                trial[i] = 1 - trial[i];
+        rc = set_tiling(b, best_zc, trial);
+        if (rc == AC_OK) rc = time_step(b, dt, save, bytes, reps, e0, e1, &t);
+        if (rc == AC_OK && t < best * (1.f - TUNE_MARGIN)) {
+            best = t;
+            best_shape = trial;
+        }
+    }
+    if (rc == AC_OK) rc = set_tiling(b, best_zc, best_shape);
+    if (rc == AC_OK) b->tune_ms[1] = best;
+    // the state as it was
+    ce = cudaMemcpyAsync(b->pool[b->cur], save, bytes, cudaMemcpyDeviceToDevice, b->stream);
+    if (ce == cudaSuccess) ce = cudaStreamSynchronize(b->stream);
+    if (rc == AC_OK && ce != cudaSuccess) rc = ac_report_cuda(ce);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    cudaFree(save);
+    return rc;
 }
 
 extern "C" int ac_batch_tune(ac_batch *b, double dt, const char *cache_path, int *zc_out) {
     if (!b || !isfinite(dt)) return AC_ERR_ARG;
     if (b->next_s != 0) return AC_ERR_STATE;
     const std::string sig = batch_signature(b);
-    if (cache_path) {
-        FILE *f = fopen(cache_path, "r");
-        if (f) {
-            char key[512];
-            int zc = 0;
-            int found = 0;
-            while (fscanf(f, "%511s %d", key, &zc) == 2)
-                if (sig == key && zc > 0) found = zc;
-            fclose(f);
-            if (found) {
-                int rc = build_items(b, found);
-                if (rc) return rc;
-                if (zc_out) *zc_out = found;
-                return AC_OK;
-            }
+    std::vector<CacheEntry> cache;
+    const bool writable = cache_path ? read_cache(cache_path, &cache) : false;
+    for (const CacheEntry &e : cache)
+        if (e.key == sig && (int)e.tiles.size() == b->nbox) {
+            std::vector<int> shape(b->nbox);
+            for (int i = 0; i < b->nbox; ++i) shape[i] = e.tiles[i] - '0';
+            int rc = set_tiling(b, e.zc, shape);
+            if (rc) return rc;
+            b->tune_ms[0] = e.ms[0];
+            b->tune_ms[1] = e.ms[1];
+            if (zc_out) *zc_out = e.zc;
+            return AC_OK;
         }
-    }
-    const int cand[5] = {8, 16, 32, 64, 128};
-    cudaEvent_t e0, e1;
-    BCK(cudaEventCreate(&e0));
-    BCK(cudaEventCreate(&e1));
-    float best = 1e30f;
-    int best_zc = b->zc;
-    for (int c = 0; c < 5; ++c) {
-        int rc = build_items(b, cand[c]);
-        if (rc) return rc;
-        BCK(launch_batch(b, dt, 0, b->cur, b->stream));  // warm-up
-        float tmin = 1e30f;
-        for (int r = 0; r < 3; ++r) {
-            BCK(cudaEventRecord(e0, b->stream));
-            BCK(launch_batch(b, dt, 0, b->cur, b->stream));
-            BCK(cudaEventRecord(e1, b->stream));
-            BCK(cudaEventSynchronize(e1));
-            float ms = 0.f;
-            BCK(cudaEventElapsedTime(&ms, e0, e1));
-            tmin = ms < tmin ? ms : tmin;
-        }
-        b->launches += 4;
-        if (tmin < best) {
-            best = tmin;
-            best_zc = cand[c];
-        }
-    }
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
-    int rc = build_items(b, best_zc);
+    int rc = tune_measure(b, dt);
     if (rc) return rc;
-    if (cache_path) {
-        FILE *f = fopen(cache_path, "a");
-        if (f) {
-            fprintf(f, "%s %d\n", sig.c_str(), best_zc);
-            fclose(f);
-        }
+    if (cache_path && writable) {
+        CacheEntry e;
+        e.key = sig;
+        e.zc = b->zc;
+        for (int i = 0; i < b->nbox; ++i) e.tiles.push_back((char)('0' + b->shape[i]));
+        e.ms[0] = b->tune_ms[0];
+        e.ms[1] = b->tune_ms[1];
+        cache.push_back(e);
+        write_cache(cache_path, cache);
     }
-    if (zc_out) *zc_out = best_zc;
+    if (zc_out) *zc_out = b->zc;
+    return AC_OK;
+}
+
+extern "C" int ac_batch_set_tiling(ac_batch *b, int zc, const int *shapes) {
+    if (!b || zc < 1 || zc > 4096) return AC_ERR_ARG;
+    std::vector<int> shape(b->nbox, AC_TILE_32X8);
+    if (shapes)
+        for (int i = 0; i < b->nbox; ++i) {
+            if (shapes[i] != AC_TILE_32X8 && shapes[i] != AC_TILE_16X16) return AC_ERR_ARG;
+            shape[i] = shapes[i];
+        }
+    return set_tiling(b, zc, shape);
+}
+
+extern "C" int ac_batch_get_tiling(const ac_batch *b, int *zc, int *shapes, float tune_ms[2]) {
+    if (!b) return AC_ERR_ARG;
+    if (zc) *zc = b->zc;
+    if (shapes)
+        for (int i = 0; i < b->nbox; ++i) shapes[i] = b->shape[i];
+    if (tune_ms) {
+        tune_ms[0] = b->tune_ms[0];
+        tune_ms[1] = b->tune_ms[1];
+    }
     return AC_OK;
 }
 

@@ -1,13 +1,14 @@
 // Shared-memory tiled, z-marching variant of the fused substep for binary32
 // fields (periodic layout).
 //
-// Each CTA owns a 32 x 8 column tile and walks a range of z.  A ring of
-// shared-memory plane tiles holds, for all eight fields, the tile plus its
-// radius-3 halo in x and y (x rounded out to 16-byte boundaries: columns
-// x0-4 .. x0+35); planes z-3 .. z+3 are resident while output plane z is
-// computed and the next planes stream in with cp.async.  Every stencil point
-// of Eq. 13 is then one shared-memory load at a compile-time offset.  The
-// periodic map of Sec. 3.3 is applied once per copied chunk.
+// Each CTA of 256 threads owns a TX x TY column tile (32 x 8 or 16 x 16) and
+// walks a range of z.  A ring of shared-memory plane tiles holds, for all eight
+// fields, the tile plus its radius-3 halo in x and y (x rounded out to 16-byte
+// boundaries: columns x0-4 .. x0+TX+3); planes z-3 .. z+3 are resident while
+// output plane z is computed and the next planes stream in with cp.async.
+// Every stencil point of Eq. 13 is then one shared-memory load at a
+// compile-time offset.  The periodic map of Sec. 3.3 is applied once per
+// copied chunk.
 #pragma once
 
 #include "stencil_pair.cuh"
@@ -15,43 +16,63 @@
 
 namespace ac {
 
-constexpr int TT_X = 32;                  // tile width (one warp)
-constexpr int TT_Y = 8;                   // tile height
-constexpr int TT_ROW = TT_X + 8;          // floats per smem row: x0-4 .. x0+TT_X+3
-constexpr int TT_ROWS = TT_Y + 6;         // rows: y0-3 .. y0+TT_Y+2
-constexpr int TT_FIELD = TT_ROW * TT_ROWS;
-constexpr int TT_PLANE = NF * TT_FIELD;   // floats per plane slot
+constexpr int TT_THREADS = 256;           // threads per CTA, launched as 32 x 8
 constexpr int TT_PF = 2;                  // planes in flight beyond z+3
 constexpr int TT_NP = 7 + TT_PF;          // ring slots
-constexpr int TT_THREADS = TT_X * TT_Y;
 constexpr int TT_NW = TT_PF + 2;          // ring slots for the accumulator w of output planes
-// Copies per thread per plane: 16-byte chunks (x rounded to 16 B) or 4-byte elements.
-constexpr int TT_VCH = NF * TT_ROWS * (TT_ROW / 4);
-constexpr int TT_VPT = (TT_VCH + TT_THREADS - 1) / TT_THREADS;
-constexpr int TT_ECH = NF * TT_ROWS * TT_ROW;
-constexpr int TT_EPT = (TT_ECH + TT_THREADS - 1) / TT_THREADS;
 
-template <typename W>
+// Tile shape: TX x TY output cells, shared-memory rows of TX + 8 floats (x0-4 ..
+// x0+TX+3) for rows y0-3 .. y0+TY+2.  Threads map to cells so that a warp's 32
+// lanes read distinct banks at any common stencil offset: for TX = 32 a warp is
+// one row; for TX = 16 its two half-warps lie two rows apart (2 x 24 floats =
+// 16 banks), warp w holding rows r and r + 2, r = 4 (w / 2) + w % 2.
+template <int TX_, int TY_>
+struct TileShape {
+    static constexpr int TX = TX_, TY = TY_;
+    static constexpr int ROW = TX + 8;        // floats per smem row
+    static constexpr int ROWS = TY + 6;       // rows per field
+    static constexpr int FIELD = ROW * ROWS;
+    static constexpr int PLANE = NF * FIELD;  // floats per plane slot
+    // copies per thread per plane: 16-byte chunks (x rounded to 16 B) or 4-byte elements
+    static constexpr int VCH = NF * ROWS * (ROW / 4);
+    static constexpr int VPT = (VCH + TT_THREADS - 1) / TT_THREADS;
+    static constexpr int ECH = NF * ROWS * ROW;
+    static constexpr int EPT = (ECH + TT_THREADS - 1) / TT_THREADS;
+    static_assert(TX * TY == TT_THREADS && (TX == 32 || TX == 16), "tile shape");
+    __device__ static __forceinline__ int tx(int tid) { return TX == 32 ? tid & 31 : tid & 15; }
+    __device__ static __forceinline__ int ty(int tid) {
+        if (TX == 32) return tid >> 5;
+        const int w = tid >> 5;
+        return 4 * (w >> 1) + (w & 1) + 2 * ((tid >> 4) & 1);
+    }
+};
+using Tile32x8 = TileShape<32, 8>;
+using Tile16x16 = TileShape<16, 16>;
+
+// Linear thread index of a 32 x 8 launch.
+__device__ __forceinline__ int tt_tid() { return threadIdx.y * 32 + threadIdx.x; }
+
+template <typename W, class S>
 constexpr size_t tt_smem_bytes() {
-    return sizeof(float) * TT_NP * TT_PLANE + sizeof(W) * TT_NW * NF * TT_THREADS;
+    return sizeof(float) * TT_NP * S::PLANE + sizeof(W) * TT_NW * NF * TT_THREADS;
 }
 
 // The values on the cell's own z-column (dx = dy = 0) come from a per-thread
 // register queue of planes z-3 .. z+3; every other point from shared memory.
-template <typename R>
+template <typename R, int ROW>
 struct SmemView {
     const R *base;
     const int (&slot)[7];
     const R (&zq)[7];
     __device__ __forceinline__ R operator()(int dx, int dy, int dz) const {
         if (dx == 0 && dy == 0) return zq[dz + 3];
-        return base[slot[dz + 3] + dy * TT_ROW + dx];
+        return base[slot[dz + 3] + dy * ROW + dx];
     }
 };
 
 // Two fields with the same stencil points read together as a float2 (x: q1,
 // y: q2) for the paired stencils of stencil_pair.cuh.
-template <typename R>
+template <typename R, int ROW>
 struct SmemPairView {
     const R *c1, *c2;
     const int (&slot)[7];
@@ -59,21 +80,21 @@ struct SmemPairView {
     const R (&z2)[7];
     __device__ __forceinline__ float2 operator()(int dx, int dy, int dz) const {
         if (dx == 0 && dy == 0) return make_float2(z1[dz + 3], z2[dz + 3]);
-        const int o = slot[dz + 3] + dy * TT_ROW + dx;
+        const int o = slot[dz + 3] + dy * ROW + dx;
         return make_float2(c1[o], c2[o]);
     }
 };
 
-template <typename R>
+template <typename R, class S>
 struct SmemCell {
-    const R *cell;  // smem + (ty + 3) * TT_ROW + tx + 4
+    const R *cell;  // smem + (ty + 3) * S::ROW + tx + 4
     const int (&slot)[7];
     const R (&zq)[NF][7];
-    __device__ __forceinline__ SmemView<R> operator[](int q) const {
-        return {cell + q * TT_FIELD, slot, zq[q]};
+    __device__ __forceinline__ SmemView<R, S::ROW> operator[](int q) const {
+        return {cell + q * S::FIELD, slot, zq[q]};
     }
-    __device__ __forceinline__ SmemPairView<R> pair(int q1, int q2) const {
-        return {cell + q1 * TT_FIELD, cell + q2 * TT_FIELD, slot, zq[q1], zq[q2]};
+    __device__ __forceinline__ SmemPairView<R, S::ROW> pair(int q1, int q2) const {
+        return {cell + q1 * S::FIELD, cell + q2 * S::FIELD, slot, zq[q1], zq[q2]};
     }
 };
 
@@ -106,31 +127,31 @@ __device__ __forceinline__ int wrap_mod(int v, int n) {
 // offset inside a ring slot and its source offset inside a z-plane (field base
 // pointer folded in).  The periodic map of Sec. 3.3 is applied here once; only
 // the z-plane offset changes from plane to plane.
-template <bool VEC>
+template <class S, bool VEC>
 struct TileCopies {
-    static constexpr int N = VEC ? TT_VPT : TT_EPT;
+    static constexpr int N = VEC ? S::VPT : S::EPT;
     int soff[N];
     const float *src[N];
     int n;
     AC_BC_ONLY(long long bc_idx[N]; long long bc_lim;)
     template <class TA>
     __device__ __forceinline__ void init(const TA &ta, const Geom &g, int x0, int y0) {
-        const int tid = threadIdx.y * TT_X + threadIdx.x;
+        const int tid = tt_tid();
         n = 0;
         constexpr int CW = VEC ? 4 : 1;             // floats per copy
-        constexpr int CH = TT_ROW / CW;             // copies per row
-        constexpr int TOTAL = NF * TT_ROWS * CH;
+        constexpr int CH = S::ROW / CW;             // copies per row
+        constexpr int TOTAL = NF * S::ROWS * CH;
 #pragma unroll
         for (int u = 0; u < N; ++u) {
             const int t = tid + u * TT_THREADS;
             if (t < TOTAL) {
-                const int q = t / (TT_ROWS * CH);
-                const int rem = t - q * (TT_ROWS * CH);
+                const int q = t / (S::ROWS * CH);
+                const int rem = t - q * (S::ROWS * CH);
                 const int r = rem / CH;
                 const int c = rem - r * CH;
                 const int gy = wrap_mod(y0 - 3 + r, g.ny);
                 const int gx = wrap_mod(x0 - 4 + CW * c, g.nx);
-                soff[u] = q * TT_FIELD + r * TT_ROW + CW * c;
+                soff[u] = q * S::FIELD + r * S::ROW + CW * c;
                 src[u] = ta.fin(q) + (long long)gy * g.px + gx;
                 AC_BC_ONLY(bc_idx[u] = (long long)gy * g.px + gx; bc_lim = g.elems;)
                 n = u + 1;
@@ -156,7 +177,7 @@ template <typename W, class TA>
 __device__ __forceinline__ void tile_load_w(W *wslot, const TA &ta, const Geom &g, int i, int j,
                                             int z, bool active) {
     if (!active) return;
-    const int tid = threadIdx.y * TT_X + threadIdx.x;
+    const int tid = tt_tid();
     const long long o = AC_BC((long long)z * g.pxy + (long long)j * g.px + i, g.elems, AC_BC_TILE_W);
 #pragma unroll
     for (int q = 0; q < NF; ++q) {
@@ -187,16 +208,18 @@ struct TileOne {
     __device__ __forceinline__ unsigned long long *cfl_max() const { return a.cfl_max; }
 };
 
-// One output tile: columns [x0, x0+32) x [y0, y0+8), planes [z0, z1).  CFL:
-// also fold the largest CFL speed of the input cells into ta.cfl_max().
-template <typename W, bool VEC, bool CFL, bool EXT, class TA>
+// One output tile of shape S: columns [x0, x0+TX) x [y0, y0+TY), planes [z0,
+// z1).  CFL: also fold the largest CFL speed of the input cells into
+// ta.cfl_max().  The per-cell arithmetic does not depend on the shape.
+template <class S, typename W, bool VEC, bool CFL, bool EXT, class TA>
 __device__ __forceinline__ void tiled_body(const TA &ta, int x0, int y0, int z0, int z1,
                                            unsigned char *smem_raw) {
+    constexpr int TT_PLANE = S::PLANE;
     float *sm = reinterpret_cast<float *>(smem_raw);
     W *wring = reinterpret_cast<W *>(sm + TT_NP * TT_PLANE);
     const Geom &g = ta.g();
-    const int tx = threadIdx.x, ty = threadIdx.y;
-    const int tid = ty * TT_X + tx;
+    const int tid = tt_tid();
+    const int tx = S::tx(tid), ty = S::ty(tid);
     const int i = x0 + tx, j = y0 + ty;
     const bool active = i < g.nx && j < g.ny;
     const int force_on = ta.force_on();
@@ -209,7 +232,7 @@ __device__ __forceinline__ void tiled_body(const TA &ta, int x0, int y0, int z0,
         exy.x = ex.x * ey.x - ex.y * ey.y;
         exy.y = ex.x * ey.y + ex.y * ey.x;
     }
-    TileCopies<VEC> cp;
+    TileCopies<S, VEC> cp;
     cp.init(ta, g, x0, y0);
 
     // One commit group per plane p; it also carries w of output plane p - 3.
@@ -234,22 +257,22 @@ __device__ __forceinline__ void tiled_body(const TA &ta, int x0, int y0, int z0,
         int slot[7];
 #pragma unroll
         for (int d = 0; d < 7; ++d) slot[d] = ((z - z0 + d) % TT_NP) * TT_PLANE;
-        const float *ctr = sm + (ty + 3) * TT_ROW + tx + 4;
+        const float *ctr = sm + (ty + 3) * S::ROW + tx + 4;
         if (z == z0) {
 #pragma unroll
             for (int q = 0; q < NF; ++q)
 #pragma unroll
-                for (int d = 0; d < 7; ++d) zq[q][d] = ctr[slot[d] + q * TT_FIELD];
+                for (int d = 0; d < 7; ++d) zq[q][d] = ctr[slot[d] + q * S::FIELD];
         } else {
 #pragma unroll
             for (int q = 0; q < NF; ++q) {
 #pragma unroll
                 for (int d = 0; d < 6; ++d) zq[q][d] = zq[q][d + 1];
-                zq[q][6] = ctr[slot[6] + q * TT_FIELD];
+                zq[q][6] = ctr[slot[6] + q * S::FIELD];
             }
         }
         if (active) {
-            const SmemCell<float> cell{ctr, slot, zq};
+            const SmemCell<float, S> cell{ctr, slot, zq};
             float frc[3] = {0.f, 0.f, 0.f};
             if (force_on) {
                 const float cph = exy.x * ez.x - exy.y * ez.y;
@@ -284,19 +307,23 @@ __device__ __forceinline__ void tiled_body(const TA &ta, int x0, int y0, int z0,
     if (CFL) block_max_to_global((double)cfl, ta.cfl_max());
 }
 
+// Tile shape of the single-box launch.
+using TileOneShape = Tile32x8;
+
 template <typename W, bool VEC, bool CFL, bool EXT>
 __global__ void __launch_bounds__(TT_THREADS, 1) substep_tiled_kernel(const SubstepArgs<float, W> a) {
     extern __shared__ __align__(128) unsigned char tt_smem_raw[];
     const int z0 = blockIdx.z * a.zchunk;
     const int z1 = min(z0 + a.zchunk, a.g.nz);
     const TileOne<W> ta{a};
-    tiled_body<W, VEC, CFL, EXT>(ta, blockIdx.x * TT_X, blockIdx.y * TT_Y, z0, z1, tt_smem_raw);
+    tiled_body<TileOneShape, W, VEC, CFL, EXT>(ta, blockIdx.x * TileOneShape::TX,
+                                               blockIdx.y * TileOneShape::TY, z0, z1, tt_smem_raw);
 }
 
 template <typename W, bool VEC, bool CFL, bool EXT>
 static cudaError_t launch_tiled_variant_e(const SubstepArgs<float, W> &a, dim3 grid, dim3 block,
                                           cudaStream_t st) {
-    const size_t smem = tt_smem_bytes<W>();
+    const size_t smem = tt_smem_bytes<W, TileOneShape>();
     cudaError_t e = cudaFuncSetAttribute(substep_tiled_kernel<W, VEC, CFL, EXT>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
@@ -334,14 +361,14 @@ cudaError_t launch_substep_tiled_t(const SubstepLaunch &L, cudaStream_t st, int 
     for (int m = 0; m < 3; ++m) a.amp_e[m] = (float)L.force.amp_e[m];
     a.cfl_max = L.cfl_max;
 
-    const unsigned gx = (L.g.nx + TT_X - 1) / TT_X;
-    const unsigned gy = (L.g.ny + TT_Y - 1) / TT_Y;
+    const unsigned gx = (L.g.nx + TileOneShape::TX - 1) / TileOneShape::TX;
+    const unsigned gy = (L.g.ny + TileOneShape::TY - 1) / TileOneShape::TY;
     // z range per CTA: up to 128 planes, fewer until there are at least two CTAs per SM.
     int zc = L.g.nz < 128 ? L.g.nz : 128;
     while (zc > 16 && (long long)gx * gy * ((L.g.nz + zc - 1) / zc) < 2 * 152) zc = (zc + 1) / 2;
     a.zchunk = zc;
     const dim3 grid(gx, gy, (L.g.nz + zc - 1) / zc);
-    const dim3 block(TT_X, TT_Y, 1);
+    const dim3 block(32, 8, 1);
     const bool vec = (L.g.nx % 4) == 0;
     const bool cfl = a.cfl_max != nullptr;
     cudaError_t e;

@@ -6,6 +6,7 @@ item), whatever the work split (autotuned z extent) and with or without the
 CUDA graph; boxes are also checked against the FP64 oracle within the binary32
 bound of the single-box tests (f 2e-6, w 2e-4 relative per field).
 """
+import json
 import math
 
 import numpy as np
@@ -66,15 +67,22 @@ def test_batch_equals_single_boxes_bitwise(graph, precision):
 def test_tuner_and_work_split_do_not_change_results(tmp_path):
     states = [_state(spec[0], 20 + i) for i, spec in enumerate(BOXES)]
     outs = []
+    cache = str(tmp_path / "tune.json")
     for tune in (False, True):
         b = ac.Batch(BOXES)
         for i, f in enumerate(states):
             b.load(i, f)
         if tune:
-            cache = str(tmp_path / "tune.txt")
             zc = ac.ac_batch_tune(b.b, 1e-3, cache)
             assert zc in (8, 16, 32, 64, 128)
+            zc1, shapes, ms = ac.ac_batch_get_tiling(b.b, len(BOXES))
+            assert zc1 == zc and set(shapes) <= {ac.AC_TILE_32X8, ac.AC_TILE_16X16}
+            assert ms[0] > 0 and 0 < ms[1] <= ms[0]  # the default split is a candidate
+            cls = {}
+            for (n, _, _, _), sh in zip(BOXES, shapes):  # one shape per (nx, ny) class
+                assert cls.setdefault(n[:2], sh) == sh
             assert ac.ac_batch_tune(b.b, 1e-3, cache) == zc  # read back from the cache
+            assert ac.ac_batch_get_tiling(b.b, len(BOXES))[1] == shapes
             assert ac.ac_batch_info(b.b)["zc"] == zc
             for i, f in enumerate(states):  # tuning leaves the state untouched
                 assert np.array_equal(b.store(i), f.astype(np.float32).astype(np.float64))
@@ -83,6 +91,42 @@ def test_tuner_and_work_split_do_not_change_results(tmp_path):
         b.close()
     for x, y in zip(*outs):
         assert np.array_equal(x, y)
+    with open(cache) as fh:  # the cache is a JSON object
+        entries = json.load(fh)
+    (entry,) = entries.values()
+    assert entry["zc"] == zc and len(entry["tiles"]) == len(BOXES)
+    assert [int(c) for c in entry["tiles"]] == shapes
+
+
+def test_cache_file_of_other_content_is_not_rewritten(tmp_path):
+    cache = tmp_path / "other.json"
+    cache.write_text('{"something": [1, 2, 3]}\n')
+    b = ac.Batch(BOXES[:2])
+    ac.ac_batch_tune(b.b, 1e-3, str(cache))
+    b.close()
+    assert cache.read_text() == '{"something": [1, 2, 3]}\n'
+
+
+@pytest.mark.parametrize("shapes", [[0, 0, 0, 0], [1, 1, 1, 1], [1, 0, 1, 0], [0, 1, 0, 1]])
+@pytest.mark.parametrize("zc", [5, 64])
+def test_tile_shapes_bitwise(shapes, zc):
+    """Either tile shape, for any box (ragged in x at nx = 36, in y at ny = 12,
+    smaller than a tile at (4, 8, 3)), gives the single-box result bitwise."""
+    b = ac.Batch(BOXES, precision=ac.AC_FP32_W64)
+    states = [_state(spec[0], 40 + i) for i, spec in enumerate(BOXES)]
+    for i, f in enumerate(states):
+        b.load(i, f)
+    ac.ac_batch_set_tiling(b.b, zc, shapes)
+    assert ac.ac_batch_get_tiling(b.b, len(BOXES))[:2] == (zc, shapes)
+    for s in range(3):
+        b.substep(1e-3, s)
+    for i, spec in enumerate(BOXES):
+        ref, refw = _single(spec, states[i], 1e-3, 1, ac.AC_FP32_W64)
+        assert np.array_equal(b.store(i), ref), i
+        assert np.array_equal(b.store_w(i), refw), i
+    with pytest.raises(ac.AcError):
+        ac.ac_batch_set_tiling(b.b, zc, [0, 1, 2, 0])
+    b.close()
 
 
 def test_batch_boxes_match_oracle():
