@@ -572,6 +572,28 @@ __global__ void __launch_bounds__(THREADS, 1)
         float gm = 0.f;  // EPI_SCALED_F32: this thread's largest |output| (NaN if any)
         uint32_t par = 0;  // bit k: parity of the tiles block k has held so far
         bool ok = true;
+        // EPI_MASK_BF16: the mask of the next tile is loaded while this one is
+        // written (otherwise every tile would wait for a global round trip)
+        constexpr int MK = EPI == EPI_MASK_BF16 ? COUT / 8 : 1;
+        uint4 mnext[MK];
+        auto load_mask = [&](int y, int x, int z, uint4(&m)[MK]) {
+            if constexpr (EPI == EPI_MASK_BF16) {
+                if (x >= a.nx) return;
+                AC_BC_ONLY(const long long lim = (long long)rp_cells(a.nx) * a.ny * a.nz * COUT;)
+#pragma unroll
+                for (int kc = 0; kc < MK; ++kc) {
+                    const long long e =
+                        ((((long long)z * a.ny + y) * MK + kc) * rp_cells(a.nx) + x + 1) * 8;
+                    m[kc] = *reinterpret_cast<const uint4 *>(a.mask + AC_BC(e, lim, AC_BC_CONV_ACT));
+                }
+            }
+        };
+        auto load_mask_seg = [&](long long g) {  // first tile of segment g
+            if (g >= nseg) return;
+            const Segment s2 = segment_of(g, a, segs);
+            load_mask(s2.y, s2.seg * TM + warp * 32 + lane, s2.z0, mnext);
+        };
+        load_mask_seg(blockIdx.x);
         for (long long g = blockIdx.x; g < nseg && ok; g += gridDim.x) {
             const Segment sg = segment_of(g, a, segs);
             const int x = sg.seg * TM + warp * 32 + lane;
@@ -591,6 +613,15 @@ __global__ void __launch_bounds__(THREADS, 1)
                 tc_fence_before_sync();
                 __syncwarp();
                 if (lane == 0) mbar_arrive(&acce[kb]);
+                uint4 mcur[MK];
+#pragma unroll
+                for (int kc = 0; kc < MK; ++kc) mcur[kc] = mnext[kc];
+                if (EPI == EPI_MASK_BF16) {
+                    if (i + 1 < sg.len)
+                        load_mask(sg.y, x, sg.z0 + i + 1, mnext);
+                    else
+                        load_mask_seg(g + gridDim.x);
+                }
                 if (x >= a.nx) continue;
                 const int z = sg.z0 + i;
                 if (EPI == EPI_RELU_BF16 || EPI == EPI_MASK_BF16) {
@@ -603,8 +634,7 @@ __global__ void __launch_bounds__(THREADS, 1)
                             ((((long long)z * a.ny + sg.y) * (COUT / 8) + kc) * rp_cells(a.nx)) * 8;
                         if constexpr (EPI == EPI_MASK_BF16) {
                             __align__(16) bf16 m[8];
-                            *reinterpret_cast<uint4 *>(m) = *reinterpret_cast<const uint4 *>(
-                                a.mask + AC_BC(plane + (long long)(x + 1) * 8, lim, AC_BC_CONV_ACT));
+                            *reinterpret_cast<uint4 *>(m) = mcur[kc];
 #pragma unroll
                             for (int c = 0; c < 8; ++c)
                                 o[8 * kc + c] = __bfloat162float(m[c]) > 0.f
@@ -782,6 +812,7 @@ __host__ __device__ constexpr size_t pair_smem_bytes(int cin) {
 template <int CIN, int COUT, int EPI>
 __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(THREADS, 1)
     conv_tc_pair_kernel(const __grid_constant__ CUtensorMap xmap, const ConvTcArgs a) {
+    static_assert(EPI != EPI_MASK_BF16, "the paired kernel has no mask epilogue");
     // N = 3 NB must be a multiple of 32 for cta_group::2, so the stack always has
     // 32 rows per kz (zero weights past COUT); the epilogue reads NR of them
     constexpr int NB = 32;
@@ -947,7 +978,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(THREADS, 1)
     } else {  // ---- epilogue: warps 0-3 of each CTA, its TMEM lanes 32 warp .. 32 warp + 31
         float bias[COUT];
 #pragma unroll
-        for (int c = 0; c < COUT; ++c) bias[c] = EPI == EPI_MASK_BF16 ? 0.f : a.bias[c];
+        for (int c = 0; c < COUT; ++c) bias[c] = a.bias[c];
         float gm = 0.f;
         uint32_t par = 0;  // bit k: parity of the tiles block k has held so far
         bool ok = true;
@@ -973,7 +1004,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(THREADS, 1)
                 if (lane == 0) mbar_arrive_cluster(leader_addr(&acce[kb]));
                 const int z = sg.z0 + i;
                 if (!ps.write || z < ps.zw || x >= a.nx) continue;
-                if (EPI == EPI_RELU_BF16 || EPI == EPI_MASK_BF16) {
+                if (EPI == EPI_RELU_BF16) {
                     __align__(16) bf16 o[COUT];
                     AC_BC_ONLY(const long long lim =
                                    (long long)rp_cells(a.nx) * a.ny * a.nz * COUT;)
@@ -981,21 +1012,10 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(THREADS, 1)
                     for (int kc = 0; kc < COUT / 8; ++kc) {
                         const long long plane =
                             ((((long long)z * a.ny + sg.y) * (COUT / 8) + kc) * rp_cells(a.nx)) * 8;
-                        if constexpr (EPI == EPI_MASK_BF16) {
-                            __align__(16) bf16 m[8];
-                            *reinterpret_cast<uint4 *>(m) = *reinterpret_cast<const uint4 *>(
-                                a.mask + AC_BC(plane + (long long)(x + 1) * 8, lim, AC_BC_CONV_ACT));
 #pragma unroll
-                            for (int c = 0; c < 8; ++c)
-                                o[8 * kc + c] = __bfloat162float(m[c]) > 0.f
-                                                    ? __float2bfloat16_rn(v[8 * kc + c])
-                                                    : __float2bfloat16_rn(0.f);
-                        } else {
-#pragma unroll
-                            for (int c = 0; c < 8; ++c)
-                                o[8 * kc + c] =
-                                    __float2bfloat16_rn(fmaxf(v[8 * kc + c] + bias[8 * kc + c], 0.f));
-                        }
+                        for (int c = 0; c < 8; ++c)
+                            o[8 * kc + c] =
+                                __float2bfloat16_rn(fmaxf(v[8 * kc + c] + bias[8 * kc + c], 0.f));
                         const uint4 val = reinterpret_cast<const uint4 *>(o)[kc];
                         if (a.y) {
                             store_rp(a.y, plane + (long long)(x + 1) * 8, AC_BC_ONLY(lim, ) val);

@@ -453,8 +453,10 @@ __global__ void restrict_kernel(const T *__restrict__ fine, int nxf, int nyf, in
 // Loss and output gradient for the tcgen05 backward pass: as loss_grad_kernel,
 // with dY (8 channels) written row-planar twice: with the periodic halo (dyh,
 // one plane, the input of the next convolution) and without it (dyn, two planes,
-// the second zero: the weight-gradient operand, N padded to 16).  Block partials
-// of the loss in partials[blockIdx.x].
+// the second zero: the weight-gradient operand, N padded to 16).  A cell's
+// eight squares are summed in binary32, the cells' sums in binary64 (binary64
+// work is slow on this part: one conversion and one add per cell); block
+// partials of the loss in partials[blockIdx.x].
 __global__ void loss_grad_rp_kernel(const float *__restrict__ y, F8 tgt,
                                     const float *__restrict__ inv_out, int nx, long long n,
                                     bf16 *__restrict__ dyh, bf16 *__restrict__ dyn,
@@ -462,17 +464,20 @@ __global__ void loss_grad_rp_kernel(const float *__restrict__ y, F8 tgt,
     double acc = 0.0;
     const float gsc = (float)(2.0 / (8.0 * (double)n));
     const long long nxp = tc::rp_cells(nx);
+    const bool narrow = n <= 0xffffffffLL;
     for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < n;
          p += (long long)gridDim.x * blockDim.x) {
-        const long long row = p / nx;  // z * ny + y
+        const long long row = narrow ? (long long)((unsigned)p / (unsigned)nx) : p / nx;  // z * ny + y
         const int xi = (int)(p - row * nx);
         __align__(16) bf16 v[8];
+        float sq = 0.f;
 #pragma unroll
         for (int c = 0; c < 8; ++c) {
             const float d = y[c * n + p] - tgt.p[c][p] * inv_out[c];
-            acc += (double)d * (double)d;
+            sq = fmaf(d, d, sq);
             v[c] = __float2bfloat16_rn(gsc * d);
         }
+        acc += (double)sq;
         const uint4 val = *reinterpret_cast<const uint4 *>(v);
         uint4 *h = reinterpret_cast<uint4 *>(dyh + row * nxp * 8);
         h[xi + 1] = val;
@@ -492,24 +497,26 @@ __global__ void loss_grad_rp_kernel(const float *__restrict__ y, F8 tgt,
 
 // Bias-gradient partials from a row-planar gradient without halo (every slot but
 // the cells' is zero): block (b, kc) sums plane kc of rows b, b + G, ... into
-// bpart[(kc * G + b) * 8 + c], channel 8 kc + c, in binary64 (fixed order).
+// bpart[(kc * G + b) * 8 + c], channel 8 kc + c.  A thread sums its values in
+// binary32 (a few dozen terms), the block its threads' sums in binary64, in a
+// fixed order.  Threads: 32 slots of a row x 8 rows at a time.
 __global__ void bias_grad_rp_kernel(const bf16 *__restrict__ zn, int kcs, int nxp, long long rows,
                                     double *__restrict__ bpart) {
     const int kc = blockIdx.y, G = gridDim.x;
-    const long long nr = rows > blockIdx.x ? (rows - 1 - blockIdx.x) / G + 1 : 0;
-    double s[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-    for (long long e = threadIdx.x; e < nr * nxp; e += blockDim.x) {
-        const long long r = blockIdx.x + (e / nxp) * G;
-        const long long j = e % nxp;
-        __align__(16) bf16 v[8];
-        *reinterpret_cast<uint4 *>(v) =
-            *reinterpret_cast<const uint4 *>(zn + ((r * kcs + kc) * nxp + j) * 8);
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    float s[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    for (long long r = blockIdx.x + (long long)ty * G; r < rows; r += 8LL * G) {
+        const uint4 *row = reinterpret_cast<const uint4 *>(zn + (r * kcs + kc) * nxp * 8);
+        for (int j = tx; j < nxp; j += 32) {
+            __align__(16) bf16 v[8];
+            *reinterpret_cast<uint4 *>(v) = row[j];
 #pragma unroll
-        for (int c = 0; c < 8; ++c) s[c] += (double)__bfloat162float(v[c]);
+            for (int c = 0; c < 8; ++c) s[c] += __bfloat162float(v[c]);
+        }
     }
     __shared__ double sh[8][256];
 #pragma unroll
-    for (int c = 0; c < 8; ++c) sh[c][threadIdx.x] = s[c];
+    for (int c = 0; c < 8; ++c) sh[c][threadIdx.x] = (double)s[c];
     __syncthreads();
     for (int o = blockDim.x / 2; o > 0; o >>= 1) {
         if ((int)threadIdx.x < o)
@@ -520,14 +527,14 @@ __global__ void bias_grad_rp_kernel(const bf16 *__restrict__ zn, int kcs, int nx
     if (threadIdx.x < 8) bpart[((long long)kc * G + blockIdx.x) * 8 + threadIdx.x] = sh[threadIdx.x][0];
 }
 
-// gb[co] = sum over blocks of the partials above (co < cout).
-__global__ void bias_reduce_kernel(const double *__restrict__ bpart, int G, int cout,
-                                   float *__restrict__ gb) {
-    const int co = threadIdx.x;
-    if (co >= cout) return;
+// gb[co] = sum over blocks of the partials above: one warp per channel, lane l
+// taking blocks l, l + 32, ..., then a fixed shuffle tree.
+__global__ void bias_reduce_kernel(const double *__restrict__ bpart, int G, float *__restrict__ gb) {
+    const int co = blockIdx.x, lane = threadIdx.x;
     double s = 0.0;
-    for (int b = 0; b < G; ++b) s += bpart[((long long)(co / 8) * G + b) * 8 + co % 8];
-    gb[co] = (float)s;
+    for (int b = lane; b < G; b += 32) s += bpart[((long long)(co / 8) * G + b) * 8 + co % 8];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) gb[co] = (float)s;
 }
 
 // Weights of the input-gradient convolution: Wt[ci][co][26 - tap] = W[co][ci][tap]
@@ -1139,7 +1146,8 @@ static int ensure_train(ac_closure *c) {
             if (per[l] * c->tr_grid[2 + l] > wmax) wmax = per[l] * c->tr_grid[2 + l];
     }
     const long long rows = (long long)c->g.ny * c->g.nz;
-    c->tr_bias_blocks = (int)(rows < 256 ? rows : 256);
+    // bias partial blocks: about 64 rows each (a thread's binary32 sum stays short)
+    c->tr_bias_blocks = (int)(rows / 64 < 1 ? 1 : (rows / 64 > 4096 ? 4096 : rows / 64));
     const long long np2 = (long long)tc::rp_cells(c->g.nx) * rows;
     const size_t b_wpart = align256(sizeof(float) * (size_t)wmax * tc::TM);
     const size_t b_bpart = align256(sizeof(double) * 4 * (size_t)c->tr_bias_blocks * 8);
@@ -1224,14 +1232,14 @@ static void launch_wgrad(const ac_closure *c, const CUtensorMap &xmap, const CUt
     a.err = c->tc_err;
     tc::wgrad_tc_kernel<CIN, COUT>
         <<<grid, tc::THREADS, tc::WgradShape<CIN, COUT>::SMEM, c->stream>>>(xmap, dmap, a);
-    tc::wgrad_tc_reduce_kernel<CIN, COUT><<<64, 256, 0, c->stream>>>(c->wpart, grid, cin_real, gW);
+    tc::wgrad_tc_reduce_kernel<CIN, COUT><<<152, 256, 0, c->stream>>>(c->wpart, grid, cin_real, gW);
 }
 
 static void launch_bias(const ac_closure *c, const bf16 *zn, int kcs, int cout, float *gb) {
     const long long rows = (long long)c->g.ny * c->g.nz;
     bias_grad_rp_kernel<<<dim3((unsigned)c->tr_bias_blocks, (unsigned)(cout / 8)), 256, 0, c->stream>>>(
         zn, kcs, tc::rp_cells(c->g.nx), rows, c->bpart);
-    bias_reduce_kernel<<<1, 32, 0, c->stream>>>(c->bpart, c->tr_bias_blocks, cout, gb);
+    bias_reduce_kernel<<<cout, 32, 0, c->stream>>>(c->bpart, c->tr_bias_blocks, gb);
 }
 
 // Backward pass on the tcgen05 kernels: forward (row-planar activations kept),

@@ -251,27 +251,29 @@ __global__ void __launch_bounds__(THREADS, 1)
     if (warp == 0) tmem_dealloc(tmem, S::TCOLS);
 }
 
-// gW[co][ci][kz][ky][kx] (ci < cin_real) = sum over CTAs of the partial of
-// its (kx, block) accumulator, row (plane - block start) * 8 + ci % 8, column co;
-// binary64 sums in CTA order.
+// gW[co][ci][kz][ky][kx] (ci < cin_real) from the per-CTA partials: one thread
+// per partial entry (accumulator k = kx * NMB + block, column co, row m), rows
+// fastest so that the CTAs' blocks are read coalesced; entries that hold no
+// gradient (padded columns and rows, planes another block owns) are skipped.
+// Row m of block mb is plane P = P0(mb) + m / 8, channel 8 (P % KC) + m % 8,
+// tap row P / KC = 3 kz + ky.  Binary64 sums in CTA order.
 template <int CIN, int COUT>
 __global__ void wgrad_tc_reduce_kernel(const float *__restrict__ part, int ctas, int cin_real,
                                        float *__restrict__ gW) {
     using S = WgradShape<CIN, COUT>;
-    const int total = COUT * cin_real * 27;
-    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < total; t += gridDim.x * blockDim.x) {
-        const int co = t / (cin_real * 27);
-        const int rem = t - co * cin_real * 27;
-        const int ci = rem / 27;
-        const int tap = rem - ci * 27;
-        const int kz = tap / 9, ky = (tap / 3) % 3, kx = tap % 3;
-        const int P = (kz * 3 + ky) * S::KC + ci / 8;
-        const int mb = S::NMB == 1 ? 0 : (P < 16 * (S::NMB - 1) ? P / 16 : S::NMB - 1);
-        const int m = (P - wgrad_p0(mb, S::NMB, S::NPL)) * 8 + ci % 8;
-        const int k = kx * S::NMB + mb;
+    constexpr int PER_CTA = S::NACC * S::NB * TM;
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < PER_CTA; t += gridDim.x * blockDim.x) {
+        const int m = t % TM, co = (t / TM) % S::NB, k = t / (TM * S::NB);
+        const int kx = k / S::NMB, mb = k % S::NMB;
+        const int P = wgrad_p0(mb, S::NMB, S::NPL) + m / 8;
+        if (co >= COUT || P >= S::NPL) continue;
+        const int owner = S::NMB == 1 ? 0 : (P < 16 * (S::NMB - 1) ? P / 16 : S::NMB - 1);
+        const int ci = 8 * (P % S::KC) + m % 8;
+        if (owner != mb || ci >= cin_real) continue;
+        const int tr = P / S::KC;
         double s = 0.0;
-        for (int b = 0; b < ctas; ++b) s += part[(((long long)b * S::NACC + k) * S::NB + co) * TM + m];
-        gW[t] = (float)s;
+        for (int b = 0; b < ctas; ++b) s += part[(long long)b * PER_CTA + t];
+        gW[(co * cin_real + ci) * 27 + tr * 3 + kx] = (float)s;
     }
 }
 
