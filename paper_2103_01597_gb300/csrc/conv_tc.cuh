@@ -294,9 +294,7 @@ __device__ __forceinline__ void bulk_load(void *dst, const void *src, uint32_t b
 // largest |value|, NaN counting as largest, folded into a guard word), or (the
 // input gradient through a ReLU, training) the value where the forward
 // activation at the same cell and channel (row-planar `mask`) is positive, else
-// 0, as row-planar bfloat16.  The bfloat16 epilogues can also write a second
-// row-planar copy without the periodic halo cells (`yn`: those slots, and the
-// padding, stay zero), the gradient operand of the weight-gradient kernel.
+// 0, as row-planar bfloat16 (one-CTA kernel only).
 enum { EPI_RELU_BF16 = 0, EPI_SCALED_F32 = 1, EPI_MASK_BF16 = 2 };
 
 // Bytes of one staged row (KC planes, rounded up so rows stay 128-byte aligned).
@@ -340,7 +338,6 @@ struct ConvTcArgs {
     const bf16 *w;        // weights in the shared-memory image order (see prep)
     const float *bias;    // [COUT] (not read by EPI_MASK_BF16)
     bf16 *y;              // EPI_RELU_BF16, EPI_MASK_BF16: row-planar output (or null)
-    bf16 *yn;             // the bfloat16 epilogues: row-planar copy without halo, or null
     const bf16 *mask;     // EPI_MASK_BF16: row-planar forward activation (COUT channels)
     float *out[8];        // EPI_SCALED_F32: channel c to out[c][cell]
     const float *out_scale;        // EPI_SCALED_F32: [8]
@@ -653,7 +650,6 @@ __global__ void __launch_bounds__(THREADS, 1)
                                 store_rp(a.y, plane + (long long)(a.nx + 1) * 8, AC_BC_ONLY(lim, ) val);
                             if (x == a.nx - 1) store_rp(a.y, plane, AC_BC_ONLY(lim, ) val);
                         }
-                        if (a.yn) store_rp(a.yn, plane + (long long)(x + 1) * 8, AC_BC_ONLY(lim, ) val);
                     }
                 } else {
                     const long long p = AC_BC(((long long)z * a.ny + sg.y) * a.nx + x,
@@ -1023,7 +1019,6 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(THREADS, 1)
                                 store_rp(a.y, plane + (long long)(a.nx + 1) * 8, AC_BC_ONLY(lim, ) val);
                             if (x == a.nx - 1) store_rp(a.y, plane, AC_BC_ONLY(lim, ) val);
                         }
-                        if (a.yn) store_rp(a.yn, plane + (long long)(x + 1) * 8, AC_BC_ONLY(lim, ) val);
                     }
                 } else {
                     const long long p = AC_BC(((long long)z * a.ny + sg.y) * a.nx + x,

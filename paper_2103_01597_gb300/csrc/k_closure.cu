@@ -451,15 +451,15 @@ __global__ void restrict_kernel(const T *__restrict__ fine, int nxf, int nyf, in
 }
 
 // Loss and output gradient for the tcgen05 backward pass: as loss_grad_kernel,
-// with dY (8 channels) written row-planar twice: with the periodic halo (dyh,
-// one plane, the input of the next convolution) and without it (dyn, two planes,
-// the second zero: the weight-gradient operand, N padded to 16).  A cell's
+// with dY (8 channels) written row-planar, with its periodic halo cells, twice:
+// one plane (dyh, the input of the next convolution) and two planes (dy2h, the
+// second zero: the weight-gradient operand, N padded to 16).  A cell's
 // eight squares are summed in binary32, the cells' sums in binary64 (binary64
 // work is slow on this part: one conversion and one add per cell); block
 // partials of the loss in partials[blockIdx.x].
 __global__ void loss_grad_rp_kernel(const float *__restrict__ y, F8 tgt,
                                     const float *__restrict__ inv_out, int nx, long long n,
-                                    bf16 *__restrict__ dyh, bf16 *__restrict__ dyn,
+                                    bf16 *__restrict__ dyh, bf16 *__restrict__ dy2h,
                                     double *__restrict__ partials) {
     double acc = 0.0;
     const float gsc = (float)(2.0 / (8.0 * (double)n));
@@ -483,7 +483,10 @@ __global__ void loss_grad_rp_kernel(const float *__restrict__ y, F8 tgt,
         h[xi + 1] = val;
         if (xi == 0) h[nx + 1] = val;
         if (xi == nx - 1) h[0] = val;
-        reinterpret_cast<uint4 *>(dyn + row * 2 * nxp * 8)[xi + 1] = val;
+        uint4 *h2 = reinterpret_cast<uint4 *>(dy2h + row * 2 * nxp * 8);
+        h2[xi + 1] = val;
+        if (xi == 0) h2[nx + 1] = val;
+        if (xi == nx - 1) h2[0] = val;
     }
     __shared__ double sh[256];
     sh[threadIdx.x] = acc;
@@ -495,19 +498,20 @@ __global__ void loss_grad_rp_kernel(const float *__restrict__ y, F8 tgt,
     if (threadIdx.x == 0) partials[blockIdx.x] = sh[0];
 }
 
-// Bias-gradient partials from a row-planar gradient without halo (every slot but
-// the cells' is zero): block (b, kc) sums plane kc of rows b, b + G, ... into
+// Bias-gradient partials from a row-planar gradient: block (b, kc) sums the cells
+// (slots 1 .. nx, not the halo copies) of plane kc of rows b, b + G, ... into
 // bpart[(kc * G + b) * 8 + c], channel 8 kc + c.  A thread sums its values in
 // binary32 (a few dozen terms), the block its threads' sums in binary64, in a
 // fixed order.  Threads: 32 slots of a row x 8 rows at a time.
-__global__ void bias_grad_rp_kernel(const bf16 *__restrict__ zn, int kcs, int nxp, long long rows,
+__global__ void bias_grad_rp_kernel(const bf16 *__restrict__ zn, int kcs, int nx, long long rows,
                                     double *__restrict__ bpart) {
+    const int nxp = tc::rp_cells(nx);
     const int kc = blockIdx.y, G = gridDim.x;
     const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
     float s[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     for (long long r = blockIdx.x + (long long)ty * G; r < rows; r += 8LL * G) {
         const uint4 *row = reinterpret_cast<const uint4 *>(zn + (r * kcs + kc) * nxp * 8);
-        for (int j = tx; j < nxp; j += 32) {
+        for (int j = 1 + tx; j <= nx; j += 32) {
             __align__(16) bf16 v[8];
             *reinterpret_cast<uint4 *>(v) = row[j];
 #pragma unroll
@@ -588,11 +592,11 @@ struct ac_closure {
     // the input-gradient convolutions) and without (n, weight-gradient operands),
     // tensor maps, per-CTA weight-gradient and bias partials
     void *train_block;
-    bf16 *img3b, *img2b, *dyh, *dyn, *dz2h, *dz2n, *dz1n;
+    bf16 *img3b, *img2b, *dyh, *dy2h, *dz2h, *dz1h;
     float *wt;      // flipped, transposed master weights of layers 3 and 2
     float *wpart;
     double *bpart;
-    CUtensorMap tr_map[5];  // dyh, dz2h, dyn, dz2n, dz1n
+    CUtensorMap tr_map[4];  // dyh, dz2h, dy2h, dz1h
     int tr_grid[5];         // conv<8,32,mask>, conv<32,32,mask>, wgrad<32,8>, <32,32>, <8,32>
     int tr_bias_blocks;
     float *part;
@@ -944,7 +948,6 @@ static void launch_tc(const ac_closure *c, int layer, bool pair, const bf16 *img
     a.w = img;
     a.bias = bias;
     a.y = y;
-    a.yn = nullptr;
     a.mask = nullptr;
     for (int i = 0; i < 8; ++i) a.out[i] = out ? out[i] : nullptr;
     a.out_scale = oscale ? oscale : c->scales + 8;
@@ -1139,9 +1142,9 @@ static int ensure_train(ac_closure *c) {
     CCK((wgrad_grid_for<8, 32>(c, sms, &c->tr_grid[4])));
     int wmax = 0;  // largest per-CTA partial block (floats) times grid
     {
-        const int per[3] = {tc::WgradShape<32, 8>::NACC * tc::WgradShape<32, 8>::NB,
-                            tc::WgradShape<32, 32>::NACC * tc::WgradShape<32, 32>::NB,
-                            tc::WgradShape<8, 32>::NACC * tc::WgradShape<8, 32>::NB};
+        const int per[3] = {tc::WgradShape<32, 8>::NACC * tc::WgradShape<32, 8>::N3,
+                            tc::WgradShape<32, 32>::NACC * tc::WgradShape<32, 32>::N3,
+                            tc::WgradShape<8, 32>::NACC * tc::WgradShape<8, 32>::N3};
         for (int l = 0; l < 3; ++l)
             if (per[l] * c->tr_grid[2 + l] > wmax) wmax = per[l] * c->tr_grid[2 + l];
     }
@@ -1154,11 +1157,11 @@ static int ensure_train(ac_closure *c) {
     const size_t b_wt = align256(sizeof(float) * (8 * 32 * 27 + 32 * 32 * 27));
     const size_t b_img3 = align256((size_t)tc::w_bytes(8, 32));
     const size_t b_img2 = align256((size_t)tc::w_bytes(32, 32));
-    const size_t b_act[5] = {align256(2 * 8 * (size_t)np2), align256(2 * 16 * (size_t)np2),
-                             align256(2 * 32 * (size_t)np2), align256(2 * 32 * (size_t)np2),
-                             align256(2 * 32 * (size_t)np2)};
+    // dyh (8 channels), dy2h (16: 8 and a zero plane), dz2h, dz1h (32), row-planar with halo
+    const size_t b_act[4] = {align256(2 * 8 * (size_t)np2), align256(2 * 16 * (size_t)np2),
+                             align256(2 * 32 * (size_t)np2), align256(2 * 32 * (size_t)np2)};
     size_t total = b_wpart + b_bpart + b_wt + b_img3 + b_img2;
-    for (int i = 0; i < 5; ++i) total += b_act[i];
+    for (int i = 0; i < 4; ++i) total += b_act[i];
     void *blk = nullptr;
     cudaError_t e = cudaMalloc(&blk, total);
     if (e == cudaSuccess) e = cudaMemsetAsync(blk, 0, total, c->stream);  // zero halos and padding
@@ -1177,8 +1180,8 @@ static int ensure_train(ac_closure *c) {
     p += b_img3;
     c->img2b = reinterpret_cast<bf16 *>(p);
     p += b_img2;
-    bf16 **acts[5] = {&c->dyh, &c->dyn, &c->dz2h, &c->dz2n, &c->dz1n};
-    for (int i = 0; i < 5; ++i) {
+    bf16 **acts[4] = {&c->dyh, &c->dy2h, &c->dz2h, &c->dz1h};
+    for (int i = 0; i < 4; ++i) {
         *acts[i] = reinterpret_cast<bf16 *>(p);
         p += b_act[i];
     }
@@ -1187,9 +1190,9 @@ static int ensure_train(ac_closure *c) {
     e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q);
     if (e == cudaSuccess && (q != cudaDriverEntryPointSuccess || !fn)) e = cudaErrorNotSupported;
     auto enc = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
-    const int kcs[5] = {1, 4, 2, 4, 4};
-    bf16 *bases[5] = {c->dyh, c->dz2h, c->dyn, c->dz2n, c->dz1n};
-    for (int i = 0; i < 5 && e == cudaSuccess; ++i) e = tc_encode(enc, c, bases[i], kcs[i], &c->tr_map[i]);
+    const int kcs[4] = {1, 4, 2, 4};
+    bf16 *bases[4] = {c->dyh, c->dz2h, c->dy2h, c->dz1h};
+    for (int i = 0; i < 4 && e == cudaSuccess; ++i) e = tc_encode(enc, c, bases[i], kcs[i], &c->tr_map[i]);
     if (e != cudaSuccess) {
         cudaFree(blk);
         return ac_report_cuda(e);
@@ -1202,14 +1205,13 @@ static int ensure_train(ac_closure *c) {
 
 // One input-gradient convolution through a ReLU on the tcgen05 kernel: from the
 // row-planar gradient behind xmap, with image img, mask = the forward activation;
-// writes y (with halo, or null) and yn (without).
+// writes y (with its halo cells).
 template <int CIN>
 static void launch_mask(const ac_closure *c, const CUtensorMap &xmap, int grid, const bf16 *img,
-                        const bf16 *mask, bf16 *y, bf16 *yn) {
+                        const bf16 *mask, bf16 *y) {
     tc::ConvTcArgs a = {};
     a.w = img;
     a.y = y;
-    a.yn = yn;
     a.mask = mask;
     a.nx = c->g.nx;
     a.ny = c->g.ny;
@@ -1238,7 +1240,7 @@ static void launch_wgrad(const ac_closure *c, const CUtensorMap &xmap, const CUt
 static void launch_bias(const ac_closure *c, const bf16 *zn, int kcs, int cout, float *gb) {
     const long long rows = (long long)c->g.ny * c->g.nz;
     bias_grad_rp_kernel<<<dim3((unsigned)c->tr_bias_blocks, (unsigned)(cout / 8)), 256, 0, c->stream>>>(
-        zn, kcs, tc::rp_cells(c->g.nx), rows, c->bpart);
+        zn, kcs, c->g.nx, rows, c->bpart);
     bias_reduce_kernel<<<cout, 32, 0, c->stream>>>(c->bpart, c->tr_bias_blocks, gb);
 }
 
@@ -1254,15 +1256,15 @@ static int run_backward_tc(ac_closure *c, const float *const in[8], const float 
     F8 t;
     for (int i = 0; i < 8; ++i) t.p[i] = target[i];
     loss_grad_rp_kernel<<<c->lossblocks, 256, 0, c->stream>>>(c->y, t, c->scales + 16, g.nx, g.n,
-                                                              c->dyh, c->dyn, c->lossp);
-    launch_mask<8>(c, c->tr_map[0], c->tr_grid[0], c->img3b, c->a2, c->dz2h, c->dz2n);
-    launch_mask<32>(c, c->tr_map[1], c->tr_grid[1], c->img2b, c->a1, nullptr, c->dz1n);
+                                                              c->dyh, c->dy2h, c->lossp);
+    launch_mask<8>(c, c->tr_map[0], c->tr_grid[0], c->img3b, c->a2, c->dz2h);
+    launch_mask<32>(c, c->tr_map[1], c->tr_grid[1], c->img2b, c->a1, c->dz1h);
     launch_wgrad<32, 8>(c, c->tc_map[2], c->tr_map[2], c->tr_grid[2], 32, c->grads + P_W3);
-    launch_wgrad<32, 32>(c, c->tc_map[1], c->tr_map[3], c->tr_grid[3], 32, c->grads + P_W2);
-    launch_wgrad<8, 32>(c, c->tc_map[0], c->tr_map[4], c->tr_grid[4], 8, c->grads + P_W1);
-    launch_bias(c, c->dyn, 2, 8, c->grads + P_B3);
-    launch_bias(c, c->dz2n, 4, 32, c->grads + P_B2);
-    launch_bias(c, c->dz1n, 4, 32, c->grads + P_B1);
+    launch_wgrad<32, 32>(c, c->tc_map[1], c->tr_map[1], c->tr_grid[3], 32, c->grads + P_W2);
+    launch_wgrad<8, 32>(c, c->tc_map[0], c->tr_map[3], c->tr_grid[4], 8, c->grads + P_W1);
+    launch_bias(c, c->dy2h, 2, 8, c->grads + P_B3);
+    launch_bias(c, c->dz2h, 4, 32, c->grads + P_B2);
+    launch_bias(c, c->dz1h, 4, 32, c->grads + P_B1);
     c->launches += 15;
     CCK(cudaGetLastError());
     return AC_OK;

@@ -9,26 +9,30 @@
 // (2176 bytes) further.  A shift of the input by one cell (the kx taps) is a
 // 16-byte shift of the operand's start.
 //
-// For an output tile (128 cells of row (y, z)), the nine input rows (y + ky - 1,
-// z + kz - 1) are three consecutive z-slices of three rows each, which a ring
-// of slices keeps contiguous in shared memory (the first two slots are mirrored
-// after the last, so any three consecutive slices form one run of planes at a
-// uniform stride).  GEMM M = 128 rows = 16 consecutive planes of that run
-// (input row, channel group) x 8 channels; N = the output channels of dZ (8
-// padded to 16 by a zero plane, or 32).  With 32 input channels the 36 planes
-// of the run are covered by blocks starting at planes 0, 16 and 20 (the last
-// overlaps the second; each plane's sums are taken from one block); with 8 input
-// channels one block covers the 9 planes (the other rows are discarded).  Each
-// (kx, block) pair owns an accumulator in TMEM for the CTA's whole run, so the
-// sum over all cells a CTA processes stays on chip; at the end the epilogue
-// warps write per-CTA partial sums, which a second kernel adds in binary64 in
-// a fixed order.
+// The sum is split by the input cell q (each tile's 128 cells):
+//     dW_kx[ci][co] = sum_q X[ci, q] dZ[co, q + 1 - kx]   (for each (kz, ky) input row),
+// so the A operand (the activations, rows of the tile's cells) is the same for
+// the three kx taps and the B operand is dZ at three one-cell shifts.  The nine
+// input rows (y + ky - 1, z + kz - 1) of a tile lie in three consecutive z-slices
+// of three rows each, held in a ring of slices.  GEMM M = 128 rows = 16
+// consecutive planes (input row, channel group) x 8 channels: with 32 input
+// channels one block per slice (its 12 planes; the 4 planes after it are read
+// into discarded rows), with 8 one block over the 9 planes of the three slices,
+// kept contiguous by mirroring the ring's first two slots after its last.
+// N = (kx, output channel): the TMA lands dZ's tile (with its periodic halo
+// cells) beside three copy areas, and the epilogue warps, idle until the end,
+// write the copies shifted by 0, 1 and 2 cells, plane after plane, so that one
+// descriptor spans all three at a uniform stride (N = 3 x 16 or 3 x 32); rows of
+// cells past nx (a ragged tile) are written as zeros, so those cells add nothing.
+// Each M block owns an accumulator in TMEM for the CTA's
+// whole run, so the sum over all cells a CTA processes stays on chip; at the end
+// the epilogue warps write per-CTA partial sums, which a second kernel adds in
+// binary64 in a fixed order.
 //
-// dZ is read from a copy without the periodic halo cells (zero there and in the
-// padding), so the cells of a ragged last K-step past nx contribute nothing.
-// Warp roles as in the forward kernel: warp 4 (one thread) issues the TMA copies,
-// warp 5 the MMAs, warps 0-3 zero the accumulators and read them at the end.
-// Every wait is bounded; on timeout the role records an error word and stops.
+// Warp roles: warp 4 (one thread) issues the TMA copies, warp 5 the MMAs, warps
+// 0-3 zero the accumulators, prepare each dZ tile's shifted copies and read the
+// accumulators at the end.  Every wait is bounded; on timeout the role records
+// an error word and stops.
 #pragma once
 
 #include "conv_tc.cuh"
@@ -37,7 +41,7 @@ namespace ac {
 namespace tc {
 
 struct WgradTcArgs {
-    float *part;  // [grid][NACC][NB][128] per-CTA partial sums
+    float *part;  // [grid][NACC][N3][128] per-CTA partial sums
     int nx, ny, nz;
     int zc;       // tiles per column segment
     unsigned *err;
@@ -48,29 +52,35 @@ template <int CIN, int COUT>
 struct WgradShape {
     static constexpr int KC = CIN / 8;                       // planes per input row
     static constexpr int NPL = 9 * KC;                       // planes of the nine-row run
-    static constexpr int NMB = NPL <= 16 ? 1 : (NPL + 15) / 16;  // M blocks per kx
+    // 32 input channels: one M block per slice (its 12 planes, 4 more rows discarded),
+    // so no block crosses a slice and the ring needs no mirror; 8 input channels: one
+    // block over the 9 planes of three slices kept contiguous by a mirrored ring
+    static constexpr bool MIRROR = KC == 1;
+    static constexpr int NMB = MIRROR ? 1 : 3;               // M blocks
+    static constexpr int BLK = MIRROR ? 0 : 3 * KC;          // planes per block (stride of P0)
     static constexpr int DKC = COUT < 16 ? 2 : COUT / 8;     // planes of a dZ tile
-    static constexpr int NB = 8 * DKC;                       // GEMM N
-    static constexpr int NACC = 3 * NMB;                     // accumulators (kx, block)
-    static constexpr int TCOLS = NACC * NB <= 32 ? 32 : NACC * NB <= 64 ? 64 : NACC * NB <= 128 ? 128
-                                 : NACC * NB <= 256 ? 256 : 512;
-    static constexpr int NSLOT = KC == 1 ? 8 : 4;            // slice ring (plus two mirrors)
+    static constexpr int NB = 8 * DKC;                       // output channels (padded)
+    static constexpr int N3 = 3 * NB;                        // GEMM N = (kx, channel)
+    static constexpr int NACC = NMB;                         // accumulators (one per M block)
+    static constexpr int TCOLS = NACC * N3 <= 32 ? 32 : NACC * N3 <= 64 ? 64 : NACC * N3 <= 128 ? 128
+                                 : NACC * N3 <= 256 ? 256 : 512;
+    static constexpr int NSLOT = MIRROR ? 8 : 5;             // slice ring (plus two mirrors)
     static constexpr int ROW = KC * PLANE;
     static constexpr int SLICE = 3 * ROW;
-    static constexpr int NDZ = 3;                            // dZ tile ring
-    static constexpr int DZT = DKC * PLANE;
-    // the last block of a run starts at plane NPL - 16 (0 for a single block)
-    static constexpr int P0LAST = NMB == 1 ? 0 : NPL - 16;
-    // bytes the A operand can reach from the last ring slot, or the mirrored ring
-    static constexpr int RING_A = (NSLOT - 1) * SLICE + (P0LAST + 16) * PLANE;
-    static constexpr int RING = RING_A > (NSLOT + 2) * SLICE ? RING_A : (NSLOT + 2) * SLICE;
-    static constexpr size_t SMEM = (size_t)RING + (size_t)NDZ * DZT;
-    static_assert(NACC * NB <= 512 && (CIN == 8 || CIN == 32) && (COUT == 8 || COUT == 32), "shape");
+    static constexpr int NL = 2;                             // landed dZ tiles (TMA ring)
+    static constexpr int NC = 2;                             // sets of three shifted copies
+    static constexpr int COPY = DKC * PLANE;                 // one dZ tile (one copy)
+    // bytes the A operand can reach past the start of the last ring slot: 16 planes
+    // from its block's start (the mirrored ring: all blocks start in the first slot)
+    static constexpr int RING_A = (NSLOT - 1) * SLICE + 16 * PLANE;
+    static constexpr int RING_S = (MIRROR ? NSLOT + 2 : NSLOT) * SLICE;
+    static constexpr int RING = RING_A > RING_S ? RING_A : RING_S;
+    static constexpr size_t SMEM = (size_t)RING + (size_t)(3 * NC + NL) * COPY;
+    static_assert(NACC * N3 <= 512 && N3 % 16 == 0 && N3 <= 256 && (CIN == 8 || CIN == 32) &&
+                      (COUT == 8 || COUT == 32), "shape");
 };
 
-__host__ __device__ constexpr int wgrad_p0(int mb, int nmb, int npl) {
-    return nmb == 1 ? 0 : (mb < nmb - 1 ? 16 * mb : npl - 16);
-}
+
 
 // Instruction descriptor with both operands MN-major (bits 15 and 16).
 __host__ __device__ constexpr uint32_t idesc_bf16_mn(int m, int n) {
@@ -82,15 +92,19 @@ __global__ void __launch_bounds__(THREADS, 1)
     wgrad_tc_kernel(const __grid_constant__ CUtensorMap xmap, const __grid_constant__ CUtensorMap dmap,
                     const WgradTcArgs a) {
     using S = WgradShape<CIN, COUT>;
-    constexpr int KC = S::KC, NMB = S::NMB, NB = S::NB, NACC = S::NACC, NSLOT = S::NSLOT;
-    constexpr int ROW = S::ROW, SLICE = S::SLICE, NDZ = S::NDZ, DZT = S::DZT;
+    constexpr int KC = S::KC, NMB = S::NMB, N3 = S::N3, NACC = S::NACC, NSLOT = S::NSLOT;
+    constexpr int ROW = S::ROW, SLICE = S::SLICE, NL = S::NL, NC = S::NC, DKC = S::DKC;
+    constexpr int COPY = S::COPY;
     constexpr uint32_t SLICE_TX = 3 * KC * PLANE;
-    constexpr uint32_t DZ_TX = S::DKC * PLANE;
+    constexpr uint32_t DZ_TX = DKC * PLANE;
     extern __shared__ __align__(1024) unsigned char smem[];
-    __shared__ uint64_t full[NSLOT], empty[NSLOT], dfull[NDZ], dempty[NDZ], done;
+    // lfull: a dZ tile landed; lempty: its copies are taken; cready: a copy set is
+    // written; cempty: the MMAs reading a copy set are done
+    __shared__ uint64_t full[NSLOT], empty[NSLOT], lfull[NL], lempty[NL], cready[NC], cempty[NC], done;
     __shared__ uint32_t tmem_base;
     unsigned char *Ss = smem;
-    unsigned char *Ds = smem + S::RING;
+    unsigned char *Cs = smem + S::RING;             // copy sets, 3 COPY each
+    unsigned char *Ls = Cs + 3 * NC * COPY;         // landed tiles
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int segs = (a.nx + TM - 1) / TM;
     const long long nseg = (long long)((a.nz + a.zc - 1) / a.zc) * a.ny * segs;
@@ -106,23 +120,27 @@ __global__ void __launch_bounds__(THREADS, 1)
             mbar_init(&full[b], 1);
             mbar_init(&empty[b], 1);
         }
-        for (int b = 0; b < NDZ; ++b) {
-            mbar_init(&dfull[b], 1);
-            mbar_init(&dempty[b], 1);
+        for (int b = 0; b < NL; ++b) {
+            mbar_init(&lfull[b], 1);
+            mbar_init(&lempty[b], 4);
+        }
+        for (int b = 0; b < NC; ++b) {
+            mbar_init(&cready[b], 4);
+            mbar_init(&cempty[b], 1);
         }
         mbar_init(&done, 1);
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
     }
-    // the ring bytes past the mirrored slots are only read into discarded rows:
-    // keep them finite
-    for (int i = (NSLOT + 2) * SLICE + 16 * (int)threadIdx.x; i < S::RING; i += 16 * THREADS)
+    // the ring bytes past the slots are only read into discarded rows: keep them finite
+    for (int i = S::RING_S + 16 * (int)threadIdx.x; i < S::RING; i += 16 * THREADS)
         *reinterpret_cast<uint4 *>(Ss + i) = make_uint4(0, 0, 0, 0);
     fence_proxy_async_smem();
     __syncthreads();  // barriers initialised, TMEM address published
     tc_fence_after_sync();
     const uint32_t tmem = tmem_base;
     if (warp < 4) {
-        for (int k = 0; k < NACC; ++k) tmem_zero<NB>(tmem + ((uint32_t)(warp * 32) << 16) + k * NB);
+        for (int k = 0; k < NACC * N3 / 16; ++k)
+            tmem_zero<16>(tmem + ((uint32_t)(warp * 32) << 16) + k * 16);
         tc_fence_before_sync();
     }
     __syncthreads();
@@ -136,7 +154,7 @@ __global__ void __launch_bounds__(THREADS, 1)
                 const int b = (int)(s % NSLOT);
                 const long long k = s / NSLOT;
                 if (k > 0 && !mbar_wait(&empty[b], (unsigned)((k - 1) & 1))) return false;
-                const int copies = b < 2 ? 2 : 1;
+                const int copies = S::MIRROR && b < 2 ? 2 : 1;
                 mbar_expect_tx(&full[b], copies * SLICE_TX);
                 const int z = wrapi(sg.z0 + j - 1, a.nz);
                 for (int c = 0; c < copies; ++c) {
@@ -155,14 +173,15 @@ __global__ void __launch_bounds__(THREADS, 1)
                 for (int i = 0; i < sg.len && ok; ++i) {
                     ok = slice(sg, i + 2);
                     if (!ok) break;
-                    const int d = (int)(t % NDZ);
-                    const long long k = t / NDZ;
-                    if (k > 0 && !mbar_wait(&dempty[d], (unsigned)((k - 1) & 1))) {
+                    const int l = (int)(t % NL);
+                    const long long k = t / NL;
+                    if (k > 0 && !mbar_wait(&lempty[l], (unsigned)((k - 1) & 1))) {
                         ok = false;
                         break;
                     }
-                    mbar_expect_tx(&dfull[d], DZ_TX);
-                    tma_load_5d(Ds + d * DZT, &dmap, &dfull[d], 0, sg.seg * (TM / 8), 0, sg.y,
+                    mbar_expect_tx(&lfull[l], DZ_TX);
+                    // landed row r = slot x0 + r, cell x0 + r - 1
+                    tma_load_5d(Ls + l * COPY, &dmap, &lfull[l], 0, sg.seg * (TM / 8), 0, sg.y,
                                 sg.z0 + i);
                     ++t;
                 }
@@ -171,47 +190,44 @@ __global__ void __launch_bounds__(THREADS, 1)
             // no copy may be in flight when the CTA exits: wait for each buffer's last fill
             for (int b = 0; b < NSLOT; ++b)
                 if (s > b) mbar_wait(&full[b], (unsigned)(((s - 1 - b) / NSLOT) & 1));
-            for (int d = 0; d < NDZ; ++d)
-                if (t > d) mbar_wait(&dfull[d], (unsigned)(((t - 1 - d) / NDZ) & 1));
+            for (int l = 0; l < NL; ++l)
+                if (t > l) mbar_wait(&lfull[l], (unsigned)(((t - 1 - l) / NL) & 1));
         }
     } else if (warp == 5) {
         // ---- MMA issuer: the whole warp runs the loop, one elected lane issues
         long long s = 0, t = 0;  // first slice of the current tile's run; dZ tiles consumed
         bool ok = true;
-        const uint32_t idesc = idesc_bf16_mn(TM, NB);
+        const uint32_t idesc = idesc_bf16_mn(TM, N3);
         for (long long g = blockIdx.x; g < nseg && ok; g += gridDim.x) {
             const Segment sg = segment_of(g, ga, segs);
             const int L = sg.len;
             const int valid = a.nx - sg.seg * TM;
             const int nks = valid >= TM ? TM / 16 : (valid + 15) / 16;  // K-steps with cells < nx
             for (int i = 0; i < L; ++i) {
-                // slices s .. s + 2 and dZ tile t have landed (the first two were
-                // waited for by the previous tile of the segment, or are waited now)
+                // slices s .. s + 2 have landed (the first two were waited for by the
+                // previous tile of the segment, or are waited now); tile t's copies are ready
                 for (int q = (i == 0 ? 0 : 2); q < 3 && ok; ++q)
                     ok = __all_sync(0xffffffffu,
                                     mbar_wait(&full[(s + q) % NSLOT], (unsigned)(((s + q) / NSLOT) & 1)));
-                const int d = (int)(t % NDZ);
+                const int c = (int)(t % NC);
                 if (ok)
-                    ok = __all_sync(0xffffffffu, mbar_wait(&dfull[d], (unsigned)((t / NDZ) & 1)));
+                    ok = __all_sync(0xffffffffu, mbar_wait(&cready[c], (unsigned)((t / NC) & 1)));
                 if (!ok) break;
                 tc_fence_after_sync();
-                const uint32_t abase = smem_u32(Ss + (int)(s % NSLOT) * SLICE);
-                const uint32_t bbase = smem_u32(Ds + d * DZT) + 16;  // smem row k + 1 = cell x0 + k
-                const uint64_t a0 = smem_desc(abase, CORE, PLANE);
-                const uint64_t b0 = smem_desc(bbase, CORE, PLANE);
+                // A: the tile's cells x0 + k are staged rows k + 1 of every plane of the run;
+                // block mb starts at plane 0 of the run's (mb)-th slice
+                uint64_t a0[NMB];
+#pragma unroll
+                for (int mb = 0; mb < NMB; ++mb)  // block mb: slice s + mb, in its own slot
+                    a0[mb] = smem_desc(smem_u32(Ss + (int)((s + mb) % NSLOT) * SLICE) + 16, CORE, PLANE);
+                const uint64_t b0 = smem_desc(smem_u32(Cs + c * 3 * COPY), CORE, PLANE);
                 for (int ks = 0; ks < nks; ++ks) {
+                    const uint64_t step = (uint32_t)(ks * 256) >> 4;
 #pragma unroll
-                    for (int kx = 0; kx < 3; ++kx)
-#pragma unroll
-                        for (int mb = 0; mb < NMB; ++mb) {
-                            const uint32_t aoff =
-                                (uint32_t)(wgrad_p0(mb, NMB, S::NPL) * PLANE + (ks * 16 + kx) * 16);
-                            const uint64_t ad = a0 + (aoff >> 4);
-                            const uint64_t bd = b0 + ((uint32_t)(ks * 256) >> 4);
-                            mma_bf16_elect(tmem + (uint32_t)((kx * NMB + mb) * NB), ad, bd, idesc);
-                        }
+                    for (int mb = 0; mb < NMB; ++mb)
+                        mma_bf16_elect(tmem + (uint32_t)(mb * N3), a0[mb] + step, b0 + step, idesc);
                 }
-                mma_commit_elect(&dempty[d]);
+                mma_commit_elect(&cempty[c]);
                 mma_commit_elect(&empty[s % NSLOT]);  // slice s serves no later tile
                 if (i == L - 1) {
                     mma_commit_elect(&empty[(s + 1) % NSLOT]);
@@ -225,23 +241,63 @@ __global__ void __launch_bounds__(THREADS, 1)
         }
         if (!ok && lane == 0) atomicExch(a.err, 1u);
         mma_commit_elect(&done);  // every MMA of the CTA, before the epilogue reads TMEM
-    } else {  // ---- epilogue: warps 0-3, TMEM lanes 32 warp .. 32 warp + 31
-        const bool ok = __all_sync(0xffffffffu, mbar_wait(&done, 0));
+    } else {  // ---- warps 0-3: the dZ tiles' shifted copies, then TMEM lanes 32 warp ..
+        const int tid = threadIdx.x;  // 0 .. 127
+        bool ok = true;
+        long long t = 0;
+        for (long long g = blockIdx.x; g < nseg && ok; g += gridDim.x) {
+            const Segment sg = segment_of(g, ga, segs);
+            const int valid = a.nx - sg.seg * TM;  // rows r < valid are cells < nx
+            for (int i = 0; i < sg.len; ++i, ++t) {
+                const int l = (int)(t % NL), c = (int)(t % NC);
+                ok = __all_sync(0xffffffffu, mbar_wait(&lfull[l], (unsigned)((t / NL) & 1)));
+                if (ok && t >= NC)  // the MMAs of tile t - NC have read this copy set
+                    ok = __all_sync(0xffffffffu,
+                                    mbar_wait(&cempty[c], (unsigned)(((t / NC) - 1) & 1)));
+                if (!ok) break;
+                unsigned char *base = Cs + c * 3 * COPY;  // copy kx at base + kx * COPY
+                const unsigned char *landed = Ls + l * COPY;
+                // copy kx, row r = landed row r + 2 - kx (cell x0 + r + 1 - kx); rows of
+                // cells past nx (r >= valid) zero
+                for (int e = tid; e < DKC * TM; e += 128) {
+                    const int pl = e / TM, r = e - pl * TM;
+                    const uint4 *src = reinterpret_cast<const uint4 *>(landed + pl * PLANE);
+                    const uint4 z = make_uint4(0, 0, 0, 0);
+                    const bool in = r < valid;
+                    reinterpret_cast<uint4 *>(base + 2 * COPY + pl * PLANE)[r] = in ? src[r] : z;
+                    reinterpret_cast<uint4 *>(base + COPY + pl * PLANE)[r] = in ? src[r + 1] : z;
+                    reinterpret_cast<uint4 *>(base + pl * PLANE)[r] = in ? src[r + 2] : z;
+                }
+                // generic reads of the landed tile before the TMA refills it, generic
+                // writes of the copies before the tensor core reads them
+                fence_proxy_async_smem();
+                __syncwarp();
+                if (lane == 0) {
+                    mbar_arrive(&lempty[l]);
+                    mbar_arrive(&cready[c]);
+                }
+            }
+        }
+        if (ok) ok = __all_sync(0xffffffffu, mbar_wait(&done, 0));
         tc_fence_after_sync();
         if (ok) {
             const int m = warp * 32 + lane;
+            constexpr int CH = N3 % 32 == 0 ? 32 : 16;
 #pragma unroll 1
-            for (int k = 0; k < NACC; ++k) {
-                const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(k * NB);
-                float v[NB];
-                if constexpr (NB == 32)
-                    tmem_ld32(taddr, v);
-                else
-                    tmem_ld16(taddr, v);
-                float *dst = a.part + ((long long)blockIdx.x * NACC + k) * NB * TM + m;
+            for (int k = 0; k < NACC; ++k)
+#pragma unroll 1
+                for (int c0 = 0; c0 < N3; c0 += CH) {
+                    const uint32_t taddr =
+                        tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(k * N3 + c0);
+                    float v[CH];
+                    if constexpr (CH == 32)
+                        tmem_ld32(taddr, v);
+                    else
+                        tmem_ld16(taddr, v);
+                    float *dst = a.part + (((long long)blockIdx.x * NACC + k) * N3 + c0) * TM + m;
 #pragma unroll
-                for (int n = 0; n < NB; ++n) dst[n * TM] = v[n];
-            }
+                    for (int n = 0; n < CH; ++n) dst[n * TM] = v[n];
+                }
         } else if (lane == 0) {
             atomicExch(a.err, 1u);
         }
@@ -252,24 +308,23 @@ __global__ void __launch_bounds__(THREADS, 1)
 }
 
 // gW[co][ci][kz][ky][kx] (ci < cin_real) from the per-CTA partials: one thread
-// per partial entry (accumulator k = kx * NMB + block, column co, row m), rows
-// fastest so that the CTAs' blocks are read coalesced; entries that hold no
-// gradient (padded columns and rows, planes another block owns) are skipped.
-// Row m of block mb is plane P = P0(mb) + m / 8, channel 8 (P % KC) + m % 8,
-// tap row P / KC = 3 kz + ky.  Binary64 sums in CTA order.
+// per partial entry (M block mb, column n = kx NB + co, row m), rows fastest so
+// that the CTAs' blocks are read coalesced; entries that hold no gradient (padded
+// columns, rows past a block's planes) are skipped.  Row m of block mb is plane
+// P = mb BLK + m / 8 of the run, channel 8 (P % KC) + m % 8, tap row P / KC = 3 kz + ky.
+// Binary64 sums in CTA order.
 template <int CIN, int COUT>
 __global__ void wgrad_tc_reduce_kernel(const float *__restrict__ part, int ctas, int cin_real,
                                        float *__restrict__ gW) {
     using S = WgradShape<CIN, COUT>;
-    constexpr int PER_CTA = S::NACC * S::NB * TM;
+    constexpr int PER_CTA = S::NACC * S::N3 * TM;
     for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < PER_CTA; t += gridDim.x * blockDim.x) {
-        const int m = t % TM, co = (t / TM) % S::NB, k = t / (TM * S::NB);
-        const int kx = k / S::NMB, mb = k % S::NMB;
-        const int P = wgrad_p0(mb, S::NMB, S::NPL) + m / 8;
-        if (co >= COUT || P >= S::NPL) continue;
-        const int owner = S::NMB == 1 ? 0 : (P < 16 * (S::NMB - 1) ? P / 16 : S::NMB - 1);
+        const int m = t % TM, n = (t / TM) % S::N3, mb = t / (TM * S::N3);
+        const int kx = n / S::NB, co = n % S::NB;
+        const int P = mb * S::BLK + m / 8;
+        if (co >= COUT || P >= S::NPL || (S::BLK > 0 && m / 8 >= S::BLK)) continue;
         const int ci = 8 * (P % S::KC) + m % 8;
-        if (owner != mb || ci >= cin_real) continue;
+        if (ci >= cin_real) continue;
         const int tr = P / S::KC;
         double s = 0.0;
         for (int b = 0; b < ctas; ++b) s += part[(long long)b * PER_CTA + t];
