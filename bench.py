@@ -52,13 +52,13 @@ def bytes_per_cell(elem_f, elem_w, s):
 # Nominal dense FP64 rate of one GB300 (no measured FP64 peak is provided).
 FP64_NOMINAL_TFLOPS = 1.25
 # DRAM bytes per cell of one launch of the integer-sum FP64 substep kernel
-# (ncu, 128^3 forced, substep-1/2 variant, group scales: 423.1 MB read +
-# 236.3 MB written over 2,097,152 cells; profiles/substep_fx_128_metrics.md).
-FX_TRAFFIC_PER_CELL = (423132416 + 236319232) / 2097152
+# (ncu, 128^3 forced, substep-1/2 variant, group scales: 426.2 MB read +
+# 236.5 MB written over 2,097,152 cells; profiles/substep_fx_128_metrics.md).
+FX_TRAFFIC_PER_CELL = (426249728 + 236466176) / 2097152
 # FP64-pipe thread instructions per cell of that kernel (ncu
 # sm__inst_executed_pipe_fp64 x 32 / cells, 128^3 forced; the instruction stream
 # does not depend on the grid), per mode: substep-0 (CFL) and substep-1/2 variants.
-FX_FP64_PIPE_INST_PER_CELL = {"group": (225.3125, 199.3125), "field": (255.3125, 229.3125)}
+FX_FP64_PIPE_INST_PER_CELL = {"group": (213.3125, 187.3125), "field": (243.3125, 217.3125)}
 # DRAM bytes per cell of one launch of the binary32 tiled substep (ncu, 256^3,
 # substep 1: 1126.6 MB read + 1023.2 MB written over 16,777,216 cells)
 TILED_TRAFFIC_PER_CELL = (1126.612e6 + 1023.183e6) / 16777216

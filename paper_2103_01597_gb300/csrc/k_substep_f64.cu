@@ -38,6 +38,9 @@ cudaError_t launch_substep_f64(const SubstepLaunch &L, cudaStream_t st, int *lau
     fc.nu2160 = (L.ph.nu + 3.0 * L.ph.zeta) / (2160.0 * L.dx * L.dx);
     fc.inv180dx2 = 1.0 / (180.0 * L.dx * L.dx);
     fc.inv720dx2 = 1.0 / (720.0 * L.dx * L.dx);
+    fc.two_nu_c1sq = 2.0 * L.ph.nu * fc.inv60dx * fc.inv60dx;
+    fc.K_c1sq = L.ph.K * fc.inv60dx * fc.inv60dx;
+    fc.zeta_c1sq = L.ph.zeta * fc.inv60dx * fc.inv60dx;
 
     const long long n = L.g.elems;
     FxPlan *plan = static_cast<FxPlan *>(L.fx_plan);

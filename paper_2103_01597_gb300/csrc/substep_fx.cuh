@@ -300,12 +300,82 @@ __device__ __forceinline__ double fx_scaled(long long N, int k_hi) {
 // Coefficients of the converted numerators (host side); the field scales
 // 2^(E - FX_BITS) come from the device plan.
 struct FxCoefs {
-    double inv60dx;    // 1 / (60 dx): first derivatives
+    double inv60dx;    // c1 = 1 / (60 dx): first derivatives
     double nu180;      // nu / (180 dx^2): nu lap u
     double nu2160;     // (nu + 3 zeta) / (2160 dx^2): (nu / 3 + zeta) grad(div u)
     double inv180dx2;  // 1 / (180 dx^2): lap A
     double inv720dx2;  // 1 / (720 dx^2): grad(div A)
+    double two_nu_c1sq;  // 2 nu c1^2: 2 nu S : S and 2 nu S grad ln rho from unscaled gradients
+    double K_c1sq;       // K c1^2: K |grad xi|^2 (conduction)
+    double zeta_c1sq;    // zeta c1^2: zeta (div u)^2
 };
+
+// Eqs. B.1-B.4 at one cell as cell_physics computes them, with the gradients of
+// ln rho, s and u passed without the grid factor c1 = 1 / (60 dx) (the integer
+// stencil numerators after their field scale): every term is linear or
+// quadratic in them, so c1 enters the coefficients (c1 for the advection terms
+// inside their fused multiply-adds, c1 cs^2 for the pressure term, c1^2 in
+// 2 nu, K and zeta) instead of 15 multiplications per cell on the FP64 pipe.
+// B = curl A comes scaled (it meets c1 in three places).
+template <bool EXT>
+__device__ __forceinline__ void cell_physics_fx(const double (&u)[3], const double (&GL)[3],
+                                                const double (&GS)[3], const double (&GU)[3][3],
+                                                const double (&B)[3], const double (&viscl)[3],
+                                                const double (&lapa)[3], const double (&J)[3],
+                                                const DevCoefs<double> &k, const FxCoefs &fc,
+                                                const double frc[3], double out[NF], double *cfl,
+                                                double lapxi, const Thermo<double> &th) {
+    const double c1 = fc.inv60dx;
+    const double rho_inv = th.rho_inv, cs2 = th.cs2, inv_T = th.inv_T;
+    const double divR = GU[0][0] + GU[1][1] + GU[2][2];  // div u / c1
+    const double third_div = divR * (1.0 / 3.0);
+    // traceless rate of strain S / c1
+    const double Sxx = GU[0][0] - third_div, Syy = GU[1][1] - third_div, Szz = GU[2][2] - third_div;
+    const double Sxy = 0.5 * (GU[0][1] + GU[1][0]);
+    const double Sxz = 0.5 * (GU[0][2] + GU[2][0]);
+    const double Syz = 0.5 * (GU[1][2] + GU[2][1]);
+    const double SS2 = Sxx * Sxx + Syy * Syy + Szz * Szz + 2.0 * (Sxy * Sxy + Sxz * Sxz + Syz * Syz);
+    const double SG[3] = {Sxx * GL[0] + Sxy * GL[1] + Sxz * GL[2],
+                          Sxy * GL[0] + Syy * GL[1] + Syz * GL[2],
+                          Sxz * GL[0] + Syz * GL[1] + Szz * GL[2]};
+    const double JxB[3] = {J[1] * B[2] - J[2] * B[1], J[2] * B[0] - J[0] * B[2],
+                           J[0] * B[1] - J[1] * B[0]};
+    const double UxB[3] = {u[1] * B[2] - u[2] * B[1], u[2] * B[0] - u[0] * B[2],
+                           u[0] * B[1] - u[1] * B[0]};
+    const double J2 = J[0] * J[0] + J[1] * J[1] + J[2] * J[2];
+    // Eq. B.1
+    out[0] = -(c1 * (u[0] * GL[0] + u[1] * GL[1] + u[2] * GL[2] + divR));
+    // Eq. B.2
+    const double c1cs2 = c1 * cs2;
+#pragma unroll
+    for (int m = 0; m < 3; ++m) {
+        const double adv = u[0] * GU[m][0] + u[1] * GU[m][1] + u[2] * GU[m][2];
+        const double press = c1cs2 * (GS[m] * k.inv_cp + GL[m]);
+        const double visc = viscl[m] + fc.two_nu_c1sq * SG[m];
+        out[1 + m] = fma(-c1, adv, visc) - press + JxB[m] * rho_inv + frc[m];
+    }
+    // Eq. B.3
+    out[4] = fma(-c1, u[0] * GS[0] + u[1] * GS[1] + u[2] * GS[2],
+                 (k.eta * J2 * rho_inv + fc.two_nu_c1sq * SS2) * inv_T);
+    if (EXT) {
+        double gxi2 = 0.0;  // |grad xi|^2 / c1^2
+#pragma unroll
+        for (int m = 0; m < 3; ++m) {
+            const double gxi = k.gamma_cp * GS[m] + k.gm1 * GL[m];
+            gxi2 += gxi * gxi;
+        }
+        out[4] += (k.hc * rho_inv + fc.zeta_c1sq * divR * divR) * inv_T +
+                  rho_inv * (k.K * lapxi + fc.K_c1sq * gxi2);
+    }
+    // Eq. B.4
+#pragma unroll
+    for (int m = 0; m < 3; ++m) out[5 + m] = UxB[m] + k.eta * lapa[m];
+    if (cfl) {
+        const double b2 = B[0] * B[0] + B[1] * B[1] + B[2] * B[2];
+        const double u2 = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+        *cfl = sqrt(u2) + sqrt(cs2 + b2 * rho_inv);
+    }
+}
 
 // One (x, y) column of the integer-sum substep.  PF: per-field scales (FX_FIELD),
 // so sums across the components of u or A are formed in binary64 from per-field
@@ -323,8 +393,10 @@ __device__ __forceinline__ void fx_column(const SubstepArgs<double, double> &a, 
     int kh[NF];
 #pragma unroll
     for (int q = 0; q < NF; ++q) kh[q] = (plan->E[q] - FX_BITS) << 20;
-    // first derivative of field q from its numerator
+    // first derivative of field q from its numerator; the gradients of ln rho, s
+    // and u stay without the factor c1 (cell_physics_fx applies it)
     auto d1 = [&](long long N, int q) -> double { return fx_scaled(N, kh[q]) * fc.inv60dx; };
+    auto d1r = [&](long long N, int q) -> double { return fx_scaled(N, kh[q]); };
     const int k0 = blockIdx.z * a.zchunk;
     const int k1 = min(k0 + a.zchunk, a.g.nz);
     IdxPeriodic32 ix;
@@ -365,18 +437,18 @@ __device__ __forceinline__ void fx_column(const SubstepArgs<double, double> &a, 
                                                              {fx.F[7], ix}};
         // first derivatives
         double gl[3], gs[3], gu[3][3], B[3];
-        gl[0] = d1(nd1<0>(Fl), 0);
-        gl[1] = d1(nd1<1>(Fl), 0);
-        gl[2] = d1(nd1<2>(Fl), 0);
-        gs[0] = d1(nd1<0>(Fs), 4);
-        gs[1] = d1(nd1<1>(Fs), 4);
-        gs[2] = d1(nd1<2>(Fs), 4);
+        gl[0] = d1r(nd1<0>(Fl), 0);
+        gl[1] = d1r(nd1<1>(Fl), 0);
+        gl[2] = d1r(nd1<2>(Fl), 0);
+        gs[0] = d1r(nd1<0>(Fs), 4);
+        gs[1] = d1r(nd1<1>(Fs), 4);
+        gs[2] = d1r(nd1<2>(Fs), 4);
 #pragma unroll
         for (int m = 0; m < 3; ++m) {
-            const int qu = PF ? 1 + m : 1;  // one live coefficient in FX_GROUP
-            gu[m][0] = d1(nd1<0>(Fu[m]), qu);
-            gu[m][1] = d1(nd1<1>(Fu[m]), qu);
-            gu[m][2] = d1(nd1<2>(Fu[m]), qu);
+            const int qu = PF ? 1 + m : 1;  // one live exponent in FX_GROUP
+            gu[m][0] = d1r(nd1<0>(Fu[m]), qu);
+            gu[m][1] = d1r(nd1<1>(Fu[m]), qu);
+            gu[m][2] = d1r(nd1<2>(Fu[m]), qu);
         }
         if constexpr (PF) {
             B[0] = (fx_scaled(nd1<1>(Fa[2]), kh[7]) - fx_scaled(nd1<2>(Fa[1]), kh[6])) * fc.inv60dx;
@@ -520,12 +592,11 @@ __device__ __forceinline__ void fx_column(const SubstepArgs<double, double> &a, 
         double rhs[NF];
         if (CFL) {
             double c;
-            cell_physics<double, EXT>(lnrho, u, ss, gl, gs, gu, B, viscl, lapa, J, a.k, frc, rhs,
-                                      &c, lapxi, th);
+            cell_physics_fx<EXT>(u, gl, gs, gu, B, viscl, lapa, J, a.k, fc, frc, rhs, &c, lapxi, th);
             cfl = (c > cfl || c != c) ? c : cfl;
         } else {
-            cell_physics<double, EXT>(lnrho, u, ss, gl, gs, gu, B, viscl, lapa, J, a.k, frc, rhs,
-                                      nullptr, lapxi, th);
+            cell_physics_fx<EXT>(u, gl, gs, gu, B, viscl, lapa, J, a.k, fc, frc, rhs, nullptr, lapxi,
+                                 th);
         }
 #pragma unroll
         for (int q = 0; q < NF; ++q) rk_update(a, q, o, rhs[q]);
