@@ -249,14 +249,15 @@ __device__ __forceinline__ void tiled_body(const TA &ta, int x0, int y0, int z0,
     float zq[NF][7];  // z-column of this thread's cell: planes z-3 .. z+3
     const float2 *ztab = force_on ? ta.ftab() + g.nx + g.ny : nullptr;
     float2 ez_next = force_on ? ztab[z0] : make_float2(0.f, 0.f);
+    // ring offsets of planes z-3 .. z+3, rolled by one slot per plane
+    int slot[7];
+#pragma unroll
+    for (int d = 0; d < 7; ++d) slot[d] = d * TT_PLANE;
     for (int z = z0; z < z1; ++z) {
         const float2 ez = ez_next;  // forcing phase of plane z, loaded one plane ahead
         if (force_on && z + 1 < z1) ez_next = ztab[z + 1];
         cp_async_wait<TT_PF>();  // plane z+3 (and w of plane z) have landed for this thread
         __syncthreads();         // ... and for every thread
-        int slot[7];
-#pragma unroll
-        for (int d = 0; d < 7; ++d) slot[d] = ((z - z0 + d) % TT_NP) * TT_PLANE;
         const float *ctr = sm + (ty + 3) * S::ROW + tx + 4;
         if (z == z0) {
 #pragma unroll
@@ -302,6 +303,9 @@ __device__ __forceinline__ void tiled_body(const TA &ta, int x0, int y0, int z0,
         }
         __syncthreads();  // reads of plane z-3's slot and of w(z) are done before refilling
         issue(z + 4 + TT_PF);
+#pragma unroll
+        for (int d = 0; d < 6; ++d) slot[d] = slot[d + 1];
+        slot[6] = slot[6] + TT_PLANE == TT_NP * TT_PLANE ? 0 : slot[6] + TT_PLANE;
     }
     cp_async_wait<0>();
     if (CFL) block_max_to_global((double)cfl, ta.cfl_max());
