@@ -158,9 +158,10 @@ struct TileCopies {
             }
         }
     }
-    // Issue the copies of plane p (wrapped) into `slot`.
+    // Issue the copies of plane p (wrapped; p lies in [-3, nz + 2]) into `slot`.
     __device__ __forceinline__ void issue(float *slot, const Geom &g, int p) const {
-        const long long zoff = (long long)wrap_mod(p, g.nz) * g.pxy;
+        const int pw = g.nz >= 3 ? (p < 0 ? p + g.nz : (p >= g.nz ? p - g.nz : p)) : wrap_mod(p, g.nz);
+        const long long zoff = (long long)pw * g.pxy;
 #pragma unroll
         for (int u = 0; u < N; ++u)
             if (u < n && AC_BC_RANGE(bc_idx[u] + zoff, VEC ? 4 : 1, bc_lim, AC_BC_TILE_IN)) {
@@ -235,16 +236,18 @@ __device__ __forceinline__ void tiled_body(const TA &ta, int x0, int y0, int z0,
     TileCopies<S, VEC> cp;
     cp.init(ta, g, x0, y0);
 
-    // One commit group per plane p; it also carries w of output plane p - 3.
-    auto issue = [&](int p) {
-        if (p <= z1 + 2) cp.issue(sm + ((p - z0 + 3) % TT_NP) * TT_PLANE, g, p);
+    // One commit group per plane p, into ring offset `off`; it also carries w of
+    // output plane p - 3 (w ring slot (p - 3 - z0) mod TT_NW).
+    static_assert((TT_NW & (TT_NW - 1)) == 0, "w ring of a power-of-two size");
+    auto issue = [&](int p, int off) {
+        if (p <= z1 + 2) cp.issue(sm + off, g, p);
         const int zw = p - 3;
         if (!s0 && zw >= z0 && zw < z1)
-            tile_load_w<W>(wring + ((zw - z0) % TT_NW) * (NF * TT_THREADS), ta, g, i, j, zw,
+            tile_load_w<W>(wring + ((zw - z0) & (TT_NW - 1)) * (NF * TT_THREADS), ta, g, i, j, zw,
                            active);
         cp_async_commit();
     };
-    for (int p = z0 - 3; p <= z0 + 3 + TT_PF; ++p) issue(p);
+    for (int p = z0 - 3; p <= z0 + 3 + TT_PF; ++p) issue(p, (p - z0 + 3) * TT_PLANE);
 
     float zq[NF][7];  // z-column of this thread's cell: planes z-3 .. z+3
     const float2 *ztab = force_on ? ta.ftab() + g.nx + g.ny : nullptr;
@@ -292,7 +295,7 @@ __device__ __forceinline__ void tiled_body(const TA &ta, int x0, int y0, int z0,
             }
             const long long o =
                 AC_BC((long long)z * g.pxy + (long long)j * g.px + i, g.elems, AC_BC_TILE_OUT);
-            const W *wz = wring + ((z - z0) % TT_NW) * (NF * TT_THREADS) + tid;
+            const W *wz = wring + ((z - z0) & (TT_NW - 1)) * (NF * TT_THREADS) + tid;
 #pragma unroll
             for (int q = 0; q < NF; ++q) {
                 W wn = ta.dt() * (W)rhs[q];
@@ -302,7 +305,7 @@ __device__ __forceinline__ void tiled_body(const TA &ta, int x0, int y0, int z0,
             }
         }
         __syncthreads();  // reads of plane z-3's slot and of w(z) are done before refilling
-        issue(z + 4 + TT_PF);
+        issue(z + 4 + TT_PF, slot[0]);  // plane z + 6 takes plane z - 3's slot
 #pragma unroll
         for (int d = 0; d < 6; ++d) slot[d] = slot[d + 1];
         slot[6] = slot[6] + TT_PLANE == TT_NP * TT_PLANE ? 0 : slot[6] + TT_PLANE;
