@@ -59,12 +59,14 @@ FX_TRAFFIC_PER_CELL = (426249728 + 236466176) / 2097152
 # sm__inst_executed_pipe_fp64 x 32 / cells, 128^3 forced; the instruction stream
 # does not depend on the grid), per mode: substep-0 (CFL) and substep-1/2 variants.
 FX_FP64_PIPE_INST_PER_CELL = {"group": (213.3125, 187.3125), "field": (243.3125, 217.3125)}
-# DRAM bytes per cell of one launch of the binary32 tiled substep (ncu, 256^3,
-# substep 1: 1126.6 MB read + 1023.2 MB written over 16,777,216 cells)
-TILED_TRAFFIC_PER_CELL = (1126.612e6 + 1023.183e6) / 16777216
-# The same for one launch of the 64-box ensemble kernel (ncu: 1834.6 MB read +
-# 1697.9 MB written over its 27,340,800 cells)
-BATCH_TRAFFIC_PER_CELL = (1834.648e6 + 1697.876e6) / 27340800
+# DRAM bytes per cell of one launch of the binary32 tiled substep, the mean over
+# substeps 0, 1, 2 (ncu, 256^3 forced, one step: 1970.6 MB read + written per
+# launch on average over 16,777,216 cells; algorithmic 96, 128, 128 B/cell)
+TILED_TRAFFIC_PER_CELL = 1970619477.3 / 16777216
+# The same for one launch of the 64-box ensemble kernel with its tuned split (ncu:
+# 3291.5 MB per launch on average over its 27,340,800 cells; 2.6% above the
+# algorithmic bytes: the halo cells of small boxes)
+BATCH_TRAFFIC_PER_CELL = 3291504810.7 / 27340800
 
 WORKLOADS = {
     "forced256_fp64": dict(n=(256, 256, 256), precision="fp64", force_amp=0.05, seed=2,
@@ -568,8 +570,8 @@ def run_ours(args, wl):
         tiled = order == 6 and not wl.get("entropy")
         roof = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                 "frac": achieved / peaks["hbm_gbs"],
-                # dram read + write per launch (ncu at 256^3 scaled by cells; the same
-                # kernel, profiles/substep_fp32_tiled_256_full.md)
+                # dram read + write per launch, mean over the three substeps (ncu at
+                # 256^3 scaled by cells; profiles/substep_fp32_tiled_256_full.md)
                 "traffic": TILED_TRAFFIC_PER_CELL * ncell if tiled else None,
                 "kernel": ("substep_tiled_kernel<float,true> (shared-memory plane ring)"
                            if order == 6 else
@@ -741,7 +743,8 @@ def run_ensemble(args, wl):
     achieved = alg / launch_s / 1e9
     roof = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
             "frac": achieved / peaks["hbm_gbs"],
-            # dram read + write per launch (ncu, profiles/ensemble_batch_substep_full.md)
+            # dram read + write per launch, mean over the three substeps (ncu,
+            # profiles/ensemble_batch_substep_full.md)
             "traffic": BATCH_TRAFFIC_PER_CELL * ncell,
             "kernel": "batch_substep_kernel<float> (persistent, graph-captured)",
             "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)",
