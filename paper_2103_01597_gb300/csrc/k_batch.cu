@@ -78,7 +78,9 @@ struct TileBox {
     __device__ __forceinline__ unsigned long long *cfl_max() const { return nullptr; }
 };
 
-template <typename W>
+// SHAPES: which tile bodies the kernel holds -- AC_TILE_32X8 or AC_TILE_16X16 alone
+// (every box on that shape: one body, its own register allocation), or both (2).
+template <typename W, int SHAPES>
 __global__ void __launch_bounds__(TT_THREADS, 1) batch_substep_kernel(const __grid_constant__ BatchArgs<W> b) {
     extern __shared__ __align__(128) unsigned char bt_smem_raw[];
     __shared__ int item_sh;
@@ -90,7 +92,7 @@ __global__ void __launch_bounds__(TT_THREADS, 1) batch_substep_kernel(const __gr
         if (it >= b.nitems) break;
         const int4 wi = b.items[it];
         const TileBox<W> ta(b, b.box[wi.x & 0xffff]);
-        if (wi.x >> 16)
+        if (SHAPES == AC_TILE_16X16 || (SHAPES == 2 && (wi.x >> 16)))
             tiled_body<Tile16x16, W, true, false, false>(ta, wi.y, wi.z, wi.w >> 16, wi.w & 0xffff,
                                                          bt_smem_raw);
         else
@@ -132,6 +134,7 @@ struct ac_batch {
     unsigned int *counter;
     int zc;           // z extent of a work item (tuned)
     std::vector<int> shape;  // tile shape of each box (AC_TILE_32X8 / AC_TILE_16X16, tuned)
+    int shapes_in_use;       // bit 0: some box on 32 x 8, bit 1: some box on 16 x 16
     float tune_ms[2];        // last tuning: full step with the default split, and tuned
     int ctas;         // persistent CTAs
     int next_s;
@@ -187,6 +190,8 @@ static int build_items(ac_batch *b, int zc) {
                    cudaMemcpyHostToDevice));
     b->nitems = (int)sorted.size();
     b->zc = zc;
+    b->shapes_in_use = 0;
+    for (int v : b->shape) b->shapes_in_use |= v == AC_TILE_16X16 ? 2 : 1;
     for (int c = 0; c < 2; ++c)
         if (b->exec[c]) {
             cudaGraphExecDestroy(b->exec[c]);
@@ -220,10 +225,13 @@ static cudaError_t launch_batch_t(ac_batch *b, double dt, int s, int cur, cudaSt
     cudaError_t e = cudaMemsetAsync(b->counter, 0, sizeof(unsigned int), st);
     if (e != cudaSuccess) return e;
     const size_t smem = batch_smem_bytes<W>();
-    e = cudaFuncSetAttribute(batch_substep_kernel<W>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)smem);
+    // one body when every box has the same shape
+    auto k = b->shapes_in_use == 1 ? batch_substep_kernel<W, AC_TILE_32X8>
+             : b->shapes_in_use == 2 ? batch_substep_kernel<W, AC_TILE_16X16>
+                                     : batch_substep_kernel<W, 2>;
+    e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    batch_substep_kernel<W><<<b->ctas, dim3(32, 8, 1), smem, st>>>(a);
+    k<<<b->ctas, dim3(32, 8, 1), smem, st>>>(a);
     return cudaGetLastError();
 }
 
@@ -300,17 +308,17 @@ extern "C" int ac_batch_init(ac_batch **out, int nbox, const ac_box *boxes, cons
     if (e == cudaSuccess) {
         const size_t smem = b->precision == AC_FP32 ? batch_smem_bytes<float>() : batch_smem_bytes<double>();
         if (b->precision == AC_FP32) {
-            e = cudaFuncSetAttribute(batch_substep_kernel<float>,
+            e = cudaFuncSetAttribute(batch_substep_kernel<float, 2>,
                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
             if (e == cudaSuccess)
-                e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, batch_substep_kernel<float>,
+                e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, batch_substep_kernel<float, 2>,
                                                                   TT_THREADS, smem);
         } else {
-            e = cudaFuncSetAttribute(batch_substep_kernel<double>,
+            e = cudaFuncSetAttribute(batch_substep_kernel<double, 2>,
                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
             if (e == cudaSuccess)
                 e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-                    &occ, batch_substep_kernel<double>, TT_THREADS, smem);
+                    &occ, batch_substep_kernel<double, 2>, TT_THREADS, smem);
         }
     }
     if (e != cudaSuccess) {
