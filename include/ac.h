@@ -151,6 +151,16 @@ int ac_store(ac_handle *h, int field, double *host_dst);
 int ac_load_w(ac_handle *h, int field, const double *host_src);
 int ac_store_w(ac_handle *h, int field, double *host_dst);
 
+/* As ac_load / ac_store with float32 host memory (unpadded, x fastest, field
+ * 0..7 or AC_ALL back to back).  For an AC_FP32 or AC_FP32_W64 state in the
+ * periodic layout the copy moves the state's own bytes, half those of the
+ * float64 format; otherwise the values pass through the staging buffer: a
+ * float64 state takes the float32 values exactly on load and is rounded to
+ * nearest on store.  ac_load_f32 resets the substep counter to 0; ac_store_f32
+ * synchronises the stream. */
+int ac_load_f32(ac_handle *h, int field, const float *host_src);
+int ac_store_f32(ac_handle *h, int field, float *host_dst);
+
 /*
  * One Runge-Kutta substep s of the step in progress (Sec. 4; Williamson's
  * third-order 2N-storage scheme):  w <- alpha_s w + dt RHS(f);  f <- f + beta_s w,

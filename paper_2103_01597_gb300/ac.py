@@ -96,6 +96,8 @@ def load_library(path=None):
         "ac_store": ([_vp, _c.c_int, _vp], _c.c_int),
         "ac_load_w": ([_vp, _c.c_int, _vp], _c.c_int),
         "ac_store_w": ([_vp, _c.c_int, _vp], _c.c_int),
+        "ac_load_f32": ([_vp, _c.c_int, _vp], _c.c_int),
+        "ac_store_f32": ([_vp, _c.c_int, _vp], _c.c_int),
         "ac_integrate_substep": ([_vp, _c.c_double, _c.c_int], _c.c_int),
         "ac_integrate_step": ([_vp, _c.c_double], _c.c_int),
         "ac_periodic_halo": ([_vp], _c.c_int),
@@ -241,15 +243,24 @@ def ac_field_elems(h):
     return n.value
 
 
-def _host_ptr(a, writable):
+def _host_ptr(a, writable, elem=8):
     if isinstance(a, int):
         return a
     if hasattr(a, "data_ptr"):  # torch CPU tensor (e.g. pinned)
-        assert a.dtype.is_floating_point and a.element_size() == 8 and a.is_contiguous()
+        assert a.dtype.is_floating_point and a.element_size() == elem and a.is_contiguous()
         return a.data_ptr()
-    assert isinstance(a, np.ndarray) and a.dtype == np.float64 and a.flags.c_contiguous
-    assert a.flags.writeable or not writable
+    assert isinstance(a, np.ndarray) and a.dtype == (np.float64 if elem == 8 else np.float32)
+    assert a.flags.c_contiguous and (a.flags.writeable or not writable)
     return a.ctypes.data
+
+
+def ac_load_f32(h, field, host_src):
+    """ac_load from float32 host memory (numpy float32 or a torch float32 CPU tensor)."""
+    _check(load_library().ac_load_f32(h, field, _host_ptr(host_src, False, 4)), "ac_load_f32")
+
+
+def ac_store_f32(h, field, host_dst):
+    _check(load_library().ac_store_f32(h, field, _host_ptr(host_dst, True, 4)), "ac_store_f32")
 
 
 def ac_load(h, field, host_src):

@@ -339,6 +339,82 @@ static int store_common(ac_handle *h, int field, double *dst, int from_w) {
     return AC_OK;
 }
 
+// Host binary32 format: the state's own bytes when it is binary32 in the periodic
+// layout, else through the staging buffer (binary32 values, twice the planes).
+static int load_array_f32(ac_handle *h, void *dst, int es, const float *src) {
+    const size_t plane = (size_t)h->g.nx * h->g.ny;
+    if (es == 4 && !h->g.padded) {
+        CK(cudaMemcpyAsync(dst, src, plane * h->g.nz * sizeof(float), cudaMemcpyHostToDevice,
+                           h->stream));
+        return AC_OK;
+    }
+    size_t np;
+    int rc = ensure_stage(h, &np);
+    if (rc) return rc;
+    np *= 2;  // the stage holds binary64 planes
+    float *stage = reinterpret_cast<float *>(h->stage);
+    for (size_t z0 = 0; z0 < (size_t)h->g.nz; z0 += np) {
+        const size_t nzc = (z0 + np <= (size_t)h->g.nz) ? np : (size_t)h->g.nz - z0;
+        CK(cudaMemcpyAsync(stage, src + z0 * plane, nzc * plane * sizeof(float),
+                           cudaMemcpyHostToDevice, h->stream));
+        CK(launch_scatter_f32(stage, dst, es, h->g, (int)z0, (int)nzc, h->stream));
+        h->launches++;
+    }
+    return AC_OK;
+}
+
+static int store_array_f32(ac_handle *h, const void *src, int es, float *dst) {
+    const size_t plane = (size_t)h->g.nx * h->g.ny;
+    if (es == 4 && !h->g.padded) {
+        CK(cudaMemcpyAsync(dst, src, plane * h->g.nz * sizeof(float), cudaMemcpyDeviceToHost,
+                           h->stream));
+        return AC_OK;
+    }
+    size_t np;
+    int rc = ensure_stage(h, &np);
+    if (rc) return rc;
+    np *= 2;
+    float *stage = reinterpret_cast<float *>(h->stage);
+    for (size_t z0 = 0; z0 < (size_t)h->g.nz; z0 += np) {
+        const size_t nzc = (z0 + np <= (size_t)h->g.nz) ? np : (size_t)h->g.nz - z0;
+        CK(launch_gather_f32(src, es, h->g, (int)z0, (int)nzc, stage, h->stream));
+        h->launches++;
+        CK(cudaMemcpyAsync(dst + z0 * plane, stage, nzc * plane * sizeof(float),
+                           cudaMemcpyDeviceToHost, h->stream));
+    }
+    return AC_OK;
+}
+
+extern "C" int ac_load_f32(ac_handle *h, int field, const float *src) {
+    AC_RANGE("ac_load_f32");
+    if (!h || !src || field < AC_ALL || field >= NF) return AC_ERR_ARG;
+    int rc = ensure_state(h);
+    if (rc) return rc;
+    const size_t n = (size_t)h->g.nx * h->g.ny * h->g.nz;
+    const int q0 = field == AC_ALL ? 0 : field, q1 = field == AC_ALL ? NF : field + 1;
+    for (int q = q0; q < q1; ++q) {
+        rc = load_array_f32(h, h->state[h->cur][q], h->elem_f, src + (field == AC_ALL ? (size_t)q * n : 0));
+        if (rc) return rc;
+    }
+    h->next_s = 0;
+    return AC_OK;
+}
+
+extern "C" int ac_store_f32(ac_handle *h, int field, float *dst) {
+    AC_RANGE("ac_store_f32");
+    if (!h || !dst || field < AC_ALL || field >= NF) return AC_ERR_ARG;
+    int rc = ensure_state(h);
+    if (rc) return rc;
+    const size_t n = (size_t)h->g.nx * h->g.ny * h->g.nz;
+    const int q0 = field == AC_ALL ? 0 : field, q1 = field == AC_ALL ? NF : field + 1;
+    for (int q = q0; q < q1; ++q) {
+        rc = store_array_f32(h, h->state[h->cur][q], h->elem_f, dst + (field == AC_ALL ? (size_t)q * n : 0));
+        if (rc) return rc;
+    }
+    CK(cudaStreamSynchronize(h->stream));
+    return AC_OK;
+}
+
 extern "C" int ac_load(ac_handle *h, int field, const double *src) {
     AC_RANGE("ac_load");
     return load_common(h, field, src, 0);

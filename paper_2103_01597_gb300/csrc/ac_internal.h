@@ -128,6 +128,11 @@ cudaError_t launch_scatter(const double *stage, void *dst, int elem_size, const 
                            int nzc, cudaStream_t st);
 cudaError_t launch_gather(const void *src, int elem_size, const Geom &g, int z0, int nzc,
                           double *stage, cudaStream_t st);
+// The same with a binary32 staging buffer (host binary32 format).
+cudaError_t launch_scatter_f32(const float *stage, void *dst, int elem_size, const Geom &g, int z0,
+                               int nzc, cudaStream_t st);
+cudaError_t launch_gather_f32(const void *src, int elem_size, const Geom &g, int z0, int nzc,
+                              float *stage, cudaStream_t st);
 
 struct ReduceLaunch {
     int precision;

@@ -185,9 +185,11 @@ cudaError_t launch_forcing_table(const Geom &g, const int k[3], double phi, doub
 // Staging: an unpadded float64 slab of nzc z-planes starting at z0 <-> a
 // device array in its layout and precision.
 // ---------------------------------------------------------------------------
-template <typename T>
-__global__ void scatter_kernel(const double *__restrict__ stage, T *__restrict__ dst, Geom g,
-                               int z0, long long count) {
+// Host-format staging (S: binary64 or binary32, unpadded planes z0 .. z0 + nzc)
+// to and from a device array of element type T in the handle's layout.
+template <typename S, typename T>
+__global__ void scatter_kernel(const S *__restrict__ stage, T *__restrict__ dst, Geom g, int z0,
+                               long long count) {
     const long long plane = (long long)g.nx * g.ny;
     for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < count;
          t += (long long)gridDim.x * blockDim.x) {
@@ -199,9 +201,9 @@ __global__ void scatter_kernel(const double *__restrict__ stage, T *__restrict__
     }
 }
 
-template <typename T>
+template <typename T, typename S>
 __global__ void gather_kernel(const T *__restrict__ src, Geom g, int z0, long long count,
-                              double *__restrict__ stage) {
+                              S *__restrict__ stage) {
     const long long plane = (long long)g.nx * g.ny;
     for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < count;
          t += (long long)gridDim.x * blockDim.x) {
@@ -209,7 +211,7 @@ __global__ void gather_kernel(const T *__restrict__ src, Geom g, int z0, long lo
         const long long rem = t - kz * plane;
         const long long j = rem / g.nx;
         const long long i = rem - j * g.nx;
-        stage[t] = (double)src[g.origin + (z0 + kz) * g.pxy + j * g.px + i];
+        stage[t] = (S)src[g.origin + (z0 + kz) * g.pxy + j * g.px + i];
     }
 }
 
@@ -218,26 +220,45 @@ static unsigned grid_for(long long count) {
     return (unsigned)(b > 152 * 16 ? 152 * 16 : (b < 1 ? 1 : b));
 }
 
-cudaError_t launch_scatter(const double *stage, void *dst, int elem_size, const Geom &g, int z0,
-                           int nzc, cudaStream_t st) {
+template <typename S>
+static cudaError_t scatter_t(const S *stage, void *dst, int elem_size, const Geom &g, int z0,
+                             int nzc, cudaStream_t st) {
     const long long count = (long long)g.nx * g.ny * nzc;
     if (elem_size == 8)
-        scatter_kernel<double><<<grid_for(count), 256, 0, st>>>(stage, (double *)dst, g, z0, count);
+        scatter_kernel<S, double><<<grid_for(count), 256, 0, st>>>(stage, (double *)dst, g, z0, count);
     else
-        scatter_kernel<float><<<grid_for(count), 256, 0, st>>>(stage, (float *)dst, g, z0, count);
+        scatter_kernel<S, float><<<grid_for(count), 256, 0, st>>>(stage, (float *)dst, g, z0, count);
     return cudaGetLastError();
 }
 
-cudaError_t launch_gather(const void *src, int elem_size, const Geom &g, int z0, int nzc,
-                          double *stage, cudaStream_t st) {
+template <typename S>
+static cudaError_t gather_t(const void *src, int elem_size, const Geom &g, int z0, int nzc,
+                            S *stage, cudaStream_t st) {
     const long long count = (long long)g.nx * g.ny * nzc;
     if (elem_size == 8)
-        gather_kernel<double><<<grid_for(count), 256, 0, st>>>((const double *)src, g, z0, count,
-                                                              stage);
+        gather_kernel<double, S><<<grid_for(count), 256, 0, st>>>((const double *)src, g, z0, count,
+                                                                 stage);
     else
-        gather_kernel<float><<<grid_for(count), 256, 0, st>>>((const float *)src, g, z0, count,
-                                                             stage);
+        gather_kernel<float, S><<<grid_for(count), 256, 0, st>>>((const float *)src, g, z0, count,
+                                                                stage);
     return cudaGetLastError();
+}
+
+cudaError_t launch_scatter(const double *stage, void *dst, int elem_size, const Geom &g, int z0,
+                           int nzc, cudaStream_t st) {
+    return scatter_t(stage, dst, elem_size, g, z0, nzc, st);
+}
+cudaError_t launch_gather(const void *src, int elem_size, const Geom &g, int z0, int nzc,
+                          double *stage, cudaStream_t st) {
+    return gather_t(src, elem_size, g, z0, nzc, stage, st);
+}
+cudaError_t launch_scatter_f32(const float *stage, void *dst, int elem_size, const Geom &g, int z0,
+                               int nzc, cudaStream_t st) {
+    return scatter_t(stage, dst, elem_size, g, z0, nzc, st);
+}
+cudaError_t launch_gather_f32(const void *src, int elem_size, const Geom &g, int z0, int nzc,
+                              float *stage, cudaStream_t st) {
+    return gather_t(src, elem_size, g, z0, nzc, stage, st);
 }
 
 // ---------------------------------------------------------------------------
