@@ -358,6 +358,11 @@ int ac_batch_load(ac_batch *b, int box, int field, const double *host_src);
 int ac_batch_store(ac_batch *b, int box, int field, double *host_dst);
 int ac_batch_load_w(ac_batch *b, int box, int field, const double *host_src);
 int ac_batch_store_w(ac_batch *b, int box, int field, double *host_dst);
+/* The same state copies with float32 host memory: the batch's state is binary32,
+ * so each call is one copy of the box's own bytes (load resets the substep
+ * counter, store synchronises the stream). */
+int ac_batch_load_f32(ac_batch *b, int box, int field, const float *host_src);
+int ac_batch_store_f32(ac_batch *b, int box, int field, float *host_dst);
 /* Substep s of every box (order rules of ac_integrate_substep). */
 int ac_batch_integrate_substep(ac_batch *b, double dt, int s);
 /* Substeps 0, 1, 2 of every box; with the graph enabled, the three launches

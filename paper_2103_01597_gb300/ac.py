@@ -142,6 +142,8 @@ def load_library(path=None):
         "ac_batch_store": ([_vp, _c.c_int, _c.c_int, _vp], _c.c_int),
         "ac_batch_load_w": ([_vp, _c.c_int, _c.c_int, _vp], _c.c_int),
         "ac_batch_store_w": ([_vp, _c.c_int, _c.c_int, _vp], _c.c_int),
+        "ac_batch_load_f32": ([_vp, _c.c_int, _c.c_int, _vp], _c.c_int),
+        "ac_batch_store_f32": ([_vp, _c.c_int, _c.c_int, _vp], _c.c_int),
         "ac_batch_integrate_substep": ([_vp, _c.c_double, _c.c_int], _c.c_int),
         "ac_batch_integrate_step": ([_vp, _c.c_double], _c.c_int),
         "ac_batch_set_graph": ([_vp, _c.c_int], _c.c_int),
@@ -586,6 +588,16 @@ def ac_batch_load_w(b, box, field, host_src):
 def ac_batch_store_w(b, box, field, host_dst):
     _check(load_library().ac_batch_store_w(b, box, field, _host_ptr(host_dst, True)),
            "ac_batch_store_w")
+
+
+def ac_batch_load_f32(b, box, field, host_src):
+    _check(load_library().ac_batch_load_f32(b, box, field, _host_ptr(host_src, False, 4)),
+           "ac_batch_load_f32")
+
+
+def ac_batch_store_f32(b, box, field, host_dst):
+    _check(load_library().ac_batch_store_f32(b, box, field, _host_ptr(host_dst, True, 4)),
+           "ac_batch_store_f32")
 
 
 def ac_batch_integrate_substep(b, dt, s):

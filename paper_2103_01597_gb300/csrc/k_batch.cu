@@ -397,6 +397,30 @@ static int batch_copy(ac_batch *b, int box, int field, double *host, int to_devi
     return AC_OK;
 }
 
+// Host float32 <-> one box's state: the pool holds binary32 fields, a box's
+// eight arrays back to back, so each call is one copy.
+static int batch_copy_f32(ac_batch *b, int box, int field, float *host, int to_device) {
+    if (!b || !host || box < 0 || box >= b->nbox || field < AC_ALL || field >= NF) return AC_ERR_ARG;
+    const long long n = b->n[box];
+    float *dev = b->pool[b->cur] + b->off[box] + (field == AC_ALL ? 0 : (long long)field * n);
+    const size_t bytes = sizeof(float) * (size_t)n * (field == AC_ALL ? NF : 1);
+    if (to_device) {
+        BCK(cudaMemcpyAsync(dev, host, bytes, cudaMemcpyHostToDevice, b->stream));
+        b->next_s = 0;
+    } else {
+        BCK(cudaMemcpyAsync(host, dev, bytes, cudaMemcpyDeviceToHost, b->stream));
+        BCK(cudaStreamSynchronize(b->stream));
+    }
+    return AC_OK;
+}
+
+extern "C" int ac_batch_load_f32(ac_batch *b, int box, int field, const float *host) {
+    return batch_copy_f32(b, box, field, const_cast<float *>(host), 1);
+}
+extern "C" int ac_batch_store_f32(ac_batch *b, int box, int field, float *host) {
+    return batch_copy_f32(b, box, field, host, 0);
+}
+
 extern "C" int ac_batch_load(ac_batch *b, int box, int field, const double *host) {
     return batch_copy(b, box, field, const_cast<double *>(host), 1, 0);
 }

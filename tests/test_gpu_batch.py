@@ -129,6 +129,33 @@ def test_tile_shapes_bitwise(shapes, zc):
     b.close()
 
 
+def test_batch_f32_host_copies():
+    """Binary32 host copies of a box move its state unchanged, and a step after
+    them equals a step after the binary64 load of the same values."""
+    states = [_state(spec[0], 60 + i).astype(np.float32) for i, spec in enumerate(BOXES)]
+    res = []
+    for f32 in (True, False):
+        b = ac.Batch(BOXES)
+        for i, f in enumerate(states):
+            if f32:
+                ac.ac_batch_load_f32(b.b, i, ac.AC_ALL, np.ascontiguousarray(f))
+            else:
+                b.load(i, f.astype(np.float64))
+        if f32:
+            for i, f in enumerate(states):
+                back = np.empty_like(f)
+                ac.ac_batch_store_f32(b.b, i, ac.AC_ALL, back)
+                assert np.array_equal(back, f)
+                one = np.empty_like(f[2])
+                ac.ac_batch_store_f32(b.b, i, 2, one)
+                assert np.array_equal(one, f[2])
+        b.step(1e-3)
+        res.append([b.store(i) for i in range(len(BOXES))])
+        b.close()
+    for x, y in zip(*res):
+        assert np.array_equal(x, y)
+
+
 def test_batch_boxes_match_oracle():
     b = ac.Batch(BOXES)
     states = [_state(spec[0], 30 + i) for i, spec in enumerate(BOXES)]
