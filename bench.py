@@ -959,24 +959,25 @@ def run_closure(args, wl):
     torch.cuda.synchronize()
     clocks = sampler.stop()
     elapsed = ta.elapsed_time(tb) / 1e3
-    # end to end through the public calls with host binary64 buffers: load the
-    # coarse state, step, apply the guarded closure, store the state
-    hstate = torch.from_numpy(sim.store().reshape(-1).copy()).pin_memory()
+    # end to end through the public calls with host binary32 buffers (the coarse
+    # state's own precision): load the coarse state, step, apply the guarded
+    # closure, store the state
+    hstate = torch.from_numpy(sim.store().reshape(-1).astype(np.float32)).pin_memory()
     hout = torch.empty_like(hstate).pin_memory()
     ne = max(2, args.e2e_steps)
     link = host_link_gbs(hout)
     torch.cuda.synchronize()
     tt0 = time.perf_counter()
     for _ in range(ne):
-        ac.ac_load(sim.h, ac.AC_ALL, hstate)
+        ac.ac_load_f32(sim.h, ac.AC_ALL, hstate)
         sim.step(2 * dtf)
         rc = lib.ac_closure_apply(c.c, sim.h, 1e3, None)
         assert rc == 0, ac.ac_strerror(rc)
-        ac.ac_store(sim.h, ac.AC_ALL, hout)
+        ac.ac_store_f32(sim.h, ac.AC_ALL, hout)
     tt = time.perf_counter() - tt0
     e2e = {"value": cells * 3 * ne / tt / 1e9, "unit": UNIT,
-           "h2d_bytes_per_step": 8 * cells * 8, "d2h_bytes_per_step": 8 * cells * 8,
-           "steps": ne, "host_link": link}
+           "h2d_bytes_per_step": 8 * cells * 4, "d2h_bytes_per_step": 8 * cells * 4,
+           "host_format": "binary32", "steps": ne, "host_link": link}
     launches = ac.ac_launch_count(sim.h) + ac.ac_closure_launch_count(c.c) - l0
     # the forward pass (input pack + three convolution launches), timed alone on
     # the same state, on both convolution paths
