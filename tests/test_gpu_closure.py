@@ -107,6 +107,54 @@ def test_forward_matches_oracle(n, path):
     c.close()
 
 
+def _patch(x, z, y, xi, r):
+    """The (8, 2r+1, 2r+1, 2r+1) periodic neighbourhood of cell (z, y, xi)."""
+    nz, ny, nx = x.shape[1:]
+    iz = np.arange(z - r, z + r + 1) % nz
+    iy = np.arange(y - r, y + r + 1) % ny
+    ix = np.arange(xi - r, xi + r + 1) % nx
+    return x[:, iz][:, :, iy][:, :, :, ix]
+
+
+@pytest.mark.parametrize("n", [(128, 128, 128), (256, 256, 256)])
+def test_forward_sampled_at_full_size(n):
+    """The inference sizes (the 128^3 coarse grid of the closure workload, the
+    256^3 inference workload) on the default path, in the bench's launch
+    configuration: 48 sampled cells against the oracle.  A cell's output depends
+    on its 7^3 neighbourhood (three 3x3x3 layers), so the oracle evaluates each
+    on a 9^3 periodic patch around it (the patch's own wrap reaches the centre
+    after no fewer than four layers)."""
+    net = oc.Net.init(11)
+    params = net.flat().astype(np.float32)
+    net = oc.Net.unflat(params.astype(np.float64))
+    x = synthetic.noise_state(n, 12, 0.5).astype(np.float32).astype(np.float64)
+    rng = np.random.default_rng(13)
+    ins = (0.5 + rng.random(8)).astype(np.float32)
+    outs = (0.01 + 0.1 * rng.random(8)).astype(np.float32)
+    c = cl.Closure(n, params=params)
+    c.set_scales(ins, outs)
+    got = c.correction(_dev(x)).double().cpu().numpy().reshape((8,) + x.shape[1:])
+    c.status()
+    c.close()
+    isc = ins.astype(np.float64)[:, None, None, None]
+    sc = outs.astype(np.float64)
+    cells = [(int(rng.integers(n[2])), int(rng.integers(n[1])), int(rng.integers(n[0])))
+             for _ in range(48)]
+    g, want, sig, wk = [], [], [], []
+    for (z, y, xi) in cells:
+        p = _patch(x, z, y, xi, 4) / isc
+        yo, _ = net.forward(p, bf16="config")
+        yk, _ = net.forward(p, bf16="kernel")
+        sp = net.rounding_spread(p, samples=8)
+        g.append(got[:, z, y, xi])
+        want.append(yo[:, 4, 4, 4] * sc)
+        wk.append(yk[:, 4, 4, 4] * sc)
+        sig.append(sp[:, 4, 4, 4] * sc)
+    g, want, sig, wk = map(np.array, (g, want, sig, wk))
+    _within_spread(g, want, sig, "forward %s, 48 sampled cells" % (n,))
+    assert _maxrel(g, wk) <= 2e-2, _maxrel(g, wk)
+
+
 def test_forward_paths_agree_at_64_cubed():
     """The tcgen05 (one CTA and paired) and mma.sync forward passes on a 64^3
     grid (4 096 tiles of a row each on the persistent grids): same bfloat16
