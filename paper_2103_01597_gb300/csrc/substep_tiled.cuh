@@ -17,7 +17,7 @@
 namespace ac {
 
 constexpr int TT_THREADS = 256;           // threads per CTA, launched as 32 x 8
-constexpr int TT_PF = 2;                  // planes in flight beyond z+3
+constexpr int TT_PF = 2;                  // planes in flight beyond z+3 (at most; >= 1)
 constexpr int TT_NP = 7 + TT_PF;          // ring slots
 constexpr int TT_NW = TT_PF + 2;          // ring slots for the accumulator w of output planes
 
@@ -247,7 +247,11 @@ __device__ __forceinline__ void tiled_body(const TA &ta, int x0, int y0, int z0,
                            active);
         cp_async_commit();
     };
-    for (int p = z0 - 3; p <= z0 + 3 + TT_PF; ++p) issue(p, (p - z0 + 3) * TT_PLANE);
+    // planes z0-3 .. z0+2+TT_PF into slots 0 .. 5+TT_PF; each plane z's iteration, after
+    // its barrier, issues plane z+3+TT_PF into the slot plane z-4 held (the slot
+    // left free for z0)
+    for (int p = z0 - 3; p <= z0 + 2 + TT_PF; ++p) issue(p, (p - z0 + 3) * TT_PLANE);
+    int free_off = (6 + TT_PF) * TT_PLANE;
 
     float zq[NF][7];  // z-column of this thread's cell: planes z-3 .. z+3
     const float2 *ztab = force_on ? ta.ftab() + g.nx + g.ny : nullptr;
@@ -259,8 +263,11 @@ __device__ __forceinline__ void tiled_body(const TA &ta, int x0, int y0, int z0,
     for (int z = z0; z < z1; ++z) {
         const float2 ez = ez_next;  // forcing phase of plane z, loaded one plane ahead
         if (force_on && z + 1 < z1) ez_next = ztab[z + 1];
-        cp_async_wait<TT_PF>();  // plane z+3 (and w of plane z) have landed for this thread
-        __syncthreads();         // ... and for every thread
+        cp_async_wait<TT_PF - 1>();  // plane z+3 (and w of plane z) have landed for this thread
+        // ... and for every thread; every thread has also finished plane z-1, so
+        // plane z-4's slot and the w slot of plane z-2 are free
+        __syncthreads();
+        issue(z + 3 + TT_PF, free_off);
         const float *ctr = sm + (ty + 3) * S::ROW + tx + 4;
         if (z == z0) {
 #pragma unroll
@@ -304,8 +311,7 @@ __device__ __forceinline__ void tiled_body(const TA &ta, int x0, int y0, int z0,
                 ta.fout(q)[o] = (float)((W)zq[q][3] + ta.beta() * wn);
             }
         }
-        __syncthreads();  // reads of plane z-3's slot and of w(z) are done before refilling
-        issue(z + 4 + TT_PF, slot[0]);  // plane z + 6 takes plane z - 3's slot
+        free_off = slot[0];  // plane z-3's slot: refilled after the next barrier
 #pragma unroll
         for (int d = 0; d < 6; ++d) slot[d] = slot[d + 1];
         slot[6] = slot[6] + TT_PLANE == TT_NP * TT_PLANE ? 0 : slot[6] + TT_PLANE;
