@@ -133,6 +133,11 @@ struct ac_decomp {
     cudaStream_t stream;   // the caller's stream: updates
     cudaStream_t comm;     // pack, messages, unpack (higher priority)
     cudaEvent_t ev_start, ev_unpacked;
+    // the outer slabs of all subdomains run on DC_OUTER streams at once (each slab
+    // alone fills the GPU poorly); the caller's stream waits for all of them
+    static constexpr int DC_OUTER = 4;
+    cudaStream_t outer[DC_OUTER];
+    cudaEvent_t ev_outer[DC_OUTER];
     std::vector<DcSub> sub;
     std::vector<DcMsg> msgs;
     DcMsg *msgs_dev;
@@ -358,6 +363,10 @@ static void dc_free(ac_decomp *d) {
     if (d->comm) cudaStreamDestroy(d->comm);
     if (d->ev_start) cudaEventDestroy(d->ev_start);
     if (d->ev_unpacked) cudaEventDestroy(d->ev_unpacked);
+    for (int k = 0; k < ac_decomp::DC_OUTER; ++k) {
+        if (d->outer[k]) cudaStreamDestroy(d->outer[k]);
+        if (d->ev_outer[k]) cudaEventDestroy(d->ev_outer[k]);
+    }
 }
 
 #define DCK(call)                                       \
@@ -437,6 +446,10 @@ static int dc_setup(ac_decomp *d) {
     DCK(cudaStreamCreateWithPriority(&d->comm, cudaStreamNonBlocking, hi));
     DCK(cudaEventCreateWithFlags(&d->ev_start, cudaEventDisableTiming));
     DCK(cudaEventCreateWithFlags(&d->ev_unpacked, cudaEventDisableTiming));
+    for (int k = 0; k < ac_decomp::DC_OUTER; ++k) {
+        DCK(cudaStreamCreateWithFlags(&d->outer[k], cudaStreamNonBlocking));
+        DCK(cudaEventCreateWithFlags(&d->ev_outer[k], cudaEventDisableTiming));
+    }
     const size_t plane = (size_t)d->nloc[0] * d->nloc[1];
     d->stage_elems = plane * d->nloc[2];
     DCK(cudaMalloc(&d->stage, d->stage_elems * sizeof(double)));
@@ -620,10 +633,20 @@ extern "C" int ac_decomp_integrate_substep(ac_decomp *d, double dt, int s) {
         // the inner segments read no halo cell: they run while the halos are exchanged
         for (int r = 0; r < d->nsub; ++r)
             DCK(ac::dc_update(d, r, inner, alpha[s], beta[s], dt, s, d->stream));
-        DCK(cudaStreamWaitEvent(d->stream, d->ev_unpacked, 0));
+        // the outer slabs start once the halos are in (the unpack event follows the
+        // previous substep and this step's forcing tables through the comm stream),
+        // alongside the inner updates, spread over the outer streams and joined back
+        for (int k = 0; k < ac_decomp::DC_OUTER; ++k)
+            DCK(cudaStreamWaitEvent(d->outer[k], d->ev_unpacked, 0));
+        int job = 0;
         for (int r = 0; r < d->nsub; ++r)
-            for (int b = 0; b < 6; ++b)
-                DCK(ac::dc_update(d, r, outer[b], alpha[s], beta[s], dt, s, d->stream));
+            for (int b = 0; b < 6; ++b, ++job)
+                DCK(ac::dc_update(d, r, outer[b], alpha[s], beta[s], dt, s,
+                                  d->outer[job % ac_decomp::DC_OUTER]));
+        for (int k = 0; k < ac_decomp::DC_OUTER; ++k) {
+            DCK(cudaEventRecord(d->ev_outer[k], d->outer[k]));
+            DCK(cudaStreamWaitEvent(d->stream, d->ev_outer[k], 0));
+        }
     } else {
         DCK(ac::dc_pack<true>(d, d->sendbuf, d->stream, geoms));
         if (d->elem_f == 8)
