@@ -593,7 +593,7 @@ def run_ours(args, wl):
     # through ac_load_f32 / ac_store_f32)
     e2e = None
     if args.e2e_steps > 0:
-        ne = max(8, args.e2e_steps)  # the first load and the last store are not overlapped
+        ne = max(16, args.e2e_steps)  # the first load and the last store are not overlapped
         hb = elem_f  # host bytes per value
         if hb == 4:
             e_in = torch.from_numpy(f0.reshape(-1).astype(np.float32)).pin_memory()
@@ -634,6 +634,10 @@ def run_ours(args, wl):
         # (b) two handles on two streams take alternate steps, so that one
         # handle's copies run while the other computes (each step still moves
         # its whole input in and its whole result out)
+        # The next handle's step waits on an event after this one's, so the two
+        # steps never share the SMs and only the copies run beside a step.
+        streams = [stream, s2]
+        done = [torch.cuda.Event(), torch.cuda.Event()]
         torch.cuda.synchronize()
         tt0 = time.perf_counter()
         load(sim.h, ac.AC_ALL, e_in)
@@ -643,6 +647,8 @@ def run_ours(args, wl):
             if k + 1 < ne:
                 nxt = pairs[(k + 1) % 2][0]
                 load(nxt.h, ac.AC_ALL, e_in)
+                done[k % 2].record(streams[k % 2])
+                streams[(k + 1) % 2].wait_event(done[k % 2])
                 ac.ac_integrate_step(nxt.h, dt)
             store(cur.h, ac.AC_ALL, hout)
         tt = time.perf_counter() - tt0
@@ -653,8 +659,9 @@ def run_ours(args, wl):
                "warmup": max(3, args.warmup),
                "host_format": "binary32" if hb == 4 else "binary64",
                "how": "two handles on two streams take alternate steps (load, "
-                      "ac_integrate_step, store each step), one's copies overlapping the "
-                      "other's compute",
+                      "ac_integrate_step, store each step); each step waits on an event "
+                      "after the previous one, and one handle's copies overlap the other's "
+                      "step",
                "serial_one_handle": {"value": serial, "d2h_bytes_per_step": d2h,
                                      "how": "load, three ac_integrate_substep calls, CFL read, store "
                                             "in sequence",
@@ -1248,11 +1255,18 @@ def run_closure_forward(args, wl):
     lanes = [(c, stream, xs, out, pin, pout, hout),
              (c2, s2, xs2, out2, ac._ptr8(cl._rows(xs2)), ac._ptr8(cl._rows(out2)), hout2)]
 
+    fdone = [torch.cuda.Event(), torch.cuda.Event()]
+
     def lane_step(k):
+        # each forward waits on an event after the previous one, so that only the
+        # copies run beside a forward
         cc, st, xk, ok, pk_in, pk_out, hk = lanes[k % 2]
         with torch.cuda.stream(st):
             xk.copy_(hin, non_blocking=True)
+            if k > 0:
+                st.wait_event(fdone[(k - 1) % 2])
             assert lib.ac_closure_forward(cc.c, pk_in, pk_out) == 0
+            fdone[k % 2].record(st)
             hk.copy_(ok, non_blocking=True)
 
     for k in range(6):  # untimed
@@ -1268,7 +1282,8 @@ def run_closure_forward(args, wl):
            "h2d_bytes_per_step": 8 * cells * 4, "d2h_bytes_per_step": 8 * cells * 4,
            "steps": ne, "warmup": 3,
            "how": "two closures on two streams take alternate forwards (copy in, "
-                  "ac_closure_forward, copy out each), one's copies overlapping the other's compute",
+                  "ac_closure_forward, copy out each); each forward waits on an event after "
+                  "the previous one, and one's copies overlap the other's forward",
            "serial_one_stream": {"value": serial}, "host_link": link}
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
