@@ -60,13 +60,13 @@ FX_TRAFFIC_PER_CELL = (426249728 + 236466176) / 2097152
 # does not depend on the grid), per mode: substep-0 (CFL) and substep-1/2 variants.
 FX_FP64_PIPE_INST_PER_CELL = {"group": (213.3125, 187.3125), "field": (243.3125, 217.3125)}
 # DRAM bytes per cell of one launch of the binary32 tiled substep, the mean over
-# substeps 0, 1, 2 (ncu, 256^3 forced, one step: 1970.6 MB read + written per
+# substeps 0, 1, 2 (ncu, 256^3 forced, one step: 1970.1 MB read + written per
 # launch on average over 16,777,216 cells; algorithmic 96, 128, 128 B/cell)
-TILED_TRAFFIC_PER_CELL = 1970619477.3 / 16777216
+TILED_TRAFFIC_PER_CELL = 1970099882.7 / 16777216
 # The same for one launch of the 64-box ensemble kernel with its tuned split (ncu:
-# 3291.5 MB per launch on average over its 27,340,800 cells; 2.6% above the
+# 3260.7 MB per launch on average over its 27,340,800 cells; 1.6% above the
 # algorithmic bytes: the halo cells of small boxes)
-BATCH_TRAFFIC_PER_CELL = 3291504810.7 / 27340800
+BATCH_TRAFFIC_PER_CELL = 3260725930.7 / 27340800
 
 WORKLOADS = {
     "forced256_fp64": dict(n=(256, 256, 256), precision="fp64", force_amp=0.05, seed=2,
