@@ -1161,8 +1161,8 @@ CF_FLOPS = {1: 2 * 27 * 8 * 32, 2: 2 * 27 * 32 * 32, 3: 2 * 27 * 32 * 8}
 # algorithmic flops per cell (8 real input channels, 8 real output channels)
 CF_ALGO_FLOPS = 2 * 27 * (8 * 32 + 32 * 32 + 32 * 8)
 # DRAM bytes per cell of one launch of the 32 -> 32 tcgen05 layer (ncu, 128^3:
-# 145.0 MB read + 93.0 MB written over 2,097,152 cells)
-CF_TRAFFIC_PER_CELL = (144.952320e6 + 92.980992e6) / 2097152
+# 144.9 MB read + 89.0 MB written over 2,097,152 cells)
+CF_TRAFFIC_PER_CELL = (144.937728e6 + 89.045248e6) / 2097152
 
 
 def _closure_oracle_sample(params, n, seed):
