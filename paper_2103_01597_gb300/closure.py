@@ -1,4 +1,4 @@
-"""Learned-closure driver: training pairs from the solver, training, rollout.
+"""Learned closure: training pairs from the solver, training, rollout.
 
 This module sequences calls into libac.so (restriction, solver steps, closure
 forward/backward/Adam/apply kernels) and holds torch-owned device buffers.

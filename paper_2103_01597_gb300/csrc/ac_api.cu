@@ -692,7 +692,7 @@ extern "C" int ac_bounds_check_take(unsigned long long *first) {
     }
     return AC_OK;
 #else
-    return AC_ERR_STATE;  // this build does not check
+    return AC_ERR_STATE;  // the library was compiled without the index checks
 #endif
 }
 
