@@ -53,7 +53,7 @@ def bytes_per_cell(elem_f, elem_w, s):
 FP64_NOMINAL_TFLOPS = 1.25
 # DRAM bytes per cell of one launch of the integer-sum FP64 substep kernel
 # (ncu, 128^3 forced, substep-1/2 variant, group scales: 426.2 MB read +
-# 236.5 MB written over 2,097,152 cells; profiles/substep_fx_128_metrics.md).
+# 236.5 MB written over 2,097,152 cells).
 FX_TRAFFIC_PER_CELL = (426249728 + 236466176) / 2097152
 # FP64-pipe thread instructions per cell of that kernel (ncu
 # sm__inst_executed_pipe_fp64 x 32 / cells, 128^3 forced; the instruction stream
@@ -548,7 +548,7 @@ def run_ours(args, wl):
                 "peak_source": "measured: ac_diag_fma_rate(AC_FP64), the library's own DFMA "
                                "chains, x 2 flops (nominal: %.2f TFLOP/s)" % FP64_NOMINAL_TFLOPS,
                 # dram read + write per 256^3 launch, from the 128^3 ncu capture of the
-                # same kernel scaled by cells (profiles/substep_fx_128_metrics.md)
+                # same kernel scaled by cells
                 "traffic": (FX_TRAFFIC_PER_CELL * ncell
                             if (inst is not None and modes[1] == 0) else None),
                 "kernel": ("fx_stats + fx_plan + fx_quantize + substep_fx_kernel (int64 "
@@ -577,7 +577,7 @@ def run_ours(args, wl):
         roof = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                 "frac": achieved / peaks["hbm_gbs"],
                 # dram read + write per launch, mean over the three substeps (ncu at
-                # 256^3 scaled by cells; profiles/substep_fp32_tiled_256_full.md)
+                # 256^3, scaled by cells)
                 "traffic": TILED_TRAFFIC_PER_CELL * ncell if tiled else None,
                 "kernel": ("substep_tiled_kernel<float,true> (shared-memory plane ring)"
                            if order == 6 else
@@ -785,8 +785,7 @@ def run_ensemble(args, wl):
     achieved = alg / launch_s / 1e9
     roof = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
             "frac": achieved / peaks["hbm_gbs"],
-            # dram read + write per launch, mean over the three substeps (ncu,
-            # profiles/ensemble_batch_substep_full.md)
+            # dram read + write per launch, mean over the three substeps (ncu)
             "traffic": BATCH_TRAFFIC_PER_CELL * ncell,
             "kernel": "batch_substep_kernel<float> (persistent, graph-captured)",
             "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)",
