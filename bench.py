@@ -52,13 +52,13 @@ def bytes_per_cell(elem_f, elem_w, s):
 # Nominal dense FP64 rate of one GB300 (no measured FP64 peak is provided).
 FP64_NOMINAL_TFLOPS = 1.25
 # DRAM bytes per cell of one launch of the integer-sum FP64 substep kernel
-# (ncu, 128^3 forced, substep-1/2 variant, group scales: 426.2 MB read +
-# 236.5 MB written over 2,097,152 cells).
-FX_TRAFFIC_PER_CELL = (426249728 + 236466176) / 2097152
+# (ncu, 128^3 forced, substep-1/2 variant, group scales: 424.2 MB read +
+# 236.7 MB written over 2,097,152 cells).
+FX_TRAFFIC_PER_CELL = (424206592 + 236677888) / 2097152
 # FP64-pipe thread instructions per cell of that kernel (ncu
 # sm__inst_executed_pipe_fp64 x 32 / cells, 128^3 forced; the instruction stream
 # does not depend on the grid), per mode: substep-0 (CFL) and substep-1/2 variants.
-FX_FP64_PIPE_INST_PER_CELL = {"group": (213.3125, 187.3125), "field": (243.3125, 217.3125)}
+FX_FP64_PIPE_INST_PER_CELL = {"group": (206.3125, 179.3125), "field": (236.3125, 209.3125)}
 # DRAM bytes per cell of one launch of the binary32 tiled substep, the mean over
 # substeps 0, 1, 2 (ncu, 256^3 forced, one step: 1970.1 MB read + written per
 # launch on average over 16,777,216 cells; algorithmic 96, 128, 128 B/cell)

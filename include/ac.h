@@ -211,7 +211,9 @@ int ac_get_stencil_order(const ac_handle *h, int *order);
 /*
  * Arithmetic of the stencil sums for AC_FP64.  AC_STENCIL_AUTO (default): exact
  * integer sums whenever they apply (binary64 fields, periodic layout, equal
- * spacing dx = dy = dz, stencil order 6), plain binary64 sums otherwise.  With
+ * spacing dx = dy = dz, stencil order 6, a step dt with |dt| in [1e-100, 1e100]:
+ * those kernels fold dt into their coefficients), plain binary64 sums
+ * otherwise.  With
  * integer sums every field is first written, on the device before each
  * substep, as int64 fixed point about its own offset: F = round((f - c)
  * 2^(50 - E)), c the midpoint of the field's range and 2^E above its

@@ -1,5 +1,7 @@
 // FP64 substep: exact integer stencil sums on cubic periodic grids (the fast
 // path), plain binary64 stencil arithmetic otherwise.
+#include <cmath>
+
 #include "substep_fx.cuh"
 
 namespace ac {
@@ -11,8 +13,12 @@ static unsigned fx_grid(long long n) {  // n work items of one thread each
 
 cudaError_t launch_substep_f64(const SubstepLaunch &L, cudaStream_t st, int *launches) {
     // Integer sums need 32-bit neighbour offsets (always true for a binary64
-    // state in HBM: fewer than 2^31 cells per array).
-    if (!L.use_fx || L.g.elems >= (1ll << 31)) return launch_substep_t<double, double>(L, st, launches);
+    // state in HBM: fewer than 2^31 cells per array); their kernels fold dt into
+    // the coefficients, so a step of zero or of extreme magnitude (1 / dt^2 out of
+    // range) takes the plain binary64 stencils.
+    const double adt = fabs(L.dt);
+    if (!L.use_fx || L.g.elems >= (1ll << 31) || !(adt >= 1e-100 && adt <= 1e100))
+        return launch_substep_t<double, double>(L, st, launches);
     SubstepArgs<double, double> a;
     a.g = L.g;
     FxPtrs fx;
@@ -32,15 +38,23 @@ cudaError_t launch_substep_f64(const SubstepLaunch &L, cudaStream_t st, int *lau
     a.ftab = L.force.tab;
     for (int m = 0; m < 3; ++m) a.amp_e[m] = L.force.amp_e[m];
     a.cfl_max = L.cfl_max;
+    // the step folded into the RHS coefficients
     FxCoefs fc;
-    fc.inv60dx = 1.0 / (60.0 * L.dx);
-    fc.nu180 = L.ph.nu / (180.0 * L.dx * L.dx);
-    fc.nu2160 = (L.ph.nu + 3.0 * L.ph.zeta) / (2160.0 * L.dx * L.dx);
+    const double dts = L.dt;
+    const double c1 = 1.0 / (60.0 * L.dx);
+    fc.c1dt = dts * c1;
+    fc.nu180 = dts * (L.ph.nu / (180.0 * L.dx * L.dx));
+    fc.nu2160 = dts * ((L.ph.nu + 3.0 * L.ph.zeta) / (2160.0 * L.dx * L.dx));
     fc.inv180dx2 = 1.0 / (180.0 * L.dx * L.dx);
     fc.inv720dx2 = 1.0 / (720.0 * L.dx * L.dx);
-    fc.two_nu_c1sq = 2.0 * L.ph.nu * fc.inv60dx * fc.inv60dx;
-    fc.K_c1sq = L.ph.K * fc.inv60dx * fc.inv60dx;
-    fc.zeta_c1sq = L.ph.zeta * fc.inv60dx * fc.inv60dx;
+    fc.two_nu_c1sq = dts * (2.0 * L.ph.nu * c1 * c1);
+    fc.K_c1sq = dts * (L.ph.K * c1 * c1);
+    fc.zeta_c1sq = dts * (L.ph.zeta * c1 * c1);
+    fc.eta_dt = dts * a.k.eta;
+    fc.hc_dt = dts * a.k.hc;
+    fc.K_dt = dts * a.k.K;
+    for (int m = 0; m < 3; ++m) fc.amp_dt[m] = dts * L.force.amp_e[m];
+    fc.inv_dt2 = 1.0 / (dts * dts);
 
     const long long n = L.g.elems;
     FxPlan *plan = static_cast<FxPlan *>(L.fx_plan);

@@ -298,25 +298,36 @@ __device__ __forceinline__ double fx_scaled(long long N, int k_hi) {
 }
 
 // Coefficients of the converted numerators (host side); the field scales
-// 2^(E - FX_BITS) come from the device plan.
+// 2^(E - FX_BITS) come from the device plan.  Every coefficient through which a
+// term enters the right-hand side also carries the step dt (dts below; the host
+// takes this path only for |dt| in [1e-100, 1e100], so that 1 / dt^2 stays in
+// range).  The RHS so formed is dt times Eqs. B.1-B.4, and the RK update adds it
+// to alpha w without multiplying it by dt.
 struct FxCoefs {
-    double inv60dx;    // c1 = 1 / (60 dx): first derivatives
-    double nu180;      // nu / (180 dx^2): nu lap u
-    double nu2160;     // (nu + 3 zeta) / (2160 dx^2): (nu / 3 + zeta) grad(div u)
-    double inv180dx2;  // 1 / (180 dx^2): lap A
+    double c1dt;       // dts c1, c1 = 1 / (60 dx): first derivatives in the RHS and B = curl A
+    double nu180;      // dts nu / (180 dx^2): nu lap u
+    double nu2160;     // dts (nu + 3 zeta) / (2160 dx^2): (nu / 3 + zeta) grad(div u)
+    double inv180dx2;  // 1 / (180 dx^2): lap A (in j, and times eta dts in Eq. B.4)
     double inv720dx2;  // 1 / (720 dx^2): grad(div A)
-    double two_nu_c1sq;  // 2 nu c1^2: 2 nu S : S and 2 nu S grad ln rho from unscaled gradients
-    double K_c1sq;       // K c1^2: K |grad xi|^2 (conduction)
-    double zeta_c1sq;    // zeta c1^2: zeta (div u)^2
+    double two_nu_c1sq;  // dts 2 nu c1^2: 2 nu S : S and 2 nu S grad ln rho from unscaled gradients
+    double K_c1sq;       // dts K c1^2: K |grad xi|^2 (conduction)
+    double zeta_c1sq;    // dts zeta c1^2: zeta (div u)^2
+    double eta_dt;       // dts eta
+    double hc_dt;        // dts (H - C)
+    double K_dt;         // dts K
+    double amp_dt[3];    // dts times the forcing amplitudes
+    double inv_dt2;      // 1 / dts^2: |B|^2 of the CFL speed from the dts-scaled B
 };
 
-// Eqs. B.1-B.4 at one cell as cell_physics computes them, with the gradients of
-// ln rho, s and u passed without the grid factor c1 = 1 / (60 dx) (the integer
-// stencil numerators after their field scale): every term is linear or
-// quadratic in them, so c1 enters the coefficients (c1 for the advection terms
-// inside their fused multiply-adds, c1 cs^2 for the pressure term, c1^2 in
+// Eqs. B.1-B.4 at one cell as cell_physics computes them, times dts (the step
+// folded into the coefficients of FxCoefs), with the gradients of ln rho, s and
+// u passed without the grid factor c1 = 1 / (60 dx) (the integer stencil
+// numerators after their field scale): every term is linear or quadratic in
+// them, so c1 enters the coefficients (dts c1 for the advection terms inside
+// their fused multiply-adds, dts c1 cs^2 for the pressure term, dts c1^2 in
 // 2 nu, K and zeta) instead of 15 multiplications per cell on the FP64 pipe.
-// B = curl A comes scaled (it meets c1 in three places).
+// B = curl A comes scaled by dts c1 (it meets c1 in three places, and dts
+// reaches the Lorentz force and the induction through it).
 template <bool EXT>
 __device__ __forceinline__ void cell_physics_fx(const double (&u)[3], const double (&GL)[3],
                                                 const double (&GS)[3], const double (&GU)[3][3],
@@ -325,7 +336,7 @@ __device__ __forceinline__ void cell_physics_fx(const double (&u)[3], const doub
                                                 const DevCoefs<double> &k, const FxCoefs &fc,
                                                 const double frc[3], double out[NF], double *cfl,
                                                 double lapxi, const Thermo<double> &th) {
-    const double c1 = fc.inv60dx;
+    const double c1 = fc.c1dt;
     const double rho_inv = th.rho_inv, cs2 = th.cs2, inv_T = th.inv_T;
     const double divR = GU[0][0] + GU[1][1] + GU[2][2];  // div u / c1
     const double third_div = divR * (1.0 / 3.0);
@@ -356,7 +367,7 @@ __device__ __forceinline__ void cell_physics_fx(const double (&u)[3], const doub
     }
     // Eq. B.3
     out[4] = fma(-c1, u[0] * GS[0] + u[1] * GS[1] + u[2] * GS[2],
-                 (k.eta * J2 * rho_inv + fc.two_nu_c1sq * SS2) * inv_T);
+                 (fc.eta_dt * J2 * rho_inv + fc.two_nu_c1sq * SS2) * inv_T);
     if (EXT) {
         double gxi2 = 0.0;  // |grad xi|^2 / c1^2
 #pragma unroll
@@ -364,14 +375,14 @@ __device__ __forceinline__ void cell_physics_fx(const double (&u)[3], const doub
             const double gxi = k.gamma_cp * GS[m] + k.gm1 * GL[m];
             gxi2 += gxi * gxi;
         }
-        out[4] += (k.hc * rho_inv + fc.zeta_c1sq * divR * divR) * inv_T +
-                  rho_inv * (k.K * lapxi + fc.K_c1sq * gxi2);
+        out[4] += (fc.hc_dt * rho_inv + fc.zeta_c1sq * divR * divR) * inv_T +
+                  rho_inv * (fc.K_dt * lapxi + fc.K_c1sq * gxi2);
     }
     // Eq. B.4
 #pragma unroll
-    for (int m = 0; m < 3; ++m) out[5 + m] = UxB[m] + k.eta * lapa[m];
+    for (int m = 0; m < 3; ++m) out[5 + m] = UxB[m] + fc.eta_dt * lapa[m];
     if (cfl) {
-        const double b2 = B[0] * B[0] + B[1] * B[1] + B[2] * B[2];
+        const double b2 = (B[0] * B[0] + B[1] * B[1] + B[2] * B[2]) * fc.inv_dt2;
         const double u2 = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
         *cfl = sqrt(u2) + sqrt(cs2 + b2 * rho_inv);
     }
@@ -395,7 +406,7 @@ __device__ __forceinline__ void fx_column(const SubstepArgs<double, double> &a, 
     for (int q = 0; q < NF; ++q) kh[q] = (plan->E[q] - FX_BITS) << 20;
     // first derivative of field q from its numerator; the gradients of ln rho, s
     // and u stay without the factor c1 (cell_physics_fx applies it)
-    auto d1 = [&](long long N, int q) -> double { return fx_scaled(N, kh[q]) * fc.inv60dx; };
+    auto d1 = [&](long long N, int q) -> double { return fx_scaled(N, kh[q]) * fc.c1dt; };
     auto d1r = [&](long long N, int q) -> double { return fx_scaled(N, kh[q]); };
     const int k0 = blockIdx.z * a.zchunk;
     const int k1 = min(k0 + a.zchunk, a.g.nz);
@@ -426,9 +437,9 @@ __device__ __forceinline__ void fx_column(const SubstepArgs<double, double> &a, 
         if (a.force_on) {
             const double2 ez = a.ftab[a.g.nx + a.g.ny + kk];
             const double cph = exy.x * ez.x - exy.y * ez.y;
-            frc[0] = a.amp_e[0] * cph;
-            frc[1] = a.amp_e[1] * cph;
-            frc[2] = a.amp_e[2] * cph;
+            frc[0] = fc.amp_dt[0] * cph;
+            frc[1] = fc.amp_dt[1] * cph;
+            frc[2] = fc.amp_dt[2] * cph;
         }
         const GlobalView<long long, IdxPeriodic32> Fl{fx.F[0], ix}, Fs{fx.F[4], ix};
         const GlobalView<long long, IdxPeriodic32> Fu[3] = {{fx.F[1], ix}, {fx.F[2], ix},
@@ -451,9 +462,9 @@ __device__ __forceinline__ void fx_column(const SubstepArgs<double, double> &a, 
             gu[m][2] = d1r(nd1<2>(Fu[m]), qu);
         }
         if constexpr (PF) {
-            B[0] = (fx_scaled(nd1<1>(Fa[2]), kh[7]) - fx_scaled(nd1<2>(Fa[1]), kh[6])) * fc.inv60dx;
-            B[1] = (fx_scaled(nd1<2>(Fa[0]), kh[5]) - fx_scaled(nd1<0>(Fa[2]), kh[7])) * fc.inv60dx;
-            B[2] = (fx_scaled(nd1<0>(Fa[1]), kh[6]) - fx_scaled(nd1<1>(Fa[0]), kh[5])) * fc.inv60dx;
+            B[0] = (fx_scaled(nd1<1>(Fa[2]), kh[7]) - fx_scaled(nd1<2>(Fa[1]), kh[6])) * fc.c1dt;
+            B[1] = (fx_scaled(nd1<2>(Fa[0]), kh[5]) - fx_scaled(nd1<0>(Fa[2]), kh[7])) * fc.c1dt;
+            B[2] = (fx_scaled(nd1<0>(Fa[1]), kh[6]) - fx_scaled(nd1<1>(Fa[0]), kh[5])) * fc.c1dt;
         } else {
             B[0] = d1(nd1<1>(Fa[2]) - nd1<2>(Fa[1]), 5);
             B[1] = d1(nd1<2>(Fa[0]) - nd1<0>(Fa[2]), 5);
@@ -598,8 +609,14 @@ __device__ __forceinline__ void fx_column(const SubstepArgs<double, double> &a, 
             cell_physics_fx<EXT>(u, gl, gs, gu, B, viscl, lapa, J, a.k, fc, frc, rhs, nullptr, lapxi,
                                  th);
         }
+        // the RK update of rk_update, the RHS already multiplied by dt
 #pragma unroll
-        for (int q = 0; q < NF; ++q) rk_update(a, q, o, rhs[q]);
+        for (int q = 0; q < NF; ++q) {
+            double wn = rhs[q];
+            if (!a.s0) wn = a.alpha * a.w[q][o] + wn;
+            a.w[q][o] = wn;
+            a.fout[q][o] = ldg(a.fin[q] + o) + a.beta * wn;
+        }
     }
 }
 

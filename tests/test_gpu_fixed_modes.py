@@ -230,3 +230,30 @@ def test_constant_fields():
     errs, counts, want = run_substeps(f)
     assert counts == want, (counts, want)
     assert_parity(errs)
+
+
+@pytest.mark.parametrize("dt", [0.0, 1e-120, -1e-120])
+def test_zero_or_tiny_dt_takes_plain_stencils(dt):
+    """The integer-sum kernels fold dt into their coefficients (1 / dt^2 must stay
+    in range for the CFL speed), so a step of zero or of magnitude below 1e-100
+    runs the plain binary64 stencils: no mode is counted, the state moves by
+    at most dt times its right-hand side, and the CFL speed of the input state
+    matches the one the integer-sum path reports for it."""
+    f = synthetic.smooth_state(N, 21, amp=0.3) + synthetic.noise_state(N, 22, 1e-3)
+    sim = ac.Simulation(N, force_amp=0.0, seed=1, **PHYS)
+    sim.load(f)
+    sim.step(dt)
+    assert tuple(ac.ac_get_stencil_modes(sim.h)) == (0, 0, 0)
+    g = sim.store()
+    if dt == 0.0:
+        assert np.array_equal(g, f)
+    else:
+        assert np.max(np.abs(g - f)) <= 1e-110
+    cfl_plain = ac.ac_last_cfl(sim.h)
+    ref = ac.Simulation(N, force_amp=0.0, seed=1, **PHYS)
+    ref.load(f)
+    ref.step(1e-3)
+    assert sum(ac.ac_get_stencil_modes(ref.h)) == 3
+    assert abs(ac.ac_last_cfl(ref.h) - cfl_plain) <= 1e-12 * cfl_plain
+    sim.close()
+    ref.close()
