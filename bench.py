@@ -52,9 +52,11 @@ def bytes_per_cell(elem_f, elem_w, s):
 # Nominal dense FP64 rate of one GB300 (no measured FP64 peak is provided).
 FP64_NOMINAL_TFLOPS = 1.25
 # DRAM bytes per cell of one launch of the integer-sum FP64 substep kernel
-# (ncu, 128^3 forced, substep-1/2 variant, group scales: 424.2 MB read +
-# 236.7 MB written over 2,097,152 cells).
-FX_TRAFFIC_PER_CELL = (424206592 + 236677888) / 2097152
+# (ncu, 128^3, substep-1/2 variant, over 2,097,152 cells): group scales (forced
+# noise state) 424.2 MB read + 236.7 MB written, per-field scales (u_z scaled by
+# 1e-3) 429.3 + 236.7 MB.
+FX_TRAFFIC_PER_CELL = {"group": (424206592 + 236677888) / 2097152,
+                       "field": (429260800 + 236704256) / 2097152}
 # FP64-pipe thread instructions per cell of that kernel (ncu
 # sm__inst_executed_pipe_fp64 x 32 / cells, 128^3 forced; the instruction stream
 # does not depend on the grid), per mode: substep-0 (CFL) and substep-1/2 variants.
@@ -530,10 +532,13 @@ def run_ours(args, wl):
         # the count per cell weighted by the modes the timed substeps ran (none
         # for plain binary64 stencils, which this table does not cover)
         inst = None
+        traffic = None
         if fixed and order == 6 and sum(modes) and not modes[2] and not wl.get("entropy"):
             fg = modes[0] / sum(modes)
             G, F = FX_FP64_PIPE_INST_PER_CELL["group"], FX_FP64_PIPE_INST_PER_CELL["field"]
             inst = [fg * G[v] + (1 - fg) * F[v] for v in range(2)]
+            traffic = (fg * FX_TRAFFIC_PER_CELL["group"] +
+                       (1 - fg) * FX_TRAFFIC_PER_CELL["field"]) * ncell
         achieved = None
         if inst is not None:
             # FP64-pipe thread instructions of each launch, as DFMA-equivalent flops
@@ -547,10 +552,10 @@ def run_ours(args, wl):
                 "fp64_pipe_inst_per_cell": inst,
                 "peak_source": "measured: ac_diag_fma_rate(AC_FP64), the library's own DFMA "
                                "chains, x 2 flops (nominal: %.2f TFLOP/s)" % FP64_NOMINAL_TFLOPS,
-                # dram read + write per 256^3 launch, from the 128^3 ncu capture of the
-                # same kernel scaled by cells
-                "traffic": (FX_TRAFFIC_PER_CELL * ncell
-                            if (inst is not None and modes[1] == 0) else None),
+                # dram read + write per launch of the substep-1/2 variant, from the
+                # 128^3 ncu captures of the same kernels scaled by cells, weighted by
+                # the modes the timed substeps ran
+                "traffic": traffic,
                 "kernel": ("fx_stats + fx_plan + fx_quantize + substep_fx_kernel (int64 "
                            "stencil sums)" if fixed else
                            "substep_kernel<double,double,IdxPeriodicR<%d>>" % (order // 2)),
@@ -601,20 +606,24 @@ def run_ours(args, wl):
         else:
             e_in = host_in
             load, store = ac.ac_load, ac.ac_store
-        e_out = torch.empty_like(e_in).pin_memory()
-        e_out2 = torch.empty_like(e_in).pin_memory()
+        # H handles on H streams take turns; up to H - 1 steps are queued ahead of
+        # the store being waited on, so a short stall of the host thread does not
+        # leave the GPU idle
+        H = 3
+        outs = [torch.empty_like(e_in).pin_memory() for _ in range(H)]
+        e_out = outs[0]
         link = host_link_gbs(e_out)
-        s2 = torch.cuda.Stream(device=local)
-        sim2 = ac.Simulation(n, precision=prec, force_amp=wl["force_amp"], seed=wl["seed"],
-                             device="cuda:%d" % local, stream=s2.cuda_stream, order=order,
-                             **wl.get("entropy", {}))
-        pairs = [(sim, e_out), (sim2, e_out2)]
+        streams = [stream] + [torch.cuda.Stream(device=local) for _ in range(H - 1)]
+        sims = [sim] + [ac.Simulation(n, precision=prec, force_amp=wl["force_amp"],
+                                      seed=wl["seed"], device="cuda:%d" % local,
+                                      stream=st.cuda_stream, order=order, **wl.get("entropy", {}))
+                        for st in streams[1:]]
         h2d = 8 * ncell * hb
         d2h = 8 * ncell * hb + 16
         # untimed warm-up of the host side: the first copies through freshly pinned
         # pages run several times slower than the later ones on these machines
         for _ in range(max(3, args.warmup)):
-            for hs, hout in pairs:
+            for hs, hout in zip(sims, outs):
                 load(hs.h, ac.AC_ALL, e_in)
                 ac.ac_integrate_step(hs.h, dt)
                 store(hs.h, ac.AC_ALL, hout)
@@ -631,37 +640,44 @@ def run_ours(args, wl):
             phase[0].append(tb - ta)
             phase[1].append(time.perf_counter() - tb)
         serial = ncell * 3 * ne * ws / (time.perf_counter() - tt0) / 1e9
-        # (b) two handles on two streams take alternate steps, so that one
-        # handle's copies run while the other computes (each step still moves
-        # its whole input in and its whole result out)
-        # The next handle's step waits on an event after this one's, so the two
-        # steps never share the SMs and only the copies run beside a step.
-        streams = [stream, s2]
-        done = [torch.cuda.Event(), torch.cuda.Event()]
+        # (b) the handles take turns: step j runs on handle j mod H, loads its whole
+        # input and stores its whole result; it waits on an event recorded after
+        # step j - 1, so two steps never share the SMs and only the copies run
+        # beside a step
+        done = [torch.cuda.Event() for _ in range(H)]
+
+        def issue(j):
+            hs, st = sims[j % H], streams[j % H]
+            load(hs.h, ac.AC_ALL, e_in)
+            if j > 0:
+                st.wait_event(done[(j - 1) % H])
+            ac.ac_integrate_step(hs.h, dt)
+            done[j % H].record(st)
+
         torch.cuda.synchronize()
+        t_store = []
         tt0 = time.perf_counter()
-        load(sim.h, ac.AC_ALL, e_in)
-        ac.ac_integrate_step(sim.h, dt)
+        for j in range(min(H - 1, ne)):
+            issue(j)
         for k in range(ne):
-            cur, hout = pairs[k % 2]
-            if k + 1 < ne:
-                nxt = pairs[(k + 1) % 2][0]
-                load(nxt.h, ac.AC_ALL, e_in)
-                done[k % 2].record(streams[k % 2])
-                streams[(k + 1) % 2].wait_event(done[k % 2])
-                ac.ac_integrate_step(nxt.h, dt)
-            store(cur.h, ac.AC_ALL, hout)
+            if k + H - 1 < ne:
+                issue(k + H - 1)  # its handle's previous step (k - 1) is stored
+            store(sims[k % H].h, ac.AC_ALL, outs[k % H])
+            t_store.append(time.perf_counter())
         tt = time.perf_counter() - tt0
         torch.cuda.synchronize()
-        sim2.close()
+        for hs in sims[1:]:
+            hs.close()
+        gaps = [b2 - a2 for a2, b2 in zip(t_store, t_store[1:])]
         e2e = {"value": ncell * 3 * ne * ws / tt / 1e9, "unit": UNIT,
                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h - 16, "steps": ne,
                "warmup": max(3, args.warmup),
                "host_format": "binary32" if hb == 4 else "binary64",
-               "how": "two handles on two streams take alternate steps (load, "
-                      "ac_integrate_step, store each step); each step waits on an event "
-                      "after the previous one, and one handle's copies overlap the other's "
-                      "step",
+               "how": "%d handles on %d streams take turns (load, ac_integrate_step, store "
+                      "each step); each step waits on an event after the previous one, and "
+                      "the copies of the others overlap a step" % (H, H),
+               "ms_between_stores": {"median": 1e3 * statistics.median(gaps),
+                                     "max": 1e3 * max(gaps)} if gaps else None,
                "serial_one_handle": {"value": serial, "d2h_bytes_per_step": d2h,
                                      "how": "load, three ac_integrate_substep calls, CFL read, store "
                                             "in sequence",
