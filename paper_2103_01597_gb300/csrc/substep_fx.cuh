@@ -227,15 +227,18 @@ __global__ void __launch_bounds__(256) fx_quantize_kernel(FxPtrs p, long long n,
     const long long n2 = n >> 1;
     for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n2;
          t += (long long)gridDim.x * blockDim.x) {
+        // all eight loads ahead of the stores, so that they are in flight together
+        double2 v[NF];
+#pragma unroll
+        for (int q = 0; q < NF; ++q) v[q] = __ldg(reinterpret_cast<const double2 *>(p.f[q]) + t);
 #pragma unroll
         for (int q = 0; q < NF; ++q) {
-            const double2 v = __ldg(reinterpret_cast<const double2 *>(p.f[q]) + t);
             longlong2 o;
             o.x = zero[q] ? 0ll
-                          : (long long)(fx_round_grid((unsigned long long)__double_as_longlong(v.x),
+                          : (long long)(fx_round_grid((unsigned long long)__double_as_longlong(v[q].x),
                                                       E[q]) - C[q]);
             o.y = zero[q] ? 0ll
-                          : (long long)(fx_round_grid((unsigned long long)__double_as_longlong(v.y),
+                          : (long long)(fx_round_grid((unsigned long long)__double_as_longlong(v[q].y),
                                                       E[q]) - C[q]);
             reinterpret_cast<longlong2 *>(p.F[q])[t] = o;
         }
