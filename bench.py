@@ -237,6 +237,20 @@ def timed_region_max(elapsed, dist, device):
     return float(t.item())
 
 
+def pipeline_schedule(ne, H):
+    """Order of the end-to-end loop over H handles taking turns: ("issue", j)
+    loads step j's input into handle j mod H and queues the step, ("store", j)
+    copies its result out and waits for it.  Steps 0 .. H-2 are issued first;
+    then each store of step k follows the issue of step k + H - 1, whose handle
+    last held step k - 1, already stored."""
+    ops = [("issue", j) for j in range(min(H - 1, ne))]
+    for k in range(ne):
+        if k + H - 1 < ne:
+            ops.append(("issue", k + H - 1))
+        ops.append(("store", k))
+    return ops
+
+
 def job_rate(units_per_rank, ws, elapsed):
     """Whole-job throughput: the units every rank processed (the same number on
     each replica) over the slowest rank's time."""
@@ -657,13 +671,12 @@ def run_ours(args, wl):
         torch.cuda.synchronize()
         t_store = []
         tt0 = time.perf_counter()
-        for j in range(min(H - 1, ne)):
-            issue(j)
-        for k in range(ne):
-            if k + H - 1 < ne:
-                issue(k + H - 1)  # its handle's previous step (k - 1) is stored
-            store(sims[k % H].h, ac.AC_ALL, outs[k % H])
-            t_store.append(time.perf_counter())
+        for op, j in pipeline_schedule(ne, H):
+            if op == "issue":
+                issue(j)
+            else:
+                store(sims[j % H].h, ac.AC_ALL, outs[j % H])
+                t_store.append(time.perf_counter())
         tt = time.perf_counter() - tt0
         torch.cuda.synchronize()
         for hs in sims[1:]:
